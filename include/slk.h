@@ -1,0 +1,223 @@
+/*
+ * slk.h -- C ABI of the sliced fast kernel summation library (GB300, sm_103a).
+ *
+ * The library computes kernel sums
+ *
+ *     s_m = sum_{n=1..N} w_n F(|x_n - y_m|),   m = 1..M,   x_n, y_m in R^d,
+ *
+ * (the problem statement of Section 3 of "Fast Kernel Summation in High
+ * Dimensions via Slicing and Fourier Transforms") for the radial kernels
+ *
+ *     Gaussian            F(r) = exp(-r^2 / (2 sigma^2))      (Table 1, Sec. 2.2)
+ *     Laplacian           F(r) = exp(-alpha r)                (Table 1, Sec. 3.3)
+ *     negative distance   F(r) = -r                           (Table 1, Sec. 3.2)
+ *
+ * by slicing (Algorithm 1): project onto P unit directions xi_p, run a 1-D
+ * summation of the 1-D counterpart f of Table 1 on every slice, and average:
+ *
+ *     s_m ~ (1/P) sum_p sum_n w_n f(|<xi_p, x_n - y_m>|).
+ *
+ * The 1-D summation is a fast Fourier summation (Section 3.1: NDFT, or the NFFT
+ * of the remark that follows it: window spreading, FFT, multiplication by the
+ * Fourier coefficients, inverse FFT, interpolation) for the Gaussian, the
+ * sorting algorithm of Section 3.2 (Algorithm 2) for the negative distance
+ * kernel, and both combined (Section 3.3) for the Laplacian.
+ *
+ * Conventions shared by every call:
+ *   - Points are row-major: point i occupies elements [i*ld, i*ld + d) of its
+ *     array (ld >= d, in elements).  Directions are row-major P x d, FP64.
+ *   - Element type of x, y, w, s and the gradient: double for
+ *     SLK_PREC_F64, float for every other precision.
+ *   - Pointers may be device pointers (memory of the plan's device, or
+ *     managed memory) or host pointers (pageable or pinned).  Host arrays are
+ *     staged through device memory inside the call, on the given stream.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every
+ *     call enqueues its work on that stream and returns without waiting,
+ *     except when an output is a host pointer (the call then synchronises the
+ *     stream before returning) or when noted.
+ *   - Every call returns a status and never aborts or throws.  The detail
+ *     of the last failure on the calling thread is in slk_last_error().
+ *   - Ownership: the caller owns x, y, w, s and gradients.  A plan owns its
+ *     directions, its cached per-slice x-side data and its workspace; it
+ *     keeps no pointer to x or w after slk_plan_create returns.
+ */
+#ifndef SLK_H
+#define SLK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SLK_VERSION_MAJOR 0
+#define SLK_VERSION_MINOR 1
+
+typedef enum {
+    SLK_OK = 0,
+    SLK_ERR_INVALID = 1,      /* a bad argument or descriptor field */
+    SLK_ERR_OOM = 2,          /* device allocation failed or over the memory budget */
+    SLK_ERR_CUDA = 3,         /* a CUDA runtime error (kernel launch, copy, ...) */
+    SLK_ERR_ACCURACY = 4,     /* the requested accuracy cannot be certified */
+    SLK_ERR_TIMEOUT = 5,      /* a bounded wait ran out */
+    SLK_ERR_BUSY = 6,         /* no slot or memory free right now; retry later */
+    SLK_ERR_UNSUPPORTED = 7,  /* valid request this build does not implement */
+    SLK_ERR_NOT_FOUND = 8     /* unknown request id */
+} slk_status;
+
+typedef enum {
+    SLK_GAUSSIAN = 0,         /* param = sigma > 0 */
+    SLK_LAPLACIAN = 1,        /* param = alpha > 0 (F = exp(-alpha r)) */
+    SLK_NEGDIST = 2           /* param ignored */
+} slk_kernel;
+
+typedef enum {
+    SLK_PREC_F64 = 0,         /* FP64 storage and arithmetic (SIMT) */
+    SLK_PREC_F32 = 1,         /* FP32 storage; FP32 SIMT projection */
+    SLK_PREC_BF16 = 2,        /* FP32 storage; BF16 tensor-core projection, FP32 accumulate */
+    SLK_PREC_F16X3 = 3        /* FP32 storage; tensor-core projection with FP16 hi/lo split
+                                 (three products), about FP32 accuracy */
+} slk_precision;
+
+typedef enum {
+    SLK_FOURIER_AUTO = 0,     /* NFFT or NDFT, whichever the plan expects to be faster */
+    SLK_FOURIER_NFFT = 1,     /* spread + FFT + multiply + inverse FFT + interpolate */
+    SLK_FOURIER_NDFT = 2      /* direct sums over the significant coefficients */
+} slk_fourier_method;
+
+/* Plan descriptor.  Zero-initialise, then set the fields you need. */
+typedef struct {
+    int32_t kernel;           /* slk_kernel */
+    int32_t precision;        /* slk_precision */
+    double param;             /* sigma (Gaussian) or alpha (Laplacian) */
+    int32_t d;                /* dimension, >= 1 */
+    int32_t P;                /* number of slices (directions), >= 1 */
+    int32_t n_coeff;          /* Fourier coefficients N_c: k in (-N_c/2, N_c/2); 0 = automatic */
+    int32_t method;           /* slk_fourier_method (Gaussian and Laplacian smooth part) */
+    uint64_t seed;            /* seed of the library's direction draw (when directions == NULL) */
+    const double* directions; /* optional P x d row-major unit directions (host or device);
+                                 NULL = draw them (Philox4x32-10 + Box-Muller, normalised) */
+    double tol;               /* target model error (truncation + periodisation + window),
+                                 relative to sum|w|; 0 = default for the precision */
+    double radius;            /* half-width R of the certified window: every projected
+                                 target must satisfy |<xi_p, y - mu>| <= R (mu = the plan's
+                                 centre); 0 = 1.25 x the largest projected source */
+    int32_t slice_batch;      /* slices processed per pass; 0 = all at once */
+    int32_t reserved[7];
+} slk_plan_desc;
+
+/* What a plan chose (filled by slk_plan_get_info). */
+typedef struct {
+    int32_t kernel, precision, d, P;
+    int64_t N;
+    int32_t method;           /* slk_fourier_method actually used (0 if none) */
+    int32_t n_coeff;          /* N_c */
+    int32_t n_grid;           /* NFFT grid size (2 N_c) */
+    int32_t window;           /* NFFT window width in grid cells */
+    int32_t k_lo, k_hi;       /* NDFT band of significant k > 0 (inclusive) */
+    double period;            /* L: period of the Fourier summation in projected units */
+    double radius;            /* certified window half-width R */
+    double model_error;       /* certified bound: truncation + periodisation + window (per unit sum|w|) */
+    double c_d;               /* sqrt(pi) Gamma((d+1)/2) / Gamma(d/2) */
+    int64_t device_bytes;     /* device memory held by the plan */
+} slk_plan_info;
+
+typedef struct slk_plan_s* slk_plan;
+
+/* Library version and the status text (static strings). */
+int32_t slk_version(void);
+const char* slk_status_string(slk_status status);
+/* Detail of the last failure on this thread ("" if none); valid until the next call. */
+const char* slk_last_error(void);
+
+/*
+ * Build a plan: draw or copy the directions, project the sources x (N x d,
+ * row stride ldx) onto them and precompute the x-side of every slice
+ * (Algorithm 1, first step, and the source half of the 1-D method:
+ * Fourier coefficients w_hat (Sec. 3.1), or sorted keys with FP64 prefix
+ * sums (Sec. 3.2)).  w holds N weights.  N >= 1.
+ * Errors: SLK_ERR_INVALID (bad descriptor, N < 1, ldx < d), SLK_ERR_OOM,
+ * SLK_ERR_ACCURACY (no Fourier parameters meet desc->tol), SLK_ERR_CUDA.
+ */
+slk_status slk_plan_create(slk_plan* plan, const slk_plan_desc* desc, const void* x, int64_t N, int64_t ldx,
+                           const void* w, void* stream);
+
+/*
+ * Kernel sums at M targets y (M x d, row stride ldy) into s (M values):
+ * project the targets, evaluate every slice's 1-D sum and average (Algorithm 1).
+ * M == 0 is a no-op.  Errors: SLK_ERR_INVALID, SLK_ERR_ACCURACY (a projected
+ * target lies outside the certified window), SLK_ERR_OOM, SLK_ERR_CUDA.
+ */
+slk_status slk_sum(slk_plan plan, const void* y, int64_t M, int64_t ldy, void* s, void* stream);
+
+/*
+ * Gradient of sum_m gs_m s_m with respect to the targets: for every m,
+ *     gy_m = gs_m (1/P) sum_p xi_p  sum_n w_n f'(|d|) sign(d),  d = <xi_p, y_m - x_n>,
+ * with sign(0) = 0 (the derivative of the sliced estimator).  gs may be NULL
+ * (all ones).  gy is M x d with row stride ldg.  Errors as slk_sum.
+ */
+slk_status slk_grad(slk_plan plan, const void* y, int64_t M, int64_t ldy, const void* gs, void* gy, int64_t ldg,
+                    void* stream);
+
+/*
+ * Wait for the plan's outstanding work and return the device-side status of
+ * its last call: SLK_ERR_ACCURACY when a projected target fell outside the
+ * certified window [-R, R] of a Fourier plan (sums with device outputs are
+ * asynchronous, so this status is otherwise reported by the next call).
+ */
+slk_status slk_plan_sync(slk_plan plan);
+
+/* Copy the plan's directions (P x d row-major FP64) to host memory xi_host. */
+slk_status slk_plan_get_directions(slk_plan plan, double* xi_host);
+
+/* Report the parameters the plan chose.  Synchronises the plan's stream. */
+slk_status slk_plan_get_info(slk_plan plan, slk_plan_info* info);
+
+/* Release the plan and its device memory (waits for its pending work). */
+slk_status slk_plan_destroy(slk_plan plan);
+
+/*
+ * Host-only: the Fourier parameters a plan with this descriptor would choose
+ * when every projected point lies in [-radius, radius] (radius > 0).  Fills the
+ * Fourier fields of *info (method, n_coeff, n_grid, window, k_lo, k_hi, period,
+ * radius, model_error, c_d).  Needs no GPU.  Errors: SLK_ERR_INVALID,
+ * SLK_ERR_ACCURACY, SLK_ERR_UNSUPPORTED (negative distance: no Fourier part).
+ */
+slk_status slk_fourier_params(const slk_plan_desc* desc, double radius, slk_plan_info* info);
+
+/*
+ * One-shot convenience: plan, sum and destroy in one call (same arguments and
+ * errors as the three calls).
+ */
+slk_status slk_kernel_sum(const slk_plan_desc* desc, const void* x, int64_t N, int64_t ldx, const void* w,
+                          const void* y, int64_t M, int64_t ldy, void* s, void* stream);
+
+/*
+ * Profiling support (not part of the paper's method).  Every kernel launch of
+ * the library is counted; while timing is enabled, each launch is also
+ * bracketed by CUDA events recorded on the stream it is launched on.
+ *   slk_launch_count   kernels launched by this process so far.
+ *   slk_timing_enable  on != 0 starts recording events for later launches.
+ *   slk_timing_read    waits for the recorded events and writes, per kernel
+ *                      name in first-launch order, the launch count and the
+ *                      summed device time in milliseconds into out[0..cap);
+ *                      *count receives the number of names (may exceed cap).
+ *   slk_timing_reset   drops the recorded events.
+ */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+} slk_kernel_time;
+
+int64_t slk_launch_count(void);
+slk_status slk_timing_enable(int32_t on);
+slk_status slk_timing_read(slk_kernel_time* out, int32_t cap, int32_t* count);
+slk_status slk_timing_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLK_H */

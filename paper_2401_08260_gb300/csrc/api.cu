@@ -1,0 +1,637 @@
+// C ABI: plans, sums and gradients (Algorithm 1 with the 1-D methods of Section 3).
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "params.cuh"
+
+// ------------------------------------------------------------ errors / memory
+
+namespace slk {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+void fail(slk_status st, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    throw Error{st, std::string(buf)};
+}
+
+void* dev_alloc(size_t bytes, cudaStream_t st) {
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(SLK_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    return p;
+}
+
+void dev_free(void* p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
+bool is_device_pointer(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Keep freed blocks in the device's default pool so that repeated plans and
+// calls reuse memory instead of returning it to the driver.
+static void configure_pool(int device) {
+    static bool done[64] = {};
+    if (device < 0 || device >= 64 || done[device]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done[device] = true;
+}
+
+}  // namespace slk
+
+using namespace slk;
+
+// ------------------------------------------------------------ plan object
+
+struct slk_plan_s {
+    slk_plan_desc desc{};
+    int device = 0;
+    bool f64 = false;
+    int64_t N = 0;
+    int d = 0, P = 0;
+    double cd = 0.0;
+    double R = 0.0;
+    cudaStream_t stream = nullptr;  // stream of the last call (frees are ordered on it)
+
+    DevBuf<double> xi64;  // P x d
+    DevBuf<float> xi32;   // P x d (FP32 storage paths)
+    DevBuf<double> mu64;  // d
+    DevBuf<float> mu32;   // d
+
+    // Fourier side (Gaussian, Laplacian smooth part)
+    bool fourier = false;
+    FourierHost fh;
+    FourierDev fd{};
+    DevBuf<double> coef, mult;
+    DevBuf<unsigned char> cw;   // Cplx<T> P x K
+    DevBuf<unsigned char> cw0;  // T P
+    DevBuf<unsigned char> hgrid;  // T P x W
+
+    // sorting side (negative distance, Laplacian non-smooth part)
+    bool sorting = false;
+    double sort_scale = 1.0;
+    DevBuf<unsigned char> keys;  // T P x N
+    DevBuf<double> A, B;         // P x (N + 1)
+    DevBuf<float> kmin, kscale;
+    DevBuf<int32_t> tab;
+    int NB = 0;
+
+    // deferred device-side status
+    DevBuf<unsigned> err_dev;
+    unsigned* err_host = nullptr;
+    cudaEvent_t done = nullptr;
+    bool pending = false;
+
+    ~slk_plan_s() {
+        if (done) {
+            cudaEventSynchronize(done);
+            cudaEventDestroy(done);
+        }
+        if (err_host) cudaFreeHost(err_host);
+    }
+    int64_t device_bytes() const {
+        return static_cast<int64_t>(xi64.bytes() + xi32.bytes() + mu64.bytes() + mu32.bytes() + coef.bytes() +
+                                    mult.bytes() + cw.bytes() + cw0.bytes() + hgrid.bytes() + keys.bytes() + A.bytes() +
+                                    B.bytes() + kmin.bytes() + kscale.bytes() + tab.bytes());
+    }
+};
+
+namespace {
+
+// Default model-error target per precision, well below the accuracy bar of the
+// arithmetic (FP64 1e-12 for the Gaussian).  The Laplacian's smooth part has
+// coefficients decaying only like k^-4 (its |x|^3 term at 0), so it asks for
+// 1e-7 (FP64) and 2e-6 (FP32) to keep the grid at a few thousand coefficients.
+double default_tol(int kernel, int precision) {
+    if (kernel == SLK_LAPLACIAN) return precision == SLK_PREC_F64 ? 1e-7 : 2e-6;
+    if (precision == SLK_PREC_F64) return 1e-12;
+    if (precision == SLK_PREC_BF16) return 1e-5;
+    return 2e-7;
+}
+
+template <class Fn>
+slk_status guarded(Fn&& fn) {
+    try {
+        fn();
+        return SLK_OK;
+    } catch (const Error& e) {
+        set_last_error(e.msg);
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        set_last_error("host allocation failed");
+        return SLK_ERR_OOM;
+    } catch (...) {
+        set_last_error("unexpected exception");
+        return SLK_ERR_CUDA;
+    }
+}
+
+// Device-side status of the previous call on the plan (non-blocking unless wait).
+slk_status collect(slk_plan plan, bool wait) {
+    if (!plan->pending) return SLK_OK;
+    if (!wait) {
+        cudaError_t q = cudaEventQuery(plan->done);
+        if (q == cudaErrorNotReady) {
+            cudaGetLastError();
+            return SLK_OK;
+        }
+    } else {
+        SLK_CHECK_CUDA(cudaEventSynchronize(plan->done));
+    }
+    plan->pending = false;
+    unsigned e = *plan->err_host;
+    *plan->err_host = 0;
+    if (e & 4u) {
+        set_last_error("a projected target lies outside the certified window [-R, R]; rebuild the plan with a larger radius");
+        return SLK_ERR_ACCURACY;
+    }
+    if (e & 3u) {
+        set_last_error("a projected point fell outside the NFFT grid window");
+        return SLK_ERR_ACCURACY;
+    }
+    return SLK_OK;
+}
+
+void finish_call(slk_plan plan, cudaStream_t st) {
+    SLK_CHECK_CUDA(cudaMemcpyAsync(plan->err_host, plan->err_dev.get(), sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    SLK_CHECK_CUDA(cudaMemsetAsync(plan->err_dev.get(), 0, sizeof(unsigned), st));
+    SLK_CHECK_CUDA(cudaEventRecord(plan->done, st));
+    plan->pending = true;
+}
+
+// Device view of a user array of n rows x d columns (row stride ld): either the
+// user's pointer or a compact staged copy.
+template <class T>
+struct InView {
+    const T* ptr = nullptr;
+    int64_t ld = 0;
+    DevBuf<T> staged;
+    InView(const void* user, int64_t n, int d, int64_t ld_user, cudaStream_t st) {
+        if (is_device_pointer(user) || n == 0) {
+            ptr = static_cast<const T*>(user);
+            ld = ld_user;
+        } else {
+            staged.alloc(static_cast<size_t>(n) * d, st);
+            SLK_CHECK_CUDA(cudaMemcpy2DAsync(staged.get(), sizeof(T) * d, user, sizeof(T) * ld_user, sizeof(T) * d, n,
+                                             cudaMemcpyHostToDevice, st));
+            ptr = staged.get();
+            ld = d;
+        }
+    }
+};
+
+template <class T>
+const T* xi_of(slk_plan plan) {
+    if constexpr (sizeof(T) == 8) return plan->xi64.get();
+    else return plan->xi32.get();
+}
+template <class T>
+const T* mu_of(slk_plan plan) {
+    if constexpr (sizeof(T) == 8) return plan->mu64.get();
+    else return plan->mu32.get();
+}
+
+// Z (P x n, ldz = n) = projections of n points onto the plan's directions, centred.
+template <class T>
+void project(slk_plan plan, const T* x, int64_t n, int64_t ldx, T* Z, cudaStream_t st) {
+    launch_project_simt<T>(xi_of<T>(plan), plan->P, x, n, plan->d, ldx, mu_of<T>(plan), Z, n, st);
+}
+
+template <class T>
+void plan_fourier_source(slk_plan plan, const T* Zx, const T* w, cudaStream_t st) {
+    const int P = plan->P;
+    const int64_t N = plan->N;
+    FourierHost& fh = plan->fh;
+    FourierDev& fd = plan->fd;
+    fd.L = fh.L;
+    fd.k_lo = fh.k_lo;
+    fd.k_hi = fh.k_hi;
+    fd.has_k0 = fh.has_k0;
+    fd.n_g = fh.n_g;
+    fd.m = fh.m;
+    fd.W = fh.W;
+    fd.win_base = fh.win_base;
+    fd.beta = fh.beta;
+    if (fh.method == SLK_FOURIER_NDFT) {
+        const int K = fh.k_hi - fh.k_lo + 1;
+        plan->coef.alloc(fh.coef.size(), st);
+        SLK_CHECK_CUDA(cudaMemcpyAsync(plan->coef.get(), fh.coef.data(), sizeof(double) * fh.coef.size(),
+                                       cudaMemcpyHostToDevice, st));
+        plan->cw.alloc(sizeof(Cplx<T>) * P * K, st);
+        plan->cw0.alloc(sizeof(T) * P, st);
+        int64_t ne = ndft_source_scratch(P, N, fd);
+        DevBuf<T> scratch(ne, st);
+        launch_ndft_source<T>(Zx, P, N, N, w, fd, plan->coef.get(), reinterpret_cast<Cplx<T>*>(plan->cw.get()),
+                              reinterpret_cast<T*>(plan->cw0.get()), scratch.get(), ne, st);
+    } else {
+        plan->mult.alloc(fh.mult.size(), st);
+        SLK_CHECK_CUDA(cudaMemcpyAsync(plan->mult.get(), fh.mult.data(), sizeof(double) * fh.mult.size(),
+                                       cudaMemcpyHostToDevice, st));
+        plan->hgrid.alloc(sizeof(T) * P * fh.W, st);
+        int64_t ne = nfft_source_scratch(P, N, fd);
+        DevBuf<T> scratch(ne, st);
+        launch_nfft_source<T>(Zx, P, N, N, w, fd, fh.n_coeff, plan->mult.get(), reinterpret_cast<T*>(plan->hgrid.get()),
+                              scratch.get(), ne, plan->err_dev.get(), st);
+    }
+    // the host copies of the coefficient tables must outlive the async copies
+    SLK_CHECK_CUDA(cudaStreamSynchronize(st));
+}
+
+template <class T>
+void plan_sort_source(slk_plan plan, const T* Zx, const T* w, cudaStream_t st) {
+    const int P = plan->P;
+    const int64_t N = plan->N;
+    plan->keys.alloc(sizeof(T) * P * N, st);
+    DevBuf<int32_t> idx(static_cast<size_t>(P) * N, st);
+    size_t sb = segmented_sort_scratch<T>(P, N);
+    {
+        DevBuf<unsigned char> scratch(sb, st);
+        launch_segmented_sort<T>(Zx, P, N, N, reinterpret_cast<T*>(plan->keys.get()), idx.get(), scratch.get(), sb, st);
+    }
+    plan->A.alloc(static_cast<size_t>(P) * (N + 1), st);
+    plan->B.alloc(static_cast<size_t>(P) * (N + 1), st);
+    launch_prefix_sums<T>(reinterpret_cast<const T*>(plan->keys.get()), idx.get(), w, P, N, plan->A.get(), plan->B.get(),
+                          st);
+    int nb = 1;
+    while (nb * 16 < N && nb < (1 << 16)) nb <<= 1;
+    plan->NB = nb;
+    plan->kmin.alloc(P, st);
+    plan->kscale.alloc(P, st);
+    plan->tab.alloc(static_cast<size_t>(P) * (nb + 1), st);
+    launch_bucket_tables<T>(reinterpret_cast<const T*>(plan->keys.get()), P, N, nb, plan->kmin.get(),
+                            plan->kscale.get(), plan->tab.get(), st);
+}
+
+template <class T>
+void create_impl(slk_plan plan, const void* x_user, int64_t ldx, const void* w_user, cudaStream_t st) {
+    const int64_t N = plan->N;
+    const int d = plan->d, P = plan->P;
+    InView<T> xv(x_user, N, d, ldx, st);
+    InView<T> wv(w_user, N, 1, 1, st);
+    // directions (Algorithm 1, first step)
+    plan->xi64.alloc(static_cast<size_t>(P) * d, st);
+    if (plan->desc.directions) {
+        SLK_CHECK_CUDA(cudaMemcpyAsync(plan->xi64.get(), plan->desc.directions, sizeof(double) * P * d,
+                                       cudaMemcpyDefault, st));
+        SLK_CHECK_CUDA(cudaStreamSynchronize(st));  // the caller may free a host copy after we return
+    } else {
+        launch_draw_directions(plan->xi64.get(), P, d, plan->desc.seed, st);
+    }
+    plan->mu64.alloc(d, st);
+    launch_sample_mean<T>(xv.ptr, N, d, xv.ld, plan->mu64.get(), st);
+    if constexpr (sizeof(T) == 4) {
+        plan->xi32.alloc(static_cast<size_t>(P) * d, st);
+        launch_convert<float>(plan->xi64.get(), plan->xi32.get(), static_cast<int64_t>(P) * d, st);
+        plan->mu32.alloc(d, st);
+        launch_convert<float>(plan->mu64.get(), plan->mu32.get(), d, st);
+    }
+    // project the sources
+    DevBuf<T> Zx(static_cast<size_t>(P) * N, st);
+    project<T>(plan, xv.ptr, N, xv.ld, Zx.get(), st);
+    const int kernel = plan->desc.kernel;
+    const bool need_fourier = kernel == SLK_GAUSSIAN || kernel == SLK_LAPLACIAN;
+    if (need_fourier) {
+        DevBuf<float> mx(1, st);
+        SLK_CHECK_CUDA(cudaMemsetAsync(mx.get(), 0, sizeof(float), st));
+        launch_absmax<T>(Zx.get(), P, N, N, mx.get(), st);
+        float rx = 0.0f;
+        SLK_CHECK_CUDA(cudaMemcpyAsync(&rx, mx.get(), sizeof(float), cudaMemcpyDeviceToHost, st));
+        SLK_CHECK_CUDA(cudaStreamSynchronize(st));
+        if (!std::isfinite(rx)) fail(SLK_ERR_INVALID, "non-finite projected sources");
+        double R = plan->desc.radius > 0.0 ? plan->desc.radius : 1.25 * static_cast<double>(rx) + 1e-6;
+        if (R < rx) fail(SLK_ERR_INVALID, "radius %.6g is smaller than the largest projected source %.6g", R, rx);
+        plan->R = R;
+        double tol = plan->desc.tol;
+        if (tol <= 0.0) tol = default_tol(kernel, plan->desc.precision);
+        if (kernel == SLK_GAUSSIAN) plan->fh = choose_gaussian(plan->desc.param, d, R, plan->desc.n_coeff, plan->desc.method, tol);
+        else plan->fh = choose_laplace_smooth(plan->desc.param, d, R, plan->desc.n_coeff, tol, plan->f64 ? 4096 : 8192);
+        plan->fourier = true;
+        plan_fourier_source<T>(plan, Zx.get(), wv.ptr, st);
+    }
+    if (kernel == SLK_NEGDIST || kernel == SLK_LAPLACIAN) {
+        plan->sorting = true;
+        plan->sort_scale = kernel == SLK_LAPLACIAN ? plan->desc.param : 1.0;
+        plan_sort_source<T>(plan, Zx.get(), wv.ptr, st);
+    }
+}
+
+template <class T>
+void sum_impl(slk_plan plan, const void* y_user, int64_t M, int64_t ldy, void* s_user, cudaStream_t st) {
+    const int P = plan->P, d = plan->d;
+    InView<T> yv(y_user, M, d, ldy, st);
+    DevBuf<T> Zy(static_cast<size_t>(P) * M, st);
+    project<T>(plan, yv.ptr, M, yv.ld, Zy.get(), st);
+    DevBuf<double> acc(M, st);
+    SLK_CHECK_CUDA(cudaMemsetAsync(acc.get(), 0, sizeof(double) * M, st));
+    if (plan->fourier) {
+        launch_range_check<T>(Zy.get(), P, M, M, plan->R, plan->err_dev.get(), st);
+        if (plan->fh.method == SLK_FOURIER_NDFT)
+            launch_ndft_target<T>(Zy.get(), P, M, M, plan->fd, reinterpret_cast<const Cplx<T>*>(plan->cw.get()),
+                                  reinterpret_cast<const T*>(plan->cw0.get()), acc.get(), nullptr, st);
+        else
+            launch_nfft_target<T>(Zy.get(), P, M, M, plan->fd, reinterpret_cast<const T*>(plan->hgrid.get()), acc.get(),
+                                  nullptr, plan->err_dev.get(), st);
+    }
+    if (plan->sorting)
+        launch_negdist_target<T>(Zy.get(), P, M, M, reinterpret_cast<const T*>(plan->keys.get()), plan->N, plan->A.get(),
+                                 plan->B.get(), plan->NB, plan->kmin.get(), plan->kscale.get(), plan->tab.get(), plan->cd,
+                                 plan->sort_scale, acc.get(), nullptr, 0, st);
+    const bool s_dev = is_device_pointer(s_user);
+    if (s_dev) {
+        launch_finalize<T>(acc.get(), static_cast<T*>(s_user), M, 1.0 / P, st);
+    } else {
+        DevBuf<T> s(M, st);
+        launch_finalize<T>(acc.get(), s.get(), M, 1.0 / P, st);
+        SLK_CHECK_CUDA(cudaMemcpyAsync(s_user, s.get(), sizeof(T) * M, cudaMemcpyDeviceToHost, st));
+        SLK_CHECK_CUDA(cudaStreamSynchronize(st));
+    }
+}
+
+template <class T>
+void grad_impl(slk_plan plan, const void* y_user, int64_t M, int64_t ldy, const void* gs_user, void* gy_user,
+               int64_t ldg, cudaStream_t st) {
+    const int P = plan->P, d = plan->d;
+    InView<T> yv(y_user, M, d, ldy, st);
+    DevBuf<T> Zy(static_cast<size_t>(P) * M, st);
+    project<T>(plan, yv.ptr, M, yv.ld, Zy.get(), st);
+    DevBuf<T> G(static_cast<size_t>(M) * P, st);
+    if (plan->fourier) {
+        launch_range_check<T>(Zy.get(), P, M, M, plan->R, plan->err_dev.get(), st);
+        if (plan->fh.method == SLK_FOURIER_NDFT)
+            launch_ndft_target<T>(Zy.get(), P, M, M, plan->fd, reinterpret_cast<const Cplx<T>*>(plan->cw.get()),
+                                  reinterpret_cast<const T*>(plan->cw0.get()), nullptr, G.get(), st);
+        else
+            launch_nfft_target<T>(Zy.get(), P, M, M, plan->fd, reinterpret_cast<const T*>(plan->hgrid.get()), nullptr,
+                                  G.get(), plan->err_dev.get(), st);
+    }
+    if (plan->sorting)
+        launch_negdist_target<T>(Zy.get(), P, M, M, reinterpret_cast<const T*>(plan->keys.get()), plan->N, plan->A.get(),
+                                 plan->B.get(), plan->NB, plan->kmin.get(), plan->kscale.get(), plan->tab.get(), plan->cd,
+                                 plan->sort_scale, nullptr, G.get(), plan->fourier ? 1 : 0, st);
+    InView<T> gsv(gs_user, gs_user ? M : 0, 1, 1, st);
+    const bool g_dev = is_device_pointer(gy_user);
+    if (g_dev) {
+        launch_grad_gemm<T>(G.get(), M, P, xi_of<T>(plan), d, gs_user ? gsv.ptr : nullptr, 1.0 / P,
+                            static_cast<T*>(gy_user), ldg, st);
+    } else {
+        DevBuf<T> gy(static_cast<size_t>(M) * d, st);
+        launch_grad_gemm<T>(G.get(), M, P, xi_of<T>(plan), d, gs_user ? gsv.ptr : nullptr, 1.0 / P, gy.get(), d, st);
+        SLK_CHECK_CUDA(cudaMemcpy2DAsync(gy_user, sizeof(T) * ldg, gy.get(), sizeof(T) * d, sizeof(T) * d, M,
+                                         cudaMemcpyDeviceToHost, st));
+        SLK_CHECK_CUDA(cudaStreamSynchronize(st));
+    }
+}
+
+void validate_desc(const slk_plan_desc* desc) {
+    SLK_REQUIRE(desc, "descriptor is NULL");
+    SLK_REQUIRE(desc->kernel >= SLK_GAUSSIAN && desc->kernel <= SLK_NEGDIST, "unknown kernel %d", desc->kernel);
+    SLK_REQUIRE(desc->precision >= SLK_PREC_F64 && desc->precision <= SLK_PREC_F16X3, "unknown precision %d",
+                desc->precision);
+    SLK_REQUIRE(desc->d >= 1, "d must be >= 1");
+    SLK_REQUIRE(desc->P >= 1 && desc->P <= 65535, "P must be in [1, 65535]");
+    SLK_REQUIRE(desc->method >= SLK_FOURIER_AUTO && desc->method <= SLK_FOURIER_NDFT, "unknown Fourier method");
+    SLK_REQUIRE(desc->n_coeff >= 0 && desc->n_coeff <= (1 << 14) && desc->n_coeff % 2 == 0,
+                "n_coeff must be even and in [0, 16384]");
+    if (desc->kernel != SLK_NEGDIST)
+        SLK_REQUIRE(desc->param > 0.0 && std::isfinite(desc->param), "kernel parameter must be positive");
+    SLK_REQUIRE(desc->tol >= 0.0 && desc->radius >= 0.0, "tol and radius must be >= 0");
+    if (desc->precision == SLK_PREC_BF16 || desc->precision == SLK_PREC_F16X3)
+        fail(SLK_ERR_UNSUPPORTED, "tensor-core projection precisions are not built in this library");
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ exported calls
+
+extern "C" {
+
+int32_t slk_version(void) { return SLK_VERSION_MAJOR * 100 + SLK_VERSION_MINOR; }
+
+const char* slk_status_string(slk_status status) {
+    switch (status) {
+    case SLK_OK: return "ok";
+    case SLK_ERR_INVALID: return "invalid argument";
+    case SLK_ERR_OOM: return "out of device memory";
+    case SLK_ERR_CUDA: return "CUDA error";
+    case SLK_ERR_ACCURACY: return "accuracy target cannot be met";
+    case SLK_ERR_TIMEOUT: return "timed out";
+    case SLK_ERR_BUSY: return "busy";
+    case SLK_ERR_UNSUPPORTED: return "unsupported";
+    case SLK_ERR_NOT_FOUND: return "not found";
+    }
+    return "unknown status";
+}
+
+const char* slk_last_error(void) { return g_last_error.c_str(); }
+
+slk_status slk_plan_create(slk_plan* out, const slk_plan_desc* desc, const void* x, int64_t N, int64_t ldx,
+                           const void* w, void* stream) {
+    set_last_error("");
+    return guarded([&] {
+        SLK_REQUIRE(out, "plan output pointer is NULL");
+        *out = nullptr;
+        validate_desc(desc);
+        SLK_REQUIRE(x && w, "x and w must not be NULL");
+        SLK_REQUIRE(N >= 1 && N < (int64_t(1) << 31), "N must be in [1, 2^31)");
+        SLK_REQUIRE(ldx >= desc->d, "ldx must be >= d");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        std::unique_ptr<slk_plan_s> plan(new slk_plan_s());
+        plan->desc = *desc;
+        SLK_CHECK_CUDA(cudaGetDevice(&plan->device));
+        configure_pool(plan->device);
+        plan->f64 = desc->precision == SLK_PREC_F64;
+        plan->N = N;
+        plan->d = desc->d;
+        plan->P = desc->P;
+        plan->cd = cd_host(desc->d);
+        plan->stream = st;
+        plan->err_dev.alloc(1, st);
+        SLK_CHECK_CUDA(cudaMemsetAsync(plan->err_dev.get(), 0, sizeof(unsigned), st));
+        SLK_CHECK_CUDA(cudaMallocHost(&plan->err_host, sizeof(unsigned)));
+        *plan->err_host = 0;
+        SLK_CHECK_CUDA(cudaEventCreateWithFlags(&plan->done, cudaEventDisableTiming));
+        if (plan->f64) create_impl<double>(plan.get(), x, ldx, w, st);
+        else create_impl<float>(plan.get(), x, ldx, w, st);
+        finish_call(plan.get(), st);
+        slk_status s = collect(plan.get(), true);
+        if (s != SLK_OK) throw Error{s, slk_last_error()};
+        SLK_CHECK_LAUNCH();
+        *out = plan.release();
+    });
+}
+
+slk_status slk_sum(slk_plan plan, const void* y, int64_t M, int64_t ldy, void* s, void* stream) {
+    set_last_error("");
+    return guarded([&] {
+        SLK_REQUIRE(plan, "plan is NULL");
+        slk_status prev = collect(plan, false);
+        if (prev != SLK_OK) throw Error{prev, slk_last_error()};
+        SLK_REQUIRE(M >= 0, "M must be >= 0");
+        if (M == 0) return;
+        SLK_REQUIRE(y && s, "y and s must not be NULL");
+        SLK_REQUIRE(ldy >= plan->d, "ldy must be >= d");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        if (plan->f64) sum_impl<double>(plan, y, M, ldy, s, st);
+        else sum_impl<float>(plan, y, M, ldy, s, st);
+        finish_call(plan, st);
+        plan->stream = st;
+        if (!is_device_pointer(s)) {
+            slk_status e = collect(plan, true);
+            if (e != SLK_OK) throw Error{e, slk_last_error()};
+        }
+    });
+}
+
+slk_status slk_grad(slk_plan plan, const void* y, int64_t M, int64_t ldy, const void* gs, void* gy, int64_t ldg,
+                    void* stream) {
+    set_last_error("");
+    return guarded([&] {
+        SLK_REQUIRE(plan, "plan is NULL");
+        slk_status prev = collect(plan, false);
+        if (prev != SLK_OK) throw Error{prev, slk_last_error()};
+        SLK_REQUIRE(M >= 0, "M must be >= 0");
+        if (M == 0) return;
+        SLK_REQUIRE(y && gy, "y and gy must not be NULL");
+        SLK_REQUIRE(ldy >= plan->d && ldg >= plan->d, "ldy and ldg must be >= d");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        if (plan->f64) grad_impl<double>(plan, y, M, ldy, gs, gy, ldg, st);
+        else grad_impl<float>(plan, y, M, ldy, gs, gy, ldg, st);
+        finish_call(plan, st);
+        plan->stream = st;
+        if (!is_device_pointer(gy)) {
+            slk_status e = collect(plan, true);
+            if (e != SLK_OK) throw Error{e, slk_last_error()};
+        }
+    });
+}
+
+slk_status slk_plan_sync(slk_plan plan) {
+    set_last_error("");
+    return guarded([&] {
+        SLK_REQUIRE(plan, "plan is NULL");
+        slk_status e = collect(plan, true);
+        if (e != SLK_OK) throw Error{e, slk_last_error()};
+    });
+}
+
+slk_status slk_plan_get_directions(slk_plan plan, double* xi_host) {
+    set_last_error("");
+    return guarded([&] {
+        SLK_REQUIRE(plan && xi_host, "plan and xi_host must not be NULL");
+        SLK_CHECK_CUDA(cudaMemcpyAsync(xi_host, plan->xi64.get(), sizeof(double) * plan->P * plan->d,
+                                       cudaMemcpyDeviceToHost, plan->stream));
+        SLK_CHECK_CUDA(cudaStreamSynchronize(plan->stream));
+    });
+}
+
+slk_status slk_plan_get_info(slk_plan plan, slk_plan_info* info) {
+    set_last_error("");
+    return guarded([&] {
+        SLK_REQUIRE(plan && info, "plan and info must not be NULL");
+        SLK_CHECK_CUDA(cudaStreamSynchronize(plan->stream));
+        std::memset(info, 0, sizeof(*info));
+        info->kernel = plan->desc.kernel;
+        info->precision = plan->desc.precision;
+        info->d = plan->d;
+        info->P = plan->P;
+        info->N = plan->N;
+        info->c_d = plan->cd;
+        info->device_bytes = plan->device_bytes();
+        if (plan->fourier) {
+            info->method = plan->fh.method;
+            info->n_coeff = plan->fh.n_coeff;
+            info->n_grid = plan->fh.n_g;
+            info->window = plan->fh.m;
+            info->k_lo = plan->fh.k_lo;
+            info->k_hi = plan->fh.k_hi;
+            info->period = plan->fh.L;
+            info->radius = plan->R;
+            info->model_error = plan->fh.model_err;
+        }
+    });
+}
+
+slk_status slk_plan_destroy(slk_plan plan) {
+    set_last_error("");
+    return guarded([&] {
+        if (!plan) return;
+        cudaStreamSynchronize(plan->stream);
+        delete plan;
+    });
+}
+
+slk_status slk_fourier_params(const slk_plan_desc* desc, double radius, slk_plan_info* info) {
+    set_last_error("");
+    return guarded([&] {
+        validate_desc(desc);
+        SLK_REQUIRE(info && radius > 0.0 && std::isfinite(radius), "info must not be NULL and radius > 0");
+        if (desc->kernel == SLK_NEGDIST) fail(SLK_ERR_UNSUPPORTED, "the negative distance kernel has no Fourier part");
+        const bool f64 = desc->precision == SLK_PREC_F64;
+        double tol = desc->tol;
+        if (tol <= 0.0) tol = default_tol(desc->kernel, desc->precision);
+        FourierHost fh = desc->kernel == SLK_GAUSSIAN
+                             ? choose_gaussian(desc->param, desc->d, radius, desc->n_coeff, desc->method, tol)
+                             : choose_laplace_smooth(desc->param, desc->d, radius, desc->n_coeff, tol, f64 ? 4096 : 8192);
+        std::memset(info, 0, sizeof(*info));
+        info->kernel = desc->kernel;
+        info->precision = desc->precision;
+        info->d = desc->d;
+        info->P = desc->P;
+        info->method = fh.method;
+        info->n_coeff = fh.n_coeff;
+        info->n_grid = fh.n_g;
+        info->window = fh.m;
+        info->k_lo = fh.k_lo;
+        info->k_hi = fh.k_hi;
+        info->period = fh.L;
+        info->radius = radius;
+        info->model_error = fh.model_err;
+        info->c_d = cd_host(desc->d);
+    });
+}
+
+slk_status slk_kernel_sum(const slk_plan_desc* desc, const void* x, int64_t N, int64_t ldx, const void* w,
+                          const void* y, int64_t M, int64_t ldy, void* s, void* stream) {
+    slk_plan plan = nullptr;
+    slk_status st = slk_plan_create(&plan, desc, x, N, ldx, w, stream);
+    if (st != SLK_OK) return st;
+    st = slk_sum(plan, y, M, ldy, s, stream);
+    if (st == SLK_OK) st = slk_plan_sync(plan);
+    std::string keep = slk_last_error();
+    slk_status d = slk_plan_destroy(plan);
+    if (st != SLK_OK) {
+        set_last_error(keep);
+        return st;
+    }
+    return d;
+}
+
+}  // extern "C"

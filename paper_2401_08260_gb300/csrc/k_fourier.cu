@@ -1,0 +1,590 @@
+// Fast Fourier summation on every slice (Section 3.1).
+//
+// Notation: a projected point z (source or target) of slice p is rescaled to
+// x~ = z / L in the periodic cell [-1/2, 1/2) (paragraph "Rescaling" of
+// Section 3.1, read as x~ = (z - c) / L with the centre c = 0 after the
+// projections were centred).  The 1-D sum on a slice is
+//     t(y~) = sum_{k in C} c_k w^_k exp(2 pi i k y~),   w^_k = sum_n w_n exp(-2 pi i k x~_n).
+//
+// NDFT ("plain" method): w^_k directly for the significant band of k.
+// NFFT (remark on the non-equispaced FFT): spread the weights onto an
+// oversampled grid of n_g cells with the "exponential of semicircle" window
+//     psi(s) = exp(beta (sqrt(1 - (2 s / m)^2) - 1)),  |s| <= m/2  (s in cells),
+// FFT, multiply by c_k / Psi(k/n_g)^2 (Psi = Fourier transform of psi), inverse
+// FFT, then interpolate with the same window.
+//
+// Because the projected data occupy only |z| <= R << L/2, only the grid cells
+// [win_base, win_base + W) that a window can touch are stored.
+#include "kernels.cuh"
+
+namespace slk {
+
+namespace {
+
+constexpr int NDFT_KC = 16;       // k values accumulated per pass (registers)
+constexpr int NDFT_CHUNK = 8192;  // sources per block in the NDFT reduction
+constexpr int SPREAD_NARROW_W = 64;
+constexpr int SPREAD_WARPS = 8;
+constexpr int SPREAD_CHUNK = 4096;  // sources per warp in the narrow spread
+
+template <class T>
+__device__ inline T es_window(T s, T two_over_m, T beta) {
+    T x = s * two_over_m;
+    T q = T(1) - x * x;
+    return q > T(0) ? exp(beta * (sqrt(q) - T(1))) : (q == T(0) ? exp(-beta) : T(0));
+}
+
+// derivative of psi with respect to s
+template <class T>
+__device__ inline T es_window_deriv(T s, T two_over_m, T beta) {
+    T x = s * two_over_m;
+    T q = T(1) - x * x;
+    if (q <= T(1e-6)) return T(0);
+    T r = sqrt(q);
+    return exp(beta * (r - T(1))) * beta * (-x * two_over_m) / r;
+}
+
+template <class T>
+__device__ inline T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// fixed-order sum of one value per thread of a 256-thread block; result valid in thread 0
+template <class T>
+__device__ inline T block_sum_256(T v, T* red) {
+    v = warp_sum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    T r = T(0);
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 8; ++i) r += red[i];
+    return r;
+}
+
+// compensated (Kahan) accumulation for the FP32 slice average
+struct KahanF {
+    float s = 0.f, c = 0.f;
+    __device__ void add(float v) {
+        float y = v - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ double value() const { return static_cast<double>(s) - static_cast<double>(c); }
+};
+struct KahanD {
+    double s = 0.0;
+    __device__ void add(double v) { s += v; }
+    __device__ double value() const { return s; }
+};
+template <class T> struct Acc;
+template <> struct Acc<float> { using type = KahanF; };
+template <> struct Acc<double> { using type = KahanD; };
+
+// ------------------------------------------------------------ NDFT source
+
+template <class T>
+__global__ void __launch_bounds__(256) k_ndft_source(const T* __restrict__ Z, int64_t n, int64_t ldz,
+                                                     const T* __restrict__ w, T inv_L, int k_lo, int K, int has_k0,
+                                                     T* __restrict__ partial, int P) {
+    __shared__ T red[8];
+    const int p = blockIdx.y;
+    const int64_t i0 = static_cast<int64_t>(blockIdx.x) * NDFT_CHUNK;
+    const int64_t i1 = (i0 + NDFT_CHUNK < n) ? i0 + NDFT_CHUNK : n;
+    const T* zr = Z + static_cast<int64_t>(p) * ldz;
+    const int stride = 2 * K + 1;
+    T* out = partial + (static_cast<int64_t>(blockIdx.x) * P + p) * stride;
+    const T two_pi = T(6.283185307179586476925286766559);
+    for (int kc = 0; kc < K; kc += NDFT_KC) {
+        T re[NDFT_KC], im[NDFT_KC];
+#pragma unroll
+        for (int j = 0; j < NDFT_KC; ++j) re[j] = im[j] = T(0);
+        T a0 = T(0);
+        const int kb = k_lo + kc;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += 256) {
+            const T wv = w[i];
+            const T th = two_pi * (zr[i] * inv_L);
+            T s, c, s1, c1;
+            sincos_t(T(kb) * th, &s, &c);
+            sincos_t(th, &s1, &c1);
+            // e^{-i k theta}, advanced by e^{-i theta}
+            T cr = c, ci = -s;
+#pragma unroll
+            for (int j = 0; j < NDFT_KC; ++j) {
+                re[j] = fma(wv, cr, re[j]);
+                im[j] = fma(wv, ci, im[j]);
+                T nr = cr * c1 + ci * s1;
+                T ni = ci * c1 - cr * s1;
+                cr = nr;
+                ci = ni;
+            }
+            if (has_k0 && kc == 0) a0 += wv;
+        }
+#pragma unroll
+        for (int j = 0; j < NDFT_KC; ++j) {
+            if (kc + j < K) {  // uniform across the block
+                T r = block_sum_256(re[j], red);
+                T m = block_sum_256(im[j], red);
+                if (threadIdx.x == 0) {
+                    out[2 * (kc + j)] = r;
+                    out[2 * (kc + j) + 1] = m;
+                }
+            }
+        }
+        if (kc == 0) {
+            T r = block_sum_256(a0, red);
+            if (threadIdx.x == 0) out[2 * K] = r;
+        }
+    }
+}
+
+// cw[p][j] = c_{k_lo + j} * sum over chunks (fixed order); cw0[p] = c_0 sum w
+template <class T>
+__global__ void k_ndft_reduce(const T* __restrict__ partial, int nchunk, int P, int K, int has_k0,
+                              const double* __restrict__ coef, Cplx<T>* __restrict__ cw, T* __restrict__ cw0) {
+    const int stride = 2 * K + 1;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < P * (K + 1); t += gridDim.x * blockDim.x) {
+        int p = t / (K + 1), j = t % (K + 1);
+        if (j == K) {
+            double a = 0.0;
+            for (int c = 0; c < nchunk; ++c) a += static_cast<double>(partial[(static_cast<int64_t>(c) * P + p) * stride + 2 * K]);
+            cw0[p] = has_k0 ? static_cast<T>(coef[K] * a) : T(0);
+        } else {
+            double r = 0.0, m = 0.0;
+            for (int c = 0; c < nchunk; ++c) {
+                const T* q = partial + (static_cast<int64_t>(c) * P + p) * stride;
+                r += static_cast<double>(q[2 * j]);
+                m += static_cast<double>(q[2 * j + 1]);
+            }
+            cw[static_cast<int64_t>(p) * K + j] = Cplx<T>{static_cast<T>(coef[j] * r), static_cast<T>(coef[j] * m)};
+        }
+    }
+}
+
+// ------------------------------------------------------------ NDFT target
+
+template <class T>
+__global__ void __launch_bounds__(256) k_ndft_target(const T* __restrict__ Z, int P, int64_t n, int64_t ldz, T inv_L,
+                                                     int k_lo, int K, const Cplx<T>* __restrict__ cw,
+                                                     const T* __restrict__ cw0, int slice_chunk,
+                                                     double* __restrict__ acc, T* __restrict__ G) {
+    extern __shared__ unsigned char smem_raw[];
+    Cplx<T>* scw = reinterpret_cast<Cplx<T>*>(smem_raw);
+    T* scw0 = reinterpret_cast<T*>(scw + static_cast<size_t>(slice_chunk) * K);
+    const int64_t m = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const T two_pi = T(6.283185307179586476925286766559);
+    typename Acc<T>::type sum;
+    for (int p0 = 0; p0 < P; p0 += slice_chunk) {
+        const int pc = (P - p0 < slice_chunk) ? P - p0 : slice_chunk;
+        __syncthreads();
+        for (int e = threadIdx.x; e < pc * K; e += blockDim.x) scw[e] = cw[static_cast<int64_t>(p0) * K + e];
+        for (int e = threadIdx.x; e < pc; e += blockDim.x) scw0[e] = cw0[p0 + e];
+        __syncthreads();
+        if (m >= n) continue;
+        for (int q = 0; q < pc; ++q) {
+            const int p = p0 + q;
+            const T th = two_pi * (Z[static_cast<int64_t>(p) * ldz + m] * inv_L);
+            T s, c, s1, c1;
+            sincos_t(T(k_lo) * th, &s, &c);
+            sincos_t(th, &s1, &c1);
+            T cr = c, ci = s;  // e^{+i k theta}
+            T t = T(0), dt = T(0);
+            const Cplx<T>* row = scw + static_cast<size_t>(q) * K;
+            for (int j = 0; j < K; ++j) {
+                const Cplx<T> a = row[j];
+                // Re(a e^{ik th}) and d/dth Re(a e^{ik th}) = -k Im(a e^{ik th})
+                t += a.re * cr - a.im * ci;
+                dt -= T(k_lo + j) * (a.re * ci + a.im * cr);
+                T nr = cr * c1 - ci * s1;
+                T ni = ci * c1 + cr * s1;
+                cr = nr;
+                ci = ni;
+            }
+            if (G) {
+                // t_p = 2 Re(...) + cw0;  dt_p/dz = 2 * (dt) * 2 pi / L
+                G[m * P + p] = T(2) * dt * two_pi * inv_L;
+            } else {
+                sum.add(T(2) * t + scw0[q]);
+            }
+        }
+    }
+    if (!G && m < n) acc[m] += sum.value();
+}
+
+// ------------------------------------------------------------ NFFT spread
+
+// Narrow window (W <= 64): lane = slice, every lane keeps a private window in
+// shared memory laid out [cell][lane] (conflict-free), warps split the sources.
+template <class T>
+__global__ void __launch_bounds__(256) k_spread_narrow(const T* __restrict__ Z, int P, int64_t n, int64_t ldz,
+                                                       const T* __restrict__ w, T scale_u, int m, T two_over_m, T beta,
+                                                       int W, int win_base, T* __restrict__ partial,
+                                                       unsigned* __restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    T* win = reinterpret_cast<T*>(smem_raw);  // [SPREAD_WARPS][W][32]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p = blockIdx.y * 32 + lane;
+    T* mine = win + static_cast<size_t>(warp) * W * 32;
+    for (int r = 0; r < W; ++r) mine[r * 32 + lane] = T(0);
+    const int64_t i0 = (static_cast<int64_t>(blockIdx.x) * SPREAD_WARPS + warp) * SPREAD_CHUNK;
+    const int64_t i1 = (i0 + SPREAD_CHUNK < n) ? i0 + SPREAD_CHUNK : n;
+    const T half_m = T(0.5) * T(m);
+    bool bad = false;
+    if (p < P) {
+        const T* zr = Z + static_cast<int64_t>(p) * ldz;
+        for (int64_t i = i0; i < i1; ++i) {
+            const T u = zr[i] * scale_u;  // grid coordinate n_g z / L
+            const T wv = w[i];
+            const T c0 = ceil(u - half_m);
+            const int r0 = static_cast<int>(c0) - win_base;
+            if (r0 < 0 || r0 + m > W) {
+                bad = true;
+                continue;
+            }
+            T s = c0 - u;
+            for (int t = 0; t < m; ++t, s += T(1)) mine[(r0 + t) * 32 + lane] += wv * es_window(s, two_over_m, beta);
+        }
+    }
+    if (bad) atomicOr(err, 1u);
+    __syncthreads();
+    // fixed-order reduction over the warps of the block
+    for (int e = threadIdx.x; e < W * 32; e += blockDim.x) {
+        T v = T(0);
+        for (int q = 0; q < SPREAD_WARPS; ++q) v += win[static_cast<size_t>(q) * W * 32 + e];
+        const int r = e / 32, l = e % 32;
+        const int pp = blockIdx.y * 32 + l;
+        if (pp < P) partial[(static_cast<int64_t>(blockIdx.x) * P + pp) * W + r] = v;
+    }
+}
+
+// Wide window: one slice per block row, a block-shared window with shared
+// atomics (sources spread over many cells, little contention).
+template <class T>
+__global__ void __launch_bounds__(256) k_spread_wide(const T* __restrict__ Z, int P, int64_t n, int64_t ldz,
+                                                     const T* __restrict__ w, T scale_u, int m, T two_over_m, T beta,
+                                                     int W, int win_base, int64_t chunk, T* __restrict__ partial,
+                                                     unsigned* __restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    T* win = reinterpret_cast<T*>(smem_raw);
+    const int p = blockIdx.y;
+    for (int r = threadIdx.x; r < W; r += blockDim.x) win[r] = T(0);
+    __syncthreads();
+    const int64_t i0 = static_cast<int64_t>(blockIdx.x) * chunk;
+    const int64_t i1 = (i0 + chunk < n) ? i0 + chunk : n;
+    const T* zr = Z + static_cast<int64_t>(p) * ldz;
+    const T half_m = T(0.5) * T(m);
+    bool bad = false;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const T u = zr[i] * scale_u;
+        const T wv = w[i];
+        const T c0 = ceil(u - half_m);
+        const int r0 = static_cast<int>(c0) - win_base;
+        if (r0 < 0 || r0 + m > W) {
+            bad = true;
+            continue;
+        }
+        T s = c0 - u;
+        for (int t = 0; t < m; ++t, s += T(1)) atomicAdd(&win[r0 + t], wv * es_window(s, two_over_m, beta));
+    }
+    if (bad) atomicOr(err, 1u);
+    __syncthreads();
+    for (int r = threadIdx.x; r < W; r += blockDim.x)
+        partial[(static_cast<int64_t>(blockIdx.x) * P + p) * W + r] = win[r];
+}
+
+template <class T>
+__global__ void k_window_reduce(const T* __restrict__ partial, int nchunk, int P, int W, T* __restrict__ g) {
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < static_cast<int64_t>(P) * W;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        T v = T(0);
+        for (int c = 0; c < nchunk; ++c) v += partial[static_cast<int64_t>(c) * P * W + e];
+        g[e] = v;
+    }
+}
+
+// ------------------------------------------------------------ FFT * multiply * IFFT
+
+// In-place radix-2 FFT of n = 2^logn complex values in shared memory
+// (bit-reversal permutation, then log2(n) butterfly stages); sign = -1 forward.
+template <class T>
+__device__ void smem_fft(Cplx<T>* a, int n, int logn, int sign) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        int j = __brev(static_cast<unsigned>(i)) >> (32 - logn);
+        if (j > i) {
+            Cplx<T> t = a[i];
+            a[i] = a[j];
+            a[j] = t;
+        }
+    }
+    __syncthreads();
+    for (int len = 2; len <= n; len <<= 1) {
+        const int half = len >> 1;
+        for (int b = threadIdx.x; b < (n >> 1); b += blockDim.x) {
+            const int grp = b / half, pos = b % half;
+            const int i = grp * len + pos, j = i + half;
+            T s, c;
+            // twiddle exp(sign 2 pi i pos / len)
+            if constexpr (sizeof(T) == 4) sincospif(T(2) * T(pos) / T(len), &s, &c);
+            else sincospi(T(2) * T(pos) / T(len), &s, &c);
+            s *= T(sign);
+            const Cplx<T> u = a[i], v = a[j];
+            const T vr = v.re * c - v.im * s, vi = v.re * s + v.im * c;
+            a[i] = Cplx<T>{u.re + vr, u.im + vi};
+            a[j] = Cplx<T>{u.re - vr, u.im - vi};
+        }
+        __syncthreads();
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(512) k_fft_multiply(const T* __restrict__ g, int P, int n_g, int logn, int W,
+                                                      int win_base, int kmax, const double* __restrict__ mult,
+                                                      T* __restrict__ h) {
+    extern __shared__ unsigned char smem_raw[];
+    Cplx<T>* a = reinterpret_cast<Cplx<T>*>(smem_raw);
+    const int p = blockIdx.x;
+    for (int j = threadIdx.x; j < n_g; j += blockDim.x) a[j] = Cplx<T>{T(0), T(0)};
+    __syncthreads();
+    for (int r = threadIdx.x; r < W; r += blockDim.x) {
+        int j = (win_base + r) % n_g;
+        if (j < 0) j += n_g;
+        // several window cells can alias onto one grid cell only if W > n_g (excluded)
+        a[j].re = g[static_cast<int64_t>(p) * W + r];
+    }
+    __syncthreads();
+    smem_fft(a, n_g, logn, -1);
+    for (int j = threadIdx.x; j < n_g; j += blockDim.x) {
+        const int k = j < n_g / 2 ? j : j - n_g;
+        const int ak = k < 0 ? -k : k;
+        const T f = ak < kmax ? static_cast<T>(mult[ak]) : T(0);
+        a[j].re *= f;
+        a[j].im *= f;
+    }
+    __syncthreads();
+    smem_fft(a, n_g, logn, +1);
+    for (int r = threadIdx.x; r < W; r += blockDim.x) {
+        int j = (win_base + r) % n_g;
+        if (j < 0) j += n_g;
+        h[static_cast<int64_t>(p) * W + r] = a[j].re;
+    }
+}
+
+// ------------------------------------------------------------ NFFT interpolation
+
+template <class T>
+__global__ void __launch_bounds__(256) k_nfft_target(const T* __restrict__ Z, int P, int64_t n, int64_t ldz, T scale_u,
+                                                     int m, T two_over_m, T beta, int W, int win_base,
+                                                     const T* __restrict__ h, int slice_chunk, double* __restrict__ acc,
+                                                     T* __restrict__ G, unsigned* __restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    T* sh = reinterpret_cast<T*>(smem_raw);
+    const int64_t mi = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const T half_m = T(0.5) * T(m);
+    typename Acc<T>::type sum;
+    bool bad = false;
+    for (int p0 = 0; p0 < P; p0 += slice_chunk) {
+        const int pc = (P - p0 < slice_chunk) ? P - p0 : slice_chunk;
+        __syncthreads();
+        for (int e = threadIdx.x; e < pc * W; e += blockDim.x) sh[e] = h[static_cast<int64_t>(p0) * W + e];
+        __syncthreads();
+        if (mi >= n) continue;
+        for (int q = 0; q < pc; ++q) {
+            const int p = p0 + q;
+            const T u = Z[static_cast<int64_t>(p) * ldz + mi] * scale_u;
+            const T c0 = ceil(u - half_m);
+            const int r0 = static_cast<int>(c0) - win_base;
+            if (r0 < 0 || r0 + m > W) {
+                bad = true;
+                continue;
+            }
+            const T* row = sh + static_cast<size_t>(q) * W + r0;
+            T s = c0 - u, t = T(0);
+            if (G) {
+                // d/du sum_j h_j psi(u - j) = -sum_j h_j psi'(j - u)
+                for (int k = 0; k < m; ++k, s += T(1)) t -= row[k] * es_window_deriv(s, two_over_m, beta);
+                G[mi * P + p] = t * scale_u;
+            } else {
+                for (int k = 0; k < m; ++k, s += T(1)) t += row[k] * es_window(s, two_over_m, beta);
+                sum.add(t);
+            }
+        }
+    }
+    if (bad) atomicOr(err, 2u);
+    if (!G && mi < n) acc[mi] += sum.value();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ launchers
+
+int64_t ndft_source_scratch(int P, int64_t n, const FourierDev& fd) {
+    int K = fd.k_hi - fd.k_lo + 1;
+    return ceil_div(n, NDFT_CHUNK) * static_cast<int64_t>(P) * (2 * K + 1);
+}
+
+template <class T>
+void launch_ndft_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, const FourierDev& fd,
+                        const double* coef, Cplx<T>* cw, T* cw0, T* scratch, int64_t scratch_elems, cudaStream_t st) {
+    const int K = fd.k_hi - fd.k_lo + 1;
+    const int64_t nchunk = ceil_div(n, NDFT_CHUNK);
+    SLK_REQUIRE(scratch_elems >= ndft_source_scratch(P, n, fd), "NDFT scratch too small");
+    SLK_REQUIRE(nchunk <= 2147483647 && P <= 65535, "NDFT launch too large");
+    dim3 grid(static_cast<unsigned>(nchunk), P);
+    {
+        SLK_TIMED("ndft_source", st);
+        k_ndft_source<T><<<grid, 256, 0, st>>>(Z, n, ldz, w, static_cast<T>(1.0 / fd.L), fd.k_lo, K, fd.has_k0, scratch, P);
+    }
+    SLK_CHECK_LAUNCH();
+    int total = P * (K + 1);
+    {
+        SLK_TIMED("ndft_reduce", st);
+        k_ndft_reduce<T><<<static_cast<unsigned>(ceil_div(total, 256)), 256, 0, st>>>(scratch, static_cast<int>(nchunk), P,
+                                                                                       K, fd.has_k0, coef, cw, cw0);
+    }
+    SLK_CHECK_LAUNCH();
+}
+
+template <class T>
+void launch_ndft_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const Cplx<T>* cw,
+                        const T* cw0, double* acc, T* G, cudaStream_t st) {
+    if (n <= 0) return;
+    const int K = fd.k_hi - fd.k_lo + 1;
+    const size_t per_slice = sizeof(Cplx<T>) * K + sizeof(T);
+    int chunk = static_cast<int>((96 * 1024) / per_slice);
+    if (chunk > P) chunk = P;
+    if (chunk < 1) chunk = 1;
+    const size_t smem = per_slice * chunk + 16;
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[sizeof(T) == 8]) {
+        SLK_CHECK_CUDA(cudaFuncSetAttribute(k_ndft_target<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+        attr_set[sizeof(T) == 8] = true;
+    }
+    {
+        SLK_TIMED("ndft_target", st);
+        k_ndft_target<T><<<static_cast<unsigned>(ceil_div(n, 256)), 256, smem, st>>>(
+            Z, P, n, ldz, static_cast<T>(1.0 / fd.L), fd.k_lo, K, cw, cw0, chunk, acc, G);
+    }
+    SLK_CHECK_LAUNCH();
+}
+
+int64_t nfft_source_scratch(int P, int64_t n, const FourierDev& fd) {
+    int64_t nchunk;
+    if (fd.W <= SPREAD_NARROW_W) nchunk = ceil_div(n, static_cast<int64_t>(SPREAD_WARPS) * SPREAD_CHUNK);
+    else nchunk = ceil_div(n, 65536);
+    return (nchunk + 1) * static_cast<int64_t>(P) * fd.W;
+}
+
+template <class T>
+void launch_nfft_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, const FourierDev& fd, int n_coeff,
+                        const double* mult, T* h, T* scratch, int64_t scratch_elems, unsigned* err, cudaStream_t st) {
+    SLK_REQUIRE(scratch_elems >= nfft_source_scratch(P, n, fd), "NFFT scratch too small");
+    SLK_REQUIRE(fd.W <= fd.n_g, "NFFT window wider than the grid");
+    const T scale_u = static_cast<T>(fd.n_g / fd.L);
+    const T two_over_m = static_cast<T>(2.0 / fd.m);
+    const T beta = static_cast<T>(fd.beta);
+    // scratch layout: [partials nchunk x P x W] [reduced grid P x W]
+    T* partial = scratch;
+    int64_t nchunk;
+    if (fd.W <= SPREAD_NARROW_W) {
+        nchunk = ceil_div(n, static_cast<int64_t>(SPREAD_WARPS) * SPREAD_CHUNK);
+        size_t smem = sizeof(T) * SPREAD_WARPS * fd.W * 32;
+        static bool attr_set[2] = {false, false};
+        if (!attr_set[sizeof(T) == 8]) {
+            SLK_CHECK_CUDA(cudaFuncSetAttribute(k_spread_narrow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                sizeof(T) * SPREAD_WARPS * SPREAD_NARROW_W * 32));
+            attr_set[sizeof(T) == 8] = true;
+        }
+        dim3 grid(static_cast<unsigned>(nchunk), static_cast<unsigned>(ceil_div(P, 32)));
+        {
+            SLK_TIMED("spread_narrow", st);
+            k_spread_narrow<T><<<grid, 256, smem, st>>>(Z, P, n, ldz, w, scale_u, fd.m, two_over_m, beta, fd.W,
+                                                         fd.win_base, partial, err);
+        }
+    } else {
+        const int64_t chunk = 65536;
+        nchunk = ceil_div(n, chunk);
+        size_t smem = sizeof(T) * fd.W;
+        SLK_REQUIRE(smem <= 200 * 1024, "NFFT window too wide");
+        static bool attr_set[2] = {false, false};
+        if (!attr_set[sizeof(T) == 8]) {
+            SLK_CHECK_CUDA(
+                cudaFuncSetAttribute(k_spread_wide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+            attr_set[sizeof(T) == 8] = true;
+        }
+        dim3 grid(static_cast<unsigned>(nchunk), P);
+        {
+            SLK_TIMED("spread_wide", st);
+            k_spread_wide<T><<<grid, 256, smem, st>>>(Z, P, n, ldz, w, scale_u, fd.m, two_over_m, beta, fd.W, fd.win_base,
+                                                       chunk, partial, err);
+        }
+    }
+    SLK_CHECK_LAUNCH();
+    T* g = partial + nchunk * static_cast<int64_t>(P) * fd.W;
+    int64_t tot = static_cast<int64_t>(P) * fd.W;
+    {
+        SLK_TIMED("window_reduce", st);
+        k_window_reduce<T><<<static_cast<unsigned>(ceil_div(tot, 256) < 8192 ? ceil_div(tot, 256) : 8192), 256, 0, st>>>(
+            partial, static_cast<int>(nchunk), P, fd.W, g);
+    }
+    SLK_CHECK_LAUNCH();
+    int logn = 0;
+    while ((1 << logn) < fd.n_g) ++logn;
+    SLK_REQUIRE((1 << logn) == fd.n_g, "NFFT grid must be a power of two");
+    size_t smem = sizeof(Cplx<T>) * fd.n_g;
+    SLK_REQUIRE(smem <= 200 * 1024, "NFFT grid too large for one block");
+    static bool attr_fft[2] = {false, false};
+    if (!attr_fft[sizeof(T) == 8]) {
+        SLK_CHECK_CUDA(cudaFuncSetAttribute(k_fft_multiply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr_fft[sizeof(T) == 8] = true;
+    }
+    {
+        SLK_TIMED("fft_multiply", st);
+        k_fft_multiply<T><<<P, 512, smem, st>>>(g, P, fd.n_g, logn, fd.W, fd.win_base, n_coeff / 2, mult, h);
+    }
+    SLK_CHECK_LAUNCH();
+}
+
+template <class T>
+void launch_nfft_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const T* h, double* acc,
+                        T* G, unsigned* err, cudaStream_t st) {
+    if (n <= 0) return;
+    int chunk = static_cast<int>((96 * 1024) / (sizeof(T) * fd.W));
+    if (chunk > P) chunk = P;
+    if (chunk < 1) chunk = 1;
+    size_t smem = sizeof(T) * fd.W * chunk;
+    SLK_REQUIRE(smem <= 100 * 1024, "NFFT window too wide for the interpolation");
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[sizeof(T) == 8]) {
+        SLK_CHECK_CUDA(cudaFuncSetAttribute(k_nfft_target<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+        attr_set[sizeof(T) == 8] = true;
+    }
+    {
+        SLK_TIMED("nfft_target", st);
+        k_nfft_target<T><<<static_cast<unsigned>(ceil_div(n, 256)), 256, smem, st>>>(
+            Z, P, n, ldz, static_cast<T>(fd.n_g / fd.L), fd.m, static_cast<T>(2.0 / fd.m), static_cast<T>(fd.beta), fd.W,
+            fd.win_base, h, chunk, acc, G, err);
+    }
+    SLK_CHECK_LAUNCH();
+}
+
+template void launch_ndft_source<float>(const float*, int, int64_t, int64_t, const float*, const FourierDev&,
+                                        const double*, Cplx<float>*, float*, float*, int64_t, cudaStream_t);
+template void launch_ndft_source<double>(const double*, int, int64_t, int64_t, const double*, const FourierDev&,
+                                         const double*, Cplx<double>*, double*, double*, int64_t, cudaStream_t);
+template void launch_ndft_target<float>(const float*, int, int64_t, int64_t, const FourierDev&, const Cplx<float>*,
+                                        const float*, double*, float*, cudaStream_t);
+template void launch_ndft_target<double>(const double*, int, int64_t, int64_t, const FourierDev&,
+                                         const Cplx<double>*, const double*, double*, double*, cudaStream_t);
+template void launch_nfft_source<float>(const float*, int, int64_t, int64_t, const float*, const FourierDev&, int,
+                                        const double*, float*, float*, int64_t, unsigned*, cudaStream_t);
+template void launch_nfft_source<double>(const double*, int, int64_t, int64_t, const double*, const FourierDev&, int,
+                                         const double*, double*, double*, int64_t, unsigned*, cudaStream_t);
+template void launch_nfft_target<float>(const float*, int, int64_t, int64_t, const FourierDev&, const float*, double*,
+                                        float*, unsigned*, cudaStream_t);
+template void launch_nfft_target<double>(const double*, int, int64_t, int64_t, const FourierDev&, const double*,
+                                         double*, double*, unsigned*, cudaStream_t);
+
+}  // namespace slk

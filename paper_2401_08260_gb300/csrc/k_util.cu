@@ -1,0 +1,208 @@
+// Directions, centring, conversions, range reduction and the final scaling.
+#include "kernels.cuh"
+
+namespace slk {
+
+// ------------------------------------------------------------ directions
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as easy
+// as 1, 2, 3", SC 2011): ten rounds of two 32x32->64 multiplies with the
+// published round multipliers and Weyl key increments.
+__device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t lo0 = M0 * c[0], hi0 = __umulhi(M0, c[0]);
+        uint32_t lo1 = M1 * c[2], hi1 = __umulhi(M1, c[2]);
+        uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+}
+
+// uniform in (0, 1) from 64 random bits (53-bit significand)
+__device__ inline double u01(uint32_t hi, uint32_t lo) {
+    unsigned long long v = (static_cast<unsigned long long>(hi) << 32) | lo;
+    return (static_cast<double>(v >> 11) + 0.5) * 0x1.0p-53;
+}
+
+__global__ void k_draw_directions(double* xi, int P, int d, uint32_t k0, uint32_t k1) {
+    int p = blockIdx.y;
+    int pairs = (d + 1) / 2;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < pairs; j += gridDim.x * blockDim.x) {
+        uint32_t c[4] = {static_cast<uint32_t>(j), static_cast<uint32_t>(p), 0x736c6b31u, 0u};
+        philox4x32_10(c, k0, k1);
+        double u1 = u01(c[0], c[1]), u2 = u01(c[2], c[3]);
+        double r = sqrt(-2.0 * log(u1));
+        double s, co;
+        sincospi(2.0 * u2, &s, &co);
+        xi[static_cast<int64_t>(p) * d + 2 * j] = r * co;
+        if (2 * j + 1 < d) xi[static_cast<int64_t>(p) * d + 2 * j + 1] = r * s;
+    }
+}
+
+__global__ void k_normalize_rows(double* xi, int d) {
+    double* row = xi + static_cast<int64_t>(blockIdx.x) * d;
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < d; k += blockDim.x) acc += row[k] * row[k];
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) red[0] = v;
+    }
+    __syncthreads();
+    double inv = 1.0 / sqrt(red[0]);
+    for (int k = threadIdx.x; k < d; k += blockDim.x) row[k] *= inv;
+}
+
+void launch_draw_directions(double* xi, int P, int d, uint64_t seed, cudaStream_t st) {
+    int pairs = (d + 1) / 2;
+    dim3 grid(static_cast<unsigned>(ceil_div(pairs, 256)), P);
+    {
+        SLK_TIMED("draw_directions", st);
+        k_draw_directions<<<grid, 256, 0, st>>>(xi, P, d, static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+    }
+    SLK_CHECK_LAUNCH();
+    launch_normalize_rows(xi, P, d, st);
+}
+
+void launch_normalize_rows(double* xi, int P, int d, cudaStream_t st) {
+    {
+        SLK_TIMED("normalize_rows", st);
+        k_normalize_rows<<<P, 256, 0, st>>>(xi, d);
+    }
+    SLK_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------ centre
+
+template <class T>
+__global__ void k_sample_mean(const T* x, int64_t N, int d, int64_t ldx, int S, double* mu) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < d; k += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int s = 0; s < S; ++s) {
+            int64_t row = (static_cast<int64_t>(s) * N) / S;
+            acc += static_cast<double>(x[row * ldx + k]);
+        }
+        mu[k] = acc / S;
+    }
+}
+
+template <class T>
+void launch_sample_mean(const T* x, int64_t N, int d, int64_t ldx, double* mu, cudaStream_t st) {
+    int S = static_cast<int>(N < 4096 ? N : 4096);
+    {
+        SLK_TIMED("sample_mean", st);
+        k_sample_mean<T><<<static_cast<unsigned>(ceil_div(d, 128)), 128, 0, st>>>(x, N, d, ldx, S, mu);
+    }
+    SLK_CHECK_LAUNCH();
+}
+
+template <class T>
+__global__ void k_convert(const double* src, T* dst, int64_t n) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        dst[i] = static_cast<T>(src[i]);
+}
+
+template <class T>
+void launch_convert(const double* src, T* dst, int64_t n, cudaStream_t st) {
+    if (n <= 0) return;
+    int64_t blocks = ceil_div(n, 256);
+    {
+        SLK_TIMED("convert", st);
+        k_convert<T><<<static_cast<unsigned>(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(src, dst, n);
+    }
+    SLK_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------ range
+
+template <class T>
+__global__ void k_absmax(const T* Z, int64_t n, int64_t ldz, float* out) {
+    const T* row = Z + static_cast<int64_t>(blockIdx.y) * ldz;
+    float m = 0.0f;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        float v = fabsf(static_cast<float>(row[i]));
+        m = v > m ? v : m;  // NaN never wins; caught by the window checks downstream
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    // non-negative floats order like their bit patterns: an integer max is exact
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned int*>(out), __float_as_uint(m));
+}
+
+template <class T>
+void launch_absmax(const T* Z, int P, int64_t n, int64_t ldz, float* out, cudaStream_t st) {
+    if (n <= 0 || P <= 0) return;
+    int64_t bx = ceil_div(n, 256);
+    dim3 grid(static_cast<unsigned>(bx < 64 ? bx : 64), P);
+    {
+        SLK_TIMED("absmax", st);
+        k_absmax<T><<<grid, 256, 0, st>>>(Z, n, ldz, out);
+    }
+    SLK_CHECK_LAUNCH();
+}
+
+template <class T>
+__global__ void k_finalize(const double* acc, T* s, int64_t n, double scale) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        s[i] = static_cast<T>(acc[i] * scale);
+}
+
+template <class T>
+void launch_finalize(const double* acc, T* s, int64_t n, double scale, cudaStream_t st) {
+    if (n <= 0) return;
+    int64_t blocks = ceil_div(n, 256);
+    {
+        SLK_TIMED("finalize", st);
+        k_finalize<T><<<static_cast<unsigned>(blocks < 8192 ? blocks : 8192), 256, 0, st>>>(acc, s, n, scale);
+    }
+    SLK_CHECK_LAUNCH();
+}
+
+template <class T>
+__global__ void k_range_check(const T* Z, int64_t n, int64_t ldz, double R, unsigned* err) {
+    const T* row = Z + static_cast<int64_t>(blockIdx.y) * ldz;
+    bool bad = false;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        double v = static_cast<double>(row[i]);
+        if (!(v <= R && v >= -R)) bad = true;  // also catches NaN
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, 4u);
+}
+
+template <class T>
+void launch_range_check(const T* Z, int P, int64_t n, int64_t ldz, double R, unsigned* err, cudaStream_t st) {
+    if (n <= 0 || P <= 0) return;
+    int64_t bx = ceil_div(n, 256);
+    dim3 grid(static_cast<unsigned>(bx < 64 ? bx : 64), P);
+    {
+        SLK_TIMED("range_check", st);
+        k_range_check<T><<<grid, 256, 0, st>>>(Z, n, ldz, R, err);
+    }
+    SLK_CHECK_LAUNCH();
+}
+
+template void launch_range_check<float>(const float*, int, int64_t, int64_t, double, unsigned*, cudaStream_t);
+template void launch_range_check<double>(const double*, int, int64_t, int64_t, double, unsigned*, cudaStream_t);
+template void launch_sample_mean<float>(const float*, int64_t, int, int64_t, double*, cudaStream_t);
+template void launch_sample_mean<double>(const double*, int64_t, int, int64_t, double*, cudaStream_t);
+template void launch_convert<float>(const double*, float*, int64_t, cudaStream_t);
+template void launch_convert<double>(const double*, double*, int64_t, cudaStream_t);
+template void launch_absmax<float>(const float*, int, int64_t, int64_t, float*, cudaStream_t);
+template void launch_absmax<double>(const double*, int, int64_t, int64_t, float*, cudaStream_t);
+template void launch_finalize<float>(const double*, float*, int64_t, double, cudaStream_t);
+template void launch_finalize<double>(const double*, double*, int64_t, double, cudaStream_t);
+
+}  // namespace slk

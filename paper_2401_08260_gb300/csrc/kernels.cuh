@@ -1,0 +1,106 @@
+// Launchers of the library's kernels (one declaration per kernel family).
+#pragma once
+
+#include "common.cuh"
+
+namespace slk {
+
+// ------------------------------------------------------------ k_util.cu
+// Draw P directions uniform on S^{d-1} (Algorithm 1, first step): Philox4x32-10
+// counter-based generator (Salmon et al. 2011), Box-Muller, row normalisation.
+void launch_draw_directions(double* xi, int P, int d, uint64_t seed, cudaStream_t st);
+// Row-normalise a P x d FP64 matrix in place.
+void launch_normalize_rows(double* xi, int P, int d, cudaStream_t st);
+// mu[k] = mean over up to 4096 evenly strided rows of x (the centre subtracted
+// before projecting; exact in exact arithmetic by translation invariance).
+template <class T>
+void launch_sample_mean(const T* x, int64_t N, int d, int64_t ldx, double* mu, cudaStream_t st);
+// dst[i] = (T) src[i].
+template <class T>
+void launch_convert(const double* src, T* dst, int64_t n, cudaStream_t st);
+// *out = max(*out, max |Z[p][i]|) over P rows of n entries (row stride ldz).
+template <class T>
+void launch_absmax(const T* Z, int P, int64_t n, int64_t ldz, float* out, cudaStream_t st);
+// s[i] = (T)(acc[i] * scale).
+template <class T>
+void launch_finalize(const double* acc, T* s, int64_t n, double scale, cudaStream_t st);
+// err |= 4 if any |Z[p][i]| > R (targets outside the certified window).
+template <class T>
+void launch_range_check(const T* Z, int P, int64_t n, int64_t ldz, double R, unsigned* err, cudaStream_t st);
+
+// ------------------------------------------------------------ k_project.cu
+// Z[p][i] = sum_k xi[p][k] (x[i][k] - mu[k]),  p < P, i < n  (SIMT, FP32 or FP64).
+template <class T>
+void launch_project_simt(const T* xi, int P, const T* x, int64_t n, int d, int64_t ldx, const T* mu, T* Z,
+                         int64_t ldz, cudaStream_t st);
+// gy[i][k] = scale * gs[i] * sum_p G[i][p] xi[p][k]   (gs may be NULL = ones).
+template <class T>
+void launch_grad_gemm(const T* G, int64_t M, int P, const T* xi, int d, const T* gs, double scale, T* gy,
+                      int64_t ldg, cudaStream_t st);
+
+// ------------------------------------------------------------ k_fourier.cu
+struct FourierDev {
+    // geometry of the periodic 1-D problem (Section 3.1 with the rescaling of
+    // the paragraph "Rescaling"): x~ = z / L, period 1 in x~
+    double L;
+    // NDFT: positive band [k_lo, k_hi] (+ k = 0 if has_k0), coefficients c_k
+    int k_lo, k_hi, has_k0;
+    // NFFT: grid n_g, window width m (cells), ES shape beta, active window
+    // [win_base, win_base + W) in grid cells
+    int n_g, m, W, win_base;
+    double beta;
+};
+
+// NDFT, source side: cw[p][j] = c_{k_lo+j} * sum_n w_n exp(-2 pi i k z_{p,n} / L),
+// j = 0..K-1 (and cw0[p] = c_0 sum_n w_n if has_k0).  coef holds c_k (FP64).
+template <class T>
+void launch_ndft_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, const FourierDev& fd,
+                        const double* coef, Cplx<T>* cw, T* cw0, T* scratch, int64_t scratch_elems, cudaStream_t st);
+// NDFT, target side: acc[m] += sum_p t_p(z_{p,m});  with G != NULL writes
+// G[m][p] = dt_p/dz instead (for the gradient).
+template <class T>
+void launch_ndft_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const Cplx<T>* cw,
+                        const T* cw0, double* acc, T* G, cudaStream_t st);
+// NFFT, source side: spread w onto the grid window of every slice (partial
+// sums per point chunk, then a fixed-order reduction), FFT, multiply by
+// mult[k] = c_k / Psi(k/n_g)^2 for |k| < n_coeff/2, inverse FFT; h is P x W.
+template <class T>
+void launch_nfft_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, const FourierDev& fd, int n_coeff,
+                        const double* mult, T* h, T* scratch, int64_t scratch_elems, unsigned* err, cudaStream_t st);
+// Scratch elements launch_nfft_source needs.
+int64_t nfft_source_scratch(int P, int64_t n, const FourierDev& fd);
+int64_t ndft_source_scratch(int P, int64_t n, const FourierDev& fd);
+// NFFT, target side: acc[m] += sum_p sum_j h[p][j] psi(n_g z/L - j); with
+// G != NULL writes the derivative dt_p/dz into G[m][p] instead.
+template <class T>
+void launch_nfft_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const T* h, double* acc,
+                        T* G, unsigned* err, cudaStream_t st);
+
+// ------------------------------------------------------------ k_sort.cu
+// Segmented LSD radix sort of P segments of n keys (row stride ldk) with an
+// int32 payload (the source index).  Output is P x n contiguous.
+template <class T>
+void launch_segmented_sort(const T* keys_in, int P, int64_t n, int64_t ldk, T* keys_out, int32_t* idx_out,
+                           void* scratch, size_t scratch_bytes, cudaStream_t st);
+template <class T>
+size_t segmented_sort_scratch(int P, int64_t n);
+// Exclusive FP64 prefix sums over each sorted segment:
+//   A[p][i] = sum_{j<i} w[idx[p][j]],  B[p][i] = sum_{j<i} w[idx[p][j]] * key[p][j],  i = 0..n
+template <class T>
+void launch_prefix_sums(const T* keys, const int32_t* idx, const T* w, int P, int64_t n, double* A, double* B,
+                        cudaStream_t st);
+// Bucket tables that narrow the binary searches: per slice, NB buckets over
+// [key_min, key_max]; tab[p][b] = first i with bucket(key[p][i]) >= b.
+template <class T>
+void launch_bucket_tables(const T* keys, int P, int64_t n, int NB, float* kmin, float* kscale, int32_t* tab,
+                          cudaStream_t st);
+// Negative-distance 1-D sums at the targets (Section 3.2 in the range-free
+// form t = -c_d [z (2 A_< - W) - (2 B_< - S)]) summed over slices into acc[m],
+// times `scale`; with G != NULL writes g = scale c_d (W - A_< - A_<=) into
+// G[m][p] instead (the derivative, sign(0) = 0).
+template <class T>
+void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const T* keys, int64_t nx, const double* A,
+                           const double* B, int NB, const float* kmin, const float* kscale, const int32_t* tab,
+                           double cd, double scale, double* acc, T* G, int accumulate_G, cudaStream_t st);
+
+}  // namespace slk

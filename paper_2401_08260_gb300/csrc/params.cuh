@@ -1,0 +1,30 @@
+// Plan-time Fourier parameters (host side).
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace slk {
+
+struct FourierHost {
+    int method = 0;          // SLK_FOURIER_NDFT or SLK_FOURIER_NFFT
+    double L = 0.0;          // period in projected units
+    double R = 0.0;          // certified window half-width
+    int n_coeff = 0;         // N_c: coefficients k with |k| < N_c / 2
+    int k_lo = 1, k_hi = 1;  // NDFT band (k > 0)
+    int has_k0 = 0;
+    std::vector<double> coef;  // NDFT: c_{k_lo..k_hi}, then c_0; Laplacian: c_0..c_{N_c/2-1}
+    int n_g = 0, m = 0, W = 0, win_base = 0;
+    double beta = 0.0;
+    std::vector<double> psi;   // Psi(k / n_g), k < N_c / 2
+    std::vector<double> mult;  // c_k / Psi(k / n_g)^2, k < N_c / 2
+    double period_err = 0.0, trunc_err = 0.0, window_err = 0.0, ndft_drop = 0.0, model_err = 0.0;
+};
+
+double cd_host(int d);
+FourierHost choose_gaussian(double sigma, int d, double R, int n_coeff_req, int method, double tol);
+// max_nc: largest N_c whose grid (2 N_c complex values) fits one block's shared memory
+FourierHost choose_laplace_smooth(double alpha, int d, double R, int n_coeff_req, double tol, int max_nc);
+
+}  // namespace slk

@@ -1,0 +1,316 @@
+"""Python binding of the C ABI in ``include/slk.h`` (argument marshalling only).
+
+Every computation runs in ``libslk.so``; this module converts tensors and
+arrays to pointers, passes torch's current CUDA stream and raises on a
+non-OK status.  It has no fallback: without the built library every call
+raises ``SlkError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+try:  # torch is used for device memory and streams only
+    import torch
+except ImportError:  # pragma: no cover
+    torch = None
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libslk.so")
+
+KERNELS = {"gaussian": 0, "laplacian": 1, "negdist": 2}
+PRECISIONS = {"f64": 0, "f32": 1, "bf16": 2, "f16x3": 3}
+METHODS = {"auto": 0, "nfft": 1, "ndft": 2}
+STATUS = {0: "SLK_OK", 1: "SLK_ERR_INVALID", 2: "SLK_ERR_OOM", 3: "SLK_ERR_CUDA", 4: "SLK_ERR_ACCURACY",
+          5: "SLK_ERR_TIMEOUT", 6: "SLK_ERR_BUSY", 7: "SLK_ERR_UNSUPPORTED", 8: "SLK_ERR_NOT_FOUND"}
+
+
+class SlkError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("precision", ctypes.c_int32), ("param", ctypes.c_double),
+                ("d", ctypes.c_int32), ("P", ctypes.c_int32), ("n_coeff", ctypes.c_int32),
+                ("method", ctypes.c_int32), ("seed", ctypes.c_uint64), ("directions", ctypes.c_void_p),
+                ("tol", ctypes.c_double), ("radius", ctypes.c_double), ("slice_batch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("precision", ctypes.c_int32), ("d", ctypes.c_int32),
+                ("P", ctypes.c_int32), ("N", ctypes.c_int64), ("method", ctypes.c_int32),
+                ("n_coeff", ctypes.c_int32), ("n_grid", ctypes.c_int32), ("window", ctypes.c_int32),
+                ("k_lo", ctypes.c_int32), ("k_hi", ctypes.c_int32), ("period", ctypes.c_double),
+                ("radius", ctypes.c_double), ("model_error", ctypes.c_double), ("c_d", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+_lib = None
+
+# exported names of include/slk.h with their ctypes signatures
+_SIGNATURES = {
+    "slk_version": (ctypes.c_int32, []),
+    "slk_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "slk_last_error": (ctypes.c_char_p, []),
+    "slk_plan_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(PlanDesc), ctypes.c_void_p,
+                                       ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
+    "slk_sum": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                               ctypes.c_void_p]),
+    "slk_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "slk_plan_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "slk_plan_get_directions": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "slk_plan_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]),
+    "slk_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "slk_fourier_params": (ctypes.c_int, [ctypes.POINTER(PlanDesc), ctypes.c_double, ctypes.POINTER(PlanInfo)]),
+    "slk_launch_count": (ctypes.c_int64, []),
+    "slk_timing_enable": (ctypes.c_int, [ctypes.c_int32]),
+    "slk_timing_read": (ctypes.c_int, [ctypes.POINTER(KernelTime), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "slk_timing_reset": (ctypes.c_int, []),
+    "slk_kernel_sum": (ctypes.c_int, [ctypes.POINTER(PlanDesc), ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                      ctypes.c_void_p, ctypes.c_void_p]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libslk.so (raises SlkError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise SlkError(3, f"{path} is missing: build it with paper_2401_08260_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(st: int):
+    if st != 0:
+        raise SlkError(st, load().slk_last_error().decode(errors="replace"))
+
+
+def _stream_of(t) -> Optional[int]:
+    if torch is not None and isinstance(t, torch.Tensor) and t.is_cuda:
+        return torch.cuda.current_stream(t.device).cuda_stream
+    return None
+
+
+def _dtype_for(precision: str):
+    return np.float64 if precision == "f64" else np.float32
+
+
+class _Arr:
+    """Pointer, leading dimension and keep-alive for a 2-D (or 1-D) argument."""
+
+    def __init__(self, a, dtype, ndim):
+        self.keep = a
+        if torch is not None and isinstance(a, torch.Tensor):
+            want = torch.float64 if dtype == np.float64 else torch.float32
+            if a.dtype != want:
+                raise TypeError(f"expected {want}, got {a.dtype}")
+            if ndim == 2:
+                if a.dim() != 2 or a.stride(1) != 1:
+                    a = a.contiguous()
+                self.ld = a.stride(0)
+            else:
+                a = a.contiguous()
+                self.ld = 1
+            self.keep = a
+            self.ptr = a.data_ptr()
+            self.rows = a.shape[0]
+        else:
+            a = np.asarray(a)
+            if a.dtype != dtype:
+                raise TypeError(f"expected {np.dtype(dtype)}, got {a.dtype}")
+            a = np.ascontiguousarray(a)
+            self.keep = a
+            self.ptr = a.ctypes.data
+            self.ld = a.shape[1] if ndim == 2 else 1
+            self.rows = a.shape[0]
+
+
+class Plan:
+    """A sliced kernel-summation plan over the sources x (N x d) with weights w.
+
+    kernel: "gaussian" (param = sigma), "laplacian" (param = alpha, F = exp(-alpha r))
+    or "negdist".  precision: "f64", "f32", "bf16" or "f16x3".  directions: optional
+    P x d unit directions (FP64); otherwise the library draws them from ``seed``."""
+
+    def __init__(self, x, w, kernel: str, param: float = 0.0, P: int = 256, precision: str = "f32",
+                 n_coeff: int = 0, method: str = "auto", seed: int = 0, directions=None, tol: float = 0.0,
+                 radius: float = 0.0):
+        lib = load()
+        self.precision = precision
+        self.dtype = _dtype_for(precision)
+        xa = _Arr(x, self.dtype, 2)
+        wa = _Arr(w, self.dtype, 1)
+        d = int(x.shape[1])
+        desc = PlanDesc()
+        desc.kernel = KERNELS[kernel]
+        desc.precision = PRECISIONS[precision]
+        desc.param = float(param)
+        desc.d = d
+        desc.P = int(P)
+        desc.n_coeff = int(n_coeff)
+        desc.method = METHODS[method]
+        desc.seed = int(seed)
+        self._dirs = None
+        if directions is not None:
+            if torch is not None and isinstance(directions, torch.Tensor):
+                self._dirs = directions.to(torch.float64).contiguous()
+                desc.directions = self._dirs.data_ptr()
+            else:
+                self._dirs = np.ascontiguousarray(np.asarray(directions, dtype=np.float64))
+                desc.directions = self._dirs.ctypes.data
+            if tuple(self._dirs.shape) != (P, d):
+                raise ValueError("directions must be P x d")
+        desc.tol = float(tol)
+        desc.radius = float(radius)
+        self.kernel, self.param, self.d, self.P = kernel, param, d, int(P)
+        self.N = int(x.shape[0])
+        self._desc = desc
+        self._stream = _stream_of(x)
+        h = ctypes.c_void_p()
+        _check(lib.slk_plan_create(ctypes.byref(h), ctypes.byref(desc), xa.ptr, xa.rows, xa.ld, wa.ptr,
+                                   self._stream))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def sum(self, y, out=None, sync: bool = True):
+        """s_m for every row of y.  Returns a tensor/array like y."""
+        lib = load()
+        ya = _Arr(y, self.dtype, 2)
+        if out is None:
+            if torch is not None and isinstance(y, torch.Tensor):
+                out = torch.empty(ya.rows, dtype=ya.keep.dtype, device=ya.keep.device)
+            else:
+                out = np.empty(ya.rows, dtype=self.dtype)
+        oa = _Arr(out, self.dtype, 1)
+        _check(lib.slk_sum(self._h, ya.ptr, ya.rows, ya.ld, oa.ptr, _stream_of(y)))
+        if sync:
+            _check(lib.slk_plan_sync(self._h))
+        return out
+
+    def grad(self, y, gs=None, out=None, sync: bool = True):
+        """Gradient of sum_m gs_m s_m with respect to y (M x d)."""
+        lib = load()
+        ya = _Arr(y, self.dtype, 2)
+        ga = _Arr(gs, self.dtype, 1) if gs is not None else None
+        if out is None:
+            if torch is not None and isinstance(y, torch.Tensor):
+                out = torch.empty(ya.rows, self.d, dtype=ya.keep.dtype, device=ya.keep.device)
+            else:
+                out = np.empty((ya.rows, self.d), dtype=self.dtype)
+        oa = _Arr(out, self.dtype, 2)
+        _check(lib.slk_grad(self._h, ya.ptr, ya.rows, ya.ld, ga.ptr if ga else None, oa.ptr, oa.ld, _stream_of(y)))
+        if sync:
+            _check(lib.slk_plan_sync(self._h))
+        return out
+
+    def sync(self):
+        _check(load().slk_plan_sync(self._h))
+
+    def directions(self) -> np.ndarray:
+        xi = np.empty((self.P, self.d), dtype=np.float64)
+        _check(load().slk_plan_get_directions(self._h, xi.ctypes.data))
+        return xi
+
+    def info(self) -> dict:
+        inf = PlanInfo()
+        _check(load().slk_plan_get_info(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in PlanInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().slk_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fourier_params(kernel: str, param: float, d: int, radius: float, precision: str = "f32", n_coeff: int = 0,
+                   method: str = "auto", tol: float = 0.0) -> dict:
+    """Host-only: the Fourier parameters a plan would choose for projected points in [-radius, radius]."""
+    desc = PlanDesc()
+    desc.kernel, desc.precision, desc.param, desc.d, desc.P = KERNELS[kernel], PRECISIONS[precision], param, d, 1
+    desc.n_coeff, desc.method, desc.tol = n_coeff, METHODS[method], tol
+    inf = PlanInfo()
+    _check(load().slk_fourier_params(ctypes.byref(desc), float(radius), ctypes.byref(inf)))
+    return {f: getattr(inf, f) for f, _ in PlanInfo._fields_}
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(load().slk_launch_count())
+
+
+def timing_enable(on: bool = True):
+    _check(load().slk_timing_enable(1 if on else 0))
+
+
+def timing_reset():
+    _check(load().slk_timing_reset())
+
+
+def timing_read() -> dict:
+    """{kernel name: (launches, total device ms)} for the launches recorded while enabled."""
+    lib = load()
+    cap = 128
+    buf = (KernelTime * cap)()
+    n = ctypes.c_int32()
+    _check(lib.slk_timing_read(buf, cap, ctypes.byref(n)))
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(n.value, cap))}
+
+
+def kernel_sum(x, w, y, kernel: str, param: float = 0.0, P: int = 256, precision: str = "f32", **kw):
+    """One-shot s = sum_n w_n F(|x_n - y_m|) via slicing (plan, sum, destroy)."""
+    plan = Plan(x, w, kernel, param, P, precision, **kw)
+    try:
+        return plan.sum(y)
+    finally:
+        plan.close()
+
+
+if torch is not None:
+
+    class SlicedKernelSum(torch.autograd.Function):
+        """s = sliced kernel sum at targets y; backward gives the y-gradient from the
+        library's derivative sums (sign(0) = 0) and the backward product."""
+
+        @staticmethod
+        def forward(ctx, y, plan: Plan):
+            ctx.plan = plan
+            ctx.save_for_backward(y)
+            return plan.sum(y.detach())
+
+        @staticmethod
+        def backward(ctx, grad_s):
+            (y,) = ctx.saved_tensors
+            gy = ctx.plan.grad(y.detach(), gs=grad_s.contiguous().to(y.dtype))
+            return gy, None
+
+    def sliced_kernel_sum(y, plan: Plan):
+        """Differentiable (in y) sliced kernel sum."""
+        return SlicedKernelSum.apply(y, plan)

@@ -1,0 +1,231 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs and the same directions, element by element, at sizes that
+span several tiles with ragged tails.  Tolerances (max-norm over sum|w|):
+1e-10 for the FP64 path, 1e-5 for FP32 paths."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_08260_gb300 import workloads
+from tests._util import cuda_or_skip, rel_inf, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _plan(x, w, kernel, param, xi, precision, **kw):
+    from paper_2401_08260_gb300.slk import Plan
+    return Plan(x, w, kernel, param, P=xi.shape[0], precision=precision, directions=xi, **kw)
+
+
+def _cube(N, M, d, P, seed=0):
+    rng = np.random.Generator(np.random.PCG64(100 + seed))
+    x = rng.random((N, d), dtype=np.float32)
+    y = rng.random((M, d), dtype=np.float32)
+    w = rng.random(N).astype(np.float32)
+    return x, y, w, workloads.directions(P, d, seed=200 + seed)
+
+
+def test_gauss_d16_fp64_ndft_full_config():
+    """Gaussian, sigma = 4, N = M = 1000, d = 16, P = 64, 64 coefficients, FP64 plain NDFT."""
+    dev = cuda_or_skip()
+    wl = workloads.make("gauss_d16")
+    plan = _plan(to_dev(wl.x, dev), to_dev(wl.w, dev), "gaussian", wl.param, wl.xi, "f64", n_coeff=64, method="ndft")
+    s = plan.sum(to_dev(wl.y, dev))
+    info = plan.info()
+    assert info["method"] == 2 and info["n_coeff"] == 64
+    ref, _ = oracle.sliced_sum("gaussian", wl.param, wl.x, wl.y, wl.w, wl.xi)
+    err = rel_inf(s, ref, np.abs(wl.w).sum())
+    assert err <= 1e-10, (err, info)
+    assert info["model_error"] <= 1e-10
+
+
+@pytest.mark.parametrize("method", ["ndft", "nfft"])
+@pytest.mark.parametrize("N,M,P", [(5003, 777, 64), (70001, 97, 40)])
+def test_gauss_d784_fp32(method, N, M, P):
+    dev = cuda_or_skip()
+    d = 784
+    x, y, w, xi = _cube(N, M, d, P)
+    sigma = math.sqrt(d)
+    plan = _plan(to_dev(x, dev), to_dev(w, dev), "gaussian", sigma, xi, "f32", n_coeff=256, method=method)
+    s = plan.sum(to_dev(y, dev))
+    info = plan.info()
+    assert info["method"] == {"nfft": 1, "ndft": 2}[method]
+    ref, _ = oracle.sliced_sum("gaussian", sigma, x, y, w, xi)
+    err = rel_inf(s, ref, np.abs(w).sum())
+    assert err <= 1e-5, (err, info)
+
+
+@pytest.mark.parametrize("method", ["ndft", "nfft"])
+def test_gauss_fp64_small_dims(method):
+    """FP64 NDFT and NFFT for d = 3 and d = 16 (d = 3 has a closed-form f)."""
+    dev = cuda_or_skip()
+    for d, sigma in [(3, 1.5), (16, 4.0)]:
+        rng = np.random.Generator(np.random.PCG64(7 + d))
+        x, y, w = rng.standard_normal((3001, d)), rng.standard_normal((501, d)), rng.random(3001)
+        xi = workloads.directions(33, d, seed=d)
+        plan = _plan(to_dev(x, dev), to_dev(w, dev), "gaussian", sigma, xi, "f64", method=method)
+        s = plan.sum(to_dev(y, dev))
+        ref, _ = oracle.sliced_sum("gaussian", sigma, x, y, w, xi)
+        err = rel_inf(s, ref, w.sum())
+        assert err <= 1e-9, (d, err, plan.info())
+
+
+def test_negdist_fp32():
+    dev = cuda_or_skip()
+    d, N, M, P = 256, 20011, 3001, 37
+    rng = np.random.Generator(np.random.PCG64(3))
+    x = rng.standard_normal((N, d), dtype=np.float32)
+    y = (rng.standard_normal((M, d), dtype=np.float32) + 0.5).astype(np.float32)
+    w = rng.random(N).astype(np.float32)
+    xi = workloads.directions(P, d, seed=5)
+    plan = _plan(to_dev(x, dev), to_dev(w, dev), "negdist", 0.0, xi, "f32")
+    s = plan.sum(to_dev(y, dev))
+    ref, _ = oracle.sliced_sum("negdist", 0.0, x, y, w, xi)
+    err = rel_inf(s, ref, w.sum())
+    assert err <= 1e-5, err
+
+
+def test_negdist_fp64_ties_and_duplicates():
+    """Duplicated sources and targets equal to sources (exact ties on every slice)."""
+    dev = cuda_or_skip()
+    d, P = 8, 19
+    rng = np.random.Generator(np.random.PCG64(4))
+    base = rng.integers(-3, 4, size=(300, d)).astype(np.float64)
+    x = np.concatenate([base, base[:100], base[:7]])
+    y = np.concatenate([base[:50], rng.integers(-3, 4, size=(31, d)).astype(np.float64)])
+    w = rng.random(x.shape[0])
+    xi = workloads.directions(P, d, seed=9)
+    plan = _plan(to_dev(x, dev), to_dev(w, dev), "negdist", 0.0, xi, "f64")
+    s = plan.sum(to_dev(y, dev))
+    ref, _ = oracle.sliced_sum("negdist", 0.0, x, y, w, xi)
+    assert rel_inf(s, ref, w.sum()) <= 1e-12
+
+
+def test_laplace_fp32_mixture():
+    dev = cuda_or_skip()
+    wl = workloads.make("laplace_d50", N=20011, M=1001, P=24)
+    plan = _plan(to_dev(wl.x, dev), to_dev(wl.w, dev), "laplacian", wl.param, wl.xi, "f32")
+    s = plan.sum(to_dev(wl.y, dev))
+    info = plan.info()
+    ref, _ = oracle.sliced_sum("laplacian", wl.param, wl.x, wl.y, wl.w, wl.xi)
+    err = rel_inf(s, ref, wl.w.sum())
+    assert err <= 1e-5, (err, info)
+
+
+def test_laplace_fp64():
+    dev = cuda_or_skip()
+    d = 5
+    rng = np.random.Generator(np.random.PCG64(8))
+    x, y, w = rng.standard_normal((4001, d)), rng.standard_normal((333, d)), rng.random(4001)
+    xi = workloads.directions(17, d, seed=3)
+    plan = _plan(to_dev(x, dev), to_dev(w, dev), "laplacian", 0.7, xi, "f64")
+    s = plan.sum(to_dev(y, dev))
+    ref, _ = oracle.sliced_sum("laplacian", 0.7, x, y, w, xi)
+    info = plan.info()
+    err = rel_inf(s, ref, w.sum())
+    assert err <= 1e-6 and err <= 4 * info["model_error"] + 1e-12, (err, info)
+
+
+@pytest.mark.parametrize("kernel,param,method", [("gaussian", None, "ndft"), ("gaussian", None, "nfft"),
+                                                 ("negdist", 0.0, "auto"), ("laplacian", None, "auto")])
+def test_gradient_fp32(kernel, param, method):
+    dev = cuda_or_skip()
+    d, N, M, P = 40, 6007, 129, 29
+    rng = np.random.Generator(np.random.PCG64(21))
+    x = rng.standard_normal((N, d), dtype=np.float32)
+    y = rng.standard_normal((M, d), dtype=np.float32)
+    w = rng.random(N).astype(np.float32)
+    gs = rng.standard_normal(M).astype(np.float32)
+    xi = workloads.directions(P, d, seed=22)
+    if param is None:
+        param = math.sqrt(d) if kernel == "gaussian" else 1.0 / math.sqrt(d)
+    plan = _plan(to_dev(x, dev), to_dev(w, dev), kernel, param, xi, "f32", method=method)
+    gy = plan.grad(to_dev(y, dev), gs=to_dev(gs, dev))
+    _, g_ref, _ = oracle.sliced_sum(kernel, param, x, y, w, xi, grad=True)
+    g_ref = g_ref * gs[:, None]
+    scale = w.sum() * (oracle.cd(d) if kernel == "negdist" else 1.0)
+    err = rel_inf(gy, g_ref, scale)
+    assert err <= 2e-5, err
+
+
+def test_gradient_fp64_gradcheck():
+    """torch.autograd.gradcheck on the FP64 path (finite differences of the CUDA sums)."""
+    dev = cuda_or_skip()
+    from paper_2401_08260_gb300.slk import Plan, sliced_kernel_sum
+    d = 3
+    rng = np.random.Generator(np.random.PCG64(2))
+    x = to_dev(rng.standard_normal((200, d)), dev)
+    w = to_dev(rng.random(200), dev)
+    xi = workloads.directions(11, d, seed=1)
+    for kernel, param in [("gaussian", 1.3), ("laplacian", 0.6), ("negdist", 0.0)]:
+        plan = Plan(x, w, kernel, param, P=11, precision="f64", directions=xi, radius=12.0)
+        y = to_dev(rng.standard_normal((6, d)), dev).requires_grad_(True)
+        assert torch.autograd.gradcheck(lambda yy: sliced_kernel_sum(yy, plan), (y,), eps=1e-6, atol=1e-6, rtol=1e-4)
+
+
+def test_host_and_device_pointers_agree():
+    dev = cuda_or_skip()
+    from paper_2401_08260_gb300.slk import Plan
+    x, y, w, xi = _cube(3000, 200, 20, 16, seed=3)
+    p_host = Plan(x, w, "gaussian", math.sqrt(20), P=16, precision="f32", directions=xi)
+    s_host = p_host.sum(y)                       # numpy in, numpy out (staged copies)
+    p_dev = Plan(to_dev(x, dev), to_dev(w, dev), "gaussian", math.sqrt(20), P=16, precision="f32", directions=xi)
+    s_dev = p_dev.sum(to_dev(y, dev)).cpu().numpy()
+    assert isinstance(s_host, np.ndarray)
+    np.testing.assert_array_equal(s_host, s_dev)
+
+
+def test_strided_rows_and_edge_sizes():
+    dev = cuda_or_skip()
+    from paper_2401_08260_gb300.slk import Plan
+    rng = np.random.Generator(np.random.PCG64(5))
+    big = rng.standard_normal((400, 12)).astype(np.float32)
+    x = torch.from_numpy(big).to(dev)[:, :9]           # row stride 12 > d = 9
+    w = to_dev(rng.random(400).astype(np.float32), dev)
+    y = torch.from_numpy(rng.standard_normal((50, 12)).astype(np.float32)).to(dev)[:, :9]
+    xi = workloads.directions(5, 9, seed=4)
+    for kernel, param in [("gaussian", 3.0), ("negdist", 0.0), ("laplacian", 0.3)]:
+        plan = Plan(x, w, kernel, param, P=5, precision="f32", directions=xi)
+        s = plan.sum(y)
+        ref, _ = oracle.sliced_sum(kernel, param, big[:, :9], y.cpu().numpy(), w.cpu().numpy(), xi)
+        assert rel_inf(s, ref, float(w.sum())) <= 1e-5, kernel
+        assert plan.sum(y[:0]).numel() == 0                 # M = 0
+    # N = 1, P = 1, d = 1
+    x1 = to_dev(np.array([[0.25]], dtype=np.float64), dev)
+    w1 = to_dev(np.array([2.0]), dev)
+    y1 = to_dev(np.array([[0.0], [1.0], [-3.0]]), dev)
+    for kernel, param in [("gaussian", 1.0), ("negdist", 0.0), ("laplacian", 0.5)]:
+        plan = Plan(x1, w1, kernel, param, P=1, precision="f64", directions=np.ones((1, 1)), radius=4.0)
+        s = plan.sum(y1).cpu().numpy()
+        r = np.abs(np.array([0.0, 1.0, -3.0]) - 0.25)
+        F = {"gaussian": np.exp(-r ** 2 / 2), "negdist": -r, "laplacian": np.exp(-0.5 * r)}[kernel]
+        np.testing.assert_allclose(s, 2.0 * F, rtol=1e-9, atol=1e-9)
+
+
+def test_target_outside_certified_window_is_reported():
+    dev = cuda_or_skip()
+    from paper_2401_08260_gb300.slk import Plan, SlkError
+    x, y, w, xi = _cube(1000, 10, 8, 4)
+    plan = Plan(to_dev(x, dev), to_dev(w, dev), "gaussian", 2.0, P=4, precision="f32", directions=xi)
+    far = to_dev(y + 100.0, dev)
+    with pytest.raises(SlkError) as e:
+        plan.sum(far)
+    assert e.value.status == 4
+    plan.sum(to_dev(y, dev))  # the plan stays usable
+
+
+def test_library_directions_are_unit_and_isotropic():
+    dev = cuda_or_skip()
+    from paper_2401_08260_gb300.slk import Plan
+    d, P = 16, 4096
+    x = to_dev(np.zeros((4, d), dtype=np.float32), dev)
+    plan = Plan(x, to_dev(np.ones(4, dtype=np.float32), dev), "negdist", 0.0, P=P, precision="f32", seed=123)
+    xi = plan.directions()
+    np.testing.assert_allclose(np.linalg.norm(xi, axis=1), 1.0, atol=1e-14)
+    assert np.abs(xi.mean(axis=0)).max() < 4.5 / math.sqrt(P * d)
+    cov = xi.T @ xi / P
+    assert np.abs(cov - np.eye(d) / d).max() < 6.0 / (d * math.sqrt(P))
+    xi2 = Plan(x, to_dev(np.ones(4, dtype=np.float32), dev), "negdist", 0.0, P=P, precision="f32", seed=123).directions()
+    np.testing.assert_array_equal(xi, xi2)  # counter-based: same seed, same directions
