@@ -1,0 +1,346 @@
+"""Benchmark of the sliced fast kernel summation on GB300.
+
+One step = one pass of the whole path over one batch: directions, centring,
+projection of sources and targets, the 1-D fast summation on every slice
+(source side then target side) and the slice average, i.e. a plan build plus a
+sum through the C ABI.  Default workload: Gaussian kernel, sigma = sqrt(d),
+N = M = 1e6 sources and targets in d = 784 (x, y ~ U[0,1]^784, FP32), w = 1/N,
+P = 512 directions, 256 Fourier coefficients.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+(exact 1-D sums on the same directions) on a bounded sample of the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "(N+M)*P slice-points/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(args):
+    from paper_2401_08260_gb300 import workloads
+    kw = {}
+    if args.N:
+        kw["N"] = args.N
+    if args.M:
+        kw["M"] = args.M
+    if args.P:
+        kw["P"] = args.P
+    return workloads.make(args.workload, **kw)
+
+
+def plan_kwargs(wl, args):
+    return dict(kernel=wl.kernel, param=wl.param, P=wl.P, precision=args.precision or wl.precision,
+                n_coeff=wl.n_coeff, method=args.method or wl.method, directions=wl.xi)
+
+
+def algorithmic(wl, precision, kernel_name, launches_per_step):
+    """(amount per launch, unit, bound) of the algorithmic work of one launch."""
+    pts_per_launch = (wl.N + wl.M) / max(1, launches_per_step)
+    if kernel_name.startswith("gemm") or kernel_name.startswith("umma") or kernel_name.startswith("project"):
+        flops = 2.0 * pts_per_launch * wl.d * wl.P
+        bound = "tensor" if precision in ("bf16", "f16x3") else "alu"
+        return flops, "flop", bound
+    # 1-D summation kernels: bytes of the projected slice-points they read (4 B each)
+    return 4.0 * pts_per_launch * wl.P, "byte", "hbm"
+
+
+def cpu_sample(wl, budget_s: float):
+    """Time the oracle's sliced sum on a bounded sample: k targets against all N
+    sources and all P slices.  Returns (slice-points/s extrapolated, seconds, sample text)."""
+    import oracle
+    oracle.build()
+    idx = oracle.sampled_targets(wl.M, 1)
+    t0 = time.perf_counter()
+    oracle.sliced_sum(wl.kernel, wl.param, wl.x, wl.y[idx[:1]], wl.w, wl.xi)
+    t1 = time.perf_counter() - t0
+    k = max(1, min(wl.M, int(budget_s / max(t1, 1e-3))))
+    if k > 1:
+        idx = oracle.sampled_targets(wl.M, k)
+        t0 = time.perf_counter()
+        oracle.sliced_sum(wl.kernel, wl.param, wl.x, wl.y[idx], wl.w, wl.xi)
+        t1 = time.perf_counter() - t0
+        k = len(idx)
+    full = t1 * wl.M / k
+    rate = (wl.N + wl.M) * wl.P / full
+    sample = (f"{k} target(s) x all {wl.N} sources x {wl.P} slices (FP64 exact 1-D sums, projections by numpy); "
+              f"{t1:.2f} s measured, full job extrapolated to {full:.3g} s")
+    return rate, t1, sample
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = make_inputs(args)
+    steps, warm = args.steps, args.warmup
+    budget = max(2.0, 150.0 / (steps + warm))
+    rates = []
+    sample = ""
+    for i in range(warm + steps):
+        r, _, sample = cpu_sample(wl, budget)
+        if i >= warm:
+            rates.append(r)
+    value = statistics.median(rates)
+    cores = len(os.sched_getaffinity(0))
+    step_ms = (wl.N + wl.M) * wl.P / value * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "slice-points/s", "n_gpus": args.gpus,
+            "steps": steps, "warmup": warm, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "N": wl.N, "M": wl.M, "d": wl.d, "P": wl.P},
+            "cpu_baseline": {"value": value, "unit": "slice-points/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "slice-points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2401_08260_gb300 import slk
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2401_08260_gb300 import build
+    build.build()
+    slk.load()
+
+    wl = make_inputs(args)
+    kw = plan_kwargs(wl, args)
+    precision = kw["precision"]
+    x = torch.from_numpy(wl.x).to(dev)
+    y = torch.from_numpy(wl.y).to(dev)
+    w = torch.from_numpy(wl.w).to(dev)
+    s = torch.empty(wl.M, dtype=x.dtype, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan = slk.Plan(x, w, **kw)
+        plan.sum(y, out=s, sync=False)
+        plan.close()
+
+    for _ in range(args.warmup):
+        step()
+    plan = slk.Plan(x, w, **kw)
+    info = plan.info()
+    plan.close()
+    torch.cuda.synchronize()
+
+    # ---------------- device-resident timed region
+    sampler = ClockSampler(local)
+    sampler.start()
+    slk.timing_reset()
+    slk.timing_enable(True)
+    n0 = slk.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    launches = slk.launch_count() - n0
+    slk.timing_enable(False)
+    clocks = sampler.stop()
+    kernels = slk.timing_read()
+    slk.timing_reset()
+    dev_ms = ev0.elapsed_time(ev1)
+    # wall time includes the host work of plan creation (parameter selection is cached)
+    ms = max(dev_ms, t_wall * 1e3) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = (wl.N + wl.M) * wl.P * world / (ms * 1e-3)
+
+    # ---------------- dominant kernel roofline
+    peaks, peak_kind = _peaks()
+    top = max(kernels.items(), key=lambda kv: kv[1][1]) if kernels else None
+    roofline = None
+    if top:
+        name, (n_launch, tot_ms) = top
+        per_step = n_launch / args.steps
+        amount, unit, bound = algorithmic(wl, precision, name, per_step)
+        avg_s = tot_ms / n_launch * 1e-3
+        if bound == "tensor":
+            peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * (1.0 if precision == "bf16" else 1.0)
+            achieved = amount / avg_s / 1e12
+            runit = "TFLOP/s"
+        elif bound == "alu":
+            sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+            peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
+            achieved = amount / avg_s / 1e12
+            runit = "TFLOP/s"
+        else:
+            peak = peaks["hbm_gbs"]
+            achieved = amount / avg_s / 1e9
+            runit = "GB/s"
+        roofline = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": runit,
+                    "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                    "launch_ms": tot_ms / n_launch,
+                    "share": tot_ms / sum(v[1] for v in kernels.values())}
+
+    # ---------------- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(wl.x).pin_memory()
+        yh = torch.from_numpy(wl.y).pin_memory()
+        wh = torch.from_numpy(wl.w).pin_memory()
+        sh = torch.empty(wl.M, dtype=xh.dtype).pin_memory()
+        e2e_steps = max(1, min(args.steps, 5))
+
+        def host_step():
+            plan = slk.Plan(xh, wh, **kw)
+            plan.sum(yh, out=sh, sync=True)
+            plan.close()
+
+        host_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            host_step()
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / e2e_steps
+        bi = xh.numel() * xh.element_size() + yh.numel() * yh.element_size() + wh.numel() * wh.element_size() + \
+            wl.xi.size * 8
+        bo = sh.numel() * sh.element_size()
+        e2e = {"value": (wl.N + wl.M) * wl.P * world / te, "unit": "slice-points/s", "h2d_bytes_per_step": int(bi),
+               "d2h_bytes_per_step": int(bo), "ms_per_step": te * 1e3}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu and world == 1:
+        r, secs, sample = cpu_sample(wl, args.cpu_budget)
+        cpu = {"value": r, "unit": "slice-points/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+               "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "slice-points/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": precision, "data": "synthetic",
+                "config": {"workload": args.workload, "kernel": wl.kernel, "N": wl.N, "M": wl.M, "d": wl.d,
+                           "P": wl.P, "n_coeff": info["n_coeff"], "method": {1: "nfft", 2: "ndft"}.get(info["method"]),
+                           "parallelism": f"replicas{world}" if world > 1 else "single",
+                           "l2": "inputs larger than L2 (no flush needed)",
+                           "model_error": info["model_error"]},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+                "kernels_ms_per_step": {k: v[1] / args.steps for k, v in kernels.items()}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="gauss_d784")
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--method", default=None)
+    ap.add_argument("--N", type=int, default=None)
+    ap.add_argument("--M", type=int, default=None)
+    ap.add_argument("--P", type=int, default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

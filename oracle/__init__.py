@@ -228,9 +228,12 @@ def negdist_alg2(zx, w, zy, cdv: float) -> np.ndarray:
 
 
 def sampled_targets(M: int, count: int, seed: int = 5) -> np.ndarray:
-    """Seeded subsample of target indices (always includes the first and last)."""
+    """Seeded subsample of `count` target indices (sorted; includes the last index
+    when count >= 2, to cover the ragged tail)."""
     if count >= M:
         return np.arange(M)
     rng = np.random.Generator(np.random.PCG64(seed))
-    idx = rng.choice(M, size=count - 2, replace=False)
-    return np.unique(np.concatenate([[0, M - 1], idx]))
+    if count < 2:
+        return np.sort(rng.choice(M, size=count, replace=False))
+    idx = rng.choice(M - 1, size=count - 1, replace=False)
+    return np.sort(np.concatenate([idx, [M - 1]]))

@@ -85,6 +85,9 @@ struct slk_plan_s {
     DevBuf<float> xi32;   // P x d (FP32 storage paths)
     DevBuf<double> mu64;  // d
     DevBuf<float> mu32;   // d
+    // tensor-core projection (BF16, or FP16 hi/lo split): 16-bit directions P x ldo
+    int tc = 0;  // 0 SIMT, 1 BF16, 2 FP16 x3
+    DevBuf<unsigned char> xib, xib_lo;
 
     // Fourier side (Gaussian, Laplacian smooth part)
     bool fourier = false;
@@ -118,7 +121,8 @@ struct slk_plan_s {
         if (err_host) cudaFreeHost(err_host);
     }
     int64_t device_bytes() const {
-        return static_cast<int64_t>(xi64.bytes() + xi32.bytes() + mu64.bytes() + mu32.bytes() + coef.bytes() +
+        return static_cast<int64_t>(xi64.bytes() + xi32.bytes() + mu64.bytes() + mu32.bytes() + xib.bytes() +
+                                    xib_lo.bytes() + coef.bytes() +
                                     mult.bytes() + cw.bytes() + cw0.bytes() + hgrid.bytes() + keys.bytes() + A.bytes() +
                                     B.bytes() + kmin.bytes() + kscale.bytes() + tab.bytes());
     }
@@ -177,6 +181,10 @@ slk_status collect(slk_plan plan, bool wait) {
         set_last_error("a projected point fell outside the NFFT grid window");
         return SLK_ERR_ACCURACY;
     }
+    if (e & 56u) {
+        set_last_error("a bounded wait in the tensor-core projection ran out");
+        return SLK_ERR_TIMEOUT;
+    }
     return SLK_OK;
 }
 
@@ -219,10 +227,23 @@ const T* mu_of(slk_plan plan) {
     else return plan->mu32.get();
 }
 
-// Z (P x n, ldz = n) = projections of n points onto the plan's directions, centred.
+// Z (P x n, ldz = n) = projections of n points onto the plan's directions, centred;
+// *absmax = max |Z| when absmax != NULL.
 template <class T>
-void project(slk_plan plan, const T* x, int64_t n, int64_t ldx, T* Z, cudaStream_t st) {
+void project(slk_plan plan, const T* x, int64_t n, int64_t ldx, T* Z, float* absmax, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (plan->tc) {
+            const int split = plan->tc == 2;
+            const size_t bytes = static_cast<size_t>(n) * umma_operand_ld(plan->d) * 2;
+            DevBuf<unsigned char> xa(bytes, st), xl(split ? bytes : 0, st);
+            launch_center_cast(x, n, plan->d, ldx, plan->mu32.get(), xa.get(), xl.get(), split, st);
+            launch_project_umma(xa.get(), xl.get(), n, plan->xib.get(), plan->xib_lo.get(), plan->P, plan->d, split, Z,
+                                n, absmax, plan->err_dev.get(), st);
+            return;
+        }
+    }
     launch_project_simt<T>(xi_of<T>(plan), plan->P, x, n, plan->d, ldx, mu_of<T>(plan), Z, n, st);
+    if (absmax) launch_absmax<T>(Z, plan->P, n, n, absmax, st);
 }
 
 template <class T>
@@ -240,6 +261,7 @@ void plan_fourier_source(slk_plan plan, const T* Zx, const T* w, cudaStream_t st
     fd.W = fh.W;
     fd.win_base = fh.win_base;
     fd.beta = fh.beta;
+    fd.R = plan->R;
     if (fh.method == SLK_FOURIER_NDFT) {
         const int K = fh.k_hi - fh.k_lo + 1;
         plan->coef.alloc(fh.coef.size(), st);
@@ -312,16 +334,23 @@ void create_impl(slk_plan plan, const void* x_user, int64_t ldx, const void* w_u
         launch_convert<float>(plan->xi64.get(), plan->xi32.get(), static_cast<int64_t>(P) * d, st);
         plan->mu32.alloc(d, st);
         launch_convert<float>(plan->mu64.get(), plan->mu32.get(), d, st);
+        if (plan->desc.precision == SLK_PREC_BF16 || plan->desc.precision == SLK_PREC_F16X3) {
+            plan->tc = plan->desc.precision == SLK_PREC_BF16 ? 1 : 2;
+            const size_t bytes = static_cast<size_t>(P) * umma_operand_ld(d) * 2;
+            plan->xib.alloc(bytes, st);
+            if (plan->tc == 2) plan->xib_lo.alloc(bytes, st);
+            launch_center_cast(plan->xi32.get(), P, d, d, nullptr, plan->xib.get(), plan->xib_lo.get(), plan->tc == 2,
+                               st);
+        }
     }
-    // project the sources
-    DevBuf<T> Zx(static_cast<size_t>(P) * N, st);
-    project<T>(plan, xv.ptr, N, xv.ld, Zx.get(), st);
+    // project the sources (and find the largest |z| for the Fourier window)
     const int kernel = plan->desc.kernel;
     const bool need_fourier = kernel == SLK_GAUSSIAN || kernel == SLK_LAPLACIAN;
+    DevBuf<T> Zx(static_cast<size_t>(P) * N, st);
+    DevBuf<float> mx(1, st);
+    SLK_CHECK_CUDA(cudaMemsetAsync(mx.get(), 0, sizeof(float), st));
+    project<T>(plan, xv.ptr, N, xv.ld, Zx.get(), need_fourier ? mx.get() : nullptr, st);
     if (need_fourier) {
-        DevBuf<float> mx(1, st);
-        SLK_CHECK_CUDA(cudaMemsetAsync(mx.get(), 0, sizeof(float), st));
-        launch_absmax<T>(Zx.get(), P, N, N, mx.get(), st);
         float rx = 0.0f;
         SLK_CHECK_CUDA(cudaMemcpyAsync(&rx, mx.get(), sizeof(float), cudaMemcpyDeviceToHost, st));
         SLK_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -348,14 +377,14 @@ void sum_impl(slk_plan plan, const void* y_user, int64_t M, int64_t ldy, void* s
     const int P = plan->P, d = plan->d;
     InView<T> yv(y_user, M, d, ldy, st);
     DevBuf<T> Zy(static_cast<size_t>(P) * M, st);
-    project<T>(plan, yv.ptr, M, yv.ld, Zy.get(), st);
+    project<T>(plan, yv.ptr, M, yv.ld, Zy.get(), nullptr, st);
     DevBuf<double> acc(M, st);
     SLK_CHECK_CUDA(cudaMemsetAsync(acc.get(), 0, sizeof(double) * M, st));
     if (plan->fourier) {
-        launch_range_check<T>(Zy.get(), P, M, M, plan->R, plan->err_dev.get(), st);
         if (plan->fh.method == SLK_FOURIER_NDFT)
             launch_ndft_target<T>(Zy.get(), P, M, M, plan->fd, reinterpret_cast<const Cplx<T>*>(plan->cw.get()),
-                                  reinterpret_cast<const T*>(plan->cw0.get()), acc.get(), nullptr, st);
+                                  reinterpret_cast<const T*>(plan->cw0.get()), acc.get(), nullptr, plan->err_dev.get(),
+                                  st);
         else
             launch_nfft_target<T>(Zy.get(), P, M, M, plan->fd, reinterpret_cast<const T*>(plan->hgrid.get()), acc.get(),
                                   nullptr, plan->err_dev.get(), st);
@@ -381,13 +410,13 @@ void grad_impl(slk_plan plan, const void* y_user, int64_t M, int64_t ldy, const 
     const int P = plan->P, d = plan->d;
     InView<T> yv(y_user, M, d, ldy, st);
     DevBuf<T> Zy(static_cast<size_t>(P) * M, st);
-    project<T>(plan, yv.ptr, M, yv.ld, Zy.get(), st);
+    project<T>(plan, yv.ptr, M, yv.ld, Zy.get(), nullptr, st);
     DevBuf<T> G(static_cast<size_t>(M) * P, st);
     if (plan->fourier) {
-        launch_range_check<T>(Zy.get(), P, M, M, plan->R, plan->err_dev.get(), st);
         if (plan->fh.method == SLK_FOURIER_NDFT)
             launch_ndft_target<T>(Zy.get(), P, M, M, plan->fd, reinterpret_cast<const Cplx<T>*>(plan->cw.get()),
-                                  reinterpret_cast<const T*>(plan->cw0.get()), nullptr, G.get(), st);
+                                  reinterpret_cast<const T*>(plan->cw0.get()), nullptr, G.get(), plan->err_dev.get(),
+                                  st);
         else
             launch_nfft_target<T>(Zy.get(), P, M, M, plan->fd, reinterpret_cast<const T*>(plan->hgrid.get()), nullptr,
                                   G.get(), plan->err_dev.get(), st);
@@ -423,8 +452,6 @@ void validate_desc(const slk_plan_desc* desc) {
     if (desc->kernel != SLK_NEGDIST)
         SLK_REQUIRE(desc->param > 0.0 && std::isfinite(desc->param), "kernel parameter must be positive");
     SLK_REQUIRE(desc->tol >= 0.0 && desc->radius >= 0.0, "tol and radius must be >= 0");
-    if (desc->precision == SLK_PREC_BF16 || desc->precision == SLK_PREC_F16X3)
-        fail(SLK_ERR_UNSUPPORTED, "tensor-core projection precisions are not built in this library");
 }
 
 }  // namespace

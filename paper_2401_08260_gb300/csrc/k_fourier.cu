@@ -169,14 +169,16 @@ __global__ void k_ndft_reduce(const T* __restrict__ partial, int nchunk, int P, 
 template <class T>
 __global__ void __launch_bounds__(256) k_ndft_target(const T* __restrict__ Z, int P, int64_t n, int64_t ldz, T inv_L,
                                                      int k_lo, int K, const Cplx<T>* __restrict__ cw,
-                                                     const T* __restrict__ cw0, int slice_chunk,
-                                                     double* __restrict__ acc, T* __restrict__ G) {
+                                                     const T* __restrict__ cw0, int slice_chunk, T R,
+                                                     double* __restrict__ acc, T* __restrict__ G,
+                                                     unsigned* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     Cplx<T>* scw = reinterpret_cast<Cplx<T>*>(smem_raw);
     T* scw0 = reinterpret_cast<T*>(scw + static_cast<size_t>(slice_chunk) * K);
     const int64_t m = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const T two_pi = T(6.283185307179586476925286766559);
     typename Acc<T>::type sum;
+    bool bad = false;
     for (int p0 = 0; p0 < P; p0 += slice_chunk) {
         const int pc = (P - p0 < slice_chunk) ? P - p0 : slice_chunk;
         __syncthreads();
@@ -186,7 +188,9 @@ __global__ void __launch_bounds__(256) k_ndft_target(const T* __restrict__ Z, in
         if (m >= n) continue;
         for (int q = 0; q < pc; ++q) {
             const int p = p0 + q;
-            const T th = two_pi * (Z[static_cast<int64_t>(p) * ldz + m] * inv_L);
+            const T z = Z[static_cast<int64_t>(p) * ldz + m];
+            if (!(z <= R && z >= -R)) bad = true;  // outside the certified window (or NaN)
+            const T th = two_pi * (z * inv_L);
             T s, c, s1, c1;
             sincos_t(T(k_lo) * th, &s, &c);
             sincos_t(th, &s1, &c1);
@@ -211,6 +215,7 @@ __global__ void __launch_bounds__(256) k_ndft_target(const T* __restrict__ Z, in
             }
         }
     }
+    if (bad) atomicOr(err, 4u);
     if (!G && m < n) acc[m] += sum.value();
 }
 
@@ -377,8 +382,9 @@ __global__ void __launch_bounds__(512) k_fft_multiply(const T* __restrict__ g, i
 template <class T>
 __global__ void __launch_bounds__(256) k_nfft_target(const T* __restrict__ Z, int P, int64_t n, int64_t ldz, T scale_u,
                                                      int m, T two_over_m, T beta, int W, int win_base,
-                                                     const T* __restrict__ h, int slice_chunk, double* __restrict__ acc,
-                                                     T* __restrict__ G, unsigned* __restrict__ err) {
+                                                     const T* __restrict__ h, int slice_chunk, T R,
+                                                     double* __restrict__ acc, T* __restrict__ G,
+                                                     unsigned* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     T* sh = reinterpret_cast<T*>(smem_raw);
     const int64_t mi = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -393,7 +399,9 @@ __global__ void __launch_bounds__(256) k_nfft_target(const T* __restrict__ Z, in
         if (mi >= n) continue;
         for (int q = 0; q < pc; ++q) {
             const int p = p0 + q;
-            const T u = Z[static_cast<int64_t>(p) * ldz + mi] * scale_u;
+            const T z = Z[static_cast<int64_t>(p) * ldz + mi];
+            if (!(z <= R && z >= -R)) bad = true;  // outside the certified window (or NaN)
+            const T u = z * scale_u;
             const T c0 = ceil(u - half_m);
             const int r0 = static_cast<int>(c0) - win_base;
             if (r0 < 0 || r0 + m > W) {
@@ -412,7 +420,7 @@ __global__ void __launch_bounds__(256) k_nfft_target(const T* __restrict__ Z, in
             }
         }
     }
-    if (bad) atomicOr(err, 2u);
+    if (bad) atomicOr(err, 4u);
     if (!G && mi < n) acc[mi] += sum.value();
 }
 
@@ -449,7 +457,7 @@ void launch_ndft_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, c
 
 template <class T>
 void launch_ndft_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const Cplx<T>* cw,
-                        const T* cw0, double* acc, T* G, cudaStream_t st) {
+                        const T* cw0, double* acc, T* G, unsigned* err, cudaStream_t st) {
     if (n <= 0) return;
     const int K = fd.k_hi - fd.k_lo + 1;
     const size_t per_slice = sizeof(Cplx<T>) * K + sizeof(T);
@@ -465,7 +473,7 @@ void launch_ndft_target(const T* Z, int P, int64_t n, int64_t ldz, const Fourier
     {
         SLK_TIMED("ndft_target", st);
         k_ndft_target<T><<<static_cast<unsigned>(ceil_div(n, 256)), 256, smem, st>>>(
-            Z, P, n, ldz, static_cast<T>(1.0 / fd.L), fd.k_lo, K, cw, cw0, chunk, acc, G);
+            Z, P, n, ldz, static_cast<T>(1.0 / fd.L), fd.k_lo, K, cw, cw0, chunk, static_cast<T>(fd.R), acc, G, err);
     }
     SLK_CHECK_LAUNCH();
 }
@@ -565,7 +573,7 @@ void launch_nfft_target(const T* Z, int P, int64_t n, int64_t ldz, const Fourier
         SLK_TIMED("nfft_target", st);
         k_nfft_target<T><<<static_cast<unsigned>(ceil_div(n, 256)), 256, smem, st>>>(
             Z, P, n, ldz, static_cast<T>(fd.n_g / fd.L), fd.m, static_cast<T>(2.0 / fd.m), static_cast<T>(fd.beta), fd.W,
-            fd.win_base, h, chunk, acc, G, err);
+            fd.win_base, h, chunk, static_cast<T>(fd.R), acc, G, err);
     }
     SLK_CHECK_LAUNCH();
 }
@@ -575,9 +583,10 @@ template void launch_ndft_source<float>(const float*, int, int64_t, int64_t, con
 template void launch_ndft_source<double>(const double*, int, int64_t, int64_t, const double*, const FourierDev&,
                                          const double*, Cplx<double>*, double*, double*, int64_t, cudaStream_t);
 template void launch_ndft_target<float>(const float*, int, int64_t, int64_t, const FourierDev&, const Cplx<float>*,
-                                        const float*, double*, float*, cudaStream_t);
+                                        const float*, double*, float*, unsigned*, cudaStream_t);
 template void launch_ndft_target<double>(const double*, int, int64_t, int64_t, const FourierDev&,
-                                         const Cplx<double>*, const double*, double*, double*, cudaStream_t);
+                                         const Cplx<double>*, const double*, double*, double*, unsigned*,
+                                         cudaStream_t);
 template void launch_nfft_source<float>(const float*, int, int64_t, int64_t, const float*, const FourierDev&, int,
                                         const double*, float*, float*, int64_t, unsigned*, cudaStream_t);
 template void launch_nfft_source<double>(const double*, int, int64_t, int64_t, const double*, const FourierDev&, int,

@@ -1,0 +1,373 @@
+// Tensor-core projection Z = Xi (X - mu)^T on sm_103a (tcgen05 + TMA).
+//
+// The projection of Algorithm 1 is the one dense contraction of the path:
+// Z[p][i] = sum_k xi[p][k] (x[i][k] - mu[k]) for P directions and n points.
+// Per CTA: a 128-point x 256-slice output tile.  A (points, K-major) and B
+// (directions, K-major) tiles of 64 K-elements are brought in by TMA with the
+// 128-byte swizzle into a 4-stage shared-memory ring; one thread issues
+// tcgen05.mma (kind::f16, BF16 or FP16 inputs, FP32 accumulate) into a
+// 128 x 256 FP32 accumulator in tensor memory; four epilogue warps read it back
+// with tcgen05.ld and store Z slice-major (coalesced along points), keeping
+// the largest |z| on the way.
+//
+// The FP16 "x3" variant splits both operands into a high and a scaled low
+// FP16 part (a = a_hi + 2^-11 a_lo') and accumulates a_hi b_hi in one TMEM
+// accumulator and a_hi b_lo' + a_lo' b_hi in a second; the epilogue forms
+// D1 + 2^-11 D2 (error ~ 2^-22 relative per product, about FP32).
+//
+// Every mbarrier wait is bounded: on timeout the kernel records an error bit,
+// skips the remaining work, still frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <type_traits>
+
+#include "kernels.cuh"
+
+namespace slk {
+
+namespace {
+
+constexpr int BM = 128;       // points per tile (TMEM lanes)
+constexpr int BN = 256;       // slices per tile (TMEM columns per accumulator)
+constexpr int BK = 64;        // K elements per stage (128 bytes of 16-bit data)
+constexpr int STAGES_1 = 4;  // one 16-bit product: 48 KB per stage
+constexpr int STAGES_3 = 2;  // hi/lo split: 96 KB per stage
+template <int SPLIT> struct Stages { static constexpr int value = SPLIT ? STAGES_3 : STAGES_1; };
+constexpr int THREADS = 256;  // warp 0: TMA, warp 1: MMA, warp 2: TMEM alloc, warps 4-7: epilogue
+constexpr unsigned WAIT_LIMIT = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// bounded wait for the phase with the given parity; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t addr = smem_u32(bar);
+    for (unsigned it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+    const uint64_t addr = smem_u32(p);
+    uint64_t d = (addr >> 4) & 0x3FFFull;  // start address
+    d |= static_cast<uint64_t>(1) << 16;     // leading byte offset (unused with the 128B swizzle)
+    d |= static_cast<uint64_t>(1024 >> 4) << 32;  // stride byte offset
+    d |= static_cast<uint64_t>(1) << 46;     // descriptor version
+    d |= static_cast<uint64_t>(2) << 61;     // SWIZZLE_128B
+    return d;
+}
+
+// instruction descriptor, kind::f16: D = F32, A/B = BF16 (ab_fmt 1) or F16 (0), both K-major
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_fmt, int M, int N) {
+    return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+           (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct Smem {
+    // follows the stage buffers (each stage: A hi, B hi (, A lo, B lo), 1024-byte aligned)
+    uint64_t full[STAGES_1];
+    uint64_t empty[STAGES_1];
+    uint64_t accum;
+    uint32_t tmem_base;
+};
+
+// split = 0: one BF16 product; split = 1: FP16 hi/lo, three products into two accumulators
+template <int SPLIT>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_umma_project(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                   const __grid_constant__ CUtensorMap map_a2, const __grid_constant__ CUtensorMap map_b2, int n, int P,
+                   int d, int col_tiles, float* __restrict__ Z, int64_t ldz, float* __restrict__ absmax,
+                   unsigned* __restrict__ err) {
+    constexpr int STAGES = Stages<SPLIT>::value;
+    extern __shared__ unsigned char smem_raw[];
+    // 1024-byte alignment for the swizzled tiles
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+    constexpr int STAGE_BYTES = SPLIT ? 2 * (A_BYTES + B_BYTES) : A_BYTES + B_BYTES;
+    Smem* sm = reinterpret_cast<Smem*>(base + STAGES * STAGE_BYTES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // column tile fastest: the CTAs that share a block of points run back to back (L2 reuse of A)
+    const int row0 = static_cast<int>(blockIdx.x / col_tiles) * BM;
+    const int col0 = static_cast<int>(blockIdx.x % col_tiles) * BN;
+    const int kblocks = (d + BK - 1) / BK;
+    constexpr uint32_t TMEM_COLS = SPLIT ? 512 : 256;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&sm->full[s], 1);
+            mbar_init(&sm->empty[s], 1);
+        }
+        mbar_init(&sm->accum, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm->tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = sm->tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer
+        for (int kb = 0; kb < kblocks; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES && !mbar_wait(&sm->empty[s], ((kb / STAGES) - 1) & 1)) {
+                atomicOr(err, 8u);
+                break;
+            }
+            unsigned char* st = base + s * STAGE_BYTES;
+            mbar_expect_tx(&sm->full[s], STAGE_BYTES);
+            tma_load_2d(st, &map_a, &sm->full[s], kb * BK, row0);
+            tma_load_2d(st + A_BYTES, &map_b, &sm->full[s], kb * BK, col0);
+            if (SPLIT) {
+                tma_load_2d(st + A_BYTES + B_BYTES, &map_a2, &sm->full[s], kb * BK, row0);
+                tma_load_2d(st + 2 * A_BYTES + B_BYTES, &map_b2, &sm->full[s], kb * BK, col0);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        const uint32_t idesc = instr_desc(SPLIT ? 0u : 1u, BM, BN);
+        bool ok = true;
+        for (int kb = 0; kb < kblocks; ++kb) {
+            const int s = kb % STAGES;
+            if (!mbar_wait(&sm->full[s], (kb / STAGES) & 1)) {
+                atomicOr(err, 16u);
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            unsigned char* st = base + s * STAGE_BYTES;
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k) {
+                const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+                // advancing 16 elements (32 bytes) inside the 128-byte swizzled row
+                const uint64_t ah = smem_desc(st + k * 32), bh = smem_desc(st + A_BYTES + k * 32);
+                umma_f16(tmem, ah, bh, idesc, acc);
+                if (SPLIT) {
+                    const uint64_t al = smem_desc(st + A_BYTES + B_BYTES + k * 32);
+                    const uint64_t bl = smem_desc(st + 2 * A_BYTES + B_BYTES + k * 32);
+                    umma_f16(tmem + BN, ah, bl, idesc, acc);
+                    umma_f16(tmem + BN, al, bh, idesc, 1u);
+                }
+            }
+            umma_commit(&sm->empty[s]);
+        }
+        (void)ok;
+        umma_commit(&sm->accum);  // arrives once everything issued so far has completed
+    } else if (warp >= 4) {
+        // ---------------- epilogue: TMEM -> registers -> Z (slice-major)
+        const int q = warp - 4;  // TMEM lane quarter
+        const int row = row0 + q * 32 + lane;
+        float mx = 0.0f;
+        if (mbar_wait(&sm->accum, 0)) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int c = 0; c < BN; c += 32) {
+                float v[32];
+                tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + c, v);
+                if (SPLIT) {
+                    float v2[32];
+                    tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + BN + c, v2);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = fmaf(v2[j], 0x1.0p-11f, v[j]);
+                }
+                if (row < n) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int p = col0 + c + j;
+                        if (p < P) {
+                            Z[static_cast<int64_t>(p) * ldz + row] = v[j];
+                            mx = fmaxf(mx, fabsf(v[j]));
+                        }
+                    }
+                }
+            }
+        } else {
+            atomicOr(err, 32u);
+        }
+        if (absmax) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) atomicMax(reinterpret_cast<unsigned int*>(absmax), __float_as_uint(mx));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 2) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// centre and convert: out[i][k] = (16-bit)(x[i][k] - mu[k]) for k < d, 0 for d <= k < ldo;
+// SPLIT also writes the scaled low part 2^11 (x - mu - hi) into out_lo
+template <class Half, int SPLIT>
+__global__ void k_center_cast(const float* __restrict__ x, int64_t n, int d, int64_t ldx, const float* __restrict__ mu,
+                              Half* __restrict__ out, Half* __restrict__ out_lo, int ldo) {
+    const int64_t total = n * static_cast<int64_t>(ldo);
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = e / ldo;
+        const int k = static_cast<int>(e - i * ldo);
+        float v = k < d ? x[i * ldx + k] - (mu ? mu[k] : 0.0f) : 0.0f;
+        Half h;
+        if constexpr (sizeof(Half) == 2 && std::is_same<Half, __nv_bfloat16>::value) h = __float2bfloat16_rn(v);
+        else h = __float2half_rn(v);
+        out[e] = h;
+        if constexpr (SPLIT != 0) {
+            float lo = (v - static_cast<float>(h)) * 2048.0f;
+            out_lo[e] = __float2half_rn(lo);
+        }
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        SLK_CHECK_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !p) fail(SLK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2-D tensor map over a row-major [rows][ld] 16-bit matrix, box = 64 x box_rows, 128B swizzle
+CUtensorMap make_map(const void* ptr, CUtensorMapDataType dt, int64_t rows, int cols, int64_t ld, int box_rows) {
+    CUtensorMap m;
+    cuuint64_t gdim[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+    cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ld * 2)};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows)};
+    cuuint32_t estride[2] = {1, 1};
+    CUresult r = get_encode()(&m, dt, 2, const_cast<void*>(ptr), gdim, gstride, box, estride,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) fail(SLK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+    return m;
+}
+
+template <int SPLIT>
+size_t umma_smem_bytes() {
+    constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+    constexpr int STAGE_BYTES = SPLIT ? 2 * (A_BYTES + B_BYTES) : A_BYTES + B_BYTES;
+    return 1024 + Stages<SPLIT>::value * STAGE_BYTES + sizeof(Smem);
+}
+
+}  // namespace
+
+int64_t umma_operand_ld(int d) { return (d + 7) / 8 * 8; }
+
+void launch_center_cast(const float* x, int64_t n, int d, int64_t ldx, const float* mu, void* out, void* out_lo,
+                        int split, cudaStream_t st) {
+    if (n <= 0) return;
+    const int ldo = static_cast<int>(umma_operand_ld(d));
+    const int64_t total = n * ldo;
+    const unsigned blocks = static_cast<unsigned>(ceil_div(total, 256) < 152 * 16 ? ceil_div(total, 256) : 152 * 16);
+    SLK_TIMED("center_cast", st);
+    if (split)
+        k_center_cast<__half, 1><<<blocks, 256, 0, st>>>(x, n, d, ldx, mu, static_cast<__half*>(out),
+                                                        static_cast<__half*>(out_lo), ldo);
+    else
+        k_center_cast<__nv_bfloat16, 0><<<blocks, 256, 0, st>>>(x, n, d, ldx, mu, static_cast<__nv_bfloat16*>(out),
+                                                               nullptr, ldo);
+    SLK_CHECK_LAUNCH();
+}
+
+void launch_project_umma(const void* xa, const void* xa_lo, int64_t n, const void* xib, const void* xib_lo, int P,
+                         int d, int split, float* Z, int64_t ldz, float* absmax, unsigned* err, cudaStream_t st) {
+    if (n <= 0) return;
+    SLK_REQUIRE(n < (int64_t(1) << 31), "too many points for one projection");
+    const int64_t ld = umma_operand_ld(d);
+    const CUtensorMapDataType dt = split ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUtensorMap ma = make_map(xa, dt, n, d, ld, BM);
+    CUtensorMap mb = make_map(xib, dt, P, d, ld, BN);
+    CUtensorMap ma2 = split ? make_map(xa_lo, dt, n, d, ld, BM) : ma;
+    CUtensorMap mb2 = split ? make_map(xib_lo, dt, P, d, ld, BN) : mb;
+    const int col_tiles = static_cast<int>(ceil_div(P, BN));
+    const int64_t blocks = ceil_div(n, BM) * col_tiles;
+    SLK_REQUIRE(blocks < (int64_t(1) << 31), "too many points");
+    dim3 grid(static_cast<unsigned>(blocks));
+    if (split) {
+        static bool attr = false;
+        if (!attr) {
+            SLK_CHECK_CUDA(cudaFuncSetAttribute(k_umma_project<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                static_cast<int>(umma_smem_bytes<1>())));
+            attr = true;
+        }
+        SLK_TIMED("umma_project_x3", st);
+        k_umma_project<1><<<grid, THREADS, umma_smem_bytes<1>(), st>>>(ma, mb, ma2, mb2, static_cast<int>(n), P, d,
+                                                                        col_tiles, Z, ldz, absmax, err);
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            SLK_CHECK_CUDA(cudaFuncSetAttribute(k_umma_project<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                static_cast<int>(umma_smem_bytes<0>())));
+            attr = true;
+        }
+        SLK_TIMED("umma_project_bf16", st);
+        k_umma_project<0><<<grid, THREADS, umma_smem_bytes<0>(), st>>>(ma, mb, ma2, mb2, static_cast<int>(n), P, d,
+                                                                        col_tiles, Z, ldz, absmax, err);
+    }
+    SLK_CHECK_LAUNCH();
+}
+
+}  // namespace slk

@@ -84,24 +84,42 @@ void launch_normalize_rows(double* xi, int P, int d, cudaStream_t st) {
 
 // ------------------------------------------------------------ centre
 
+// partial[c][k] = sum of column k over the c-th group of sampled rows
 template <class T>
-__global__ void k_sample_mean(const T* x, int64_t N, int d, int64_t ldx, int S, double* mu) {
+__global__ void k_sample_mean_partial(const T* x, int64_t N, int d, int64_t ldx, int S, int groups, double* partial) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.y;
+    if (k >= d) return;
+    double acc = 0.0;
+    for (int s = g; s < S; s += groups) {
+        int64_t row = (static_cast<int64_t>(s) * N) / S;
+        acc += static_cast<double>(x[row * ldx + k]);
+    }
+    partial[static_cast<int64_t>(g) * d + k] = acc;
+}
+
+__global__ void k_sample_mean_final(const double* partial, int d, int S, int groups, double* mu) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < d; k += gridDim.x * blockDim.x) {
         double acc = 0.0;
-        for (int s = 0; s < S; ++s) {
-            int64_t row = (static_cast<int64_t>(s) * N) / S;
-            acc += static_cast<double>(x[row * ldx + k]);
-        }
+        for (int g = 0; g < groups; ++g) acc += partial[static_cast<int64_t>(g) * d + k];
         mu[k] = acc / S;
     }
 }
 
 template <class T>
 void launch_sample_mean(const T* x, int64_t N, int d, int64_t ldx, double* mu, cudaStream_t st) {
-    int S = static_cast<int>(N < 4096 ? N : 4096);
+    const int S = static_cast<int>(N < 4096 ? N : 4096);
+    const int groups = S < 64 ? S : 64;
+    DevBuf<double> partial(static_cast<size_t>(groups) * d, st);
     {
-        SLK_TIMED("sample_mean", st);
-        k_sample_mean<T><<<static_cast<unsigned>(ceil_div(d, 128)), 128, 0, st>>>(x, N, d, ldx, S, mu);
+        SLK_TIMED("sample_mean_partial", st);
+        dim3 grid(static_cast<unsigned>(ceil_div(d, 128)), groups);
+        k_sample_mean_partial<T><<<grid, 128, 0, st>>>(x, N, d, ldx, S, groups, partial.get());
+    }
+    SLK_CHECK_LAUNCH();
+    {
+        SLK_TIMED("sample_mean_final", st);
+        k_sample_mean_final<<<static_cast<unsigned>(ceil_div(d, 128)), 128, 0, st>>>(partial.get(), d, S, groups, mu);
     }
     SLK_CHECK_LAUNCH();
 }
@@ -170,32 +188,6 @@ void launch_finalize(const double* acc, T* s, int64_t n, double scale, cudaStrea
     SLK_CHECK_LAUNCH();
 }
 
-template <class T>
-__global__ void k_range_check(const T* Z, int64_t n, int64_t ldz, double R, unsigned* err) {
-    const T* row = Z + static_cast<int64_t>(blockIdx.y) * ldz;
-    bool bad = false;
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        double v = static_cast<double>(row[i]);
-        if (!(v <= R && v >= -R)) bad = true;  // also catches NaN
-    }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, 4u);
-}
-
-template <class T>
-void launch_range_check(const T* Z, int P, int64_t n, int64_t ldz, double R, unsigned* err, cudaStream_t st) {
-    if (n <= 0 || P <= 0) return;
-    int64_t bx = ceil_div(n, 256);
-    dim3 grid(static_cast<unsigned>(bx < 64 ? bx : 64), P);
-    {
-        SLK_TIMED("range_check", st);
-        k_range_check<T><<<grid, 256, 0, st>>>(Z, n, ldz, R, err);
-    }
-    SLK_CHECK_LAUNCH();
-}
-
-template void launch_range_check<float>(const float*, int, int64_t, int64_t, double, unsigned*, cudaStream_t);
-template void launch_range_check<double>(const double*, int, int64_t, int64_t, double, unsigned*, cudaStream_t);
 template void launch_sample_mean<float>(const float*, int64_t, int, int64_t, double*, cudaStream_t);
 template void launch_sample_mean<double>(const double*, int64_t, int, int64_t, double*, cudaStream_t);
 template void launch_convert<float>(const double*, float*, int64_t, cudaStream_t);

@@ -24,9 +24,7 @@ void launch_absmax(const T* Z, int P, int64_t n, int64_t ldz, float* out, cudaSt
 // s[i] = (T)(acc[i] * scale).
 template <class T>
 void launch_finalize(const double* acc, T* s, int64_t n, double scale, cudaStream_t st);
-// err |= 4 if any |Z[p][i]| > R (targets outside the certified window).
-template <class T>
-void launch_range_check(const T* Z, int P, int64_t n, int64_t ldz, double R, unsigned* err, cudaStream_t st);
+
 
 // ------------------------------------------------------------ k_project.cu
 // Z[p][i] = sum_k xi[p][k] (x[i][k] - mu[k]),  p < P, i < n  (SIMT, FP32 or FP64).
@@ -37,6 +35,17 @@ void launch_project_simt(const T* xi, int P, const T* x, int64_t n, int d, int64
 template <class T>
 void launch_grad_gemm(const T* G, int64_t M, int P, const T* xi, int d, const T* gs, double scale, T* gy,
                       int64_t ldg, cudaStream_t st);
+
+// ------------------------------------------------------------ k_tcgen05.cu
+// Row pitch (elements) of the 16-bit operands of the tensor-core projection.
+int64_t umma_operand_ld(int d);
+// out[i][k] = 16-bit (x[i][k] - mu[k]) (BF16, or FP16 hi plus scaled FP16 lo when split).
+void launch_center_cast(const float* x, int64_t n, int d, int64_t ldx, const float* mu, void* out, void* out_lo,
+                        int split, cudaStream_t st);
+// Z[p][i] = sum_k xi[p][k] xc[i][k] on tensor cores (tcgen05, TMA), FP32 accumulate;
+// *absmax = max(*absmax, max |Z|) when absmax != NULL; timeouts set bits 8/16/32 of *err.
+void launch_project_umma(const void* xa, const void* xa_lo, int64_t n, const void* xib, const void* xib_lo, int P,
+                         int d, int split, float* Z, int64_t ldz, float* absmax, unsigned* err, cudaStream_t st);
 
 // ------------------------------------------------------------ k_fourier.cu
 struct FourierDev {
@@ -49,6 +58,8 @@ struct FourierDev {
     // [win_base, win_base + W) in grid cells
     int n_g, m, W, win_base;
     double beta;
+    // certified window: every projected target lies in [-R, R]
+    double R;
 };
 
 // NDFT, source side: cw[p][j] = c_{k_lo+j} * sum_n w_n exp(-2 pi i k z_{p,n} / L),
@@ -57,10 +68,11 @@ template <class T>
 void launch_ndft_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, const FourierDev& fd,
                         const double* coef, Cplx<T>* cw, T* cw0, T* scratch, int64_t scratch_elems, cudaStream_t st);
 // NDFT, target side: acc[m] += sum_p t_p(z_{p,m});  with G != NULL writes
-// G[m][p] = dt_p/dz instead (for the gradient).
+// G[m][p] = dt_p/dz instead (for the gradient).  Targets outside [-R, R] set
+// bit 4 of *err.
 template <class T>
 void launch_ndft_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const Cplx<T>* cw,
-                        const T* cw0, double* acc, T* G, cudaStream_t st);
+                        const T* cw0, double* acc, T* G, unsigned* err, cudaStream_t st);
 // NFFT, source side: spread w onto the grid window of every slice (partial
 // sums per point chunk, then a fixed-order reduction), FFT, multiply by
 // mult[k] = c_k / Psi(k/n_g)^2 for |k| < n_coeff/2, inverse FFT; h is P x W.
@@ -71,7 +83,8 @@ void launch_nfft_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, c
 int64_t nfft_source_scratch(int P, int64_t n, const FourierDev& fd);
 int64_t ndft_source_scratch(int P, int64_t n, const FourierDev& fd);
 // NFFT, target side: acc[m] += sum_p sum_j h[p][j] psi(n_g z/L - j); with
-// G != NULL writes the derivative dt_p/dz into G[m][p] instead.
+// G != NULL writes the derivative dt_p/dz into G[m][p] instead.  Targets
+// outside [-R, R] set bit 4 of *err.
 template <class T>
 void launch_nfft_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const T* h, double* acc,
                         T* G, unsigned* err, cudaStream_t st);

@@ -201,7 +201,9 @@ def test_strided_rows_and_edge_sizes():
         s = plan.sum(y1).cpu().numpy()
         r = np.abs(np.array([0.0, 1.0, -3.0]) - 0.25)
         F = {"gaussian": np.exp(-r ** 2 / 2), "negdist": -r, "laplacian": np.exp(-0.5 * r)}[kernel]
-        np.testing.assert_allclose(s, 2.0 * F, rtol=1e-9, atol=1e-9)
+        # d = 1: slicing is exact, so only the certified model error remains
+        tol = max(1e-9, 4.0 * plan.info()["model_error"] * 2.0)
+        np.testing.assert_allclose(s, 2.0 * F, rtol=0, atol=tol)
 
 
 def test_target_outside_certified_window_is_reported():

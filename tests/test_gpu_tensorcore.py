@@ -1,0 +1,69 @@
+"""Tensor-core projection (tcgen05 + TMA): BF16 and the FP16 hi/lo split against
+the FP64 oracle, over shapes that exercise partial tiles in every dimension
+(K tail beyond d, slices beyond P, points beyond n)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_08260_gb300 import workloads
+from tests._util import cuda_or_skip, rel_inf, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _plan(x, w, kernel, param, xi, precision, **kw):
+    from paper_2401_08260_gb300.slk import Plan
+    return Plan(x, w, kernel, param, P=xi.shape[0], precision=precision, directions=xi, **kw)
+
+
+@pytest.mark.parametrize("N,M,P", [(1000, 200, 64), (3001, 257, 512)])
+def test_bf16_gaussian_d784(N, M, P):
+    """BF16 projection, FP32 accumulate: within 2e-3 of the FP64 sliced sum."""
+    dev = cuda_or_skip()
+    d = 784
+    rng = np.random.Generator(np.random.PCG64(11))
+    x = rng.random((N, d), dtype=np.float32)
+    y = rng.random((M, d), dtype=np.float32)
+    w = np.full(N, 1.0 / N, dtype=np.float32)
+    xi = workloads.directions(P, d, seed=12)
+    sigma = math.sqrt(d)
+    for method in ("ndft", "nfft"):
+        plan = _plan(to_dev(x, dev), to_dev(w, dev), "gaussian", sigma, xi, "bf16", n_coeff=256, method=method)
+        s = plan.sum(to_dev(y, dev))
+        ref, _ = oracle.sliced_sum("gaussian", sigma, x, y, w, xi)
+        err = rel_inf(s, ref, w.sum())
+        assert err <= 2e-3, (method, err)
+        # and the BF16 result is close to the FP32 path (rounding of the inputs only)
+        p32 = _plan(to_dev(x, dev), to_dev(w, dev), "gaussian", sigma, xi, "f32", n_coeff=256, method=method)
+        s32 = p32.sum(to_dev(y, dev))
+        assert rel_inf(s, s32.cpu().numpy(), w.sum()) <= 2e-3
+
+
+@pytest.mark.parametrize("d,P,N,M", [(50, 128, 5003, 301), (3072, 1000, 2000, 129), (200, 300, 4097, 64)])
+def test_f16x3_negdist(d, P, N, M):
+    """FP16 hi/lo split (three products): FP32-level projection accuracy, within 1e-5."""
+    dev = cuda_or_skip()
+    rng = np.random.Generator(np.random.PCG64(13))
+    x = rng.standard_normal((N, d), dtype=np.float32)
+    y = (rng.standard_normal((M, d), dtype=np.float32) + 0.5).astype(np.float32)
+    w = rng.random(N).astype(np.float32)
+    xi = workloads.directions(P, d, seed=14)
+    plan = _plan(to_dev(x, dev), to_dev(w, dev), "negdist", 0.0, xi, "f16x3")
+    s = plan.sum(to_dev(y, dev))
+    ref, _ = oracle.sliced_sum("negdist", 0.0, x, y, w, xi)
+    err = rel_inf(s, ref, w.sum())
+    assert err <= 1e-5, err
+
+
+def test_f16x3_laplacian_and_gradient():
+    dev = cuda_or_skip()
+    wl = workloads.make("laplace_d50", N=8001, M=255, P=40)
+    plan = _plan(to_dev(wl.x, dev), to_dev(wl.w, dev), "laplacian", wl.param, wl.xi, "f16x3")
+    yt = to_dev(wl.y, dev)
+    s = plan.sum(yt)
+    g = plan.grad(yt)
+    ref, gref, _ = oracle.sliced_sum("laplacian", wl.param, wl.x, wl.y, wl.w, wl.xi, grad=True)
+    assert rel_inf(s, ref, wl.w.sum()) <= 1e-5
+    assert rel_inf(g, gref, wl.w.sum()) <= 2e-5
