@@ -161,6 +161,19 @@ slk_status slk_grad(slk_plan plan, const void* y, int64_t M, int64_t ldy, const 
                     void* stream);
 
 /*
+ * Projections of n points onto the plan's directions (Algorithm 1, the inner
+ * products <xi_p, x_i>), centred by the plan's centre mu:
+ *     Z[p * ldz + i] = <xi_p, x_i - mu>,   p < P, i < n,
+ * computed on the plan's projection path (SIMT FP64/FP32, or tensor cores for
+ * SLK_PREC_BF16 / SLK_PREC_F16X3).  x is n x d (row stride ldx); Z holds
+ * P x ldz elements of the plan's element type (ldz >= n).  Host or device.
+ */
+slk_status slk_plan_project(slk_plan plan, const void* x, int64_t n, int64_t ldx, void* Z, int64_t ldz, void* stream);
+
+/* The plan's centre mu (d values, FP64) into host memory. */
+slk_status slk_plan_get_center(slk_plan plan, double* mu_host);
+
+/*
  * Wait for the plan's outstanding work and return the device-side status of
  * its last call: SLK_ERR_ACCURACY when a projected target fell outside the
  * certified window [-R, R] of a Fourier plan (sums with device outputs are

@@ -405,6 +405,17 @@ void sum_impl(slk_plan plan, const void* y_user, int64_t M, int64_t ldy, void* s
 }
 
 template <class T>
+void project_impl(slk_plan plan, const void* x_user, int64_t n, int64_t ldx, void* Z_user, int64_t ldz,
+                  cudaStream_t st) {
+    InView<T> xv(x_user, n, plan->d, ldx, st);
+    DevBuf<T> Z(static_cast<size_t>(plan->P) * n, st);
+    project<T>(plan, xv.ptr, n, xv.ld, Z.get(), nullptr, st);
+    SLK_CHECK_CUDA(cudaMemcpy2DAsync(Z_user, sizeof(T) * ldz, Z.get(), sizeof(T) * n, sizeof(T) * n, plan->P,
+                                     cudaMemcpyDefault, st));
+    if (!is_device_pointer(Z_user)) SLK_CHECK_CUDA(cudaStreamSynchronize(st));
+}
+
+template <class T>
 void grad_impl(slk_plan plan, const void* y_user, int64_t M, int64_t ldy, const void* gs_user, void* gy_user,
                int64_t ldg, cudaStream_t st) {
     const int P = plan->P, d = plan->d;
@@ -557,6 +568,38 @@ slk_status slk_grad(slk_plan plan, const void* y, int64_t M, int64_t ldy, const 
             slk_status e = collect(plan, true);
             if (e != SLK_OK) throw Error{e, slk_last_error()};
         }
+    });
+}
+
+slk_status slk_plan_project(slk_plan plan, const void* x, int64_t n, int64_t ldx, void* Z, int64_t ldz, void* stream) {
+    set_last_error("");
+    return guarded([&] {
+        SLK_REQUIRE(plan, "plan is NULL");
+        slk_status prev = collect(plan, false);
+        if (prev != SLK_OK) throw Error{prev, slk_last_error()};
+        SLK_REQUIRE(n >= 0, "n must be >= 0");
+        if (n == 0) return;
+        SLK_REQUIRE(x && Z, "x and Z must not be NULL");
+        SLK_REQUIRE(ldx >= plan->d && ldz >= n, "ldx must be >= d and ldz >= n");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        if (plan->f64) project_impl<double>(plan, x, n, ldx, Z, ldz, st);
+        else project_impl<float>(plan, x, n, ldx, Z, ldz, st);
+        finish_call(plan, st);
+        plan->stream = st;
+        if (!is_device_pointer(Z)) {
+            slk_status e = collect(plan, true);
+            if (e != SLK_OK) throw Error{e, slk_last_error()};
+        }
+    });
+}
+
+slk_status slk_plan_get_center(slk_plan plan, double* mu_host) {
+    set_last_error("");
+    return guarded([&] {
+        SLK_REQUIRE(plan && mu_host, "plan and mu_host must not be NULL");
+        SLK_CHECK_CUDA(cudaMemcpyAsync(mu_host, plan->mu64.get(), sizeof(double) * plan->d, cudaMemcpyDeviceToHost,
+                                       plan->stream));
+        SLK_CHECK_CUDA(cudaStreamSynchronize(plan->stream));
     });
 }
 

@@ -70,6 +70,9 @@ _SIGNATURES = {
     "slk_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
                                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "slk_plan_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "slk_plan_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "slk_plan_get_center": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "slk_plan_get_directions": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "slk_plan_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]),
     "slk_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
@@ -224,6 +227,26 @@ class Plan:
         if sync:
             _check(lib.slk_plan_sync(self._h))
         return out
+
+    def project(self, x, out=None, sync: bool = True):
+        """Z[p, i] = <xi_p, x_i - mu> on the plan's projection path (P x n)."""
+        lib = load()
+        xa = _Arr(x, self.dtype, 2)
+        if out is None:
+            if torch is not None and isinstance(x, torch.Tensor):
+                out = torch.empty(self.P, xa.rows, dtype=xa.keep.dtype, device=xa.keep.device)
+            else:
+                out = np.empty((self.P, xa.rows), dtype=self.dtype)
+        oa = _Arr(out, self.dtype, 2)
+        _check(lib.slk_plan_project(self._h, xa.ptr, xa.rows, xa.ld, oa.ptr, oa.ld, _stream_of(x)))
+        if sync:
+            _check(lib.slk_plan_sync(self._h))
+        return out
+
+    def center(self) -> np.ndarray:
+        mu = np.empty(self.d, dtype=np.float64)
+        _check(load().slk_plan_get_center(self._h, mu.ctypes.data))
+        return mu
 
     def sync(self):
         _check(load().slk_plan_sync(self._h))
