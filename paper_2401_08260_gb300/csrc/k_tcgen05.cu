@@ -10,10 +10,11 @@
 // with tcgen05.ld and store Z slice-major (coalesced along points), keeping
 // the largest |z| on the way.
 //
-// The FP16 "x3" variant splits both operands into a high and a scaled low
-// FP16 part (a = a_hi + 2^-11 a_lo') and accumulates a_hi b_hi in one TMEM
-// accumulator and a_hi b_lo' + a_lo' b_hi in a second; the epilogue forms
-// D1 + 2^-11 D2 (error ~ 2^-22 relative per product, about FP32).
+// The FP16 "x3" variant (k_umma_project_x3) splits both operands into a high
+// and a scaled low FP16 part (a = a_hi + 2^-11 a_lo') and forms
+// a_hi b_hi + 2^-11 (a_hi b_lo' + a_lo' b_hi) (error ~ 2^-22 relative per
+// product, about FP32), promoting the dominant product to FP32 registers
+// after every 16-wide K step (see the kernel's comment).
 //
 // Every mbarrier wait is bounded: on timeout the kernel records an error bit,
 // skips the remaining work, still frees its tensor memory and returns.
@@ -47,6 +48,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // bounded wait for the phase with the given parity; false on timeout
@@ -257,6 +262,189 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
+// FP16 hi/lo split with promotion.  The tensor core's FP32 accumulation
+// rounds toward zero inside each MMA, so every partial sum it forms is biased
+// towards zero by about 2^-24 of itself; summed over K these biases add up to
+// a systematic relative error (about the number of chained MMA steps x 2^-24)
+// that slicing does not average out.  Here the dominant product a_hi b_hi of
+// every 16-wide K step goes to a fresh accumulator (three TMEM buffers in
+// rotation) and the epilogue warps add it into FP32 registers with
+// round-to-nearest, so the tensor core only ever rounds one 16-term group;
+// the small correction a_hi b_lo + a_lo b_hi (scaled by 2^-11, so its drift
+// is negligible) stays in one accumulator.
+// Tile: 128 points x 128 slices; TMEM columns: D1[0..2] at 0, 128, 256, D2 at 384.
+// Warps: 0 TMA, 1 MMA, 2 TMEM allocation, 4-11 epilogue (warp 4 + q + 4 h owns
+// TMEM lanes 32q..32q+31 and columns 64h..64h+63).
+constexpr int X3_BN = 128;
+constexpr int X3_STAGES = 3;
+constexpr int X3_BUF = 3;
+constexpr int X3_THREADS = 384;
+
+struct SmemX3 {
+    uint64_t full[X3_STAGES];
+    uint64_t empty[X3_STAGES];
+    uint64_t d1_full[X3_BUF];
+    uint64_t d1_empty[X3_BUF];
+    uint64_t accum;
+    uint32_t tmem_base;
+};
+
+__global__ void __launch_bounds__(X3_THREADS, 1)
+    k_umma_project_x3(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                      const __grid_constant__ CUtensorMap map_a2, const __grid_constant__ CUtensorMap map_b2, int n,
+                      int P, int d, int col_tiles, float* __restrict__ Z, int64_t ldz, float* __restrict__ absmax,
+                      unsigned* __restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    constexpr int A_BYTES = BM * BK * 2, B_BYTES = X3_BN * BK * 2;
+    constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);
+    SmemX3* sm = reinterpret_cast<SmemX3*>(base + X3_STAGES * STAGE_BYTES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row0 = static_cast<int>(blockIdx.x / col_tiles) * BM;
+    const int col0 = static_cast<int>(blockIdx.x % col_tiles) * X3_BN;
+    const int kblocks = (d + BK - 1) / BK;
+    const int ksteps = kblocks * (BK / 16);
+    constexpr uint32_t TMEM_COLS = 512;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < X3_STAGES; ++s) {
+            mbar_init(&sm->full[s], 1);
+            mbar_init(&sm->empty[s], 1);
+        }
+        for (int b = 0; b < X3_BUF; ++b) {
+            mbar_init(&sm->d1_full[b], 1);
+            mbar_init(&sm->d1_empty[b], 8);  // one arrival per epilogue warp
+        }
+        mbar_init(&sm->accum, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm->tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = sm->tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        for (int kb = 0; kb < kblocks; ++kb) {
+            const int s = kb % X3_STAGES;
+            if (kb >= X3_STAGES && !mbar_wait(&sm->empty[s], ((kb / X3_STAGES) - 1) & 1)) {
+                atomicOr(err, 8u);
+                break;
+            }
+            unsigned char* st = base + s * STAGE_BYTES;
+            mbar_expect_tx(&sm->full[s], STAGE_BYTES);
+            tma_load_2d(st, &map_a, &sm->full[s], kb * BK, row0);
+            tma_load_2d(st + A_BYTES, &map_b, &sm->full[s], kb * BK, col0);
+            tma_load_2d(st + A_BYTES + B_BYTES, &map_a2, &sm->full[s], kb * BK, row0);
+            tma_load_2d(st + 2 * A_BYTES + B_BYTES, &map_b2, &sm->full[s], kb * BK, col0);
+        }
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t idesc = instr_desc(0u, BM, X3_BN);
+        const uint32_t d2 = tmem + X3_BUF * X3_BN;
+        bool ok = true;
+        for (int kb = 0; kb < kblocks && ok; ++kb) {
+            const int s = kb % X3_STAGES;
+            if (!mbar_wait(&sm->full[s], (kb / X3_STAGES) & 1)) {
+                atomicOr(err, 16u);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            unsigned char* st = base + s * STAGE_BYTES;
+            for (int k = 0; k < BK / 16; ++k) {
+                const int t = kb * (BK / 16) + k;  // global K step
+                const int b = t % X3_BUF;
+                if (t >= X3_BUF && !mbar_wait(&sm->d1_empty[b], ((t / X3_BUF) - 1) & 1)) {
+                    atomicOr(err, 16u);
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t ah = smem_desc(st + k * 32), bh = smem_desc(st + A_BYTES + k * 32);
+                const uint64_t al = smem_desc(st + A_BYTES + B_BYTES + k * 32);
+                const uint64_t bl = smem_desc(st + 2 * A_BYTES + B_BYTES + k * 32);
+                umma_f16(tmem + b * X3_BN, ah, bh, idesc, 0u);
+                umma_commit(&sm->d1_full[b]);
+                umma_f16(d2, ah, bl, idesc, t > 0 ? 1u : 0u);
+                umma_f16(d2, al, bh, idesc, 1u);
+            }
+            umma_commit(&sm->empty[s]);
+        }
+        umma_commit(&sm->accum);
+    } else if (warp >= 4) {
+        const int q = warp & 3, h = (warp - 4) >> 2;
+        const int row = row0 + q * 32 + lane;
+        const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+        const int cbase = h * 64;
+        float acc[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) acc[j] = 0.0f;
+        bool ok = true;
+        for (int t = 0; t < ksteps; ++t) {
+            const int b = t % X3_BUF;
+            if (!mbar_wait(&sm->d1_full[b], (t / X3_BUF) & 1)) {
+                atomicOr(err, 32u);
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int c = 0; c < 64; c += 32) {
+                float v[32];
+                tmem_ld32(tmem + lane_off + b * X3_BN + cbase + c, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[c + j] = __fadd_rn(acc[c + j], v[j]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm->d1_empty[b]);
+        }
+        float mx = 0.0f;
+        if (ok && mbar_wait(&sm->accum, 0)) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int c = 0; c < 64; c += 32) {
+                float v[32];
+                tmem_ld32(tmem + lane_off + X3_BUF * X3_BN + cbase + c, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[c + j] = fmaf(v[j], 0x1.0p-11f, acc[c + j]);
+            }
+            if (row < n) {
+#pragma unroll
+                for (int j = 0; j < 64; ++j) {
+                    const int p = col0 + cbase + j;
+                    if (p < P) {
+                        Z[static_cast<int64_t>(p) * ldz + row] = acc[j];
+                        mx = fmaxf(mx, fabsf(acc[j]));
+                    }
+                }
+            }
+        } else if (ok) {
+            atomicOr(err, 32u);
+        }
+        if (absmax) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) atomicMax(reinterpret_cast<unsigned int*>(absmax), __float_as_uint(mx));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 2) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+size_t x3_smem_bytes() {
+    constexpr int A_BYTES = BM * BK * 2, B_BYTES = X3_BN * BK * 2;
+    return 1024 + X3_STAGES * 2 * (A_BYTES + B_BYTES) + sizeof(SmemX3);
+}
+
 // centre and convert: out[i][k] = (16-bit)(x[i][k] - mu[k]) for k < d, 0 for d <= k < ldo;
 // SPLIT also writes the scaled low part 2^11 (x - mu - hi) into out_lo
 template <class Half, int SPLIT>
@@ -338,24 +526,25 @@ void launch_project_umma(const void* xa, const void* xa_lo, int64_t n, const voi
     SLK_REQUIRE(n < (int64_t(1) << 31), "too many points for one projection");
     const int64_t ld = umma_operand_ld(d);
     const CUtensorMapDataType dt = split ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const int bn = split ? X3_BN : BN;
     CUtensorMap ma = make_map(xa, dt, n, d, ld, BM);
-    CUtensorMap mb = make_map(xib, dt, P, d, ld, BN);
+    CUtensorMap mb = make_map(xib, dt, P, d, ld, bn);
     CUtensorMap ma2 = split ? make_map(xa_lo, dt, n, d, ld, BM) : ma;
-    CUtensorMap mb2 = split ? make_map(xib_lo, dt, P, d, ld, BN) : mb;
-    const int col_tiles = static_cast<int>(ceil_div(P, BN));
+    CUtensorMap mb2 = split ? make_map(xib_lo, dt, P, d, ld, bn) : mb;
+    const int col_tiles = static_cast<int>(ceil_div(P, bn));
     const int64_t blocks = ceil_div(n, BM) * col_tiles;
     SLK_REQUIRE(blocks < (int64_t(1) << 31), "too many points");
     dim3 grid(static_cast<unsigned>(blocks));
     if (split) {
         static bool attr = false;
         if (!attr) {
-            SLK_CHECK_CUDA(cudaFuncSetAttribute(k_umma_project<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                static_cast<int>(umma_smem_bytes<1>())));
+            SLK_CHECK_CUDA(cudaFuncSetAttribute(k_umma_project_x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                static_cast<int>(x3_smem_bytes())));
             attr = true;
         }
         SLK_TIMED("umma_project_x3", st);
-        k_umma_project<1><<<grid, THREADS, umma_smem_bytes<1>(), st>>>(ma, mb, ma2, mb2, static_cast<int>(n), P, d,
-                                                                        col_tiles, Z, ldz, absmax, err);
+        k_umma_project_x3<<<grid, X3_THREADS, x3_smem_bytes(), st>>>(ma, mb, ma2, mb2, static_cast<int>(n), P, d,
+                                                                     col_tiles, Z, ldz, absmax, err);
     } else {
         static bool attr = false;
         if (!attr) {
