@@ -22,7 +22,8 @@ namespace slk {
 namespace {
 
 constexpr int NDFT_KC = 16;       // k values accumulated per pass (registers)
-constexpr int NDFT_CHUNK = 8192;  // sources per block in the NDFT reduction
+constexpr int NDFT_CHUNK = 32768;  // sources per block in the NDFT reduction
+constexpr int NDFT_KMAX = 64;     // largest band the NDFT kernels take
 constexpr int SPREAD_NARROW_W = 64;
 constexpr int SPREAD_WARPS = 8;
 constexpr int SPREAD_CHUNK = 4096;  // sources per warp in the narrow spread
@@ -86,58 +87,68 @@ template <> struct Acc<double> { using type = KahanD; };
 
 // ------------------------------------------------------------ NDFT source
 
-template <class T>
+// Phases in units of pi: with s = 2 z / L, exp(-2 pi i k z / L) = cospi(k s) - i sinpi(k s)
+// (exact argument reduction); consecutive k by the recurrence e^{-i(k+1)th} = e^{-ik th} e^{-i th}.
+__device__ inline void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ inline void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
+
+// One block: slice p, sources [chunk * NDFT_CHUNK, ...).  Each thread accumulates the K band
+// sums (and sum w for k = 0) in registers; warp shuffles, then one shared-memory pass.
+template <class T, int KMAX>
 __global__ void __launch_bounds__(256) k_ndft_source(const T* __restrict__ Z, int64_t n, int64_t ldz,
-                                                     const T* __restrict__ w, T inv_L, int k_lo, int K, int has_k0,
-                                                     T* __restrict__ partial, int P) {
-    __shared__ T red[8];
+                                                     const T* __restrict__ w, T two_over_L, int k_lo, int K,
+                                                     int has_k0, T* __restrict__ partial, int P) {
+    __shared__ T red[8][2 * KMAX + 1];
     const int p = blockIdx.y;
     const int64_t i0 = static_cast<int64_t>(blockIdx.x) * NDFT_CHUNK;
     const int64_t i1 = (i0 + NDFT_CHUNK < n) ? i0 + NDFT_CHUNK : n;
     const T* zr = Z + static_cast<int64_t>(p) * ldz;
-    const int stride = 2 * K + 1;
-    T* out = partial + (static_cast<int64_t>(blockIdx.x) * P + p) * stride;
-    const T two_pi = T(6.283185307179586476925286766559);
-    for (int kc = 0; kc < K; kc += NDFT_KC) {
-        T re[NDFT_KC], im[NDFT_KC];
+    T re[KMAX], im[KMAX], a0 = T(0);
 #pragma unroll
-        for (int j = 0; j < NDFT_KC; ++j) re[j] = im[j] = T(0);
-        T a0 = T(0);
-        const int kb = k_lo + kc;
-        for (int64_t i = i0 + threadIdx.x; i < i1; i += 256) {
-            const T wv = w[i];
-            const T th = two_pi * (zr[i] * inv_L);
-            T s, c, s1, c1;
-            sincos_t(T(kb) * th, &s, &c);
-            sincos_t(th, &s1, &c1);
-            // e^{-i k theta}, advanced by e^{-i theta}
-            T cr = c, ci = -s;
+    for (int j = 0; j < KMAX; ++j) re[j] = im[j] = T(0);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += 256) {
+        const T wv = w[i];
+        const T s = zr[i] * two_over_L;
+        T sb, cb, s1, c1;
+        sincospi_t(T(k_lo) * s, &sb, &cb);
+        sincospi_t(s, &s1, &c1);
+        T cr = cb, ci = -sb;
 #pragma unroll
-            for (int j = 0; j < NDFT_KC; ++j) {
+        for (int j = 0; j < KMAX; ++j) {
+            if (j < K) {
                 re[j] = fma(wv, cr, re[j]);
                 im[j] = fma(wv, ci, im[j]);
-                T nr = cr * c1 + ci * s1;
-                T ni = ci * c1 - cr * s1;
+                const T nr = cr * c1 + ci * s1;
+                const T ni = ci * c1 - cr * s1;
                 cr = nr;
                 ci = ni;
             }
-            if (has_k0 && kc == 0) a0 += wv;
         }
+        a0 += wv;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-        for (int j = 0; j < NDFT_KC; ++j) {
-            if (kc + j < K) {  // uniform across the block
-                T r = block_sum_256(re[j], red);
-                T m = block_sum_256(im[j], red);
-                if (threadIdx.x == 0) {
-                    out[2 * (kc + j)] = r;
-                    out[2 * (kc + j) + 1] = m;
-                }
+    for (int j = 0; j < KMAX; ++j) {
+        if (j < K) {
+            const T r = warp_sum(re[j]), m = warp_sum(im[j]);
+            if (lane == 0) {
+                red[warp][2 * j] = r;
+                red[warp][2 * j + 1] = m;
             }
         }
-        if (kc == 0) {
-            T r = block_sum_256(a0, red);
-            if (threadIdx.x == 0) out[2 * K] = r;
-        }
+    }
+    {
+        const T a = warp_sum(a0);
+        if (lane == 0) red[warp][2 * KMAX] = a;
+    }
+    __syncthreads();
+    const int stride = 2 * K + 1;
+    T* out = partial + (static_cast<int64_t>(blockIdx.x) * P + p) * stride;
+    for (int v = threadIdx.x; v < stride; v += blockDim.x) {
+        const int src = v < 2 * K ? v : 2 * KMAX;
+        T acc = T(0);
+        for (int q = 0; q < 8; ++q) acc += red[q][src];
+        out[v] = has_k0 || v < 2 * K ? acc : T(0);
     }
 }
 
@@ -166,9 +177,11 @@ __global__ void k_ndft_reduce(const T* __restrict__ partial, int nchunk, int P, 
 
 // ------------------------------------------------------------ NDFT target
 
-template <class T>
-__global__ void __launch_bounds__(256) k_ndft_target(const T* __restrict__ Z, int P, int64_t n, int64_t ldz, T inv_L,
-                                                     int k_lo, int K, const Cplx<T>* __restrict__ cw,
+// One thread per target: t_p(z) = 2 Re sum_j cw[p][j] e^{+i (k_lo + j) th} + cw0[p] for every
+// slice, averaged into acc[m]; GRAD writes dt_p/dz into G[m][p] instead.
+template <class T, int KMAX, bool GRAD>
+__global__ void __launch_bounds__(256) k_ndft_target(const T* __restrict__ Z, int P, int64_t n, int64_t ldz,
+                                                     T two_over_L, int k_lo, int K, const Cplx<T>* __restrict__ cw,
                                                      const T* __restrict__ cw0, int slice_chunk, T R,
                                                      double* __restrict__ acc, T* __restrict__ G,
                                                      unsigned* __restrict__ err) {
@@ -176,7 +189,7 @@ __global__ void __launch_bounds__(256) k_ndft_target(const T* __restrict__ Z, in
     Cplx<T>* scw = reinterpret_cast<Cplx<T>*>(smem_raw);
     T* scw0 = reinterpret_cast<T*>(scw + static_cast<size_t>(slice_chunk) * K);
     const int64_t m = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const T two_pi = T(6.283185307179586476925286766559);
+    const T two_pi_over_L = two_over_L * T(3.141592653589793238462643383279);
     typename Acc<T>::type sum;
     bool bad = false;
     for (int p0 = 0; p0 < P; p0 += slice_chunk) {
@@ -190,33 +203,32 @@ __global__ void __launch_bounds__(256) k_ndft_target(const T* __restrict__ Z, in
             const int p = p0 + q;
             const T z = Z[static_cast<int64_t>(p) * ldz + m];
             if (!(z <= R && z >= -R)) bad = true;  // outside the certified window (or NaN)
-            const T th = two_pi * (z * inv_L);
-            T s, c, s1, c1;
-            sincos_t(T(k_lo) * th, &s, &c);
-            sincos_t(th, &s1, &c1);
-            T cr = c, ci = s;  // e^{+i k theta}
+            const T s = z * two_over_L;
+            T sb, cb, s1, c1;
+            sincospi_t(T(k_lo) * s, &sb, &cb);
+            sincospi_t(s, &s1, &c1);
+            T cr = cb, ci = sb;  // e^{+i k th}
             T t = T(0), dt = T(0);
             const Cplx<T>* row = scw + static_cast<size_t>(q) * K;
-            for (int j = 0; j < K; ++j) {
-                const Cplx<T> a = row[j];
-                // Re(a e^{ik th}) and d/dth Re(a e^{ik th}) = -k Im(a e^{ik th})
-                t += a.re * cr - a.im * ci;
-                dt -= T(k_lo + j) * (a.re * ci + a.im * cr);
-                T nr = cr * c1 - ci * s1;
-                T ni = ci * c1 + cr * s1;
-                cr = nr;
-                ci = ni;
+#pragma unroll
+            for (int j = 0; j < KMAX; ++j) {
+                if (j < K) {
+                    const Cplx<T> a = row[j];
+                    if (GRAD) dt -= T(k_lo + j) * (a.re * ci + a.im * cr);  // d/dth Re(a e^{ik th})
+                    else t += a.re * cr - a.im * ci;                        // Re(a e^{ik th})
+                    const T nr = cr * c1 - ci * s1;
+                    const T ni = ci * c1 + cr * s1;
+                    cr = nr;
+                    ci = ni;
+                }
             }
-            if (G) {
-                // t_p = 2 Re(...) + cw0;  dt_p/dz = 2 * (dt) * 2 pi / L
-                G[m * P + p] = T(2) * dt * two_pi * inv_L;
-            } else {
-                sum.add(T(2) * t + scw0[q]);
-            }
+            // th = 2 pi z / L: dt_p/dz = 2 * dt * 2 pi / L
+            if (GRAD) G[m * P + p] = T(2) * dt * two_pi_over_L;
+            else sum.add(T(2) * t + scw0[q]);
         }
     }
     if (bad) atomicOr(err, 4u);
-    if (!G && m < n) acc[m] += sum.value();
+    if (!GRAD && m < n) acc[m] += sum.value();
 }
 
 // ------------------------------------------------------------ NFFT spread
@@ -433,24 +445,39 @@ int64_t ndft_source_scratch(int P, int64_t n, const FourierDev& fd) {
     return ceil_div(n, NDFT_CHUNK) * static_cast<int64_t>(P) * (2 * K + 1);
 }
 
+#define SLK_NDFT_DISPATCH(KV, ...)                                                        \
+    do {                                                                                  \
+        if ((KV) <= 4) { constexpr int KM = 4; __VA_ARGS__; }                             \
+        else if ((KV) <= 8) { constexpr int KM = 8; __VA_ARGS__; }                        \
+        else if ((KV) <= 12) { constexpr int KM = 12; __VA_ARGS__; }                      \
+        else if ((KV) <= 16) { constexpr int KM = 16; __VA_ARGS__; }                      \
+        else if ((KV) <= 24) { constexpr int KM = 24; __VA_ARGS__; }                      \
+        else if ((KV) <= 32) { constexpr int KM = 32; __VA_ARGS__; }                      \
+        else if ((KV) <= 48) { constexpr int KM = 48; __VA_ARGS__; }                      \
+        else { constexpr int KM = 64; __VA_ARGS__; }                                      \
+    } while (0)
+
 template <class T>
 void launch_ndft_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, const FourierDev& fd,
                         const double* coef, Cplx<T>* cw, T* cw0, T* scratch, int64_t scratch_elems, cudaStream_t st) {
     const int K = fd.k_hi - fd.k_lo + 1;
+    SLK_REQUIRE(K >= 1 && K <= NDFT_KMAX, "NDFT band of %d coefficients exceeds %d", K, NDFT_KMAX);
     const int64_t nchunk = ceil_div(n, NDFT_CHUNK);
     SLK_REQUIRE(scratch_elems >= ndft_source_scratch(P, n, fd), "NDFT scratch too small");
     SLK_REQUIRE(nchunk <= 2147483647 && P <= 65535, "NDFT launch too large");
     dim3 grid(static_cast<unsigned>(nchunk), P);
+    const T two_over_L = static_cast<T>(2.0 / fd.L);
     {
         SLK_TIMED("ndft_source", st);
-        k_ndft_source<T><<<grid, 256, 0, st>>>(Z, n, ldz, w, static_cast<T>(1.0 / fd.L), fd.k_lo, K, fd.has_k0, scratch, P);
+        SLK_NDFT_DISPATCH(K, k_ndft_source<T, KM><<<grid, 256, 0, st>>>(Z, n, ldz, w, two_over_L, fd.k_lo, K,
+                                                                        fd.has_k0, scratch, P));
     }
     SLK_CHECK_LAUNCH();
     int total = P * (K + 1);
     {
         SLK_TIMED("ndft_reduce", st);
-        k_ndft_reduce<T><<<static_cast<unsigned>(ceil_div(total, 256)), 256, 0, st>>>(scratch, static_cast<int>(nchunk), P,
-                                                                                       K, fd.has_k0, coef, cw, cw0);
+        k_ndft_reduce<T><<<static_cast<unsigned>(ceil_div(total, 256)), 256, 0, st>>>(
+            scratch, static_cast<int>(nchunk), P, K, fd.has_k0, coef, cw, cw0);
     }
     SLK_CHECK_LAUNCH();
 }
@@ -460,20 +487,27 @@ void launch_ndft_target(const T* Z, int P, int64_t n, int64_t ldz, const Fourier
                         const T* cw0, double* acc, T* G, unsigned* err, cudaStream_t st) {
     if (n <= 0) return;
     const int K = fd.k_hi - fd.k_lo + 1;
+    SLK_REQUIRE(K >= 1 && K <= NDFT_KMAX, "NDFT band of %d coefficients exceeds %d", K, NDFT_KMAX);
     const size_t per_slice = sizeof(Cplx<T>) * K + sizeof(T);
     int chunk = static_cast<int>((96 * 1024) / per_slice);
     if (chunk > P) chunk = P;
     if (chunk < 1) chunk = 1;
     const size_t smem = per_slice * chunk + 16;
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[sizeof(T) == 8]) {
-        SLK_CHECK_CUDA(cudaFuncSetAttribute(k_ndft_target<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-        attr_set[sizeof(T) == 8] = true;
-    }
-    {
-        SLK_TIMED("ndft_target", st);
-        k_ndft_target<T><<<static_cast<unsigned>(ceil_div(n, 256)), 256, smem, st>>>(
-            Z, P, n, ldz, static_cast<T>(1.0 / fd.L), fd.k_lo, K, cw, cw0, chunk, static_cast<T>(fd.R), acc, G, err);
+    const T two_over_L = static_cast<T>(2.0 / fd.L);
+    const unsigned blocks = static_cast<unsigned>(ceil_div(n, 256));
+    SLK_TIMED(G ? "ndft_target_grad" : "ndft_target", st);
+    if (G) {
+        SLK_NDFT_DISPATCH(K, {
+            cudaFuncSetAttribute(k_ndft_target<T, KM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+            k_ndft_target<T, KM, true><<<blocks, 256, smem, st>>>(Z, P, n, ldz, two_over_L, fd.k_lo, K, cw, cw0, chunk,
+                                                                 static_cast<T>(fd.R), acc, G, err);
+        });
+    } else {
+        SLK_NDFT_DISPATCH(K, {
+            cudaFuncSetAttribute(k_ndft_target<T, KM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+            k_ndft_target<T, KM, false><<<blocks, 256, smem, st>>>(Z, P, n, ldz, two_over_L, fd.k_lo, K, cw, cw0,
+                                                                  chunk, static_cast<T>(fd.R), acc, G, err);
+        });
     }
     SLK_CHECK_LAUNCH();
 }

@@ -33,8 +33,6 @@ constexpr int BM = 128;       // points per tile (TMEM lanes)
 constexpr int BN = 256;       // slices per tile (TMEM columns per accumulator)
 constexpr int BK = 64;        // K elements per stage (128 bytes of 16-bit data)
 constexpr int STAGES_1 = 4;  // one 16-bit product: 48 KB per stage
-constexpr int STAGES_3 = 2;  // hi/lo split: 96 KB per stage
-template <int SPLIT> struct Stages { static constexpr int value = SPLIT ? STAGES_3 : STAGES_1; };
 constexpr int THREADS = 256;  // warp 0: TMA, warp 1: MMA, warp 2: TMEM alloc, warps 4-7: epilogue
 constexpr unsigned WAIT_LIMIT = 1u << 26;
 
@@ -124,40 +122,41 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 }
 
 struct Smem {
-    // follows the stage buffers (each stage: A hi, B hi (, A lo, B lo), 1024-byte aligned)
+    // follows the stage buffers (each stage: A tile then B tile, 1024-byte aligned)
     uint64_t full[STAGES_1];
     uint64_t empty[STAGES_1];
-    uint64_t accum;
+    uint64_t acc_full[2];
+    uint64_t acc_empty[2];
     uint32_t tmem_base;
 };
 
-// split = 0: one BF16 product; split = 1: FP16 hi/lo, three products into two accumulators
-template <int SPLIT>
+// BF16 projection, persistent: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// (column tile fastest, so the CTAs that share a block of points run together and the
+// second read of A hits L2).  Two 256-column TMEM accumulators alternate between tiles:
+// the epilogue of one tile overlaps the MMAs of the next.
 __global__ void __launch_bounds__(THREADS, 1)
-    k_umma_project(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
-                   const __grid_constant__ CUtensorMap map_a2, const __grid_constant__ CUtensorMap map_b2, int n, int P,
-                   int d, int col_tiles, float* __restrict__ Z, int64_t ldz, float* __restrict__ absmax,
+    k_umma_project(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int n, int P,
+                   int d, int col_tiles, int tiles, float* __restrict__ Z, int64_t ldz, float* __restrict__ absmax,
                    unsigned* __restrict__ err) {
-    constexpr int STAGES = Stages<SPLIT>::value;
+    constexpr int STAGES = STAGES_1;
     extern __shared__ unsigned char smem_raw[];
-    // 1024-byte alignment for the swizzled tiles
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
-    constexpr int STAGE_BYTES = SPLIT ? 2 * (A_BYTES + B_BYTES) : A_BYTES + B_BYTES;
+    constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     Smem* sm = reinterpret_cast<Smem*>(base + STAGES * STAGE_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // column tile fastest: the CTAs that share a block of points run back to back (L2 reuse of A)
-    const int row0 = static_cast<int>(blockIdx.x / col_tiles) * BM;
-    const int col0 = static_cast<int>(blockIdx.x % col_tiles) * BN;
     const int kblocks = (d + BK - 1) / BK;
-    constexpr uint32_t TMEM_COLS = SPLIT ? 512 : 256;
+    constexpr uint32_t TMEM_COLS = 512;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&sm->full[s], 1);
             mbar_init(&sm->empty[s], 1);
         }
-        mbar_init(&sm->accum, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sm->acc_full[b], 1);
+            mbar_init(&sm->acc_empty[b], 4);  // one arrival per epilogue warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 2) {
@@ -172,68 +171,73 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t tmem = sm->tmem_base;
 
     if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer
-        for (int kb = 0; kb < kblocks; ++kb) {
-            const int s = kb % STAGES;
-            if (kb >= STAGES && !mbar_wait(&sm->empty[s], ((kb / STAGES) - 1) & 1)) {
-                atomicOr(err, 8u);
-                break;
-            }
-            unsigned char* st = base + s * STAGE_BYTES;
-            mbar_expect_tx(&sm->full[s], STAGE_BYTES);
-            tma_load_2d(st, &map_a, &sm->full[s], kb * BK, row0);
-            tma_load_2d(st + A_BYTES, &map_b, &sm->full[s], kb * BK, col0);
-            if (SPLIT) {
-                tma_load_2d(st + A_BYTES + B_BYTES, &map_a2, &sm->full[s], kb * BK, row0);
-                tma_load_2d(st + 2 * A_BYTES + B_BYTES, &map_b2, &sm->full[s], kb * BK, col0);
+        // ---------------- TMA producer: one ring across all tiles of this CTA
+        int g = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+            const int row0 = (tile / col_tiles) * BM, col0 = (tile % col_tiles) * BN;
+            for (int kb = 0; kb < kblocks; ++kb, ++g) {
+                const int s = g % STAGES;
+                if (g >= STAGES && !mbar_wait(&sm->empty[s], ((g / STAGES) - 1) & 1)) {
+                    atomicOr(err, 8u);
+                    ok = false;
+                    break;
+                }
+                unsigned char* st = base + s * STAGE_BYTES;
+                mbar_expect_tx(&sm->full[s], STAGE_BYTES);
+                tma_load_2d(st, &map_a, &sm->full[s], kb * BK, row0);
+                tma_load_2d(st + A_BYTES, &map_b, &sm->full[s], kb * BK, col0);
             }
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
-        const uint32_t idesc = instr_desc(SPLIT ? 0u : 1u, BM, BN);
+        const uint32_t idesc = instr_desc(1u, BM, BN);
+        int g = 0, local = 0;
         bool ok = true;
-        for (int kb = 0; kb < kblocks; ++kb) {
-            const int s = kb % STAGES;
-            if (!mbar_wait(&sm->full[s], (kb / STAGES) & 1)) {
+        for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++local) {
+            const int b = local & 1;
+            if (local >= 2 && !mbar_wait(&sm->acc_empty[b], ((local >> 1) - 1) & 1)) {
                 atomicOr(err, 16u);
-                ok = false;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            unsigned char* st = base + s * STAGE_BYTES;
-#pragma unroll
-            for (int k = 0; k < BK / 16; ++k) {
-                const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
-                // advancing 16 elements (32 bytes) inside the 128-byte swizzled row
-                const uint64_t ah = smem_desc(st + k * 32), bh = smem_desc(st + A_BYTES + k * 32);
-                umma_f16(tmem, ah, bh, idesc, acc);
-                if (SPLIT) {
-                    const uint64_t al = smem_desc(st + A_BYTES + B_BYTES + k * 32);
-                    const uint64_t bl = smem_desc(st + 2 * A_BYTES + B_BYTES + k * 32);
-                    umma_f16(tmem + BN, ah, bl, idesc, acc);
-                    umma_f16(tmem + BN, al, bh, idesc, 1u);
+            const uint32_t acc_t = tmem + b * BN;
+            for (int kb = 0; kb < kblocks; ++kb, ++g) {
+                const int s = g % STAGES;
+                if (!mbar_wait(&sm->full[s], (g / STAGES) & 1)) {
+                    atomicOr(err, 16u);
+                    ok = false;
+                    break;
                 }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                unsigned char* st = base + s * STAGE_BYTES;
+#pragma unroll
+                for (int k = 0; k < BK / 16; ++k) {
+                    // advancing 16 elements (32 bytes) inside the 128-byte swizzled row
+                    umma_f16(acc_t, smem_desc(st + k * 32), smem_desc(st + A_BYTES + k * 32), idesc,
+                             (kb > 0 || k > 0) ? 1u : 0u);
+                }
+                umma_commit(&sm->empty[s]);
             }
-            umma_commit(&sm->empty[s]);
+            umma_commit(&sm->acc_full[b]);
         }
-        (void)ok;
-        umma_commit(&sm->accum);  // arrives once everything issued so far has completed
     } else if (warp >= 4) {
         // ---------------- epilogue: TMEM -> registers -> Z (slice-major)
         const int q = warp - 4;  // TMEM lane quarter
-        const int row = row0 + q * 32 + lane;
+        const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
         float mx = 0.0f;
-        if (mbar_wait(&sm->accum, 0)) {
+        int local = 0;
+        for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++local) {
+            const int b = local & 1;
+            const int row = (tile / col_tiles) * BM + q * 32 + lane, col0 = (tile % col_tiles) * BN;
+            if (!mbar_wait(&sm->acc_full[b], (local >> 1) & 1)) {
+                atomicOr(err, 32u);
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             for (int c = 0; c < BN; c += 32) {
                 float v[32];
-                tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + c, v);
-                if (SPLIT) {
-                    float v2[32];
-                    tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + BN + c, v2);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = fmaf(v2[j], 0x1.0p-11f, v[j]);
-                }
+                tmem_ld32(tmem + lane_off + b * BN + c, v);
                 if (row < n) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
@@ -245,8 +249,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                 }
             }
-        } else {
-            atomicOr(err, 32u);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm->acc_empty[b]);
         }
         if (absmax) {
 #pragma unroll
@@ -446,24 +451,45 @@ size_t x3_smem_bytes() {
 }
 
 // centre and convert: out[i][k] = (16-bit)(x[i][k] - mu[k]) for k < d, 0 for d <= k < ldo;
-// SPLIT also writes the scaled low part 2^11 (x - mu - hi) into out_lo
+// SPLIT also writes the scaled low part 2^11 (x - mu - hi) into out_lo.  One thread
+// converts 8 consecutive elements of a row (one 16-byte store per output).
+template <class Half>
+__device__ __forceinline__ Half to_half(float v);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_half<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half to_half<__half>(float v) { return __float2half_rn(v); }
+
 template <class Half, int SPLIT>
-__global__ void k_center_cast(const float* __restrict__ x, int64_t n, int d, int64_t ldx, const float* __restrict__ mu,
-                              Half* __restrict__ out, Half* __restrict__ out_lo, int ldo) {
-    const int64_t total = n * static_cast<int64_t>(ldo);
+__global__ void __launch_bounds__(256) k_center_cast(const float* __restrict__ x, int64_t n, int d, int64_t ldx,
+                                                     const float* __restrict__ mu, Half* __restrict__ out,
+                                                     Half* __restrict__ out_lo, int ldo, int vec_ok) {
+    const int chunks = ldo / 8;
+    const int64_t total = n * static_cast<int64_t>(chunks);
     for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
          e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t i = e / ldo;
-        const int k = static_cast<int>(e - i * ldo);
-        float v = k < d ? x[i * ldx + k] - (mu ? mu[k] : 0.0f) : 0.0f;
-        Half h;
-        if constexpr (sizeof(Half) == 2 && std::is_same<Half, __nv_bfloat16>::value) h = __float2bfloat16_rn(v);
-        else h = __float2half_rn(v);
-        out[e] = h;
-        if constexpr (SPLIT != 0) {
-            float lo = (v - static_cast<float>(h)) * 2048.0f;
-            out_lo[e] = __float2half_rn(lo);
+        const int64_t i = e / chunks;
+        const int k0 = static_cast<int>(e - i * chunks) * 8;
+        float v[8];
+        const float* row = x + i * ldx + k0;
+        if (vec_ok && k0 + 8 <= d) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(row));
+            const float4 b = __ldg(reinterpret_cast<const float4*>(row + 4));
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = k0 + j < d ? row[j] : 0.0f;
         }
+        union { Half h[8]; uint4 u; } hi, lo;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float c = k0 + j < d ? v[j] - (mu ? __ldg(mu + k0 + j) : 0.0f) : 0.0f;
+            hi.h[j] = to_half<Half>(c);
+            if constexpr (SPLIT != 0) lo.h[j] = __float2half_rn((c - static_cast<float>(hi.h[j])) * 2048.0f);
+        }
+        *reinterpret_cast<uint4*>(out + i * ldo + k0) = hi.u;
+        if constexpr (SPLIT != 0) *reinterpret_cast<uint4*>(out_lo + i * ldo + k0) = lo.u;
     }
 }
 
@@ -493,11 +519,9 @@ CUtensorMap make_map(const void* ptr, CUtensorMapDataType dt, int64_t rows, int 
     return m;
 }
 
-template <int SPLIT>
 size_t umma_smem_bytes() {
     constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
-    constexpr int STAGE_BYTES = SPLIT ? 2 * (A_BYTES + B_BYTES) : A_BYTES + B_BYTES;
-    return 1024 + Stages<SPLIT>::value * STAGE_BYTES + sizeof(Smem);
+    return 1024 + STAGES_1 * (A_BYTES + B_BYTES) + sizeof(Smem);
 }
 
 }  // namespace
@@ -508,15 +532,16 @@ void launch_center_cast(const float* x, int64_t n, int d, int64_t ldx, const flo
                         int split, cudaStream_t st) {
     if (n <= 0) return;
     const int ldo = static_cast<int>(umma_operand_ld(d));
-    const int64_t total = n * ldo;
-    const unsigned blocks = static_cast<unsigned>(ceil_div(total, 256) < 152 * 16 ? ceil_div(total, 256) : 152 * 16);
+    const int64_t total = n * (ldo / 8);
+    const unsigned blocks = static_cast<unsigned>(ceil_div(total, 256) < 152 * 8 ? ceil_div(total, 256) : 152 * 8);
+    const int vec_ok = (ldx % 4 == 0) && (reinterpret_cast<uintptr_t>(x) % 16 == 0);
     SLK_TIMED("center_cast", st);
     if (split)
         k_center_cast<__half, 1><<<blocks, 256, 0, st>>>(x, n, d, ldx, mu, static_cast<__half*>(out),
-                                                        static_cast<__half*>(out_lo), ldo);
+                                                        static_cast<__half*>(out_lo), ldo, vec_ok);
     else
         k_center_cast<__nv_bfloat16, 0><<<blocks, 256, 0, st>>>(x, n, d, ldx, mu, static_cast<__nv_bfloat16*>(out),
-                                                               nullptr, ldo);
+                                                               nullptr, ldo, vec_ok);
     SLK_CHECK_LAUNCH();
 }
 
@@ -547,14 +572,19 @@ void launch_project_umma(const void* xa, const void* xa_lo, int64_t n, const voi
                                                                      col_tiles, Z, ldz, absmax, err);
     } else {
         static bool attr = false;
+        static int sms = 0;
         if (!attr) {
-            SLK_CHECK_CUDA(cudaFuncSetAttribute(k_umma_project<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                static_cast<int>(umma_smem_bytes<0>())));
+            SLK_CHECK_CUDA(cudaFuncSetAttribute(k_umma_project, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                static_cast<int>(umma_smem_bytes())));
+            int dev = 0;
+            SLK_CHECK_CUDA(cudaGetDevice(&dev));
+            SLK_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
             attr = true;
         }
+        const int64_t persistent = blocks < sms ? blocks : sms;
         SLK_TIMED("umma_project_bf16", st);
-        k_umma_project<0><<<grid, THREADS, umma_smem_bytes<0>(), st>>>(ma, mb, ma2, mb2, static_cast<int>(n), P, d,
-                                                                        col_tiles, Z, ldz, absmax, err);
+        k_umma_project<<<static_cast<unsigned>(persistent), THREADS, umma_smem_bytes(), st>>>(
+            ma, mb, static_cast<int>(n), P, d, col_tiles, static_cast<int>(blocks), Z, ldz, absmax, err);
     }
     SLK_CHECK_LAUNCH();
 }

@@ -389,10 +389,15 @@ FourierHost choose_gaussian(double sigma, int d, double R, int n_coeff_req, int 
     set_active_window(&fp);
     fp.mult.resize(Nc / 2);
     for (int k = 0; k < Nc / 2; ++k) fp.mult[k] = ck(k) / (fp.psi[k] * fp.psi[k]);
-    // method
+    // method (the NDFT kernels take bands of at most 64 coefficients)
     const int K = fp.k_hi - fp.k_lo + 1;
-    if (method == SLK_FOURIER_AUTO) method = (K <= 2 * fp.m) ? SLK_FOURIER_NDFT : SLK_FOURIER_NFFT;
-    if (method == SLK_FOURIER_NFFT && fp.W > fp.n_g) method = SLK_FOURIER_NDFT;
+    if (method == SLK_FOURIER_NDFT && K > 64)
+        fail(SLK_ERR_UNSUPPORTED, "the NDFT band has %d coefficients (at most 64); use the NFFT", K);
+    if (method == SLK_FOURIER_AUTO) method = (K <= 2 * fp.m && K <= 64) ? SLK_FOURIER_NDFT : SLK_FOURIER_NFFT;
+    if (method == SLK_FOURIER_NFFT && fp.W > fp.n_g) {
+        if (K > 64) fail(SLK_ERR_ACCURACY, "neither the NFFT window nor the NDFT band fits");
+        method = SLK_FOURIER_NDFT;
+    }
     fp.method = method;
     fp.model_err = fp.period_err + (method == SLK_FOURIER_NDFT ? trunc + dropped : trunc + fp.window_err);
     {
