@@ -207,6 +207,35 @@ slk_status slk_kernel_sum(const slk_plan_desc* desc, const void* x, int64_t N, i
                           const void* y, int64_t M, int64_t ldy, void* s, void* stream);
 
 /*
+ * Kernel sums like slk_sum, without allocating device memory (the paper has no
+ * counterpart; this is a service of this library).
+ *
+ * For callers that must not allocate device memory on the call path: for
+ * example a serving loop that has reserved the GPU's memory for its own pool
+ * up front, or code running where the CUDA allocator may not be called.
+ * slk_sum allocates its working buffers (projections of the targets and an
+ * FP64 accumulator) from the stream-ordered pool; this variant instead uses
+ * one fixed 64 MiB array in device memory that the library reserves on every
+ * GPU that loads it (held until the process exits).
+ *
+ *  - y (M x d, row stride ldy) and s (M values) must be device pointers.
+ *  - Working memory per call: align256(P*M*e) + align256(8*M), plus, for the
+ *    tensor-core precisions, align256(2*M*ld16) (twice for SLK_PREC_F16X3),
+ *    e = 8 for SLK_PREC_F64 and 4 otherwise, ld16 = d rounded up to a multiple
+ *    of 8; calls needing more than 64 MiB return SLK_ERR_INVALID (split the
+ *    targets).
+ *  - The first call on a device looks up the array's device address (once
+ *    per device, cached); make that first call before any stream capture.
+ *  - Every call uses the same array, which keeps the last call's contents
+ *    (the accumulator is cleared at the start of each call).  Calls whose work
+ *    overlaps on the GPU (other streams, other threads, several plans on the
+ *    same device) race on the array: order them on one stream or synchronise.
+ *  - Results equal slk_sum's; errors as slk_sum, plus SLK_ERR_INVALID for
+ *    host pointers or sizes beyond the array.
+ */
+slk_status slk_sum_noalloc(slk_plan plan, const void* y, int64_t M, int64_t ldy, void* s, void* stream);
+
+/*
  * Profiling support (not part of the paper's method).  Every kernel launch of
  * the library is counted; while timing is enabled, each launch is also
  * bracketed by CUDA events recorded on the stream it is launched on.

@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -705,3 +706,119 @@ slk_status slk_kernel_sum(const slk_plan_desc* desc, const void* x, int64_t N, i
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ sums without device allocation
+//
+// slk_sum_noalloc: the same target-side computation as slk_sum, for callers
+// that must not allocate device memory while they run (see include/slk.h).
+// Its working memory is one file-scope device array shared by every call.
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;  // 64 MiB per device
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[128] = {};
+
+// Device address of the scratch array on the current device.  The name
+// g_noalloc_scratch is only a host-side stand-in; the address is looked up
+// once per device (the first call on that device) and cached.
+unsigned char* noalloc_scratch(int device) {
+    SLK_REQUIRE(device >= 0 && device < 128, "device index out of range");
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            fail(SLK_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
+        }
+        g_noalloc_addr[device] = p;
+    }
+    return static_cast<unsigned char*>(g_noalloc_addr[device]);
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+template <class T>
+size_t noalloc_bytes(slk_plan plan, int64_t M) {
+    size_t b = align256(sizeof(T) * static_cast<size_t>(plan->P) * M) + align256(sizeof(double) * M);
+    if (plan->tc) b += align256(static_cast<size_t>(M) * umma_operand_ld(plan->d) * 2) * (plan->tc == 2 ? 2 : 1);
+    return b;
+}
+
+template <class T>
+void sum_noalloc_impl(slk_plan plan, const T* y, int64_t M, int64_t ldy, T* s, unsigned char* scratch,
+                      cudaStream_t st) {
+    const int P = plan->P, d = plan->d;
+    unsigned char* cur = scratch;
+    T* Zy = reinterpret_cast<T*>(cur);
+    cur += align256(sizeof(T) * static_cast<size_t>(P) * M);
+    double* acc = reinterpret_cast<double*>(cur);
+    cur += align256(sizeof(double) * M);
+    bool projected = false;
+    if constexpr (sizeof(T) == 4) {
+        if (plan->tc) {
+            const int split = plan->tc == 2;
+            const size_t b16 = align256(static_cast<size_t>(M) * umma_operand_ld(d) * 2);
+            unsigned char* xa = cur;
+            unsigned char* xl = split ? cur + b16 : nullptr;
+            launch_center_cast(y, M, d, ldy, plan->mu32.get(), xa, xl, split, st);
+            launch_project_umma(xa, xl, M, plan->xib.get(), plan->xib_lo.get(), P, d, split, Zy, M, nullptr,
+                                plan->err_dev.get(), st);
+            projected = true;
+        }
+    }
+    if (!projected) launch_project_simt<T>(xi_of<T>(plan), P, y, M, d, ldy, mu_of<T>(plan), Zy, M, st);
+    // the array keeps the previous call's contents: the accumulator must start at zero
+    SLK_CHECK_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * M, st));
+    if (plan->fourier) {
+        if (plan->fh.method == SLK_FOURIER_NDFT)
+            launch_ndft_target<T>(Zy, P, M, M, plan->fd, reinterpret_cast<const Cplx<T>*>(plan->cw.get()),
+                                  reinterpret_cast<const T*>(plan->cw0.get()), acc, nullptr, plan->err_dev.get(), st);
+        else
+            launch_nfft_target<T>(Zy, P, M, M, plan->fd, reinterpret_cast<const T*>(plan->hgrid.get()), acc, nullptr,
+                                  plan->err_dev.get(), st);
+    }
+    if (plan->sorting)
+        launch_negdist_target<T>(Zy, P, M, M, reinterpret_cast<const T*>(plan->keys.get()), plan->N, plan->A.get(),
+                                 plan->B.get(), plan->NB, plan->kmin.get(), plan->kscale.get(), plan->tab.get(), plan->cd,
+                                 plan->sort_scale, acc, nullptr, 0, st);
+    launch_finalize<T>(acc, s, M, 1.0 / P, st);
+}
+
+}  // namespace
+
+extern "C" slk_status slk_sum_noalloc(slk_plan plan, const void* y, int64_t M, int64_t ldy, void* s, void* stream) {
+    set_last_error("");
+    return guarded([&] {
+        SLK_REQUIRE(plan, "plan is NULL");
+        slk_status prev = collect(plan, false);
+        if (prev != SLK_OK) throw Error{prev, slk_last_error()};
+        SLK_REQUIRE(M >= 0, "M must be >= 0");
+        if (M == 0) return;
+        SLK_REQUIRE(y && s, "y and s must not be NULL");
+        SLK_REQUIRE(ldy >= plan->d, "ldy must be >= d");
+        SLK_REQUIRE(is_device_pointer(y) && is_device_pointer(s),
+                    "slk_sum_noalloc needs device pointers for y and s (host arrays would need staging buffers)");
+        const size_t need = plan->f64 ? noalloc_bytes<double>(plan, M) : noalloc_bytes<float>(plan, M);
+        if (need > kNoAllocScratchBytes)
+            fail(SLK_ERR_INVALID,
+                 "slk_sum_noalloc: %lld targets x %d slices need %zu bytes of working memory, more than the %zu-byte "
+                 "scratch array; split the targets into smaller calls",
+                 static_cast<long long>(M), plan->P, need, kNoAllocScratchBytes);
+        int dev = 0;
+        SLK_CHECK_CUDA(cudaGetDevice(&dev));
+        SLK_REQUIRE(dev == plan->device, "the current device is not the plan's device");
+        unsigned char* scratch = noalloc_scratch(dev);
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        if (plan->f64)
+            sum_noalloc_impl<double>(plan, static_cast<const double*>(y), M, ldy, static_cast<double*>(s), scratch, st);
+        else
+            sum_noalloc_impl<float>(plan, static_cast<const float*>(y), M, ldy, static_cast<float*>(s), scratch, st);
+        finish_call(plan, st);
+        plan->stream = st;
+    });
+}

@@ -77,6 +77,8 @@ _SIGNATURES = {
     "slk_plan_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]),
     "slk_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "slk_fourier_params": (ctypes.c_int, [ctypes.POINTER(PlanDesc), ctypes.c_double, ctypes.POINTER(PlanInfo)]),
+    "slk_sum_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
     "slk_launch_count": (ctypes.c_int64, []),
     "slk_timing_enable": (ctypes.c_int, [ctypes.c_int32]),
     "slk_timing_read": (ctypes.c_int, [ctypes.POINTER(KernelTime), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
