@@ -110,15 +110,25 @@ def plan_kwargs(wl, args):
                 n_coeff=wl.n_coeff, method=args.method or wl.method, directions=wl.xi)
 
 
-def algorithmic(wl, precision, kernel_name, launches_per_step):
-    """(amount per launch, unit, bound) of the algorithmic work of one launch."""
-    pts_per_launch = (wl.N + wl.M) / max(1, launches_per_step)
-    if kernel_name.startswith("gemm") or kernel_name.startswith("umma") or kernel_name.startswith("project"):
-        flops = 2.0 * pts_per_launch * wl.d * wl.P
-        bound = "tensor" if precision in ("bf16", "f16x3") else "alu"
-        return flops, "flop", bound
-    # 1-D summation kernels: bytes of the projected slice-points they read (4 B each)
-    return 4.0 * pts_per_launch * wl.P, "byte", "hbm"
+def algorithmic(wl, info, precision, kernel_name, launches_per_step):
+    """(algorithmic amount per launch, unit, bound) of one launch of a library kernel.
+
+    Units of work: a point (row of x or y) and a slice-point (one point on one slice).
+    Projection: 2 d P flop per point (tensor for BF16 / FP16x3, FP32 ALU otherwise).
+    NDFT source / target: one complex multiply-add per band coefficient, 8 K flop per
+    slice-point (FP32 ALU).  Centring cast: 4 d bytes read + 2 ld16 (x2 for the hi/lo
+    split) written per point.  Other kernels: the 4-byte projections they read."""
+    pts = (wl.N + wl.M) / max(1.0, launches_per_step)
+    if kernel_name.startswith(("gemm", "umma")):
+        bound = "tensor" if kernel_name.startswith("umma") else "alu"
+        return 2.0 * pts * wl.d * wl.P, "flop", bound
+    if kernel_name.startswith("ndft_source") or kernel_name.startswith("ndft_target"):
+        K = info["k_hi"] - info["k_lo"] + 1
+        return 8.0 * K * pts * wl.P, "flop", "alu"
+    if kernel_name.startswith("center_cast"):
+        ld16 = (wl.d + 7) // 8 * 8
+        return pts * (4.0 * wl.d + 2.0 * ld16 * (2 if precision == "f16x3" else 1)), "byte", "hbm"
+    return 4.0 * pts * wl.P, "byte", "hbm"
 
 
 def cpu_sample(wl, budget_s: float):
@@ -195,9 +205,13 @@ def run_ours(args):
     s = torch.empty(wl.M, dtype=x.dtype, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    gy = torch.empty_like(y) if args.grad else None
+
     def step():
         plan = slk.Plan(x, w, **kw)
         plan.sum(y, out=s, sync=False)
+        if args.grad:
+            plan.grad(y, out=gy, sync=False)
         plan.close()
 
     for _ in range(args.warmup):
@@ -247,10 +261,11 @@ def run_ours(args):
     if top:
         name, (n_launch, tot_ms) = top
         per_step = n_launch / args.steps
-        amount, unit, bound = algorithmic(wl, precision, name, per_step)
+        amount, unit, bound = algorithmic(wl, info, precision, name, per_step)
         avg_s = tot_ms / n_launch * 1e-3
         if bound == "tensor":
-            peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * (1.0 if precision == "bf16" else 1.0)
+            # a kernel timed inside a long step: the sustained dense BF16 figure (FP16 runs at the same rate)
+            peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
             achieved = amount / avg_s / 1e12
             runit = "TFLOP/s"
         elif bound == "alu":
@@ -276,9 +291,13 @@ def run_ours(args):
         sh = torch.empty(wl.M, dtype=xh.dtype).pin_memory()
         e2e_steps = max(1, min(args.steps, 5))
 
+        gh = torch.empty_like(yh).pin_memory() if args.grad else None
+
         def host_step():
             plan = slk.Plan(xh, wh, **kw)
             plan.sum(yh, out=sh, sync=True)
+            if args.grad:
+                plan.grad(yh, out=gh, sync=True)
             plan.close()
 
         host_step()
@@ -292,7 +311,7 @@ def run_ours(args):
         te = (time.perf_counter() - t0) / e2e_steps
         bi = xh.numel() * xh.element_size() + yh.numel() * yh.element_size() + wh.numel() * wh.element_size() + \
             wl.xi.size * 8
-        bo = sh.numel() * sh.element_size()
+        bo = sh.numel() * sh.element_size() + (gh.numel() * gh.element_size() if args.grad else 0)
         e2e = {"value": (wl.N + wl.M) * wl.P * world / te, "unit": "slice-points/s", "h2d_bytes_per_step": int(bi),
                "d2h_bytes_per_step": int(bo), "ms_per_step": te * 1e3}
 
@@ -310,7 +329,7 @@ def run_ours(args):
                            "P": wl.P, "n_coeff": info["n_coeff"], "method": {1: "nfft", 2: "ndft"}.get(info["method"]),
                            "parallelism": f"replicas{world}" if world > 1 else "single",
                            "l2": "inputs larger than L2 (no flush needed)",
-                           "model_error": info["model_error"]},
+                           "model_error": info["model_error"], "backward": bool(args.grad)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                 "kernels_ms_per_step": {k: v[1] / args.steps for k, v in kernels.items()}}
         print(json.dumps(line), flush=True)
@@ -330,6 +349,7 @@ def main():
     ap.add_argument("--N", type=int, default=None)
     ap.add_argument("--M", type=int, default=None)
     ap.add_argument("--P", type=int, default=None)
+    ap.add_argument("--grad", action="store_true", help="include the y-gradient (backward) in every step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
