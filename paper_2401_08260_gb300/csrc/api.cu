@@ -89,6 +89,7 @@ struct slk_plan_s {
     // tensor-core projection (BF16, or FP16 hi/lo split): 16-bit directions P x ldo
     int tc = 0;  // 0 SIMT, 1 BF16, 2 FP16 x3
     DevBuf<unsigned char> xib, xib_lo;
+    DevBuf<unsigned char> xit16;  // xi^T in BF16 (d x ld16(P)) for the tensor-core backward product
 
     // Fourier side (Gaussian, Laplacian smooth part)
     bool fourier = false;
@@ -102,10 +103,10 @@ struct slk_plan_s {
     // sorting side (negative distance, Laplacian non-smooth part)
     bool sorting = false;
     double sort_scale = 1.0;
-    DevBuf<unsigned char> keys;  // T P x N
-    DevBuf<double> A, B;         // P x (N + 1)
+    DevBuf<unsigned char> kw;  // sorted (key, w) pairs, P x N
+    DevBuf<double2> AB;        // FP64 prefix sums of w and w*key at bucket starts, P x (NB + 1)
     DevBuf<float> kmin, kscale;
-    DevBuf<int32_t> tab;
+    DevBuf<int32_t> tab;       // first sorted index of each bucket, P x (NB + 1)
     int NB = 0;
 
     // deferred device-side status
@@ -123,9 +124,9 @@ struct slk_plan_s {
     }
     int64_t device_bytes() const {
         return static_cast<int64_t>(xi64.bytes() + xi32.bytes() + mu64.bytes() + mu32.bytes() + xib.bytes() +
-                                    xib_lo.bytes() + coef.bytes() +
-                                    mult.bytes() + cw.bytes() + cw0.bytes() + hgrid.bytes() + keys.bytes() + A.bytes() +
-                                    B.bytes() + kmin.bytes() + kscale.bytes() + tab.bytes());
+                                    xib_lo.bytes() + xit16.bytes() + coef.bytes() +
+                                    mult.bytes() + cw.bytes() + cw0.bytes() + hgrid.bytes() + kw.bytes() + AB.bytes() +
+                                    kmin.bytes() + kscale.bytes() + tab.bytes());
     }
 };
 
@@ -292,25 +293,24 @@ template <class T>
 void plan_sort_source(slk_plan plan, const T* Zx, const T* w, cudaStream_t st) {
     const int P = plan->P;
     const int64_t N = plan->N;
-    plan->keys.alloc(sizeof(T) * P * N, st);
-    DevBuf<int32_t> idx(static_cast<size_t>(P) * N, st);
-    size_t sb = segmented_sort_scratch<T>(P, N);
-    {
-        DevBuf<unsigned char> scratch(sb, st);
-        launch_segmented_sort<T>(Zx, P, N, N, reinterpret_cast<T*>(plan->keys.get()), idx.get(), scratch.get(), sb, st);
-    }
-    plan->A.alloc(static_cast<size_t>(P) * (N + 1), st);
-    plan->B.alloc(static_cast<size_t>(P) * (N + 1), st);
-    launch_prefix_sums<T>(reinterpret_cast<const T*>(plan->keys.get()), idx.get(), w, P, N, plan->A.get(), plan->B.get(),
-                          st);
+    // about 8 sources per bucket
     int nb = 1;
-    while (nb * 16 < N && nb < (1 << 16)) nb <<= 1;
+    while (static_cast<int64_t>(nb) * 8 < N && nb < (1 << 22)) nb <<= 1;
     plan->NB = nb;
+    DevBuf<T> keys(static_cast<size_t>(P) * N, st);
+    DevBuf<int32_t> idx(static_cast<size_t>(P) * N, st);
+    {
+        size_t sb = segmented_sort_scratch<T>(P, N);
+        DevBuf<unsigned char> scratch(sb, st);
+        launch_segmented_sort<T>(Zx, P, N, N, keys.get(), idx.get(), scratch.get(), sb, st);
+    }
+    plan->kw.alloc(sorted_pairs_bytes<T>(P, N), st);
+    plan->AB.alloc(static_cast<size_t>(P) * (nb + 1), st);
     plan->kmin.alloc(P, st);
     plan->kscale.alloc(P, st);
     plan->tab.alloc(static_cast<size_t>(P) * (nb + 1), st);
-    launch_bucket_tables<T>(reinterpret_cast<const T*>(plan->keys.get()), P, N, nb, plan->kmin.get(),
-                            plan->kscale.get(), plan->tab.get(), st);
+    launch_sorted_pairs<T>(keys.get(), idx.get(), w, P, N, plan->kw.get(), nb, plan->kmin.get(), plan->kscale.get(),
+                           plan->tab.get(), plan->AB.get(), st);
 }
 
 template <class T>
@@ -342,6 +342,8 @@ void create_impl(slk_plan plan, const void* x_user, int64_t ldx, const void* w_u
             if (plan->tc == 2) plan->xib_lo.alloc(bytes, st);
             launch_center_cast(plan->xi32.get(), P, d, d, nullptr, plan->xib.get(), plan->xib_lo.get(), plan->tc == 2,
                                st);
+            plan->xit16.alloc(static_cast<size_t>(d) * umma_operand_ld(P) * 2, st);
+            launch_transpose_bf16(plan->xi32.get(), P, d, plan->xit16.get(), st);
         }
     }
     // project the sources (and find the largest |z| for the Fourier window)
@@ -391,8 +393,8 @@ void sum_impl(slk_plan plan, const void* y_user, int64_t M, int64_t ldy, void* s
                                   nullptr, plan->err_dev.get(), st);
     }
     if (plan->sorting)
-        launch_negdist_target<T>(Zy.get(), P, M, M, reinterpret_cast<const T*>(plan->keys.get()), plan->N, plan->A.get(),
-                                 plan->B.get(), plan->NB, plan->kmin.get(), plan->kscale.get(), plan->tab.get(), plan->cd,
+        launch_negdist_target<T>(Zy.get(), P, M, M, plan->kw.get(), plan->N, plan->AB.get(), plan->NB,
+                                 plan->kmin.get(), plan->kscale.get(), plan->tab.get(), plan->cd,
                                  plan->sort_scale, acc.get(), nullptr, 0, st);
     const bool s_dev = is_device_pointer(s_user);
     if (s_dev) {
@@ -434,11 +436,29 @@ void grad_impl(slk_plan plan, const void* y_user, int64_t M, int64_t ldy, const 
                                   G.get(), plan->err_dev.get(), st);
     }
     if (plan->sorting)
-        launch_negdist_target<T>(Zy.get(), P, M, M, reinterpret_cast<const T*>(plan->keys.get()), plan->N, plan->A.get(),
-                                 plan->B.get(), plan->NB, plan->kmin.get(), plan->kscale.get(), plan->tab.get(), plan->cd,
+        launch_negdist_target<T>(Zy.get(), P, M, M, plan->kw.get(), plan->N, plan->AB.get(), plan->NB,
+                                 plan->kmin.get(), plan->kscale.get(), plan->tab.get(), plan->cd,
                                  plan->sort_scale, nullptr, G.get(), plan->fourier ? 1 : 0, st);
     InView<T> gsv(gs_user, gs_user ? M : 0, 1, 1, st);
     const bool g_dev = is_device_pointer(gy_user);
+    if constexpr (sizeof(T) == 4) {
+        if (plan->tc) {
+            // backward product on tensor cores (BF16 operands, FP32 accumulate)
+            DevBuf<unsigned char> g16(static_cast<size_t>(M) * umma_operand_ld(P) * 2, st);
+            launch_center_cast(G.get(), M, P, P, nullptr, g16.get(), nullptr, 0, st);
+            DevBuf<T> gy_tmp(g_dev ? 0 : static_cast<size_t>(M) * d, st);
+            T* out = g_dev ? static_cast<T*>(gy_user) : gy_tmp.get();
+            const int64_t ldo = g_dev ? ldg : d;
+            launch_grad_umma(g16.get(), M, P, plan->xit16.get(), d, gs_user ? gsv.ptr : nullptr, 1.0 / P, out, ldo,
+                             plan->err_dev.get(), st);
+            if (!g_dev) {
+                SLK_CHECK_CUDA(cudaMemcpy2DAsync(gy_user, sizeof(T) * ldg, out, sizeof(T) * d, sizeof(T) * d, M,
+                                                 cudaMemcpyDeviceToHost, st));
+                SLK_CHECK_CUDA(cudaStreamSynchronize(st));
+            }
+            return;
+        }
+    }
     if (g_dev) {
         launch_grad_gemm<T>(G.get(), M, P, xi_of<T>(plan), d, gs_user ? gsv.ptr : nullptr, 1.0 / P,
                             static_cast<T*>(gy_user), ldg, st);
@@ -783,8 +803,8 @@ void sum_noalloc_impl(slk_plan plan, const T* y, int64_t M, int64_t ldy, T* s, u
                                   plan->err_dev.get(), st);
     }
     if (plan->sorting)
-        launch_negdist_target<T>(Zy, P, M, M, reinterpret_cast<const T*>(plan->keys.get()), plan->N, plan->A.get(),
-                                 plan->B.get(), plan->NB, plan->kmin.get(), plan->kscale.get(), plan->tab.get(), plan->cd,
+        launch_negdist_target<T>(Zy, P, M, M, plan->kw.get(), plan->N, plan->AB.get(), plan->NB,
+                                 plan->kmin.get(), plan->kscale.get(), plan->tab.get(), plan->cd,
                                  plan->sort_scale, acc, nullptr, 0, st);
     launch_finalize<T>(acc, s, M, 1.0 / P, st);
 }

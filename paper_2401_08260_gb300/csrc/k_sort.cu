@@ -3,15 +3,17 @@
 //
 // Per slice the sources are sorted by their projection (segmented LSD radix
 // sort on order-preserving key bits, 8-bit digits, stable, with the source
-// index as payload), FP64 exclusive prefix sums
-//     A_i = sum_{j<i} w_(j),   B_i = sum_{j<i} w_(j) z_(j)      (sorted order)
-// are formed, and each target z gets
+// index as payload) and stored as (key, w) pairs in sorted order.  The sorted
+// range of each slice is cut into NB buckets of equal key width; FP64
+// exclusive prefix sums of w and w z are kept only at bucket starts:
+//     A_b = sum over sources in buckets < b of w,   B_b = same of w z.
+// A target z in bucket b then has
+//     A_< = A_b + sum_{sources of bucket b with key < z} w,   B_< likewise,
+// (a short scan of the sorted bucket, stopped at the insertion point) and
 //     t(z) = -c_d sum_n w_n |z - x_n| = -c_d [ z (2 A_< - W) - (2 B_< - S) ],
-// with A_<, B_< the prefix at the first source >= z, W = A_n, S = B_n.  This is
-// Algorithm 2 regrouped: splitting the sum at z gives
+// W, S the totals.  This is Algorithm 2 regrouped: splitting the sum at z gives
 //     sum_{x<z} w (z - x) + sum_{x>=z} w (x - z) = z (2 A_< - W) - (2 B_< - S),
-// the same value without the joint sort of sources and targets (targets are
-// located by a bucketed binary search instead).
+// the same value without the joint sort of sources and targets.
 #include "kernels.cuh"
 
 namespace slk {
@@ -155,97 +157,20 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const U* __restric
     }
 }
 
-// ------------------------------------------------------------ prefix sums
-
-__device__ inline void block_scan_excl2(double a, double b, double* ea, double* eb, double* ta, double* tb) {
-    __shared__ double wa[32], wb[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double xa = a, xb = b;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        double ya = __shfl_up_sync(0xffffffffu, xa, o), yb = __shfl_up_sync(0xffffffffu, xb, o);
-        if (lane >= o) {
-            xa += ya;
-            xb += yb;
-        }
-    }
-    if (lane == 31) {
-        wa[warp] = xa;
-        wb[warp] = xb;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-        double sa = lane < nw ? wa[lane] : 0.0, sb = lane < nw ? wb[lane] : 0.0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            double ya = __shfl_up_sync(0xffffffffu, sa, o), yb = __shfl_up_sync(0xffffffffu, sb, o);
-            if (lane >= o) {
-                sa += ya;
-                sb += yb;
-            }
-        }
-        wa[lane] = sa;
-        wb[lane] = sb;
-    }
-    __syncthreads();
-    *ea = (warp ? wa[warp - 1] : 0.0) + xa - a;
-    *eb = (warp ? wb[warp - 1] : 0.0) + xb - b;
-    *ta = wa[(blockDim.x >> 5) - 1];
-    *tb = wb[(blockDim.x >> 5) - 1];
-    __syncthreads();
-}
+// ------------------------------------------------------------ sorted pairs and bucket sums
 
 template <class T>
-__global__ void __launch_bounds__(1024) k_prefix(const T* __restrict__ keys, const int32_t* __restrict__ idx,
-                                                const T* __restrict__ w, int64_t n, double* __restrict__ A,
-                                                double* __restrict__ B) {
-    constexpr int IT = 4;
-    const int p = blockIdx.x;
-    const T* ks = keys + static_cast<int64_t>(p) * n;
-    const int32_t* is = idx + static_cast<int64_t>(p) * n;
-    double* As = A + static_cast<int64_t>(p) * (n + 1);
-    double* Bs = B + static_cast<int64_t>(p) * (n + 1);
-    double ca = 0.0, cb = 0.0;
-    for (int64_t base = 0; base < n; base += 1024 * IT) {
-        double va[IT], vb[IT];
-        double la = 0.0, lb = 0.0;
-#pragma unroll
-        for (int j = 0; j < IT; ++j) {
-            int64_t i = base + threadIdx.x * IT + j;
-            double v = 0.0, z = 0.0;
-            if (i < n) {
-                v = static_cast<double>(w[is[i]]);
-                z = static_cast<double>(ks[i]);
-            }
-            va[j] = v;
-            vb[j] = v * z;
-            la += va[j];
-            lb += vb[j];
-        }
-        double ea, eb, ta, tb;
-        block_scan_excl2(la, lb, &ea, &eb, &ta, &tb);
-        double ra = ca + ea, rb = cb + eb;
-#pragma unroll
-        for (int j = 0; j < IT; ++j) {
-            int64_t i = base + threadIdx.x * IT + j;
-            if (i < n) {
-                As[i] = ra;
-                Bs[i] = rb;
-            }
-            ra += va[j];
-            rb += vb[j];
-        }
-        ca += ta;
-        cb += tb;
-    }
-    if (threadIdx.x == 0) {
-        As[n] = ca;
-        Bs[n] = cb;
-    }
-}
+struct KW {
+    T key, w;
+};
 
-// ------------------------------------------------------------ bucket tables
+template <class T>
+__global__ void k_gather_pairs(const T* __restrict__ keys, const int32_t* __restrict__ idx, const T* __restrict__ w,
+                               int64_t total, int64_t n, KW<T>* __restrict__ kw) {
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        kw[e] = KW<T>{keys[e], w[idx[e]]};
+}
 
 __device__ inline int bucket_of(float z, float kmin, float kscale, int NB) {
     float f = (z - kmin) * kscale;
@@ -254,84 +179,152 @@ __device__ inline int bucket_of(float z, float kmin, float kscale, int NB) {
 }
 
 template <class T>
-__global__ void k_bucket_minmax(const T* __restrict__ keys, int P, int64_t n, int NB, float* kmin, float* kscale) {
+__global__ void k_bucket_minmax(const KW<T>* __restrict__ kw, int P, int64_t n, int NB, float* kmin, float* kscale) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-        float lo = static_cast<float>(keys[static_cast<int64_t>(p) * n]);
-        float hi = static_cast<float>(keys[static_cast<int64_t>(p) * n + n - 1]);
+        float lo = static_cast<float>(kw[static_cast<int64_t>(p) * n].key);
+        float hi = static_cast<float>(kw[static_cast<int64_t>(p) * n + n - 1].key);
         kmin[p] = lo;
         kscale[p] = hi > lo ? static_cast<float>(NB) / (hi - lo) : 0.0f;
     }
 }
 
+// tab[p][b] = first sorted index whose bucket is >= b (b = 0..NB)
 template <class T>
-__global__ void k_bucket_tab(const T* __restrict__ keys, int64_t n, int NB, const float* __restrict__ kmin,
+__global__ void k_bucket_tab(const KW<T>* __restrict__ kw, int64_t n, int NB, const float* __restrict__ kmin,
                              const float* __restrict__ kscale, int32_t* __restrict__ tab) {
     const int p = blockIdx.y;
-    const T* ks = keys + static_cast<int64_t>(p) * n;
+    const KW<T>* ks = kw + static_cast<int64_t>(p) * n;
     int32_t* tb = tab + static_cast<int64_t>(p) * (NB + 1);
     const float lo = kmin[p], sc = kscale[p];
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int b = bucket_of(static_cast<float>(ks[i]), lo, sc, NB);
-        const int bp = i > 0 ? bucket_of(static_cast<float>(ks[i - 1]), lo, sc, NB) : -1;
+        const int b = bucket_of(static_cast<float>(ks[i].key), lo, sc, NB);
+        const int bp = i > 0 ? bucket_of(static_cast<float>(ks[i - 1].key), lo, sc, NB) : -1;
         for (int q = bp + 1; q <= b; ++q) tb[q] = static_cast<int32_t>(i);
         if (i == n - 1)
             for (int q = b + 1; q <= NB; ++q) tb[q] = static_cast<int32_t>(n);
     }
 }
 
+// per bucket sums of w and w z in FP64 (fixed order: the sorted order)
+template <class T>
+__global__ void k_bucket_sums(const KW<T>* __restrict__ kw, int64_t n, int NB, const int32_t* __restrict__ tab,
+                              double2* __restrict__ AB) {
+    const int p = blockIdx.y;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < NB; b += gridDim.x * blockDim.x) {
+        const int32_t* tb = tab + static_cast<int64_t>(p) * (NB + 1);
+        const KW<T>* ks = kw + static_cast<int64_t>(p) * n;
+        double a = 0.0, c = 0.0;
+        for (int32_t i = tb[b]; i < tb[b + 1]; ++i) {
+            const double wv = static_cast<double>(ks[i].w);
+            a += wv;
+            c += wv * static_cast<double>(ks[i].key);
+        }
+        AB[static_cast<int64_t>(p) * (NB + 1) + b] = make_double2(a, c);
+    }
+}
+
+// exclusive FP64 scan of the bucket sums of one slice, in place; AB[NB] = totals
+__global__ void __launch_bounds__(1024) k_bucket_prefix(double2* __restrict__ AB, int NB) {
+    __shared__ double wa[32], wb[32];
+    __shared__ double ca_s, cb_s;
+    double2* row = AB + static_cast<int64_t>(blockIdx.x) * (NB + 1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        ca_s = 0.0;
+        cb_s = 0.0;
+    }
+    __syncthreads();
+    for (int base = 0; base < NB; base += 1024) {
+        const int b = base + threadIdx.x;
+        const double2 v = b < NB ? row[b] : make_double2(0.0, 0.0);
+        double xa = v.x, xb = v.y;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double ya = __shfl_up_sync(0xffffffffu, xa, o), yb = __shfl_up_sync(0xffffffffu, xb, o);
+            if (lane >= o) {
+                xa += ya;
+                xb += yb;
+            }
+        }
+        if (lane == 31) {
+            wa[warp] = xa;
+            wb[warp] = xb;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double sa = wa[lane], sb = wb[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double ya = __shfl_up_sync(0xffffffffu, sa, o), yb = __shfl_up_sync(0xffffffffu, sb, o);
+                if (lane >= o) {
+                    sa += ya;
+                    sb += yb;
+                }
+            }
+            wa[lane] = sa;
+            wb[lane] = sb;
+        }
+        __syncthreads();
+        const double ca = ca_s, cb = cb_s;
+        const double ea = ca + (warp ? wa[warp - 1] : 0.0) + xa - v.x;
+        const double eb = cb + (warp ? wb[warp - 1] : 0.0) + xb - v.y;
+        if (b < NB) row[b] = make_double2(ea, eb);
+        __syncthreads();
+        if (threadIdx.x == 1023) {
+            ca_s = ea + v.x;
+            cb_s = eb + v.y;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) row[NB] = make_double2(ca_s, cb_s);
+}
+
 // ------------------------------------------------------------ targets
 
+// Slices [p0, p1): for target m, bucket b of z; A_< and B_< from the bucket's FP64
+// prefix plus the sorted pairs of bucket b below z (and A_<= for the gradient).
 template <class T>
-__device__ inline int64_t lower_bound_in(const T* ks, int64_t lo, int64_t hi, T z) {
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (ks[mid] < z) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-template <class T>
-__device__ inline int64_t upper_bound_in(const T* ks, int64_t lo, int64_t hi, T z) {
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (ks[mid] <= z) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-template <class T>
-__global__ void __launch_bounds__(256) k_negdist_target(const T* __restrict__ Z, int P, int64_t n, int64_t ldz,
-                                                       const T* __restrict__ keys, int64_t nx,
-                                                       const double* __restrict__ A, const double* __restrict__ B,
-                                                       int NB, const float* __restrict__ kmin,
-                                                       const float* __restrict__ kscale,
+__global__ void __launch_bounds__(256) k_negdist_target(const T* __restrict__ Z, int P, int p0, int p1, int64_t n,
+                                                       int64_t ldz, const KW<T>* __restrict__ kw, int64_t nx,
+                                                       const double2* __restrict__ AB, int NB,
+                                                       const float* __restrict__ kmin, const float* __restrict__ kscale,
                                                        const int32_t* __restrict__ tab, double cd, double scale,
-                                                       double* __restrict__ acc, T* __restrict__ G,
-                                                       int accumulate_G) {
+                                                       double* __restrict__ acc, T* __restrict__ G, int accumulate_G) {
     const int64_t m = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (m >= n) return;
     double sum = 0.0;
-    for (int p = 0; p < P; ++p) {
+    for (int p = p0; p < p1; ++p) {
         const T z = Z[static_cast<int64_t>(p) * ldz + m];
-        const T* ks = keys + static_cast<int64_t>(p) * nx;
+        const KW<T>* ks = kw + static_cast<int64_t>(p) * nx;
         const int32_t* tb = tab + static_cast<int64_t>(p) * (NB + 1);
+        const double2* ab = AB + static_cast<int64_t>(p) * (NB + 1);
         const int b = bucket_of(static_cast<float>(z), kmin[p], kscale[p], NB);
-        const int64_t lo = tb[b], hi = tb[b + 1];
-        const int64_t l = lower_bound_in(ks, lo, hi, z);
-        const double* Ap = A + static_cast<int64_t>(p) * (nx + 1);
-        const double W = Ap[nx];
-        const double Al = Ap[l];
+        const int32_t hi = tb[b + 1];
+        int32_t i = tb[b];
+        T a = T(0), bz = T(0);
+        for (; i < hi; ++i) {
+            const KW<T> e = ks[i];
+            if (!(e.key < z)) break;
+            a += e.w;
+            bz += e.w * e.key;
+        }
+        const double2 base = ab[b], tot = ab[NB];
+        const double Al = base.x + static_cast<double>(a);
         if (G) {
-            const int64_t u = upper_bound_in(ks, l, hi, z);
-            const double g = scale * cd * (W - Al - Ap[u]);
+            T aeq = T(0);
+            for (; i < hi; ++i) {
+                const KW<T> e = ks[i];
+                if (e.key != z) break;
+                aeq += e.w;
+            }
+            const double g = scale * cd * (tot.x - 2.0 * Al - static_cast<double>(aeq));
             T* gp = G + m * P + p;
             *gp = accumulate_G ? static_cast<T>(static_cast<double>(*gp) + g) : static_cast<T>(g);
         } else {
-            const double* Bp = B + static_cast<int64_t>(p) * (nx + 1);
+            const double Bl = base.y + static_cast<double>(bz);
             const double zd = static_cast<double>(z);
-            sum += -cd * (zd * (2.0 * Al - W) - (2.0 * Bp[l] - Bp[nx]));
+            sum += -cd * (zd * (2.0 * Al - tot.x) - (2.0 * Bl - tot.y));
         }
     }
     if (!G) acc[m] += scale * sum;
@@ -411,53 +404,74 @@ void launch_segmented_sort(const T* keys_in, int P, int64_t n, int64_t ldk, T* k
 }
 
 template <class T>
-void launch_prefix_sums(const T* keys, const int32_t* idx, const T* w, int P, int64_t n, double* A, double* B,
-                        cudaStream_t st) {
-    {
-        SLK_TIMED("prefix", st);
-        k_prefix<T><<<P, 1024, 0, st>>>(keys, idx, w, n, A, B);
-    }
-    SLK_CHECK_LAUNCH();
+int64_t sorted_pairs_bytes(int P, int64_t n) {
+    return static_cast<int64_t>(sizeof(KW<T>)) * P * n;
 }
 
 template <class T>
-void launch_bucket_tables(const T* keys, int P, int64_t n, int NB, float* kmin, float* kscale, int32_t* tab,
-                          cudaStream_t st) {
+void launch_sorted_pairs(const T* keys, const int32_t* idx, const T* w, int P, int64_t n, void* kw, int NB,
+                         float* kmin, float* kscale, int32_t* tab, double2* AB, cudaStream_t st) {
+    const int64_t total = static_cast<int64_t>(P) * n;
+    KW<T>* pairs = static_cast<KW<T>*>(kw);
+    {
+        SLK_TIMED("gather_pairs", st);
+        k_gather_pairs<T><<<static_cast<unsigned>(ceil_div(total, 256) < 16384 ? ceil_div(total, 256) : 16384), 256, 0,
+                            st>>>(keys, idx, w, total, n, pairs);
+    }
+    SLK_CHECK_LAUNCH();
     {
         SLK_TIMED("bucket_minmax", st);
-        k_bucket_minmax<T><<<static_cast<unsigned>(ceil_div(P, 128)), 128, 0, st>>>(keys, P, n, NB, kmin, kscale);
+        k_bucket_minmax<T><<<static_cast<unsigned>(ceil_div(P, 128)), 128, 0, st>>>(pairs, P, n, NB, kmin, kscale);
     }
     SLK_CHECK_LAUNCH();
-    dim3 g(static_cast<unsigned>(ceil_div(n, 256) < 1024 ? ceil_div(n, 256) : 1024), P);
     {
         SLK_TIMED("bucket_tab", st);
-        k_bucket_tab<T><<<g, 256, 0, st>>>(keys, n, NB, kmin, kscale, tab);
+        dim3 g(static_cast<unsigned>(ceil_div(n, 256) < 1024 ? ceil_div(n, 256) : 1024), P);
+        k_bucket_tab<T><<<g, 256, 0, st>>>(pairs, n, NB, kmin, kscale, tab);
+    }
+    SLK_CHECK_LAUNCH();
+    {
+        SLK_TIMED("bucket_sums", st);
+        dim3 g(static_cast<unsigned>(ceil_div(NB, 256)), P);
+        k_bucket_sums<T><<<g, 256, 0, st>>>(pairs, n, NB, tab, AB);
+    }
+    SLK_CHECK_LAUNCH();
+    {
+        SLK_TIMED("bucket_prefix", st);
+        k_bucket_prefix<<<P, 1024, 0, st>>>(AB, NB);
     }
     SLK_CHECK_LAUNCH();
 }
 
 template <class T>
-void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const T* keys, int64_t nx, const double* A,
-                           const double* B, int NB, const float* kmin, const float* kscale, const int32_t* tab,
-                           double cd, double scale, double* acc, T* G, int accumulate_G, cudaStream_t st) {
+void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const void* kw, int64_t nx, const double2* AB,
+                           int NB, const float* kmin, const float* kscale, const int32_t* tab, double cd, double scale,
+                           double* acc, T* G, int accumulate_G, cudaStream_t st) {
     if (n <= 0) return;
-    {
-        SLK_TIMED("negdist_target", st);
+    // slices per launch: keep one batch's pairs (the randomly accessed state) within ~64 MB of L2
+    const int64_t per_slice = static_cast<int64_t>(sizeof(KW<T>)) * nx + static_cast<int64_t>(NB + 1) * 20;
+    int batch = static_cast<int>((int64_t(64) << 20) / (per_slice > 0 ? per_slice : 1));
+    if (batch < 1) batch = 1;
+    if (batch > P) batch = P;
+    for (int p0 = 0; p0 < P; p0 += batch) {
+        const int p1 = p0 + batch < P ? p0 + batch : P;
+        SLK_TIMED(G ? "negdist_target_grad" : "negdist_target", st);
         k_negdist_target<T><<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, st>>>(
-            Z, P, n, ldz, keys, nx, A, B, NB, kmin, kscale, tab, cd, scale, acc, G, accumulate_G);
+            Z, P, p0, p1, n, ldz, static_cast<const KW<T>*>(kw), nx, AB, NB, kmin, kscale, tab, cd, scale, acc, G,
+            accumulate_G);
+        SLK_CHECK_LAUNCH();
     }
-    SLK_CHECK_LAUNCH();
 }
 
 #define SLK_INST(T)                                                                                                   \
     template size_t segmented_sort_scratch<T>(int, int64_t);                                                          \
     template void launch_segmented_sort<T>(const T*, int, int64_t, int64_t, T*, int32_t*, void*, size_t, cudaStream_t); \
-    template void launch_prefix_sums<T>(const T*, const int32_t*, const T*, int, int64_t, double*, double*,            \
-                                        cudaStream_t);                                                                \
-    template void launch_bucket_tables<T>(const T*, int, int64_t, int, float*, float*, int32_t*, cudaStream_t);       \
-    template void launch_negdist_target<T>(const T*, int, int64_t, int64_t, const T*, int64_t, const double*,          \
-                                           const double*, int, const float*, const float*, const int32_t*, double,    \
-                                           double, double*, T*, int, cudaStream_t);
+    template int64_t sorted_pairs_bytes<T>(int, int64_t);                                                             \
+    template void launch_sorted_pairs<T>(const T*, const int32_t*, const T*, int, int64_t, void*, int, float*, float*, \
+                                         int32_t*, double2*, cudaStream_t);                                           \
+    template void launch_negdist_target<T>(const T*, int, int64_t, int64_t, const void*, int64_t, const double2*, int, \
+                                           const float*, const float*, const int32_t*, double, double, double*, T*,   \
+                                           int, cudaStream_t);
 SLK_INST(float)
 SLK_INST(double)
 #undef SLK_INST

@@ -121,6 +121,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+template <class Half>
+__device__ __forceinline__ Half to_half(float v);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_half<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half to_half<__half>(float v) { return __float2half_rn(v); }
+
 struct Smem {
     // follows the stage buffers (each stage: A tile then B tile, 1024-byte aligned)
     uint64_t full[STAGES_1];
@@ -134,10 +141,14 @@ struct Smem {
 // (column tile fastest, so the CTAs that share a block of points run together and the
 // second read of A hits L2).  Two 256-column TMEM accumulators alternate between tiles:
 // the epilogue of one tile overlaps the MMAs of the next.
+// ROWMAJOR = false: Z[col * ldz + row] (slice-major projections);
+// ROWMAJOR = true:  Z[row * ldz + col] * rowscale(row), rowscale = scale * (rs ? rs[row] : 1)
+// (the backward product, rows = targets, columns = coordinates).
+template <bool ROWMAJOR>
 __global__ void __launch_bounds__(THREADS, 1)
     k_umma_project(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int n, int P,
                    int d, int col_tiles, int tiles, float* __restrict__ Z, int64_t ldz, float* __restrict__ absmax,
-                   unsigned* __restrict__ err) {
+                   unsigned* __restrict__ err, const float* __restrict__ rs, float scale) {
     constexpr int STAGES = STAGES_1;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -235,16 +246,31 @@ __global__ void __launch_bounds__(THREADS, 1)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const float rsc = ROWMAJOR && row < n ? scale * (rs ? rs[row] : 1.0f) : 1.0f;
             for (int c = 0; c < BN; c += 32) {
                 float v[32];
                 tmem_ld32(tmem + lane_off + b * BN + c, v);
                 if (row < n) {
+                    if constexpr (ROWMAJOR) {
+                        float* out = Z + static_cast<int64_t>(row) * ldz + col0 + c;
+                        if (col0 + c + 32 <= P && (ldz % 4) == 0) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int p = col0 + c + j;
-                        if (p < P) {
-                            Z[static_cast<int64_t>(p) * ldz + row] = v[j];
-                            mx = fmaxf(mx, fabsf(v[j]));
+                            for (int j = 0; j < 32; j += 4)
+                                *reinterpret_cast<float4*>(out + j) =
+                                    make_float4(v[j] * rsc, v[j + 1] * rsc, v[j + 2] * rsc, v[j + 3] * rsc);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                if (col0 + c + j < P) out[j] = v[j] * rsc;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int p = col0 + c + j;
+                            if (p < P) {
+                                Z[static_cast<int64_t>(p) * ldz + row] = v[j];
+                                mx = fmaxf(mx, fabsf(v[j]));
+                            }
                         }
                     }
                 }
@@ -453,12 +479,6 @@ size_t x3_smem_bytes() {
 // centre and convert: out[i][k] = (16-bit)(x[i][k] - mu[k]) for k < d, 0 for d <= k < ldo;
 // SPLIT also writes the scaled low part 2^11 (x - mu - hi) into out_lo.  One thread
 // converts 8 consecutive elements of a row (one 16-byte store per output).
-template <class Half>
-__device__ __forceinline__ Half to_half(float v);
-template <>
-__device__ __forceinline__ __nv_bfloat16 to_half<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
-template <>
-__device__ __forceinline__ __half to_half<__half>(float v) { return __float2half_rn(v); }
 
 template <class Half, int SPLIT>
 __global__ void __launch_bounds__(256) k_center_cast(const float* __restrict__ x, int64_t n, int d, int64_t ldx,
@@ -524,9 +544,62 @@ size_t umma_smem_bytes() {
     return 1024 + STAGES_1 * (A_BYTES + B_BYTES) + sizeof(Smem);
 }
 
+// SM count of the current device; sets the shared-memory limit of the persistent kernel once
+template <bool ROWMAJOR>
+int sm_count() {
+    static int sms[128] = {};
+    int dev = 0;
+    SLK_CHECK_CUDA(cudaGetDevice(&dev));
+    SLK_REQUIRE(dev >= 0 && dev < 128, "device index out of range");
+    if (!sms[dev]) {
+        SLK_CHECK_CUDA(cudaFuncSetAttribute(k_umma_project<ROWMAJOR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            static_cast<int>(umma_smem_bytes())));
+        SLK_CHECK_CUDA(cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev));
+    }
+    return sms[dev];
+}
+
+template <class Half>
+__global__ void k_transpose_cast(const float* __restrict__ src, int rows, int cols, Half* __restrict__ dst, int ldd) {
+    // dst[c][r] = src[r][c] for r < rows, 0 for rows <= r < ldd
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < static_cast<int64_t>(cols) * ldd;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int c = static_cast<int>(e / ldd), r = static_cast<int>(e % ldd);
+        dst[e] = to_half<Half>(r < rows ? src[static_cast<int64_t>(r) * cols + c] : 0.0f);
+    }
+}
+
 }  // namespace
 
 int64_t umma_operand_ld(int d) { return (d + 7) / 8 * 8; }
+
+void launch_transpose_bf16(const float* src, int rows, int cols, void* dst, cudaStream_t st) {
+    const int ldd = static_cast<int>(umma_operand_ld(rows));
+    const int64_t total = static_cast<int64_t>(cols) * ldd;
+    SLK_TIMED("transpose_cast", st);
+    k_transpose_cast<__nv_bfloat16><<<static_cast<unsigned>(ceil_div(total, 256) < 4096 ? ceil_div(total, 256) : 4096),
+                                      256, 0, st>>>(src, rows, cols, static_cast<__nv_bfloat16*>(dst), ldd);
+    SLK_CHECK_LAUNCH();
+}
+
+void launch_grad_umma(const void* g16, int64_t M, int P, const void* xit16, int d, const float* gs, double scale,
+                      float* gy, int64_t ldg, unsigned* err, cudaStream_t st) {
+    if (M <= 0) return;
+    SLK_REQUIRE(M < (int64_t(1) << 31), "too many targets for one backward product");
+    const int64_t ld = umma_operand_ld(P);
+    CUtensorMap ma = make_map(g16, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, M, P, ld, BM);
+    CUtensorMap mb = make_map(xit16, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, d, P, ld, BN);
+    const int col_tiles = static_cast<int>(ceil_div(d, BN));
+    const int64_t blocks = ceil_div(M, BM) * col_tiles;
+    SLK_REQUIRE(blocks < (int64_t(1) << 31), "too many targets");
+    const int sms = sm_count<true>();
+    const int64_t persistent = blocks < sms ? blocks : sms;
+    SLK_TIMED("umma_grad_bf16", st);
+    k_umma_project<true><<<static_cast<unsigned>(persistent), THREADS, umma_smem_bytes(), st>>>(
+        ma, mb, static_cast<int>(M), d, P, col_tiles, static_cast<int>(blocks), gy, ldg, nullptr, err, gs,
+        static_cast<float>(scale));
+    SLK_CHECK_LAUNCH();
+}
 
 void launch_center_cast(const float* x, int64_t n, int d, int64_t ldx, const float* mu, void* out, void* out_lo,
                         int split, cudaStream_t st) {
@@ -571,20 +644,11 @@ void launch_project_umma(const void* xa, const void* xa_lo, int64_t n, const voi
         k_umma_project_x3<<<grid, X3_THREADS, x3_smem_bytes(), st>>>(ma, mb, ma2, mb2, static_cast<int>(n), P, d,
                                                                      col_tiles, Z, ldz, absmax, err);
     } else {
-        static bool attr = false;
-        static int sms = 0;
-        if (!attr) {
-            SLK_CHECK_CUDA(cudaFuncSetAttribute(k_umma_project, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                static_cast<int>(umma_smem_bytes())));
-            int dev = 0;
-            SLK_CHECK_CUDA(cudaGetDevice(&dev));
-            SLK_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-            attr = true;
-        }
+        const int sms = sm_count<false>();
         const int64_t persistent = blocks < sms ? blocks : sms;
         SLK_TIMED("umma_project_bf16", st);
-        k_umma_project<<<static_cast<unsigned>(persistent), THREADS, umma_smem_bytes(), st>>>(
-            ma, mb, static_cast<int>(n), P, d, col_tiles, static_cast<int>(blocks), Z, ldz, absmax, err);
+        k_umma_project<false><<<static_cast<unsigned>(persistent), THREADS, umma_smem_bytes(), st>>>(
+            ma, mb, static_cast<int>(n), P, d, col_tiles, static_cast<int>(blocks), Z, ldz, absmax, err, nullptr, 1.0f);
     }
     SLK_CHECK_LAUNCH();
 }

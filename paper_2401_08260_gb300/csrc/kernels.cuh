@@ -47,6 +47,13 @@ void launch_center_cast(const float* x, int64_t n, int d, int64_t ldx, const flo
 void launch_project_umma(const void* xa, const void* xa_lo, int64_t n, const void* xib, const void* xib_lo, int P,
                          int d, int split, float* Z, int64_t ldz, float* absmax, unsigned* err, cudaStream_t st);
 
+// dst[c][r] = BF16(src[r][c]) (rows x cols FP32 in; cols x ld16(rows) out, zero padded).
+void launch_transpose_bf16(const float* src, int rows, int cols, void* dst, cudaStream_t st);
+// Backward product on tensor cores: gy[m][k] = scale * gs[m] * sum_p G[m][p] xi[p][k] with G (M x P)
+// and xi^T (d x P) in BF16 (row pitch ld16(P)); gs may be NULL (ones).
+void launch_grad_umma(const void* g16, int64_t M, int P, const void* xit16, int d, const float* gs, double scale,
+                      float* gy, int64_t ldg, unsigned* err, cudaStream_t st);
+
 // ------------------------------------------------------------ k_fourier.cu
 struct FourierDev {
     // geometry of the periodic 1-D problem (Section 3.1 with the rescaling of
@@ -97,23 +104,25 @@ void launch_segmented_sort(const T* keys_in, int P, int64_t n, int64_t ldk, T* k
                            void* scratch, size_t scratch_bytes, cudaStream_t st);
 template <class T>
 size_t segmented_sort_scratch(int P, int64_t n);
-// Exclusive FP64 prefix sums over each sorted segment:
-//   A[p][i] = sum_{j<i} w[idx[p][j]],  B[p][i] = sum_{j<i} w[idx[p][j]] * key[p][j],  i = 0..n
+// Bytes of the sorted (key, w) pairs of P segments of n sources.
 template <class T>
-void launch_prefix_sums(const T* keys, const int32_t* idx, const T* w, int P, int64_t n, double* A, double* B,
-                        cudaStream_t st);
-// Bucket tables that narrow the binary searches: per slice, NB buckets over
-// [key_min, key_max]; tab[p][b] = first i with bucket(key[p][i]) >= b.
+int64_t sorted_pairs_bytes(int P, int64_t n);
+// From sorted keys and their source indices: (key, w) pairs in sorted order
+// (kw), NB equal-width buckets per slice over [key_min, key_max] (kmin,
+// kscale; tab[p][b] = first sorted index of bucket >= b) and FP64 exclusive
+// prefix sums of w and w*key at the bucket starts (AB[p][b], AB[p][NB] =
+// totals).
 template <class T>
-void launch_bucket_tables(const T* keys, int P, int64_t n, int NB, float* kmin, float* kscale, int32_t* tab,
-                          cudaStream_t st);
+void launch_sorted_pairs(const T* keys, const int32_t* idx, const T* w, int P, int64_t n, void* kw, int NB,
+                         float* kmin, float* kscale, int32_t* tab, double2* AB, cudaStream_t st);
 // Negative-distance 1-D sums at the targets (Section 3.2 in the range-free
 // form t = -c_d [z (2 A_< - W) - (2 B_< - S)]) summed over slices into acc[m],
 // times `scale`; with G != NULL writes g = scale c_d (W - A_< - A_<=) into
-// G[m][p] instead (the derivative, sign(0) = 0).
+// G[m][p] instead (the derivative, sign(0) = 0).  Slices are processed in
+// batches whose sorted pairs fit in L2.
 template <class T>
-void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const T* keys, int64_t nx, const double* A,
-                           const double* B, int NB, const float* kmin, const float* kscale, const int32_t* tab,
-                           double cd, double scale, double* acc, T* G, int accumulate_G, cudaStream_t st);
+void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const void* kw, int64_t nx, const double2* AB,
+                           int NB, const float* kmin, const float* kscale, const int32_t* tab, double cd, double scale,
+                           double* acc, T* G, int accumulate_G, cudaStream_t st);
 
 }  // namespace slk

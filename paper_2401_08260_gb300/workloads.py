@@ -22,7 +22,7 @@ Named workloads (sizes at full scale):
 * ``laplace_d50``    Laplacian exp(-alpha r) with alpha = 1/sqrt(50) (length scale
                      sqrt(d)), 10-component Gaussian mixture (means ~ N(0, 4I),
                      unit covariance, equal weights) for x and y, d = 50,
-                     N = M = 1e7, P = 128, FP32.
+                     N = M = 1e7, P = 128, FP32-accurate (FP16 hi/lo tensor-core) projection.
 * ``paper_sec4``     the paper's Section 4.1 setup: x, y ~ N(0, 0.1^2 I), w ~ U[0,1].
 """
 from __future__ import annotations
@@ -69,7 +69,7 @@ SPECS = {
                        method="auto", dtype=np.float32, dist="cube"),
     "negdist_d3072": dict(kernel="negdist", d=3072, N=2 * 10 ** 5, M=2 * 10 ** 5, P=1000, n_coeff=0,
                           precision="f16x3", method="auto", dtype=np.float32, dist="normal_shift"),
-    "laplace_d50": dict(kernel="laplacian", d=50, N=10 ** 7, M=10 ** 7, P=128, n_coeff=0, precision="f32",
+    "laplace_d50": dict(kernel="laplacian", d=50, N=10 ** 7, M=10 ** 7, P=128, n_coeff=0, precision="f16x3",
                         method="auto", dtype=np.float32, dist="mixture"),
     "paper_sec4": dict(kernel="gaussian", d=50, N=10 ** 4, M=10 ** 4, P=256, n_coeff=0, precision="f32",
                        method="auto", dtype=np.float32, dist="paper"),
