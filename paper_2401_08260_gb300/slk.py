@@ -339,3 +339,106 @@ if torch is not None:
     def sliced_kernel_sum(y, plan: Plan):
         """Differentiable (in y) sliced kernel sum."""
         return SlicedKernelSum.apply(y, plan)
+
+
+# ---------------------------------------------------------------- serving (include/slk_serve.h)
+
+class ServeDesc(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("memory_budget", ctypes.c_int64), ("plan_cache_bytes", ctypes.c_int64),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+class RequestDesc(ctypes.Structure):
+    _fields_ = [("desc", PlanDesc), ("x", ctypes.c_void_p), ("N", ctypes.c_int64), ("ldx", ctypes.c_int64),
+                ("w", ctypes.c_void_p), ("y", ctypes.c_void_p), ("M", ctypes.c_int64), ("ldy", ctypes.c_int64),
+                ("s", ctypes.c_void_p), ("source_key", ctypes.c_uint64)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("plan_cached", ctypes.c_int32), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("message", ctypes.c_char * 128)]
+
+
+_SERVE_SIGNATURES = {
+    "slk_serve_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ServeDesc)]),
+    "slk_serve_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(RequestDesc), ctypes.POINTER(ctypes.c_uint64)]),
+    "slk_serve_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(RequestResult)]),
+    "slk_serve_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "slk_request_bytes": (ctypes.c_int64, [ctypes.POINTER(PlanDesc), ctypes.c_int64, ctypes.c_int64]),
+}
+
+
+def _serve_lib():
+    lib = load()
+    if not getattr(lib, "_serve_ready", False):
+        for name, (res, args) in _SERVE_SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        lib._serve_ready = True
+    return lib
+
+
+def make_desc(kernel: str, param: float, d: int, P: int, precision: str = "f32", n_coeff: int = 0,
+              method: str = "auto", seed: int = 0, tol: float = 0.0, radius: float = 0.0) -> PlanDesc:
+    desc = PlanDesc()
+    desc.kernel, desc.precision, desc.param, desc.d, desc.P = KERNELS[kernel], PRECISIONS[precision], param, d, P
+    desc.n_coeff, desc.method, desc.seed, desc.tol, desc.radius = n_coeff, METHODS[method], seed, tol, radius
+    return desc
+
+
+def request_bytes(desc: PlanDesc, N: int, M: int) -> int:
+    """Conservative device bytes of one request (plan build plus one sum); host-only."""
+    return int(_serve_lib().slk_request_bytes(ctypes.byref(desc), N, M))
+
+
+class Server:
+    """Concurrent request server on the current device (admission by a memory budget,
+    worker streams, a cache of source-side plans keyed by `source_key`)."""
+
+    def __init__(self, workers: int = 0, memory_budget: int = 0, plan_cache_bytes: int = 0):
+        lib = _serve_lib()
+        sd = ServeDesc()
+        sd.workers, sd.memory_budget, sd.plan_cache_bytes = workers, memory_budget, plan_cache_bytes
+        h = ctypes.c_void_p()
+        _check(lib.slk_serve_create(ctypes.byref(h), ctypes.byref(sd)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, x, w, y, out, desc: PlanDesc, source_key: int = 0) -> int:
+        """Queue s = kernel sums of (x, w) at y into `out`; returns the request id.
+        x, w, y and out stay referenced until the request is polled."""
+        dtype = np.float64 if desc.precision == PRECISIONS["f64"] else np.float32
+        xa, wa, ya, oa = _Arr(x, dtype, 2), _Arr(w, dtype, 1), _Arr(y, dtype, 2), _Arr(out, dtype, 1)
+        r = RequestDesc()
+        r.desc = desc
+        r.x, r.N, r.ldx, r.w = xa.ptr, xa.rows, xa.ld, wa.ptr
+        r.y, r.M, r.ldy, r.s = ya.ptr, ya.rows, ya.ld, oa.ptr
+        r.source_key = source_key
+        rid = ctypes.c_uint64()
+        _check(_serve_lib().slk_serve_submit(self._h, ctypes.byref(r), ctypes.byref(rid)))
+        self._keep[rid.value] = (xa, wa, ya, oa)
+        return rid.value
+
+    def poll(self, rid: int, timeout_us: int = -1):
+        """Result dict when finished, None on timeout."""
+        res = RequestResult()
+        st = _serve_lib().slk_serve_poll(self._h, rid, timeout_us, ctypes.byref(res))
+        if st == 5:
+            return None
+        _check(st)
+        self._keep.pop(rid, None)
+        return {"status": int(res.status), "plan_cached": bool(res.plan_cached), "queue_ms": res.queue_ms,
+                "run_ms": res.run_ms, "total_ms": res.total_ms, "message": res.message.decode(errors="replace")}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _serve_lib().slk_serve_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -21,7 +21,7 @@ def lib():
 
 def _declared_functions():
     names = set()
-    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         for m in re.finditer(r"\b(slk_[a-z0-9_]+)\s*\(", text):
@@ -45,24 +45,22 @@ def test_struct_layout_matches_header(tmp_path):
     """Compile a probe against include/slk.h with gcc and compare sizes and offsets."""
     from paper_2401_08260_gb300 import slk
     src = tmp_path / "probe.c"
-    fields = [f for f, _ in slk.PlanDesc._fields_]
-    ifields = [f for f, _ in slk.PlanInfo._fields_]
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "slk.h"', "int main(void){",
-             'printf("%zu %zu\\n", sizeof(slk_plan_desc), sizeof(slk_plan_info));']
-    for f in fields:
-        lines.append(f'printf("%zu\\n", offsetof(slk_plan_desc, {f}));')
-    for f in ifields:
-        lines.append(f'printf("%zu\\n", offsetof(slk_plan_info, {f}));')
+    structs = [("slk_plan_desc", slk.PlanDesc), ("slk_plan_info", slk.PlanInfo), ("slk_kernel_time", slk.KernelTime),
+               ("slk_serve_desc", slk.ServeDesc), ("slk_request", slk.RequestDesc), ("slk_result", slk.RequestResult)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "slk_serve.h"', "int main(void){"]
+    expect = []
+    for cname, py in structs:
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        expect.append(ctypes.sizeof(py))
+        for f, _ in py._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {f}));')
+            expect.append(getattr(py, f).offset)
     lines.append("return 0;}")
     src.write_text("\n".join(lines))
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
-    vals = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
-    assert int(vals[0]) == ctypes.sizeof(slk.PlanDesc)
-    assert int(vals[1]) == ctypes.sizeof(slk.PlanInfo)
-    offs = [int(v) for v in vals[2:]]
-    assert offs[:len(fields)] == [getattr(slk.PlanDesc, f).offset for f in fields]
-    assert offs[len(fields):] == [getattr(slk.PlanInfo, f).offset for f in ifields]
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals == expect
 
 
 def test_status_strings_and_version(lib):
@@ -104,3 +102,29 @@ def test_python_binding_fails_loudly_without_library(tmp_path):
             slk.load(str(tmp_path / "nope.so"))
         finally:
             slk._lib = slk._lib_saved
+
+
+def test_request_bytes_estimate_is_monotone(lib):
+    """The serving admission estimate (host-only) grows with every size and rejects bad input."""
+    from paper_2401_08260_gb300 import slk
+    base = dict(kernel="negdist", param=0.0, d=64, P=128, precision="f32")
+    b0 = slk.request_bytes(slk.make_desc(**base), 10000, 10000)
+    assert b0 > 0
+    for key, val in [("d", 128), ("P", 256)]:
+        assert slk.request_bytes(slk.make_desc(**dict(base, **{key: val})), 10000, 10000) > b0
+    assert slk.request_bytes(slk.make_desc(**base), 20000, 10000) > b0
+    # peak over phases (plan build, then plan + sum): non-decreasing in M, growing once the sum dominates
+    assert slk.request_bytes(slk.make_desc(**base), 10000, 20000) >= b0
+    assert slk.request_bytes(slk.make_desc(**base), 10000, 10 ** 6) > b0
+    assert slk.request_bytes(slk.make_desc(**base), -1, 10) == -1
+    # a cached plan needs only the target side
+    assert slk.request_bytes(slk.make_desc(**base), 0, 10000) < b0
+
+
+def test_serve_calls_report_errors_without_a_device(lib):
+    from paper_2401_08260_gb300 import slk
+    sl = slk._serve_lib()
+    res = slk.RequestResult()
+    assert sl.slk_serve_poll(None, 1, 0, ctypes.byref(res)) == 1
+    assert sl.slk_serve_submit(None, None, None) == 1
+    assert sl.slk_serve_destroy(None) == 0
