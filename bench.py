@@ -337,6 +337,158 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- serving workload
+
+SERVE_D = (50, 784, 3072)
+SERVE_P = (64, 256, 1000)
+SERVE_KERNELS = ("gaussian", "laplacian", "negdist")
+SERVE_PRECISION = {50: "f16x3", 784: "bf16", 3072: "f16x3"}
+
+
+def serve_requests(n_req: int, seed: int = 11, max_nm: float = 1e6):
+    """Request specs of the serving workload: N, M log-uniform in [1e3, max_nm], d in {50, 784,
+    3072} (each with the data distribution of its workload), kernels mixed uniformly, P in
+    {64, 256, 1000}; 30% of the requests repeat the sources of one of the last 8 distinct
+    requests (same kernel, P and sources: a plan-cache hit) with new targets."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    specs, distinct = [], []
+    for i in range(n_req):
+        M = int(round(10 ** rng.uniform(3, math.log10(max_nm))))
+        if distinct and rng.random() < 0.3:
+            base = distinct[int(rng.integers(max(0, len(distinct) - 8), len(distinct)))]
+            specs.append(dict(base, M=M, y_seed=10_000 + i, repeat=True))
+            continue
+        d = int(rng.choice(SERVE_D))
+        kernel = str(rng.choice(SERVE_KERNELS))
+        spec = dict(key=len(distinct) + 1, kernel=kernel, d=d, P=int(rng.choice(SERVE_P)),
+                    N=int(round(10 ** rng.uniform(3, math.log10(max_nm)))), M=M, x_seed=i, y_seed=10_000 + i,
+                    precision=SERVE_PRECISION[d], repeat=False)
+        distinct.append(spec)
+        specs.append(spec)
+    return specs
+
+
+def serve_inputs(spec, dev, cache):
+    """Device tensors (x, w, y, directions) of a request; sources of repeats come from `cache`."""
+    import torch
+    d = spec["d"]
+
+    def points(n, seed, shift):
+        g = torch.Generator(device=dev).manual_seed(seed)
+        if d == 784:
+            return torch.rand(n, d, device=dev, generator=g)
+        if d == 50:
+            gm = torch.Generator(device=dev).manual_seed(4)
+            means = 2.0 * torch.randn(10, d, device=dev, generator=gm)
+            comp = torch.randint(0, 10, (n,), device=dev, generator=g)
+            return torch.randn(n, d, device=dev, generator=g) + means[comp]
+        return torch.randn(n, d, device=dev, generator=g) + shift
+
+    key = spec["key"]
+    if key not in cache:
+        g = torch.Generator(device=dev).manual_seed(spec["x_seed"] + 77)
+        from paper_2401_08260_gb300 import workloads
+        cache[key] = (points(spec["N"], spec["x_seed"], 0.0), torch.rand(spec["N"], device=dev, generator=g),
+                      np.ascontiguousarray(workloads.directions(spec["P"], d, seed=spec["x_seed"])))
+        while len(cache) > 8:
+            cache.pop(next(iter(cache)))
+    x, w, xi = cache[key]
+    y = points(spec["M"], spec["y_seed"], 0.5 if d == 3072 else 0.0)
+    return x, w, y, xi
+
+
+def serve_desc(spec, xi):
+    from paper_2401_08260_gb300 import slk
+    d = spec["d"]
+    param = {"gaussian": math.sqrt(d), "laplacian": 1.0 / math.sqrt(d), "negdist": 0.0}[spec["kernel"]]
+    # certified window half-width per data distribution (projections of the centred data stay inside)
+    radius = {50: 16.0, 784: 3.0, 3072: 8.0}[d]
+    desc = slk.make_desc(spec["kernel"], param, d, spec["P"], spec["precision"], radius=radius)
+    desc.directions = xi.ctypes.data
+    return desc
+
+
+def run_serve(args):
+    """Serving benchmark: a Poisson stream of requests served concurrently (memory-budgeted
+    admission, worker streams, plan cache), beside the plain one-request-at-a-time method
+    (plan + sum per request, in arrival order) on the same GPU, same requests, same accuracy."""
+    import torch
+    from paper_2401_08260_gb300 import build, slk
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    specs = serve_requests(args.serve_requests, max_nm=args.serve_max_nm)
+    cache = {}
+    # ---- plain method: one request at a time, no plan cache (this also measures capacity)
+    service = []
+    outs = {}
+    for spec in specs:
+        x, w, y, xi = serve_inputs(spec, dev, cache)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan = slk.Plan(x, w, spec["kernel"], serve_desc(spec, xi).param, P=spec["P"], precision=spec["precision"],
+                        directions=xi, radius=serve_desc(spec, xi).radius)
+        plan.sum(y)
+        plan.close()
+        service.append(time.perf_counter() - t0)
+    mean_service = float(np.mean(service))
+    rate = args.serve_load / mean_service
+    rng = np.random.Generator(np.random.PCG64(12))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(specs)))
+    # simulated FIFO single server with the measured plain service times
+    finish, lat_plain = 0.0, []
+    for a, s in zip(arrivals, service):
+        start = max(a, finish)
+        finish = start + s
+        lat_plain.append((finish - a) * 1e3)
+    # ---- served: submit at the arrival times, poll as requests finish
+    srv = slk.Server(workers=args.serve_workers)
+    cache.clear()
+    pending, lat, cached, outstanding = {}, [], 0, []
+    t_start = time.perf_counter()
+    slice_points = 0
+    for i, spec in enumerate(specs):
+        while True:
+            now = time.perf_counter() - t_start
+            if now >= arrivals[i] and len(pending) < args.serve_max_outstanding:
+                break
+            # collect finished requests while waiting
+            for rid in list(pending):
+                res = srv.poll(rid, timeout_us=0)
+                if res is not None:
+                    assert res["status"] == 0, res
+                    lat.append(res["total_ms"])
+                    cached += res["plan_cached"]
+                    pending.pop(rid)
+            time.sleep(0.0002)
+        x, w, y, xi = serve_inputs(spec, dev, cache)
+        out = torch.empty(spec["M"], device=dev)
+        torch.cuda.synchronize()
+        rid = srv.submit(x, w, y, out, serve_desc(spec, xi), source_key=spec["key"])
+        pending[rid] = (out, y)
+        slice_points += (spec["N"] + spec["M"]) * spec["P"]
+    for rid in list(pending):
+        res = srv.poll(rid, timeout_us=-1)
+        assert res["status"] == 0, res
+        lat.append(res["total_ms"])
+        cached += res["plan_cached"]
+    wall = time.perf_counter() - t_start
+    srv.close()
+    line = {"metric": "serving p50/p99 latency", "unit": "ms", "higher_is_better": False,
+            "value": float(np.percentile(lat, 50)), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "throughput_req_s": len(specs) / wall,
+            "slice_points_per_s": slice_points / wall, "n_gpus": 1, "requests": len(specs),
+            "load": args.serve_load, "arrival_rate_req_s": rate, "workers": args.serve_workers,
+            "plan_cache_hits": cached, "data": "synthetic",
+            "plain_one_at_a_time": {"p50_ms": float(np.percentile(lat_plain, 50)),
+                                    "p99_ms": float(np.percentile(lat_plain, 99)),
+                                    "mean_service_ms": mean_service * 1e3,
+                                    "throughput_req_s": 1.0 / mean_service},
+            "config": {"workload": "serving mix", "N_M": f"log-uniform [1e3, {args.serve_max_nm:g}]",
+                       "d": list(SERVE_D), "P": list(SERVE_P), "kernels": list(SERVE_KERNELS), "repeats": 0.3}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -353,10 +505,18 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-load", type=float, default=0.8, help="arrival rate / plain capacity")
+    ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-max-nm", type=float, default=1e6)
+    ap.add_argument("--serve-max-outstanding", type=int, default=32)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
-    if args.impl == "reference":
+    if args.serve:
+        run_serve(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -66,6 +66,7 @@ struct slk_server_s {
     std::unordered_map<uint64_t, std::unique_ptr<Request>> all;
     std::unordered_map<uint64_t, std::unique_ptr<CacheEntry>> cache;
     std::vector<std::thread> workers;
+    std::vector<cudaStream_t> streams;  // one per worker; destroyed after the cached plans
 
     void worker_loop(int index);
     bool try_admit(Request* r);
@@ -168,13 +169,8 @@ void slk_server_s::finish(Request* r, CacheEntry* entry, slk_plan plan, bool kee
 }
 
 void slk_server_s::worker_loop(int index) {
-    (void)index;
     cudaSetDevice(device);
-    cudaStream_t st = nullptr;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        st = nullptr;
-    }
+    cudaStream_t st = streams[index];
     for (;;) {
         Request* r = nullptr;
         {
@@ -229,10 +225,7 @@ void slk_server_s::worker_loop(int index) {
         r->message = msg;
         finish(r, entry, plan, keep, plan_bytes);
     }
-    if (st) {
-        cudaStreamSynchronize(st);
-        cudaStreamDestroy(st);
-    }
+    cudaStreamSynchronize(st);
 }
 
 using slk::Error;
@@ -274,6 +267,11 @@ slk_status slk_serve_create(slk_server* out, const slk_serve_desc* desc) {
         srv->budget = dd.memory_budget ? dd.memory_budget : static_cast<int64_t>(0.8 * static_cast<double>(free_b));
         srv->cache_cap = dd.plan_cache_bytes ? std::min(dd.plan_cache_bytes, srv->budget) : srv->budget / 4;
         const int nw = dd.workers ? dd.workers : 4;
+        for (int i = 0; i < nw; ++i) {
+            cudaStream_t st = nullptr;
+            SLK_CHECK_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            srv->streams.push_back(st);
+        }
         slk_server_s* raw = srv.get();
         for (int i = 0; i < nw; ++i) srv->workers.emplace_back([raw, i] { raw->worker_loop(i); });
         *out = srv.release();
@@ -339,8 +337,14 @@ slk_status slk_serve_destroy(slk_server srv) {
     }
     srv->cv.notify_all();
     for (auto& t : srv->workers) t.join();
+    // cached plans free their memory on the streams that built them: before those streams go
     for (auto& kv : srv->cache)
         if (kv.second->plan) slk_plan_destroy(kv.second->plan);
+    srv->cache.clear();
+    for (cudaStream_t st : srv->streams) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
     delete srv;
     return SLK_OK;
 }
