@@ -114,17 +114,26 @@ def algorithmic(wl, info, precision, kernel_name, launches_per_step):
     """(algorithmic amount per launch, unit, bound) of one launch of a library kernel.
 
     Units of work: a point (row of x or y) and a slice-point (one point on one slice).
-    Projection: 2 d P flop per point (tensor for BF16 / FP16x3, FP32 ALU otherwise).
+    The projection, centring, Fourier and Chebyshev kernels run once per point set
+    (the N sources or the M targets; N = M in every workload here), so one launch
+    covers N points; other kernels (sort passes, batched lookups) split the N + M
+    points of a step over their launches.
+    Projection: 2 d P flop per point (tensor for BF16 / FP16x3, FP32 ALU otherwise;
+    the fused Chebyshev target kernel is counted by its contraction alone).
     NDFT source / target: one complex multiply-add per band coefficient, 8 K flop per
-    slice-point (FP32 ALU).  Centring cast: 4 d bytes read + 2 ld16 (x2 for the hi/lo
-    split) written per point.  Other kernels: the 4-byte projections they read."""
-    pts = (wl.N + wl.M) / max(1.0, launches_per_step)
+    slice-point (FP32 ALU).  Chebyshev moments / Clenshaw: two FMAs per term, 4 q flop
+    per slice-point (FP32 ALU).  Centring cast: 4 d bytes read + 2 ld16 (x2 for the
+    hi/lo split) written per point.  Other kernels: the 4-byte projections they read."""
+    per_set = kernel_name.startswith(("gemm", "umma", "ndft", "nfft", "cheb", "center_cast")) and "reduce" not in kernel_name
+    pts = 0.5 * (wl.N + wl.M) if per_set else (wl.N + wl.M) / max(1.0, launches_per_step)
     if kernel_name.startswith(("gemm", "umma")):
         bound = "tensor" if kernel_name.startswith("umma") else "alu"
         return 2.0 * pts * wl.d * wl.P, "flop", bound
     if kernel_name.startswith("ndft_source") or kernel_name.startswith("ndft_target"):
         K = info["k_hi"] - info["k_lo"] + 1
         return 8.0 * K * pts * wl.P, "flop", "alu"
+    if kernel_name.startswith(("cheb_moments", "cheb_target")):
+        return 4.0 * info["cheb_terms"] * pts * wl.P, "flop", "alu"
     if kernel_name.startswith("center_cast"):
         ld16 = (wl.d + 7) // 8 * 8
         return pts * (4.0 * wl.d + 2.0 * ld16 * (2 if precision == "f16x3" else 1)), "byte", "hbm"

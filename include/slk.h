@@ -81,9 +81,12 @@ typedef enum {
 } slk_precision;
 
 typedef enum {
-    SLK_FOURIER_AUTO = 0,     /* NFFT or NDFT, whichever the plan expects to be faster */
+    SLK_FOURIER_AUTO = 0,     /* the fastest method that meets the target (Chebyshev, NDFT or NFFT) */
     SLK_FOURIER_NFFT = 1,     /* spread + FFT + multiply + inverse FFT + interpolate */
-    SLK_FOURIER_NDFT = 2      /* direct sums over the significant coefficients */
+    SLK_FOURIER_NDFT = 2,     /* direct sums over the significant coefficients */
+    SLK_FOURIER_CHEB = 3      /* the NDFT's exponentials expanded in Chebyshev polynomials on the
+                                 certified window (Jacobi-Anger): moments at the sources, a
+                                 Chebyshev series at the targets (Gaussian kernel) */
 } slk_fourier_method;
 
 /* Plan descriptor.  Zero-initialise, then set the fields you need. */
@@ -116,6 +119,11 @@ typedef struct {
     int32_t n_grid;           /* NFFT grid size (2 N_c) */
     int32_t window;           /* NFFT window width in grid cells */
     int32_t k_lo, k_hi;       /* NDFT band of significant k > 0 (inclusive) */
+    int32_t cheb_terms;       /* Chebyshev terms q (SLK_FOURIER_CHEB) */
+    int32_t cheb_horner;      /* 1: targets evaluate the Chebyshev sum by Horner's rule on its
+                                 monomial coefficients (chosen only where that rounding bound is
+                                 within twice Clenshaw's), 0: Clenshaw's recurrence */
+    int32_t reserved0;
     double period;            /* L: period of the Fourier summation in projected units */
     double radius;            /* certified window half-width R */
     double model_error;       /* certified bound: truncation + periodisation + window (per unit sum|w|) */

@@ -95,7 +95,9 @@ struct slk_plan_s {
     bool fourier = false;
     FourierHost fh;
     FourierDev fd{};
-    DevBuf<double> coef, mult;
+    DevBuf<double> coef, mult, chebM;
+    DevBuf<unsigned char> beta;  // T P x q (Chebyshev)
+    DevBuf<unsigned char> mono;  // T P x q (the same polynomials in powers of z / R)
     DevBuf<unsigned char> cw;   // Cplx<T> P x K
     DevBuf<unsigned char> cw0;  // T P
     DevBuf<unsigned char> hgrid;  // T P x W
@@ -125,7 +127,8 @@ struct slk_plan_s {
     int64_t device_bytes() const {
         return static_cast<int64_t>(xi64.bytes() + xi32.bytes() + mu64.bytes() + mu32.bytes() + xib.bytes() +
                                     xib_lo.bytes() + xit16.bytes() + coef.bytes() +
-                                    mult.bytes() + cw.bytes() + cw0.bytes() + hgrid.bytes() + kw.bytes() + AB.bytes() +
+                                    mult.bytes() + chebM.bytes() + beta.bytes() + mono.bytes() + cw.bytes() + cw0.bytes() + hgrid.bytes() + kw.bytes() +
+                                    AB.bytes() +
                                     kmin.bytes() + kscale.bytes() + tab.bytes());
     }
 };
@@ -264,7 +267,31 @@ void plan_fourier_source(slk_plan plan, const T* Zx, const T* w, cudaStream_t st
     fd.win_base = fh.win_base;
     fd.beta = fh.beta;
     fd.R = plan->R;
-    if (fh.method == SLK_FOURIER_NDFT) {
+    fd.q = fh.cheb_qp;
+    if (fh.method == SLK_FOURIER_CHEB) {
+        plan->chebM.alloc(fh.cheb_M.size(), st);
+        SLK_CHECK_CUDA(cudaMemcpyAsync(plan->chebM.get(), fh.cheb_M.data(), sizeof(double) * fh.cheb_M.size(),
+                                       cudaMemcpyHostToDevice, st));
+        plan->beta.alloc(sizeof(T) * P * fh.cheb_qp, st);
+        const bool try_mono = fh.cheb_qp <= 16;
+        if (try_mono) plan->mono.alloc(sizeof(T) * P * fh.cheb_qp, st);
+        DevBuf<unsigned> bad(1, st);
+        SLK_CHECK_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(unsigned), st));
+        int64_t ne = cheb_source_scratch(P, N, fd);
+        DevBuf<T> scratch(ne, st);
+        // Horner's rounding bound gamma_2q sum|a| against Clenshaw's scale sum|beta|: at most
+        // twice it for FP32 / FP64 evaluation; for BF16 projections (whose input rounding,
+        // 2^-9 of each coordinate, dominates) up to 8x, i.e. below 2^-16 sum|beta| for q <= 16
+        const double mono_ratio = plan->tc == 1 ? 8.0 : 2.0;
+        launch_cheb_source<T>(Zx, P, N, N, w, fd, plan->chebM.get(), reinterpret_cast<T*>(plan->beta.get()),
+                              try_mono ? reinterpret_cast<T*>(plan->mono.get()) : nullptr, bad.get(), mono_ratio,
+                              scratch.get(), ne, st);
+        unsigned bad_host = 1;
+        SLK_CHECK_CUDA(cudaMemcpyAsync(&bad_host, bad.get(), sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        SLK_CHECK_CUDA(cudaStreamSynchronize(st));
+        fd.horner = try_mono && bad_host == 0;
+        fd.mono = fd.horner ? plan->mono.get() : nullptr;
+    } else if (fh.method == SLK_FOURIER_NDFT) {
         const int K = fh.k_hi - fh.k_lo + 1;
         plan->coef.alloc(fh.coef.size(), st);
         SLK_CHECK_CUDA(cudaMemcpyAsync(plan->coef.get(), fh.coef.data(), sizeof(double) * fh.coef.size(),
@@ -341,7 +368,7 @@ void create_impl(slk_plan plan, const void* x_user, int64_t ldx, const void* w_u
             plan->xib.alloc(bytes, st);
             if (plan->tc == 2) plan->xib_lo.alloc(bytes, st);
             launch_center_cast(plan->xi32.get(), P, d, d, nullptr, plan->xib.get(), plan->xib_lo.get(), plan->tc == 2,
-                               st);
+                               st, "cast_directions");
             plan->xit16.alloc(static_cast<size_t>(d) * umma_operand_ld(P) * 2, st);
             launch_transpose_bf16(plan->xi32.get(), P, d, plan->xit16.get(), st);
         }
@@ -375,16 +402,49 @@ void create_impl(slk_plan plan, const void* x_user, int64_t ldx, const void* w_u
     }
 }
 
+// Gaussian sums on the BF16 tensor-core path with the Chebyshev evaluation take the
+// fused route: the targets' projections stay in TMEM and only per-tile row sums reach HBM.
+template <class T>
+bool sum_fused_cheb(slk_plan plan, const T* y, int64_t M, int64_t ldy, void* s_user, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (plan->tc != 1 || !plan->fourier || plan->sorting || plan->fh.method != SLK_FOURIER_CHEB ||
+            !umma_cheb_fits(plan->P, plan->fh.cheb_qp) || M >= (int64_t(1) << 31))
+            return false;
+        const size_t bytes = static_cast<size_t>(M) * umma_operand_ld(plan->d) * 2;
+        DevBuf<unsigned char> ya(bytes, st);
+        launch_center_cast(y, M, plan->d, ldy, plan->mu32.get(), ya.get(), nullptr, 0, st);
+        const int parts = static_cast<int>(umma_cheb_parts(plan->P));
+        DevBuf<double> part(static_cast<size_t>(parts) * M, st);
+        const void* coef = plan->fd.horner ? plan->fd.mono : plan->beta.get();
+        launch_umma_cheb_target(ya.get(), M, plan->xib.get(), plan->P, plan->d, static_cast<const float*>(coef),
+                                plan->fh.cheb_qp, plan->fd.horner, plan->R, part.get(), plan->err_dev.get(), st);
+        if (is_device_pointer(s_user)) {
+            launch_sum_parts<T>(part.get(), parts, M, 1.0 / plan->P, static_cast<T*>(s_user), st);
+        } else {
+            DevBuf<T> s(M, st);
+            launch_sum_parts<T>(part.get(), parts, M, 1.0 / plan->P, s.get(), st);
+            SLK_CHECK_CUDA(cudaMemcpyAsync(s_user, s.get(), sizeof(T) * M, cudaMemcpyDeviceToHost, st));
+            SLK_CHECK_CUDA(cudaStreamSynchronize(st));
+        }
+        return true;
+    }
+    return false;
+}
+
 template <class T>
 void sum_impl(slk_plan plan, const void* y_user, int64_t M, int64_t ldy, void* s_user, cudaStream_t st) {
     const int P = plan->P, d = plan->d;
     InView<T> yv(y_user, M, d, ldy, st);
+    if (sum_fused_cheb<T>(plan, yv.ptr, M, yv.ld, s_user, st)) return;
     DevBuf<T> Zy(static_cast<size_t>(P) * M, st);
     project<T>(plan, yv.ptr, M, yv.ld, Zy.get(), nullptr, st);
     DevBuf<double> acc(M, st);
     SLK_CHECK_CUDA(cudaMemsetAsync(acc.get(), 0, sizeof(double) * M, st));
     if (plan->fourier) {
-        if (plan->fh.method == SLK_FOURIER_NDFT)
+        if (plan->fh.method == SLK_FOURIER_CHEB)
+            launch_cheb_target<T>(Zy.get(), P, M, M, plan->fd, reinterpret_cast<const T*>(plan->beta.get()), acc.get(),
+                                  nullptr, plan->err_dev.get(), st);
+        else if (plan->fh.method == SLK_FOURIER_NDFT)
             launch_ndft_target<T>(Zy.get(), P, M, M, plan->fd, reinterpret_cast<const Cplx<T>*>(plan->cw.get()),
                                   reinterpret_cast<const T*>(plan->cw0.get()), acc.get(), nullptr, plan->err_dev.get(),
                                   st);
@@ -427,7 +487,10 @@ void grad_impl(slk_plan plan, const void* y_user, int64_t M, int64_t ldy, const 
     project<T>(plan, yv.ptr, M, yv.ld, Zy.get(), nullptr, st);
     DevBuf<T> G(static_cast<size_t>(M) * P, st);
     if (plan->fourier) {
-        if (plan->fh.method == SLK_FOURIER_NDFT)
+        if (plan->fh.method == SLK_FOURIER_CHEB)
+            launch_cheb_target<T>(Zy.get(), P, M, M, plan->fd, reinterpret_cast<const T*>(plan->beta.get()), nullptr,
+                                  G.get(), plan->err_dev.get(), st);
+        else if (plan->fh.method == SLK_FOURIER_NDFT)
             launch_ndft_target<T>(Zy.get(), P, M, M, plan->fd, reinterpret_cast<const Cplx<T>*>(plan->cw.get()),
                                   reinterpret_cast<const T*>(plan->cw0.get()), nullptr, G.get(), plan->err_dev.get(),
                                   st);
@@ -478,7 +541,9 @@ void validate_desc(const slk_plan_desc* desc) {
                 desc->precision);
     SLK_REQUIRE(desc->d >= 1, "d must be >= 1");
     SLK_REQUIRE(desc->P >= 1 && desc->P <= 65535, "P must be in [1, 65535]");
-    SLK_REQUIRE(desc->method >= SLK_FOURIER_AUTO && desc->method <= SLK_FOURIER_NDFT, "unknown Fourier method");
+    SLK_REQUIRE(desc->method >= SLK_FOURIER_AUTO && desc->method <= SLK_FOURIER_CHEB, "unknown Fourier method");
+    if (desc->kernel == SLK_LAPLACIAN && desc->method == SLK_FOURIER_CHEB)
+        fail(SLK_ERR_UNSUPPORTED, "the Chebyshev evaluation serves the Gaussian kernel; the Laplacian uses the NFFT");
     SLK_REQUIRE(desc->n_coeff >= 0 && desc->n_coeff <= (1 << 14) && desc->n_coeff % 2 == 0,
                 "n_coeff must be even and in [0, 16384]");
     if (desc->kernel != SLK_NEGDIST)
@@ -663,6 +728,8 @@ slk_status slk_plan_get_info(slk_plan plan, slk_plan_info* info) {
             info->window = plan->fh.m;
             info->k_lo = plan->fh.k_lo;
             info->k_hi = plan->fh.k_hi;
+            info->cheb_terms = plan->fh.cheb_q;
+            info->cheb_horner = plan->fd.horner;
             info->period = plan->fh.L;
             info->radius = plan->R;
             info->model_error = plan->fh.model_err;
@@ -702,6 +769,7 @@ slk_status slk_fourier_params(const slk_plan_desc* desc, double radius, slk_plan
         info->window = fh.m;
         info->k_lo = fh.k_lo;
         info->k_hi = fh.k_hi;
+        info->cheb_terms = fh.cheb_q;
         info->period = fh.L;
         info->radius = radius;
         info->model_error = fh.model_err;
@@ -795,7 +863,10 @@ void sum_noalloc_impl(slk_plan plan, const T* y, int64_t M, int64_t ldy, T* s, u
     // the array keeps the previous call's contents: the accumulator must start at zero
     SLK_CHECK_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * M, st));
     if (plan->fourier) {
-        if (plan->fh.method == SLK_FOURIER_NDFT)
+        if (plan->fh.method == SLK_FOURIER_CHEB)
+            launch_cheb_target<T>(Zy, P, M, M, plan->fd, reinterpret_cast<const T*>(plan->beta.get()), acc, nullptr,
+                                  plan->err_dev.get(), st);
+        else if (plan->fh.method == SLK_FOURIER_NDFT)
             launch_ndft_target<T>(Zy, P, M, M, plan->fd, reinterpret_cast<const Cplx<T>*>(plan->cw.get()),
                                   reinterpret_cast<const T*>(plan->cw0.get()), acc, nullptr, plan->err_dev.get(), st);
         else

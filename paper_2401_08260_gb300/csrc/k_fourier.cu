@@ -231,6 +231,206 @@ __global__ void __launch_bounds__(256) k_ndft_target(const T* __restrict__ Z, in
     if (!GRAD && m < n) acc[m] += sum.value();
 }
 
+// ------------------------------------------------------------ Chebyshev evaluation
+
+// One source's contribution w T_j(u), j < QMAX, to the moments (Chebyshev recurrence
+// T_{j+1} = 2u T_j - T_{j-1}).
+template <class T, int QMAX>
+__device__ __forceinline__ void cheb_accumulate(T (&mu)[QMAX], T wv, T u) {
+    const T u2 = u + u;
+    T tm1 = T(1), t = u;  // T_0, T_1
+    mu[0] += wv;
+#pragma unroll
+    for (int j = 1; j < QMAX; ++j) {
+        mu[j] = fma(wv, t, mu[j]);
+        const T tn = fma(u2, t, -tm1);
+        tm1 = t;
+        t = tn;
+    }
+}
+
+// Source side: mu[p][j] = sum_n w_n T_j(z_{p,n} / R), j < q; per-thread registers, warp
+// shuffles, one shared pass.  VEC: FP32 rows 16-byte aligned, read four sources per load.
+template <class T, int QMAX, bool VEC>
+__global__ void __launch_bounds__(256) k_cheb_moments(const T* __restrict__ Z, int64_t n, int64_t ldz,
+                                                      const T* __restrict__ w, T inv_R, int q, T* __restrict__ partial,
+                                                      int P) {
+    __shared__ T red[8][QMAX];
+    const int p = blockIdx.y;
+    const int64_t i0 = static_cast<int64_t>(blockIdx.x) * NDFT_CHUNK;
+    const int64_t i1 = (i0 + NDFT_CHUNK < n) ? i0 + NDFT_CHUNK : n;
+    const T* zr = Z + static_cast<int64_t>(p) * ldz;
+    T mu[QMAX];
+#pragma unroll
+    for (int j = 0; j < QMAX; ++j) mu[j] = T(0);
+    int64_t rest = i0;  // first source left for the scalar loop
+    if constexpr (VEC && sizeof(T) == 4) {
+        // two float4 groups per step: eight sources whose loads are issued together
+        const int64_t nv = (i1 - i0) >> 2;
+        const float4* z4 = reinterpret_cast<const float4*>(zr + i0);
+        const float4* w4 = reinterpret_cast<const float4*>(w + i0);
+        for (int64_t g = threadIdx.x; g < nv; g += 512) {
+            float4 zz[2], ww[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int64_t gi = g + r * 256;
+                zz[r] = gi < nv ? z4[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
+                ww[r] = gi < nv ? w4[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                cheb_accumulate<T, QMAX>(mu, ww[r].x, zz[r].x * inv_R);
+                cheb_accumulate<T, QMAX>(mu, ww[r].y, zz[r].y * inv_R);
+                cheb_accumulate<T, QMAX>(mu, ww[r].z, zz[r].z * inv_R);
+                cheb_accumulate<T, QMAX>(mu, ww[r].w, zz[r].w * inv_R);
+            }
+        }
+        rest = i0 + 4 * nv;
+    }
+    // four sources per step: their loads are issued together (memory-level parallelism)
+    constexpr int U = 4;
+    for (int64_t ib = rest + threadIdx.x; ib < i1; ib += 256 * U) {
+        T wv[U], u[U];
+#pragma unroll
+        for (int r = 0; r < U; ++r) {
+            const int64_t i = ib + static_cast<int64_t>(r) * 256;
+            wv[r] = i < i1 ? w[i] : T(0);
+            u[r] = i < i1 ? zr[i] * inv_R : T(0);
+        }
+#pragma unroll
+        for (int r = 0; r < U; ++r) cheb_accumulate<T, QMAX>(mu, wv[r], u[r]);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < QMAX; ++j) {
+        const T v = warp_sum(mu[j]);
+        if (lane == 0) red[warp][j] = v;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < q; j += blockDim.x) {
+        T acc = T(0);
+        for (int r = 0; r < 8; ++r) acc += red[r][j];
+        partial[(static_cast<int64_t>(blockIdx.x) * P + p) * q + j] = acc;
+    }
+}
+
+// beta[p][l] = sum_j M[l][j] mu[p][j], mu summed over chunks in a fixed order (FP64);
+// optionally the monomial form of the same polynomial (q <= 16, see launch_cheb_source).
+template <class T>
+__global__ void k_cheb_reduce(const T* __restrict__ partial, int nchunk, int P, int q, const double* __restrict__ M,
+                              T* __restrict__ beta, T* __restrict__ mono, unsigned* __restrict__ mono_bad,
+                              double mono_ratio) {
+    extern __shared__ double smu[];  // mu[q], then beta[q]
+    double* sbeta = smu + q;
+    const int p = blockIdx.x;
+    for (int j = threadIdx.x; j < q; j += blockDim.x) {
+        double a = 0.0;
+        for (int c = 0; c < nchunk; ++c) a += static_cast<double>(partial[(static_cast<int64_t>(c) * P + p) * q + j]);
+        smu[j] = a;
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < q; l += blockDim.x) {
+        double a = 0.0;
+        for (int j = 0; j < q; ++j) a += M[static_cast<int64_t>(l) * q + j] * smu[j];
+        sbeta[l] = a;
+        beta[static_cast<int64_t>(p) * q + l] = static_cast<T>(a);
+    }
+    if (mono == nullptr) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // coefficients of T_l in powers of u from T_{l+1} = 2u T_l - T_{l-1} (integers, exact)
+        double a[16], tm[16], tc[16], tn[16];
+        double sb = 0.0;
+        for (int k = 0; k < 16; ++k) a[k] = tm[k] = tc[k] = 0.0;
+        tm[0] = 1.0;  // T_0
+        tc[1] = 1.0;  // T_1
+        for (int l = 0; l < q && l < 16; ++l) {
+            const double* t = l == 0 ? tm : tc;
+            if (l >= 2) {
+                for (int k = 0; k < 16; ++k) tn[k] = (k ? 2.0 * tc[k - 1] : 0.0) - tm[k];
+                for (int k = 0; k < 16; ++k) {
+                    tm[k] = tc[k];
+                    tc[k] = tn[k];
+                }
+                t = tc;
+            }
+            for (int k = 0; k <= l; ++k) a[k] += sbeta[l] * t[k];
+            sb += fabs(sbeta[l]);
+        }
+        double sa = 0.0;
+        for (int k = 0; k < q && k < 16; ++k) {
+            sa += fabs(a[k]);
+            mono[static_cast<int64_t>(p) * q + k] = static_cast<T>(a[k]);
+        }
+        if (q > 16 || !(sa <= mono_ratio * sb)) atomicOr(mono_bad, 1u);
+    }
+}
+
+// Target side: t_p(z) = sum_l beta[p][l] T_l(z / R) by Clenshaw's recurrence, summed over
+// slices into acc[m]; GRAD writes dt_p/dz = (1/R) sum_l l beta_l U_{l-1}(v) into G[m][p].
+template <class T, int QMAX, bool GRAD, bool HORNER>
+__global__ void __launch_bounds__(256) k_cheb_target(const T* __restrict__ Z, int P, int64_t n, int64_t ldz, T inv_R,
+                                                     int q, const T* __restrict__ beta, int slice_chunk, T R,
+                                                     double* __restrict__ acc, T* __restrict__ G,
+                                                     unsigned* __restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    T* sb = reinterpret_cast<T*>(smem_raw);
+    const int64_t m = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    typename Acc<T>::type sum;
+    bool bad = false;
+    for (int p0 = 0; p0 < P; p0 += slice_chunk) {
+        const int pc = (P - p0 < slice_chunk) ? P - p0 : slice_chunk;
+        __syncthreads();
+        for (int e = threadIdx.x; e < pc * q; e += blockDim.x) sb[e] = beta[static_cast<int64_t>(p0) * q + e];
+        __syncthreads();
+        if (m >= n) continue;
+        // four slices per step: their loads are issued together (memory-level parallelism)
+        constexpr int U = 4;
+        for (int s0 = 0; s0 < pc; s0 += U) {
+        T zz[U];
+#pragma unroll
+        for (int r = 0; r < U; ++r) zz[r] = s0 + r < pc ? Z[static_cast<int64_t>(p0 + s0 + r) * ldz + m] : T(0);
+#pragma unroll
+        for (int r = 0; r < U; ++r) {
+            const int s = s0 + r;
+            if (s >= pc) break;
+            const int p = p0 + s;
+            const T z = zz[r];
+            if (!(z <= R && z >= -R)) bad = true;  // outside the certified window (or NaN)
+            const T v = z * inv_R, v2 = v + v;
+            const T* b = sb + static_cast<size_t>(s) * q;
+            T b1 = T(0), b2 = T(0);
+            if (GRAD) {
+                // sum_{n < q-1} (n+1) beta_{n+1} U_n(v):  Clenshaw for U (result b_0)
+#pragma unroll
+                for (int k = QMAX - 2; k >= 0; --k) {
+                    const T bk = fma(v2, b1, T(k + 1) * b[k + 1] - b2);
+                    b2 = b1;
+                    b1 = bk;
+                }
+                G[m * P + p] = b1 * inv_R;
+            } else if (HORNER) {
+                // b holds the monomial coefficients
+                T r = b[QMAX - 1];
+#pragma unroll
+                for (int k = QMAX - 2; k >= 0; --k) r = fma(r, v, b[k]);
+                sum.add(r);
+            } else {
+#pragma unroll
+                for (int k = QMAX - 1; k >= 1; --k) {
+                    const T bk = fma(v2, b1, b[k] - b2);
+                    b2 = b1;
+                    b1 = bk;
+                }
+                sum.add(fma(v, b1, b[0] - b2));
+            }
+        }
+        }
+    }
+    if (bad) atomicOr(err, 4u);
+    if (!GRAD && m < n) acc[m] += sum.value();
+}
+
 // ------------------------------------------------------------ NFFT spread
 
 // Narrow window (W <= 64): lane = slice, every lane keeps a private window in
@@ -511,6 +711,91 @@ void launch_ndft_target(const T* Z, int P, int64_t n, int64_t ldz, const Fourier
     }
     SLK_CHECK_LAUNCH();
 }
+
+// The term count is padded on the host to one of these (zero coefficients beyond the
+// certified q), so every loop over the terms has a compile-time length.
+#define SLK_CHEB_DISPATCH(QV, ...)                                                        \
+    do {                                                                                  \
+        switch (QV) {                                                                     \
+            case 8: { constexpr int QM = 8; __VA_ARGS__; } break;                         \
+            case 12: { constexpr int QM = 12; __VA_ARGS__; } break;                       \
+            case 16: { constexpr int QM = 16; __VA_ARGS__; } break;                       \
+            case 24: { constexpr int QM = 24; __VA_ARGS__; } break;                       \
+            case 32: { constexpr int QM = 32; __VA_ARGS__; } break;                       \
+            case 48: { constexpr int QM = 48; __VA_ARGS__; } break;                       \
+            case 64: { constexpr int QM = 64; __VA_ARGS__; } break;                       \
+            case 96: { constexpr int QM = 96; __VA_ARGS__; } break;                       \
+            default: fail(SLK_ERR_INVALID, "Chebyshev term count %d is not a padded size", QV); \
+        }                                                                                 \
+    } while (0)
+
+int64_t cheb_source_scratch(int P, int64_t n, const FourierDev& fd) {
+    return ceil_div(n, NDFT_CHUNK) * static_cast<int64_t>(P) * fd.q;
+}
+
+template <class T>
+void launch_cheb_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, const FourierDev& fd,
+                        const double* M, T* beta, T* mono, unsigned* mono_bad, double mono_ratio, T* scratch,
+                        int64_t scratch_elems, cudaStream_t st) {
+    const int q = fd.q;
+    SLK_REQUIRE(q >= 1 && q <= 96, "Chebyshev terms out of range");
+    const int64_t nchunk = ceil_div(n, NDFT_CHUNK);
+    SLK_REQUIRE(scratch_elems >= cheb_source_scratch(P, n, fd), "Chebyshev scratch too small");
+    SLK_REQUIRE(nchunk <= 2147483647 && P <= 65535, "Chebyshev launch too large");
+    dim3 grid(static_cast<unsigned>(nchunk), P);
+    const T inv_R = static_cast<T>(1.0 / fd.R);
+    {
+        SLK_TIMED("cheb_moments", st);
+        const bool vec = sizeof(T) == 4 && ldz % 4 == 0 && reinterpret_cast<uintptr_t>(Z) % 16 == 0 &&
+                         reinterpret_cast<uintptr_t>(w) % 16 == 0;
+        if (vec)
+            SLK_CHEB_DISPATCH(q, (k_cheb_moments<T, QM, true><<<grid, 256, 0, st>>>(Z, n, ldz, w, inv_R, q, scratch, P)));
+        else
+            SLK_CHEB_DISPATCH(q, (k_cheb_moments<T, QM, false><<<grid, 256, 0, st>>>(Z, n, ldz, w, inv_R, q, scratch, P)));
+    }
+    SLK_CHECK_LAUNCH();
+    {
+        SLK_TIMED("cheb_reduce", st);
+        k_cheb_reduce<T><<<P, 128, 2 * sizeof(double) * q, st>>>(scratch, static_cast<int>(nchunk), P, q, M, beta,
+                                                                  q <= 16 ? mono : nullptr, mono_bad, mono_ratio);
+    }
+    SLK_CHECK_LAUNCH();
+}
+
+template <class T>
+void launch_cheb_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const T* beta, double* acc,
+                        T* G, unsigned* err, cudaStream_t st) {
+    if (n <= 0) return;
+    const int q = fd.q;
+    int chunk = static_cast<int>((48 * 1024) / (sizeof(T) * q));
+    if (chunk > P) chunk = P;
+    if (chunk < 1) chunk = 1;
+    const size_t smem = sizeof(T) * q * chunk;
+    const T inv_R = static_cast<T>(1.0 / fd.R);
+    const unsigned blocks = static_cast<unsigned>(ceil_div(n, 256));
+    SLK_TIMED(G ? "cheb_target_grad" : "cheb_target", st);
+    if (G) {
+        SLK_CHEB_DISPATCH(q, (k_cheb_target<T, QM, true, false><<<blocks, 256, smem, st>>>(
+                                 Z, P, n, ldz, inv_R, q, beta, chunk, static_cast<T>(fd.R), acc, G, err)));
+    } else if (fd.horner && fd.mono) {
+        const T* mono = static_cast<const T*>(fd.mono);
+        SLK_CHEB_DISPATCH(q, (k_cheb_target<T, QM, false, true><<<blocks, 256, smem, st>>>(
+                                 Z, P, n, ldz, inv_R, q, mono, chunk, static_cast<T>(fd.R), acc, G, err)));
+    } else {
+        SLK_CHEB_DISPATCH(q, (k_cheb_target<T, QM, false, false><<<blocks, 256, smem, st>>>(
+                                 Z, P, n, ldz, inv_R, q, beta, chunk, static_cast<T>(fd.R), acc, G, err)));
+    }
+    SLK_CHECK_LAUNCH();
+}
+
+template void launch_cheb_source<float>(const float*, int, int64_t, int64_t, const float*, const FourierDev&,
+                                        const double*, float*, float*, unsigned*, double, float*, int64_t, cudaStream_t);
+template void launch_cheb_source<double>(const double*, int, int64_t, int64_t, const double*, const FourierDev&,
+                                         const double*, double*, double*, unsigned*, double, double*, int64_t, cudaStream_t);
+template void launch_cheb_target<float>(const float*, int, int64_t, int64_t, const FourierDev&, const float*, double*,
+                                        float*, unsigned*, cudaStream_t);
+template void launch_cheb_target<double>(const double*, int, int64_t, int64_t, const FourierDev&, const double*,
+                                         double*, double*, unsigned*, cudaStream_t);
 
 int64_t nfft_source_scratch(int P, int64_t n, const FourierDev& fd) {
     int64_t nchunk;

@@ -67,6 +67,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
+// bring a box of a tensor into L2 ahead of its load (no shared memory, no barrier)
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int c0, int c1) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -141,14 +148,31 @@ struct Smem {
 // (column tile fastest, so the CTAs that share a block of points run together and the
 // second read of A hits L2).  Two 256-column TMEM accumulators alternate between tiles:
 // the epilogue of one tile overlaps the MMAs of the next.
-// ROWMAJOR = false: Z[col * ldz + row] (slice-major projections);
-// ROWMAJOR = true:  Z[row * ldz + col] * rowscale(row), rowscale = scale * (rs ? rs[row] : 1)
-// (the backward product, rows = targets, columns = coordinates).
-template <bool ROWMAJOR>
-__global__ void __launch_bounds__(THREADS, 1)
+// Epilogues:
+//   EPI_Z:    Z[col * ldz + row] (slice-major projections), largest |z| into *absmax;
+//   EPI_ROW:  Z[row * ldz + col] * rowscale(row), rowscale = scale * (rs ? rs[row] : 1)
+//             (the backward product, rows = targets, columns = coordinates);
+//   EPI_CHEB: the target side of the Chebyshev evaluation fused in: for every row
+//             (target) and column (slice p) t_p = sum_l beta[p][l] T_l(z / R) by Clenshaw,
+//             summed over the tile's columns; Z receives the FP64 partial row sums
+//             Z_part[(col_tile * 2 + half) * n + row] (no projection is stored).
+enum { EPI_Z = 0, EPI_ROW = 1, EPI_CHEB = 2 };
+
+struct ChebEpi {
+    const float* beta;  // P x q: Chebyshev coefficients, or monomial ones when horner
+    int q;
+    int horner;
+    float inv_R, R;
+    double* part;  // (2 * col_tiles) x n
+};
+
+template <int EPI>
+__global__ void __launch_bounds__(EPI == EPI_CHEB ? 384 : 256, 1)
     k_umma_project(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int n, int P,
                    int d, int col_tiles, int tiles, float* __restrict__ Z, int64_t ldz, float* __restrict__ absmax,
-                   unsigned* __restrict__ err, const float* __restrict__ rs, float scale) {
+                   unsigned* __restrict__ err, const float* __restrict__ rs, float scale, ChebEpi ce) {
+    constexpr bool ROWMAJOR = EPI == EPI_ROW;
+    constexpr int EPI_WARPS = EPI == EPI_CHEB ? 8 : 4;
     constexpr int STAGES = STAGES_1;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -166,10 +190,19 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sm->acc_full[b], 1);
-            mbar_init(&sm->acc_empty[b], 4);  // one arrival per epilogue warp
+            mbar_init(&sm->acc_empty[b], EPI_WARPS);  // one arrival per epilogue warp
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    // Chebyshev coefficients in shared memory (after the Smem struct), degree-major
+    // sbeta[l * ppad + p], zero for the padding slices p >= P (whose projections are 0)
+    const int ppad = col_tiles * BN;
+    float* sbeta = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES + ((sizeof(Smem) + 15) & ~size_t(15)));
+    if (EPI == EPI_CHEB)
+        for (int e = threadIdx.x; e < ppad * ce.q; e += blockDim.x) {
+            const int l = e / ppad, p = e - l * ppad;
+            sbeta[e] = p < P ? ce.beta[static_cast<int64_t>(p) * ce.q + l] : 0.0f;
+        }
     if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm->tmem_base)),
                      "r"(TMEM_COLS)
@@ -187,6 +220,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         bool ok = true;
         for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
             const int row0 = (tile / col_tiles) * BM, col0 = (tile % col_tiles) * BN;
+            // the points of this CTA's next tile come from HBM: start them towards L2 now
+            const int next = tile + static_cast<int>(gridDim.x);
+            if (next < tiles && (next / col_tiles) != (tile / col_tiles))
+                for (int kb = 0; kb < kblocks; ++kb) tma_prefetch_2d(&map_a, kb * BK, (next / col_tiles) * BM);
             for (int kb = 0; kb < kblocks; ++kb, ++g) {
                 const int s = g % STAGES;
                 if (g >= STAGES && !mbar_wait(&sm->empty[s], ((g / STAGES) - 1) & 1)) {
@@ -232,7 +269,81 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             umma_commit(&sm->acc_full[b]);
         }
-    } else if (warp >= 4) {
+    } else if (warp >= 4 && EPI == EPI_CHEB) {
+        // ---------------- fused target side: Clenshaw per (row, slice), row sums per tile
+        const int q4 = warp & 3, half = (warp - 4) >> 2;  // TMEM lane quarter, column half
+        const uint32_t lane_off = static_cast<uint32_t>(q4 * 32) << 16;
+        const int qn = ce.q;
+        bool bad = false;
+        int local = 0;
+        for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++local) {
+            const int b = local & 1;
+            const int ct = tile % col_tiles;
+            const int row = (tile / col_tiles) * BM + q4 * 32 + lane, col0 = ct * BN + half * (BN / 2);
+            if (!mbar_wait(&sm->acc_full[b], (local >> 1) & 1)) {
+                atomicOr(err, 32u);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float s = 0.0f, c = 0.0f;  // Kahan
+            for (int cc = 0; cc < BN / 2; cc += 32) {
+                float v[32];
+                tmem_ld32(tmem + lane_off + b * BN + half * (BN / 2) + cc, v);
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                    // four slices at once: independent Clenshaw chains, one LDS.128 per degree
+                    const float* bt = sbeta + col0 + cc + j;
+                    float u[4], u2[4], b1[4], b2[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const float z = v[j + r];
+                        if (!(z <= ce.R && z >= -ce.R)) bad = true;
+                        u[r] = z * ce.inv_R;
+                        u2[r] = u[r] + u[r];
+                        b1[r] = 0.0f;
+                        b2[r] = 0.0f;
+                    }
+                    if (ce.horner) {
+                        // monomial coefficients: Horner's rule, the result left in b1 with b2 = 0
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) b1[r] = 0.0f;
+                        for (int kk = qn - 1; kk >= 1; --kk) {
+                            const float4 c4 = *reinterpret_cast<const float4*>(bt + kk * ppad);
+                            const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) b1[r] = fmaf(b1[r], u[r], cv[r]);
+                        }
+                    } else {
+                        for (int kk = qn - 1; kk >= 1; --kk) {
+                            const float4 c4 = *reinterpret_cast<const float4*>(bt + kk * ppad);
+                            const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) {
+                                const float bk = fmaf(u2[r], b1[r], cv[r] - b2[r]);
+                                b2[r] = b1[r];
+                                b1[r] = bk;
+                            }
+                        }
+                    }
+                    const float4 c0 = *reinterpret_cast<const float4*>(bt);
+                    const float cv0[4] = {c0.x, c0.y, c0.z, c0.w};
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const float t = fmaf(u[r], b1[r], cv0[r] - b2[r]);
+                        const float y = t - c;
+                        const float tt = s + y;
+                        c = (tt - s) - y;
+                        s = tt;
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm->acc_empty[b]);
+            if (row < n) ce.part[static_cast<int64_t>(ct * 2 + half) * n + row] = static_cast<double>(s) - static_cast<double>(c);
+        }
+        if (bad) atomicOr(err, 4u);
+    } else if (warp >= 4 && warp < 8) {
         // ---------------- epilogue: TMEM -> registers -> Z (slice-major)
         const int q = warp - 4;  // TMEM lane quarter
         const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
@@ -539,21 +650,22 @@ CUtensorMap make_map(const void* ptr, CUtensorMapDataType dt, int64_t rows, int 
     return m;
 }
 
-size_t umma_smem_bytes() {
+size_t umma_smem_bytes(size_t extra = 0) {
     constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
-    return 1024 + STAGES_1 * (A_BYTES + B_BYTES) + sizeof(Smem);
+    return 1024 + STAGES_1 * (A_BYTES + B_BYTES) + ((sizeof(Smem) + 15) & ~size_t(15)) + extra;
 }
+constexpr size_t kChebSmem = 32 * 1024;  // room for beta (padded P x q floats) in the fused kernel
 
 // SM count of the current device; sets the shared-memory limit of the persistent kernel once
-template <bool ROWMAJOR>
+template <int EPI>
 int sm_count() {
     static int sms[128] = {};
     int dev = 0;
     SLK_CHECK_CUDA(cudaGetDevice(&dev));
     SLK_REQUIRE(dev >= 0 && dev < 128, "device index out of range");
     if (!sms[dev]) {
-        SLK_CHECK_CUDA(cudaFuncSetAttribute(k_umma_project<ROWMAJOR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            static_cast<int>(umma_smem_bytes())));
+        SLK_CHECK_CUDA(cudaFuncSetAttribute(k_umma_project<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            static_cast<int>(umma_smem_bytes(EPI == EPI_CHEB ? kChebSmem : 0))));
         SLK_CHECK_CUDA(cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev));
     }
     return sms[dev];
@@ -582,6 +694,32 @@ void launch_transpose_bf16(const float* src, int rows, int cols, void* dst, cuda
     SLK_CHECK_LAUNCH();
 }
 
+int64_t umma_cheb_parts(int P) { return 2 * ceil_div(P, BN); }
+
+bool umma_cheb_fits(int P, int q) {
+    return q >= 1 && static_cast<size_t>(ceil_div(P, BN) * BN) * q * sizeof(float) <= kChebSmem;
+}
+
+void launch_umma_cheb_target(const void* xa, int64_t n, const void* xib, int P, int d, const float* coef, int q,
+                             int horner, double R, double* part, unsigned* err, cudaStream_t st) {
+    if (n <= 0) return;
+    SLK_REQUIRE(umma_cheb_fits(P, q), "Chebyshev coefficients do not fit the fused kernel");
+    SLK_REQUIRE(n < (int64_t(1) << 31), "too many points for one projection");
+    const int64_t ld = umma_operand_ld(d);
+    CUtensorMap ma = make_map(xa, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, n, d, ld, BM);
+    CUtensorMap mb = make_map(xib, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, P, d, ld, BN);
+    const int col_tiles = static_cast<int>(ceil_div(P, BN));
+    const int64_t blocks = ceil_div(n, BM) * col_tiles;
+    const int sms = sm_count<EPI_CHEB>();
+    const int64_t persistent = blocks < sms ? blocks : sms;
+    ChebEpi ce{coef, q, horner, static_cast<float>(1.0 / R), static_cast<float>(R), part};
+    SLK_TIMED("umma_cheb_target", st);
+    k_umma_project<EPI_CHEB><<<static_cast<unsigned>(persistent), 384, umma_smem_bytes(kChebSmem), st>>>(
+        ma, mb, static_cast<int>(n), P, d, col_tiles, static_cast<int>(blocks), nullptr, 0, nullptr, err, nullptr,
+        1.0f, ce);
+    SLK_CHECK_LAUNCH();
+}
+
 void launch_grad_umma(const void* g16, int64_t M, int P, const void* xit16, int d, const float* gs, double scale,
                       float* gy, int64_t ldg, unsigned* err, cudaStream_t st) {
     if (M <= 0) return;
@@ -592,23 +730,23 @@ void launch_grad_umma(const void* g16, int64_t M, int P, const void* xit16, int 
     const int col_tiles = static_cast<int>(ceil_div(d, BN));
     const int64_t blocks = ceil_div(M, BM) * col_tiles;
     SLK_REQUIRE(blocks < (int64_t(1) << 31), "too many targets");
-    const int sms = sm_count<true>();
+    const int sms = sm_count<EPI_ROW>();
     const int64_t persistent = blocks < sms ? blocks : sms;
     SLK_TIMED("umma_grad_bf16", st);
-    k_umma_project<true><<<static_cast<unsigned>(persistent), THREADS, umma_smem_bytes(), st>>>(
+    k_umma_project<EPI_ROW><<<static_cast<unsigned>(persistent), THREADS, umma_smem_bytes(), st>>>(
         ma, mb, static_cast<int>(M), d, P, col_tiles, static_cast<int>(blocks), gy, ldg, nullptr, err, gs,
-        static_cast<float>(scale));
+        static_cast<float>(scale), ChebEpi{});
     SLK_CHECK_LAUNCH();
 }
 
 void launch_center_cast(const float* x, int64_t n, int d, int64_t ldx, const float* mu, void* out, void* out_lo,
-                        int split, cudaStream_t st) {
+                        int split, cudaStream_t st, const char* label) {
     if (n <= 0) return;
     const int ldo = static_cast<int>(umma_operand_ld(d));
     const int64_t total = n * (ldo / 8);
     const unsigned blocks = static_cast<unsigned>(ceil_div(total, 256) < 152 * 8 ? ceil_div(total, 256) : 152 * 8);
     const int vec_ok = (ldx % 4 == 0) && (reinterpret_cast<uintptr_t>(x) % 16 == 0);
-    SLK_TIMED("center_cast", st);
+    SLK_TIMED(label, st);
     if (split)
         k_center_cast<__half, 1><<<blocks, 256, 0, st>>>(x, n, d, ldx, mu, static_cast<__half*>(out),
                                                         static_cast<__half*>(out_lo), ldo, vec_ok);
@@ -644,11 +782,12 @@ void launch_project_umma(const void* xa, const void* xa_lo, int64_t n, const voi
         k_umma_project_x3<<<grid, X3_THREADS, x3_smem_bytes(), st>>>(ma, mb, ma2, mb2, static_cast<int>(n), P, d,
                                                                      col_tiles, Z, ldz, absmax, err);
     } else {
-        const int sms = sm_count<false>();
+        const int sms = sm_count<EPI_Z>();
         const int64_t persistent = blocks < sms ? blocks : sms;
         SLK_TIMED("umma_project_bf16", st);
-        k_umma_project<false><<<static_cast<unsigned>(persistent), THREADS, umma_smem_bytes(), st>>>(
-            ma, mb, static_cast<int>(n), P, d, col_tiles, static_cast<int>(blocks), Z, ldz, absmax, err, nullptr, 1.0f);
+        k_umma_project<EPI_Z><<<static_cast<unsigned>(persistent), THREADS, umma_smem_bytes(), st>>>(
+            ma, mb, static_cast<int>(n), P, d, col_tiles, static_cast<int>(blocks), Z, ldz, absmax, err, nullptr, 1.0f,
+            ChebEpi{});
     }
     SLK_CHECK_LAUNCH();
 }

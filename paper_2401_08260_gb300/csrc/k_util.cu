@@ -188,6 +188,27 @@ void launch_finalize(const double* acc, T* s, int64_t n, double scale, cudaStrea
     SLK_CHECK_LAUNCH();
 }
 
+template <class T>
+__global__ void k_sum_parts(const double* part, int parts, int64_t n, double scale, T* s) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        double a = 0.0;
+        for (int r = 0; r < parts; ++r) a += part[r * n + i];
+        s[i] = static_cast<T>(a * scale);
+    }
+}
+
+template <class T>
+void launch_sum_parts(const double* part, int parts, int64_t n, double scale, T* s, cudaStream_t st) {
+    if (n <= 0) return;
+    const int64_t blocks = ceil_div(n, 256);
+    SLK_TIMED("sum_parts", st);
+    k_sum_parts<T><<<static_cast<unsigned>(blocks < 8192 ? blocks : 8192), 256, 0, st>>>(part, parts, n, scale, s);
+    SLK_CHECK_LAUNCH();
+}
+
+template void launch_sum_parts<float>(const double*, int, int64_t, double, float*, cudaStream_t);
+template void launch_sum_parts<double>(const double*, int, int64_t, double, double*, cudaStream_t);
 template void launch_sample_mean<float>(const float*, int64_t, int, int64_t, double*, cudaStream_t);
 template void launch_sample_mean<double>(const double*, int64_t, int, int64_t, double*, cudaStream_t);
 template void launch_convert<float>(const double*, float*, int64_t, cudaStream_t);

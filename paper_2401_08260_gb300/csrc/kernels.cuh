@@ -39,14 +39,27 @@ void launch_grad_gemm(const T* G, int64_t M, int P, const T* xi, int d, const T*
 // ------------------------------------------------------------ k_tcgen05.cu
 // Row pitch (elements) of the 16-bit operands of the tensor-core projection.
 int64_t umma_operand_ld(int d);
-// out[i][k] = 16-bit (x[i][k] - mu[k]) (BF16, or FP16 hi plus scaled FP16 lo when split).
+// out[i][k] = 16-bit (x[i][k] - mu[k]) (BF16, or FP16 hi plus scaled FP16 lo when split);
+// label names the launch in the timing registry.
 void launch_center_cast(const float* x, int64_t n, int d, int64_t ldx, const float* mu, void* out, void* out_lo,
-                        int split, cudaStream_t st);
+                        int split, cudaStream_t st, const char* label = "center_cast");
 // Z[p][i] = sum_k xi[p][k] xc[i][k] on tensor cores (tcgen05, TMA), FP32 accumulate;
 // *absmax = max(*absmax, max |Z|) when absmax != NULL; timeouts set bits 8/16/32 of *err.
 void launch_project_umma(const void* xa, const void* xa_lo, int64_t n, const void* xib, const void* xib_lo, int P,
                          int d, int split, float* Z, int64_t ldz, float* absmax, unsigned* err, cudaStream_t st);
 
+// Fused target side of the Chebyshev evaluation: BF16 tensor-core projection of n
+// centred targets (xa) onto the P directions (xib) with, in the epilogue, the
+// Clenshaw sum t_p = sum_l beta[p][l] T_l(z/R) accumulated over the slices of each
+// tile; part receives umma_cheb_parts(P) x n FP64 partial sums (no projection is
+// stored).  Targets outside [-R, R] set bit 4 of *err.
+int64_t umma_cheb_parts(int P);
+bool umma_cheb_fits(int P, int q);
+void launch_umma_cheb_target(const void* xa, int64_t n, const void* xib, int P, int d, const float* coef, int q,
+                             int horner, double R, double* part, unsigned* err, cudaStream_t st);
+// s[i] = scale * sum_{r < parts} part[r * n + i] (fixed order).
+template <class T>
+void launch_sum_parts(const double* part, int parts, int64_t n, double scale, T* s, cudaStream_t st);
 // dst[c][r] = BF16(src[r][c]) (rows x cols FP32 in; cols x ld16(rows) out, zero padded).
 void launch_transpose_bf16(const float* src, int rows, int cols, void* dst, cudaStream_t st);
 // Backward product on tensor cores: gy[m][k] = scale * gs[m] * sum_p G[m][p] xi[p][k] with G (M x P)
@@ -67,7 +80,30 @@ struct FourierDev {
     double beta;
     // certified window: every projected target lies in [-R, R]
     double R;
+    // Chebyshev evaluation: number of terms (padded); horner = 1 when the monomial
+    // coefficients mono (T, P x q) may replace Clenshaw on the target side
+    int q;
+    int horner;
+    const void* mono;
 };
+
+// Chebyshev evaluation of the truncated Fourier sum (Jacobi-Anger expansion on [-R, R]):
+// source side beta[p][l] = sum_j M[l][j] sum_n w_n T_j(z_{p,n}/R) (M is q x q, FP64);
+// target side acc[m] += sum_p sum_l beta[p][l] T_l(z_{p,m}/R), or the z-derivative into
+// G[m][p]; targets outside [-R, R] set bit 4 of *err.
+// With mono != nullptr (q <= 16) the source side also writes the same polynomials in the
+// monomial basis, mono[p][k] = sum_l beta[p][l] [u^k] T_l(u) (converted in FP64), and sets
+// *mono_bad when for some slice sum_k |mono| > mono_ratio sum_l |beta|.  Only otherwise is
+// Horner's rule (one FMA per term, rounding bound gamma_2q sum_k |mono_k|) used on the
+// target side.
+template <class T>
+void launch_cheb_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, const FourierDev& fd,
+                        const double* M, T* beta, T* mono, unsigned* mono_bad, double mono_ratio, T* scratch,
+                        int64_t scratch_elems, cudaStream_t st);
+int64_t cheb_source_scratch(int P, int64_t n, const FourierDev& fd);
+template <class T>
+void launch_cheb_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const T* beta, double* acc,
+                        T* G, unsigned* err, cudaStream_t st);
 
 // NDFT, source side: cw[p][j] = c_{k_lo+j} * sum_n w_n exp(-2 pi i k z_{p,n} / L),
 // j = 0..K-1 (and cw0[p] = c_0 sum_n w_n if has_k0).  coef holds c_k (FP64).

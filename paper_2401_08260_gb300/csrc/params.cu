@@ -297,6 +297,93 @@ void fft_inplace(std::vector<std::complex<double>>& a, int sign) {
     }
 }
 
+// J_0(x) .. J_nmax(x) for x >= 0 by Miller's backward recurrence
+// J_{n-1} = (2n/x) J_n - J_{n+1}, normalised with J_0 + 2 sum_k J_{2k} = 1.
+void bessel_j_all(double x, int nmax, std::vector<double>& out) {
+    out.assign(nmax + 1, 0.0);
+    if (x == 0.0) {
+        out[0] = 1.0;
+        return;
+    }
+    int start = std::max(nmax, static_cast<int>(x)) + 40 + static_cast<int>(std::sqrt(40.0 * std::max(nmax, 1)));
+    if (start % 2) ++start;
+    double jp1 = 0.0, j = 1e-300, norm = 0.0;
+    std::vector<double> tmp(start + 1, 0.0);
+    for (int n = start; n >= 1; --n) {
+        const double jm1 = (2.0 * n / x) * j - jp1;
+        jp1 = j;
+        j = jm1;
+        tmp[n - 1] = j;
+        if (std::fabs(j) > 1e250) {  // rescale to stay in range
+            for (int q = n - 1; q <= start; ++q) tmp[q] *= 1e-250;
+            jp1 *= 1e-250;
+            j *= 1e-250;
+        }
+    }
+    tmp[start] = 0.0;
+    // recompute the normalisation over the stored values: J_0 + 2 sum J_{2k}
+    norm = tmp[0];
+    for (int n = 2; n <= start; n += 2) norm += 2.0 * tmp[n];
+    for (int n = 0; n <= nmax; ++n) out[n] = tmp[n] / norm;
+}
+
+// Chebyshev evaluation of the truncated Fourier sum on [-R, R] (Jacobi-Anger expansion):
+// with u = z / R and w_k = 2 pi k R / L,
+//   exp(+-i w u) = sum_j eps_j (+-i)^j J_j(w) T_j(u),   eps_0 = 1, eps_j = 2,
+// so  t(v) = c_0 w^_0 + 2 Re sum_{k>0} c_k w^_k e^{i w_k v} = sum_l beta_l T_l(v),  beta = M mu,
+//   mu_j = sum_n w_n T_j(u_n),
+//   M_lj = 2 eps_l eps_j cos(pi (l - j) / 2) sum_{k>0} c_k J_l(w_k) J_j(w_k)  (+ c_0 at l = j = 0).
+// Truncating the expansion at q terms changes t by at most 4 sum|w| sum_k c_k tau_k,
+// tau_k = 2 sum_{j >= q} |J_j(w_k)|; q is the smallest value keeping that below tol_c.
+void choose_chebyshev(FourierHost* fp, double tol_c) {
+    const int K = fp->k_hi - fp->k_lo + 1;
+    const double wmax = 2.0 * PI * fp->k_hi * fp->R / fp->L;
+    const int qcap = 96;
+    std::vector<std::vector<double>> J(K);
+    for (int i = 0; i < K; ++i) bessel_j_all(2.0 * PI * (fp->k_lo + i) * fp->R / fp->L, qcap + 64, J[i]);
+    int q = 0;
+    double err = 0.0;
+    for (int cand = 4; cand <= qcap; ++cand) {
+        double e = 0.0;
+        for (int i = 0; i < K; ++i) {
+            double tau = 0.0;
+            for (int j = cand; j <= qcap + 64; ++j) tau += 2.0 * std::fabs(J[i][j]);
+            e += 4.0 * fp->coef[i] * tau;
+        }
+        if (e <= tol_c) {
+            q = cand;
+            err = e;
+            break;
+        }
+    }
+    (void)wmax;
+    if (!q) {
+        fp->cheb_q = fp->cheb_qp = 0;
+        return;
+    }
+    int qp = 96;
+    for (int b : {8, 12, 16, 24, 32, 48, 64, 96})
+        if (q <= b) {
+            qp = b;
+            break;
+        }
+    fp->cheb_q = q;
+    fp->cheb_qp = qp;
+    fp->cheb_err = err;
+    fp->cheb_M.assign(static_cast<size_t>(qp) * qp, 0.0);
+    for (int l = 0; l < q; ++l)
+        for (int j = 0; j < q; ++j) {
+            const int e = l - j;
+            if (e % 2) continue;
+            const double sgn = ((e / 2) % 2) ? -1.0 : 1.0;
+            const double el = l ? 2.0 : 1.0, ej = j ? 2.0 : 1.0;
+            double acc = 0.0;
+            for (int i = 0; i < K; ++i) acc += fp->coef[i] * J[i][l] * J[i][j];
+            fp->cheb_M[static_cast<size_t>(l) * qp + j] = 2.0 * el * ej * sgn * acc;
+        }
+    if (fp->has_k0) fp->cheb_M[0] += fp->coef[K];  // c_0 w^_0, w^_0 = mu_0
+}
+
 std::mutex cache_mu;
 std::map<std::tuple<int, double, int, double, double, int, int>, FourierHost> cache;
 
@@ -389,17 +476,23 @@ FourierHost choose_gaussian(double sigma, int d, double R, int n_coeff_req, int 
     set_active_window(&fp);
     fp.mult.resize(Nc / 2);
     for (int k = 0; k < Nc / 2; ++k) fp.mult[k] = ck(k) / (fp.psi[k] * fp.psi[k]);
-    // method (the NDFT kernels take bands of at most 64 coefficients)
+    // method (the NDFT kernels take bands of at most 64 coefficients; the Chebyshev
+    // evaluation needs at most 96 terms)
     const int K = fp.k_hi - fp.k_lo + 1;
     if (method == SLK_FOURIER_NDFT && K > 64)
         fail(SLK_ERR_UNSUPPORTED, "the NDFT band has %d coefficients (at most 64); use the NFFT", K);
-    if (method == SLK_FOURIER_AUTO) method = (K <= 2 * fp.m && K <= 64) ? SLK_FOURIER_NDFT : SLK_FOURIER_NFFT;
+    if (method == SLK_FOURIER_CHEB || method == SLK_FOURIER_AUTO) choose_chebyshev(&fp, 0.25 * tol);
+    if (method == SLK_FOURIER_CHEB && fp.cheb_q == 0)
+        fail(SLK_ERR_UNSUPPORTED, "the Chebyshev evaluation would need more than 96 terms; use the NFFT");
+    if (method == SLK_FOURIER_AUTO)
+        method = fp.cheb_q ? SLK_FOURIER_CHEB : ((K <= 2 * fp.m && K <= 64) ? SLK_FOURIER_NDFT : SLK_FOURIER_NFFT);
     if (method == SLK_FOURIER_NFFT && fp.W > fp.n_g) {
         if (K > 64) fail(SLK_ERR_ACCURACY, "neither the NFFT window nor the NDFT band fits");
         method = SLK_FOURIER_NDFT;
     }
     fp.method = method;
-    fp.model_err = fp.period_err + (method == SLK_FOURIER_NDFT ? trunc + dropped : trunc + fp.window_err);
+    fp.model_err = fp.period_err + trunc +
+                   (method == SLK_FOURIER_NDFT ? dropped : (method == SLK_FOURIER_CHEB ? dropped + fp.cheb_err : fp.window_err));
     {
         std::lock_guard<std::mutex> g(cache_mu);
         cache[{0, sigma, d, R, tol, n_coeff_req, method_req}] = fp;

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libslk.so")
 
 KERNELS = {"gaussian": 0, "laplacian": 1, "negdist": 2}
 PRECISIONS = {"f64": 0, "f32": 1, "bf16": 2, "f16x3": 3}
-METHODS = {"auto": 0, "nfft": 1, "ndft": 2}
+METHODS = {"auto": 0, "nfft": 1, "ndft": 2, "cheb": 3}
 STATUS = {0: "SLK_OK", 1: "SLK_ERR_INVALID", 2: "SLK_ERR_OOM", 3: "SLK_ERR_CUDA", 4: "SLK_ERR_ACCURACY",
           5: "SLK_ERR_TIMEOUT", 6: "SLK_ERR_BUSY", 7: "SLK_ERR_UNSUPPORTED", 8: "SLK_ERR_NOT_FOUND"}
 
@@ -47,7 +47,8 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("precision", ctypes.c_int32), ("d", ctypes.c_int32),
                 ("P", ctypes.c_int32), ("N", ctypes.c_int64), ("method", ctypes.c_int32),
                 ("n_coeff", ctypes.c_int32), ("n_grid", ctypes.c_int32), ("window", ctypes.c_int32),
-                ("k_lo", ctypes.c_int32), ("k_hi", ctypes.c_int32), ("period", ctypes.c_double),
+                ("k_lo", ctypes.c_int32), ("k_hi", ctypes.c_int32), ("cheb_terms", ctypes.c_int32),
+                ("cheb_horner", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("period", ctypes.c_double),
                 ("radius", ctypes.c_double), ("model_error", ctypes.c_double), ("c_d", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64)]
 

@@ -41,7 +41,7 @@ def test_gauss_d16_fp64_ndft_full_config():
     assert info["model_error"] <= 1e-10
 
 
-@pytest.mark.parametrize("method", ["ndft", "nfft"])
+@pytest.mark.parametrize("method", ["ndft", "nfft", "cheb"])
 @pytest.mark.parametrize("N,M,P", [(5003, 777, 64), (70001, 97, 40)])
 def test_gauss_d784_fp32(method, N, M, P):
     dev = cuda_or_skip()
@@ -51,13 +51,34 @@ def test_gauss_d784_fp32(method, N, M, P):
     plan = _plan(to_dev(x, dev), to_dev(w, dev), "gaussian", sigma, xi, "f32", n_coeff=256, method=method)
     s = plan.sum(to_dev(y, dev))
     info = plan.info()
-    assert info["method"] == {"nfft": 1, "ndft": 2}[method]
+    assert info["method"] == {"nfft": 1, "ndft": 2, "cheb": 3}[method]
     ref, _ = oracle.sliced_sum("gaussian", sigma, x, y, w, xi)
     err = rel_inf(s, ref, np.abs(w).sum())
     assert err <= 1e-5, (err, info)
 
 
-@pytest.mark.parametrize("method", ["ndft", "nfft"])
+@pytest.mark.parametrize("precision,radius,P,horner", [("f32", 3.0, 48, 0), ("f32", 40.0, 48, 0),
+                                                        ("bf16", 2.5, 48, 1), ("bf16", 2.5, 600, 1)])
+def test_cheb_target_evaluation_forms(precision, radius, P, horner):
+    """Chebyshev target side by Horner's rule on monomial coefficients (BF16 projections,
+    few terms, small coefficient growth; fused into the projection for P = 48, a separate
+    kernel for P = 600) or by Clenshaw's recurrence (FP32, or many terms)."""
+    dev = cuda_or_skip()
+    d, N, M = 784, 6007, 513
+    x, y, w, xi = _cube(N, M, d, P)
+    sigma = math.sqrt(d)
+    plan = _plan(to_dev(x, dev), to_dev(w, dev), "gaussian", sigma, xi, precision, method="cheb", radius=radius)
+    info = plan.info()
+    assert info["method"] == 3 and info["cheb_horner"] == horner, info
+    s = plan.sum(to_dev(y, dev))
+    ref, gref, _ = oracle.sliced_sum("gaussian", sigma, x, y, w, xi, grad=True)
+    tol = 1e-5 if precision == "f32" else 2e-3
+    assert rel_inf(s, ref, w.sum()) <= tol
+    g = plan.grad(to_dev(y, dev))
+    assert rel_inf(g, gref, w.sum()) <= 2 * tol
+
+
+@pytest.mark.parametrize("method", ["ndft", "nfft", "cheb"])
 def test_gauss_fp64_small_dims(method):
     """FP64 NDFT and NFFT for d = 3 and d = 16 (d = 3 has a closed-form f)."""
     dev = cuda_or_skip()
@@ -129,7 +150,8 @@ def test_laplace_fp64():
 
 
 @pytest.mark.parametrize("kernel,param,method", [("gaussian", None, "ndft"), ("gaussian", None, "nfft"),
-                                                 ("negdist", 0.0, "auto"), ("laplacian", None, "auto")])
+                                                 ("gaussian", None, "cheb"), ("negdist", 0.0, "auto"),
+                                                 ("laplacian", None, "auto")])
 def test_gradient_fp32(kernel, param, method):
     dev = cuda_or_skip()
     d, N, M, P = 40, 6007, 129, 29
