@@ -232,18 +232,27 @@ const T* mu_of(slk_plan plan) {
     else return plan->mu32.get();
 }
 
+// Centre and cast n FP32 points to the 16-bit tensor-core operand (one pass), then run
+// tc_kernel(xa, xa_lo, rows, st) on it.
+template <class F>
+void cast_and_run(slk_plan plan, const float* x, int64_t n, int64_t ldx, cudaStream_t st, F&& tc_kernel) {
+    const int split = plan->tc == 2;
+    const size_t bytes = static_cast<size_t>(n) * umma_operand_ld(plan->d) * 2;
+    DevBuf<unsigned char> xa(bytes, st), xl(split ? bytes : 0, st);
+    launch_center_cast(x, n, plan->d, ldx, plan->mu32.get(), xa.get(), xl.get(), split, st);
+    tc_kernel(static_cast<const void*>(xa.get()), static_cast<const void*>(xl.get()), n, st);
+}
+
 // Z (P x n, ldz = n) = projections of n points onto the plan's directions, centred;
 // *absmax = max |Z| when absmax != NULL.
 template <class T>
 void project(slk_plan plan, const T* x, int64_t n, int64_t ldx, T* Z, float* absmax, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
         if (plan->tc) {
-            const int split = plan->tc == 2;
-            const size_t bytes = static_cast<size_t>(n) * umma_operand_ld(plan->d) * 2;
-            DevBuf<unsigned char> xa(bytes, st), xl(split ? bytes : 0, st);
-            launch_center_cast(x, n, plan->d, ldx, plan->mu32.get(), xa.get(), xl.get(), split, st);
-            launch_project_umma(xa.get(), xl.get(), n, plan->xib.get(), plan->xib_lo.get(), plan->P, plan->d, split, Z,
-                                n, absmax, plan->err_dev.get(), st);
+            cast_and_run(plan, x, n, ldx, st, [&](const void* xa, const void* xl, int64_t rows, cudaStream_t s) {
+                launch_project_umma(xa, xl, rows, plan->xib.get(), plan->xib_lo.get(), plan->P, plan->d, plan->tc == 2,
+                                    Z, n, absmax, plan->err_dev.get(), s);
+            });
             return;
         }
     }
@@ -410,14 +419,13 @@ bool sum_fused_cheb(slk_plan plan, const T* y, int64_t M, int64_t ldy, void* s_u
         if (plan->tc != 1 || !plan->fourier || plan->sorting || plan->fh.method != SLK_FOURIER_CHEB ||
             !umma_cheb_fits(plan->P, plan->fh.cheb_qp) || M >= (int64_t(1) << 31))
             return false;
-        const size_t bytes = static_cast<size_t>(M) * umma_operand_ld(plan->d) * 2;
-        DevBuf<unsigned char> ya(bytes, st);
-        launch_center_cast(y, M, plan->d, ldy, plan->mu32.get(), ya.get(), nullptr, 0, st);
         const int parts = static_cast<int>(umma_cheb_parts(plan->P));
         DevBuf<double> part(static_cast<size_t>(parts) * M, st);
         const void* coef = plan->fd.horner ? plan->fd.mono : plan->beta.get();
-        launch_umma_cheb_target(ya.get(), M, plan->xib.get(), plan->P, plan->d, static_cast<const float*>(coef),
-                                plan->fh.cheb_qp, plan->fd.horner, plan->R, part.get(), plan->err_dev.get(), st);
+        cast_and_run(plan, y, M, ldy, st, [&](const void* ya, const void*, int64_t rows, cudaStream_t s) {
+            launch_umma_cheb_target(ya, rows, plan->xib.get(), plan->P, plan->d, static_cast<const float*>(coef),
+                                    plan->fh.cheb_qp, plan->fd.horner, plan->R, part.get(), M, plan->err_dev.get(), s);
+        });
         if (is_device_pointer(s_user)) {
             launch_sum_parts<T>(part.get(), parts, M, 1.0 / plan->P, static_cast<T*>(s_user), st);
         } else {

@@ -67,13 +67,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
-// bring a box of a tensor into L2 ahead of its load (no shared memory, no barrier)
-__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int c0, int c1) {
-    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(map)),
-                 "r"(c0), "r"(c1)
-                 : "memory");
-}
-
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -113,6 +106,30 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                  : "memory");
 }
 
+// the same arrival on the barrier at this offset in every CTA of mask (cluster)
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+}
+
+// TMA load delivered to this shared-memory offset (and mbarrier) in every CTA of mask
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
+        "%3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+
+// all threads of every CTA in the cluster
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     uint32_t r[32];
     asm volatile(
@@ -126,6 +143,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 template <class Half>
@@ -148,6 +175,54 @@ struct Smem {
 // (column tile fastest, so the CTAs that share a block of points run together and the
 // second read of A hits L2).  Two 256-column TMEM accumulators alternate between tiles:
 // the epilogue of one tile overlaps the MMAs of the next.
+// Target-side evaluation of one 8-column accumulator chunk (one row per thread): four
+// slices at a time, the QP coefficients of the group loaded up front (one broadcast
+// LDS.128 per degree from the degree-major table), then Horner's rule on monomial
+// coefficients or Clenshaw's recurrence on Chebyshev ones; the 32 values are added to
+// (s, c) with Kahan compensation.  Projections outside [-R, R] (or NaN) set bad.
+// Chunks of 8 keep the unrolled evaluation within the register budget of 384 threads.
+template <int QP, bool HORNER>
+__device__ __forceinline__ void cheb_chunk(const float (&v)[8], const float* __restrict__ bt0, int ppad, float R,
+                                           float inv_R, float& s, float& c, bool& bad) {
+#pragma unroll
+    for (int j = 0; j < 8; j += 4) {
+        float u[4], b1[4], b2[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float z = v[j + r];
+            if (!(z <= R && z >= -R)) bad = true;
+            u[r] = z * inv_R;
+            b1[r] = 0.0f;
+            b2[r] = 0.0f;
+        }
+        // fully unrolled over the degrees: the coefficient loads carry no loop dependence
+#pragma unroll
+        for (int k = QP - 1; k >= 0; --k) {
+            const float4 c4 = *reinterpret_cast<const float4*>(bt0 + j + k * ppad);
+            const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (HORNER) {
+                    b1[r] = fmaf(b1[r], u[r], cv[r]);
+                } else if (k >= 1) {
+                    const float bk = fmaf(u[r] + u[r], b1[r], cv[r] - b2[r]);
+                    b2[r] = b1[r];
+                    b1[r] = bk;
+                } else {
+                    b1[r] = fmaf(u[r], b1[r], cv[r] - b2[r]);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float y = b1[r] - c;
+            const float tt = s + y;
+            c = (tt - s) - y;
+            s = tt;
+        }
+    }
+}
+
 // Epilogues:
 //   EPI_Z:    Z[col * ldz + row] (slice-major projections), largest |z| into *absmax;
 //   EPI_ROW:  Z[row * ldz + col] * rowscale(row), rowscale = scale * (rs ? rs[row] : 1)
@@ -163,15 +238,28 @@ struct ChebEpi {
     int q;
     int horner;
     float inv_R, R;
-    double* part;  // (2 * col_tiles) x n
+    double* part;  // (2 * col_tiles) x ldp
+    int64_t ldp;
 };
 
-template <int EPI>
+//
+// CL = 2: clusters of two CTAs work on neighbouring 128-point blocks against the same
+// 256-slice tile; each CTA loads its own A tile and one half of the B tile, the B halves
+// multicast into both CTAs' shared memory, so the directions are read from L2 once per
+// cluster instead of once per CTA.  A stage is refilled only after both CTAs' MMAs have
+// released it (the MMA commit arrives on the empty barriers of both CTAs).
+// Work items: item -> slice tile (item % col_tiles), point blocks (item / col_tiles) * CL + rank.
+template <int EPI, int CL>
 __global__ void __launch_bounds__(EPI == EPI_CHEB ? 384 : 256, 1)
     k_umma_project(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int n, int P,
                    int d, int col_tiles, int tiles, float* __restrict__ Z, int64_t ldz, float* __restrict__ absmax,
                    unsigned* __restrict__ err, const float* __restrict__ rs, float scale, ChebEpi ce) {
+    static_assert(CL == 1 || CL == 2, "cluster of one or two CTAs");
     constexpr bool ROWMAJOR = EPI == EPI_ROW;
+    const int rank = CL > 1 ? static_cast<int>(blockIdx.x % CL) : 0;
+    const int unit = static_cast<int>(blockIdx.x / CL), nunits = static_cast<int>(gridDim.x / CL);
+    auto row_of = [&](int item) { return ((item / col_tiles) * CL + rank) * BM; };
+    auto col_of = [&](int item) { return (item % col_tiles) * BN; };
     constexpr int EPI_WARPS = EPI == EPI_CHEB ? 8 : 4;
     constexpr int STAGES = STAGES_1;
     extern __shared__ unsigned char smem_raw[];
@@ -186,7 +274,7 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB ? 384 : 256, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&sm->full[s], 1);
-            mbar_init(&sm->empty[s], 1);
+            mbar_init(&sm->empty[s], CL);  // one MMA commit per CTA of the cluster
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sm->acc_full[b], 1);
@@ -212,18 +300,16 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB ? 384 : 256, 1)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // the peer's barriers must be initialised before anything is multicast into them
+    if (CL > 1) cluster_sync();
     const uint32_t tmem = sm->tmem_base;
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer: one ring across all tiles of this CTA
         int g = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-            const int row0 = (tile / col_tiles) * BM, col0 = (tile % col_tiles) * BN;
-            // the points of this CTA's next tile come from HBM: start them towards L2 now
-            const int next = tile + static_cast<int>(gridDim.x);
-            if (next < tiles && (next / col_tiles) != (tile / col_tiles))
-                for (int kb = 0; kb < kblocks; ++kb) tma_prefetch_2d(&map_a, kb * BK, (next / col_tiles) * BM);
+        for (int tile = unit; tile < tiles && ok; tile += nunits) {
+            const int row0 = row_of(tile), col0 = col_of(tile);
             for (int kb = 0; kb < kblocks; ++kb, ++g) {
                 const int s = g % STAGES;
                 if (g >= STAGES && !mbar_wait(&sm->empty[s], ((g / STAGES) - 1) & 1)) {
@@ -234,15 +320,29 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB ? 384 : 256, 1)
                 unsigned char* st = base + s * STAGE_BYTES;
                 mbar_expect_tx(&sm->full[s], STAGE_BYTES);
                 tma_load_2d(st, &map_a, &sm->full[s], kb * BK, row0);
-                tma_load_2d(st + A_BYTES, &map_b, &sm->full[s], kb * BK, col0);
+                if constexpr (CL == 1) {
+                    tma_load_2d(st + A_BYTES, &map_b, &sm->full[s], kb * BK, col0);
+                } else {
+                    // this CTA's half of the directions, delivered to both CTAs
+                    tma_load_2d_mc(st + A_BYTES + rank * (B_BYTES / 2), &map_b, &sm->full[s], kb * BK,
+                                   col0 + rank * (BN / 2), static_cast<uint16_t>(0x3));
+                }
             }
         }
+        // wait until every stage this CTA filled has been released by both MMAs, so that
+        // no commit of the peer is still on its way to this CTA's barriers at exit
+        if (CL > 1 && ok)
+            for (int j = g > STAGES ? g - STAGES : 0; j < g; ++j)
+                if (!mbar_wait(&sm->empty[j % STAGES], (j / STAGES) & 1)) {
+                    atomicOr(err, 8u);
+                    break;
+                }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
         const uint32_t idesc = instr_desc(1u, BM, BN);
         int g = 0, local = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++local) {
+        for (int tile = unit; tile < tiles && ok; tile += nunits, ++local) {
             const int b = local & 1;
             if (local >= 2 && !mbar_wait(&sm->acc_empty[b], ((local >> 1) - 1) & 1)) {
                 atomicOr(err, 16u);
@@ -265,82 +365,47 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB ? 384 : 256, 1)
                     umma_f16(acc_t, smem_desc(st + k * 32), smem_desc(st + A_BYTES + k * 32), idesc,
                              (kb > 0 || k > 0) ? 1u : 0u);
                 }
-                umma_commit(&sm->empty[s]);
+                if constexpr (CL == 1) umma_commit(&sm->empty[s]);
+                else umma_commit_mc(&sm->empty[s], static_cast<uint16_t>(0x3));
             }
             umma_commit(&sm->acc_full[b]);
         }
     } else if (warp >= 4 && EPI == EPI_CHEB) {
-        // ---------------- fused target side: Clenshaw per (row, slice), row sums per tile
+        // ---------------- fused target side: t_p(z) per (row, slice), row sums per tile
         const int q4 = warp & 3, half = (warp - 4) >> 2;  // TMEM lane quarter, column half
         const uint32_t lane_off = static_cast<uint32_t>(q4 * 32) << 16;
         const int qn = ce.q;
         bool bad = false;
         int local = 0;
-        for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++local) {
+        for (int tile = unit; tile < tiles; tile += nunits, ++local) {
             const int b = local & 1;
             const int ct = tile % col_tiles;
-            const int row = (tile / col_tiles) * BM + q4 * 32 + lane, col0 = ct * BN + half * (BN / 2);
+            const int row = row_of(tile) + q4 * 32 + lane, col0 = ct * BN + half * (BN / 2);
             if (!mbar_wait(&sm->acc_full[b], (local >> 1) & 1)) {
                 atomicOr(err, 32u);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             float s = 0.0f, c = 0.0f;  // Kahan
-            for (int cc = 0; cc < BN / 2; cc += 32) {
-                float v[32];
-                tmem_ld32(tmem + lane_off + b * BN + half * (BN / 2) + cc, v);
-#pragma unroll
-                for (int j = 0; j < 32; j += 4) {
-                    // four slices at once: independent Clenshaw chains, one LDS.128 per degree
-                    const float* bt = sbeta + col0 + cc + j;
-                    float u[4], u2[4], b1[4], b2[4];
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const float z = v[j + r];
-                        if (!(z <= ce.R && z >= -ce.R)) bad = true;
-                        u[r] = z * ce.inv_R;
-                        u2[r] = u[r] + u[r];
-                        b1[r] = 0.0f;
-                        b2[r] = 0.0f;
-                    }
-                    if (ce.horner) {
-                        // monomial coefficients: Horner's rule, the result left in b1 with b2 = 0
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) b1[r] = 0.0f;
-                        for (int kk = qn - 1; kk >= 1; --kk) {
-                            const float4 c4 = *reinterpret_cast<const float4*>(bt + kk * ppad);
-                            const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-                            for (int r = 0; r < 4; ++r) b1[r] = fmaf(b1[r], u[r], cv[r]);
-                        }
-                    } else {
-                        for (int kk = qn - 1; kk >= 1; --kk) {
-                            const float4 c4 = *reinterpret_cast<const float4*>(bt + kk * ppad);
-                            const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-                            for (int r = 0; r < 4; ++r) {
-                                const float bk = fmaf(u2[r], b1[r], cv[r] - b2[r]);
-                                b2[r] = b1[r];
-                                b1[r] = bk;
-                            }
-                        }
-                    }
-                    const float4 c0 = *reinterpret_cast<const float4*>(bt);
-                    const float cv0[4] = {c0.x, c0.y, c0.z, c0.w};
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const float t = fmaf(u[r], b1[r], cv0[r] - b2[r]);
-                        const float y = t - c;
-                        const float tt = s + y;
-                        c = (tt - s) - y;
-                        s = tt;
-                    }
+            for (int cc = 0; cc < BN / 2; cc += 8) {
+                float v[8];
+                tmem_ld8(tmem + lane_off + b * BN + half * (BN / 2) + cc, v);
+                const float* bt = sbeta + col0 + cc;
+                if (qn == 12) {
+                    if (ce.horner) cheb_chunk<12, true>(v, bt, ppad, ce.R, ce.inv_R, s, c, bad);
+                    else cheb_chunk<12, false>(v, bt, ppad, ce.R, ce.inv_R, s, c, bad);
+                } else if (qn == 8) {
+                    if (ce.horner) cheb_chunk<8, true>(v, bt, ppad, ce.R, ce.inv_R, s, c, bad);
+                    else cheb_chunk<8, false>(v, bt, ppad, ce.R, ce.inv_R, s, c, bad);
+                } else {
+                    if (ce.horner) cheb_chunk<16, true>(v, bt, ppad, ce.R, ce.inv_R, s, c, bad);
+                    else cheb_chunk<16, false>(v, bt, ppad, ce.R, ce.inv_R, s, c, bad);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm->acc_empty[b]);
-            if (row < n) ce.part[static_cast<int64_t>(ct * 2 + half) * n + row] = static_cast<double>(s) - static_cast<double>(c);
+            if (row < n) ce.part[static_cast<int64_t>(ct * 2 + half) * ce.ldp + row] = static_cast<double>(s) - static_cast<double>(c);
         }
         if (bad) atomicOr(err, 4u);
     } else if (warp >= 4 && warp < 8) {
@@ -349,9 +414,9 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB ? 384 : 256, 1)
         const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
         float mx = 0.0f;
         int local = 0;
-        for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++local) {
+        for (int tile = unit; tile < tiles; tile += nunits, ++local) {
             const int b = local & 1;
-            const int row = (tile / col_tiles) * BM + q * 32 + lane, col0 = (tile % col_tiles) * BN;
+            const int row = row_of(tile) + q * 32 + lane, col0 = col_of(tile);
             if (!mbar_wait(&sm->acc_full[b], (local >> 1) & 1)) {
                 atomicOr(err, 32u);
                 break;
@@ -398,6 +463,8 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB ? 384 : 256, 1)
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    // neither CTA leaves while the other may still deliver into its shared memory
+    if (CL > 1) cluster_sync();
     if (warp == 2) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
@@ -589,38 +656,52 @@ size_t x3_smem_bytes() {
 
 // centre and convert: out[i][k] = (16-bit)(x[i][k] - mu[k]) for k < d, 0 for d <= k < ldo;
 // SPLIT also writes the scaled low part 2^11 (x - mu - hi) into out_lo.  One thread
-// converts 8 consecutive elements of a row (one 16-byte store per output).
+// converts 8 consecutive elements of a row (one 16-byte store per output), four such
+// groups per step with their loads issued together, so that a small grid (one sharing
+// the SMs with the projection) still keeps enough reads in flight.
 
 template <class Half, int SPLIT>
 __global__ void __launch_bounds__(256) k_center_cast(const float* __restrict__ x, int64_t n, int d, int64_t ldx,
                                                      const float* __restrict__ mu, Half* __restrict__ out,
                                                      Half* __restrict__ out_lo, int ldo, int vec_ok) {
+    constexpr int U = 4;
     const int chunks = ldo / 8;
     const int64_t total = n * static_cast<int64_t>(chunks);
-    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
-         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t i = e / chunks;
-        const int k0 = static_cast<int>(e - i * chunks) * 8;
-        float v[8];
-        const float* row = x + i * ldx + k0;
-        if (vec_ok && k0 + 8 <= d) {
-            const float4 a = __ldg(reinterpret_cast<const float4*>(row));
-            const float4 b = __ldg(reinterpret_cast<const float4*>(row + 4));
-            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-        } else {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t e0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e0 < total; e0 += U * stride) {
+        float v[U][8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = k0 + j < d ? row[j] : 0.0f;
-        }
-        union { Half h[8]; uint4 u; } hi, lo;
+        for (int u = 0; u < U; ++u) {
+            const int64_t e = e0 + u * stride;
+            const int64_t i = e / chunks;
+            const int k0 = static_cast<int>(e - i * chunks) * 8;
+            const float* row = x + i * ldx + k0;
+            if (e < total && vec_ok && k0 + 8 <= d) {
+                const float4 a = __ldg(reinterpret_cast<const float4*>(row));
+                const float4 b = __ldg(reinterpret_cast<const float4*>(row + 4));
+                v[u][0] = a.x; v[u][1] = a.y; v[u][2] = a.z; v[u][3] = a.w;
+                v[u][4] = b.x; v[u][5] = b.y; v[u][6] = b.z; v[u][7] = b.w;
+            } else {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const float c = k0 + j < d ? v[j] - (mu ? __ldg(mu + k0 + j) : 0.0f) : 0.0f;
-            hi.h[j] = to_half<Half>(c);
-            if constexpr (SPLIT != 0) lo.h[j] = __float2half_rn((c - static_cast<float>(hi.h[j])) * 2048.0f);
+                for (int j = 0; j < 8; ++j) v[u][j] = e < total && k0 + j < d ? row[j] : 0.0f;
+            }
         }
-        *reinterpret_cast<uint4*>(out + i * ldo + k0) = hi.u;
-        if constexpr (SPLIT != 0) *reinterpret_cast<uint4*>(out_lo + i * ldo + k0) = lo.u;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t e = e0 + u * stride;
+            if (e >= total) break;
+            const int64_t i = e / chunks;
+            const int k0 = static_cast<int>(e - i * chunks) * 8;
+            union { Half h[8]; uint4 u4; } hi, lo;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float c = k0 + j < d ? v[u][j] - (mu ? __ldg(mu + k0 + j) : 0.0f) : 0.0f;
+                hi.h[j] = to_half<Half>(c);
+                if constexpr (SPLIT != 0) lo.h[j] = __float2half_rn((c - static_cast<float>(hi.h[j])) * 2048.0f);
+            }
+            *reinterpret_cast<uint4*>(out + i * ldo + k0) = hi.u4;
+            if constexpr (SPLIT != 0) *reinterpret_cast<uint4*>(out_lo + i * ldo + k0) = lo.u4;
+        }
     }
 }
 
@@ -654,20 +735,90 @@ size_t umma_smem_bytes(size_t extra = 0) {
     constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
     return 1024 + STAGES_1 * (A_BYTES + B_BYTES) + ((sizeof(Smem) + 15) & ~size_t(15)) + extra;
 }
-constexpr size_t kChebSmem = 32 * 1024;  // room for beta (padded P x q floats) in the fused kernel
+// room for beta (padded P x q floats) in the fused kernel; kept a few KB under the SM's
+// capacity so that small kernels of another stream can share the SM
+constexpr size_t kChebSmem = 28 * 1024;
 
-// SM count of the current device; sets the shared-memory limit of the persistent kernel once
 template <int EPI>
-int sm_count() {
+size_t epi_smem() {
+    return umma_smem_bytes(EPI == EPI_CHEB ? kChebSmem : 0);
+}
+template <int EPI>
+constexpr int epi_threads() {
+    return EPI == EPI_CHEB ? 384 : THREADS;
+}
+
+// Co-resident work units of the persistent kernel on the current device (SMs for CL = 1,
+// clusters of two CTAs for CL = 2); sets the kernel's shared-memory limit once.
+template <int EPI, int CL>
+int persistent_units() {
+    static int units[128] = {};
+    int dev = 0;
+    SLK_CHECK_CUDA(cudaGetDevice(&dev));
+    SLK_REQUIRE(dev >= 0 && dev < 128, "device index out of range");
+    if (!units[dev]) {
+        SLK_CHECK_CUDA(cudaFuncSetAttribute(k_umma_project<EPI, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            static_cast<int>(epi_smem<EPI>())));
+        int sms = 0;
+        SLK_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (CL == 1) {
+            units[dev] = sms;
+        } else {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = CL;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(static_cast<unsigned>(sms / CL * CL));
+            cfg.blockDim = dim3(epi_threads<EPI>());
+            cfg.dynamicSmemBytes = epi_smem<EPI>();
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int clusters = 0;
+            SLK_CHECK_CUDA(cudaOccupancyMaxActiveClusters(&clusters, k_umma_project<EPI, CL>, &cfg));
+            SLK_REQUIRE(clusters > 0, "no cluster of the projection kernel fits on this device");
+            units[dev] = clusters;
+        }
+    }
+    return units[dev];
+}
+
+// Launch the persistent projection over n rows (A) and col_tiles 256-wide column tiles
+// (B); for CL = 2, map_b must have 128-row boxes (each CTA loads one half of a tile).
+template <int EPI, int CL>
+void launch_persistent(const CUtensorMap& ma, const CUtensorMap& mb, int64_t n, int P, int d, int col_tiles, float* Z,
+                       int64_t ldz, float* absmax, unsigned* err, const float* rs, float scale, const ChebEpi& ce,
+                       cudaStream_t st) {
+    const int64_t items = ceil_div(ceil_div(n, BM), CL) * col_tiles;
+    SLK_REQUIRE(items < (int64_t(1) << 31) && n < (int64_t(1) << 31), "too many points for one projection");
+    const int64_t units = persistent_units<EPI, CL>();
+    const int64_t grid = (items < units ? items : units) * CL;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(epi_threads<EPI>());
+    cfg.dynamicSmemBytes = epi_smem<EPI>();
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = CL > 1 ? 1 : 0;
+    SLK_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_umma_project<EPI, CL>, ma, mb, static_cast<int>(n), P, d, col_tiles,
+                                      static_cast<int>(items), Z, ldz, absmax, err, rs, scale, ce));
+}
+
+// Clusters of two for the forward projections (B multicast); 1 = one CTA per tile.
+constexpr int kProjCluster = 2;
+
+int sm_count_dev() {
     static int sms[128] = {};
     int dev = 0;
     SLK_CHECK_CUDA(cudaGetDevice(&dev));
     SLK_REQUIRE(dev >= 0 && dev < 128, "device index out of range");
-    if (!sms[dev]) {
-        SLK_CHECK_CUDA(cudaFuncSetAttribute(k_umma_project<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            static_cast<int>(umma_smem_bytes(EPI == EPI_CHEB ? kChebSmem : 0))));
-        SLK_CHECK_CUDA(cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev));
-    }
+    if (!sms[dev]) SLK_CHECK_CUDA(cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev));
     return sms[dev];
 }
 
@@ -697,27 +848,21 @@ void launch_transpose_bf16(const float* src, int rows, int cols, void* dst, cuda
 int64_t umma_cheb_parts(int P) { return 2 * ceil_div(P, BN); }
 
 bool umma_cheb_fits(int P, int q) {
-    return q >= 1 && static_cast<size_t>(ceil_div(P, BN) * BN) * q * sizeof(float) <= kChebSmem;
+    return (q == 8 || q == 12 || q == 16) && static_cast<size_t>(ceil_div(P, BN) * BN) * q * sizeof(float) <= kChebSmem;
 }
 
 void launch_umma_cheb_target(const void* xa, int64_t n, const void* xib, int P, int d, const float* coef, int q,
-                             int horner, double R, double* part, unsigned* err, cudaStream_t st) {
+                             int horner, double R, double* part, int64_t ldp, unsigned* err, cudaStream_t st) {
     if (n <= 0) return;
     SLK_REQUIRE(umma_cheb_fits(P, q), "Chebyshev coefficients do not fit the fused kernel");
-    SLK_REQUIRE(n < (int64_t(1) << 31), "too many points for one projection");
     const int64_t ld = umma_operand_ld(d);
     CUtensorMap ma = make_map(xa, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, n, d, ld, BM);
-    CUtensorMap mb = make_map(xib, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, P, d, ld, BN);
+    CUtensorMap mb = make_map(xib, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, P, d, ld, BN / kProjCluster);
     const int col_tiles = static_cast<int>(ceil_div(P, BN));
-    const int64_t blocks = ceil_div(n, BM) * col_tiles;
-    const int sms = sm_count<EPI_CHEB>();
-    const int64_t persistent = blocks < sms ? blocks : sms;
-    ChebEpi ce{coef, q, horner, static_cast<float>(1.0 / R), static_cast<float>(R), part};
+    ChebEpi ce{coef, q, horner, static_cast<float>(1.0 / R), static_cast<float>(R), part, ldp};
     SLK_TIMED("umma_cheb_target", st);
-    k_umma_project<EPI_CHEB><<<static_cast<unsigned>(persistent), 384, umma_smem_bytes(kChebSmem), st>>>(
-        ma, mb, static_cast<int>(n), P, d, col_tiles, static_cast<int>(blocks), nullptr, 0, nullptr, err, nullptr,
-        1.0f, ce);
-    SLK_CHECK_LAUNCH();
+    launch_persistent<EPI_CHEB, kProjCluster>(ma, mb, n, P, d, col_tiles, nullptr, 0, nullptr, err, nullptr, 1.0f, ce,
+                                              st);
 }
 
 void launch_grad_umma(const void* g16, int64_t M, int P, const void* xit16, int d, const float* gs, double scale,
@@ -728,23 +873,20 @@ void launch_grad_umma(const void* g16, int64_t M, int P, const void* xit16, int 
     CUtensorMap ma = make_map(g16, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, M, P, ld, BM);
     CUtensorMap mb = make_map(xit16, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, d, P, ld, BN);
     const int col_tiles = static_cast<int>(ceil_div(d, BN));
-    const int64_t blocks = ceil_div(M, BM) * col_tiles;
-    SLK_REQUIRE(blocks < (int64_t(1) << 31), "too many targets");
-    const int sms = sm_count<EPI_ROW>();
-    const int64_t persistent = blocks < sms ? blocks : sms;
     SLK_TIMED("umma_grad_bf16", st);
-    k_umma_project<EPI_ROW><<<static_cast<unsigned>(persistent), THREADS, umma_smem_bytes(), st>>>(
-        ma, mb, static_cast<int>(M), d, P, col_tiles, static_cast<int>(blocks), gy, ldg, nullptr, err, gs,
-        static_cast<float>(scale), ChebEpi{});
-    SLK_CHECK_LAUNCH();
+    launch_persistent<EPI_ROW, 1>(ma, mb, M, d, P, col_tiles, gy, ldg, nullptr, err, gs, static_cast<float>(scale),
+                                  ChebEpi{}, st);
 }
 
+int device_sm_count() { return sm_count_dev(); }
+
 void launch_center_cast(const float* x, int64_t n, int d, int64_t ldx, const float* mu, void* out, void* out_lo,
-                        int split, cudaStream_t st, const char* label) {
+                        int split, cudaStream_t st, const char* label, int max_blocks) {
     if (n <= 0) return;
     const int ldo = static_cast<int>(umma_operand_ld(d));
     const int64_t total = n * (ldo / 8);
-    const unsigned blocks = static_cast<unsigned>(ceil_div(total, 256) < 152 * 8 ? ceil_div(total, 256) : 152 * 8);
+    const int64_t cap = max_blocks > 0 ? max_blocks : 8 * sm_count_dev();
+    const unsigned blocks = static_cast<unsigned>(ceil_div(total, 256) < cap ? ceil_div(total, 256) : cap);
     const int vec_ok = (ldx % 4 == 0) && (reinterpret_cast<uintptr_t>(x) % 16 == 0);
     SLK_TIMED(label, st);
     if (split)
@@ -782,12 +924,10 @@ void launch_project_umma(const void* xa, const void* xa_lo, int64_t n, const voi
         k_umma_project_x3<<<grid, X3_THREADS, x3_smem_bytes(), st>>>(ma, mb, ma2, mb2, static_cast<int>(n), P, d,
                                                                      col_tiles, Z, ldz, absmax, err);
     } else {
-        const int sms = sm_count<EPI_Z>();
-        const int64_t persistent = blocks < sms ? blocks : sms;
+        CUtensorMap mbh = kProjCluster > 1 ? make_map(xib, dt, P, d, ld, BN / kProjCluster) : mb;
         SLK_TIMED("umma_project_bf16", st);
-        k_umma_project<EPI_Z><<<static_cast<unsigned>(persistent), THREADS, umma_smem_bytes(), st>>>(
-            ma, mb, static_cast<int>(n), P, d, col_tiles, static_cast<int>(blocks), Z, ldz, absmax, err, nullptr, 1.0f,
-            ChebEpi{});
+        launch_persistent<EPI_Z, kProjCluster>(ma, mbh, n, P, d, col_tiles, Z, ldz, absmax, err, nullptr, 1.0f,
+                                               ChebEpi{}, st);
     }
     SLK_CHECK_LAUNCH();
 }

@@ -40,9 +40,11 @@ void launch_grad_gemm(const T* G, int64_t M, int P, const T* xi, int d, const T*
 // Row pitch (elements) of the 16-bit operands of the tensor-core projection.
 int64_t umma_operand_ld(int d);
 // out[i][k] = 16-bit (x[i][k] - mu[k]) (BF16, or FP16 hi plus scaled FP16 lo when split);
-// label names the launch in the timing registry.
+// label names the launch in the timing registry; max_blocks > 0 caps the grid.
 void launch_center_cast(const float* x, int64_t n, int d, int64_t ldx, const float* mu, void* out, void* out_lo,
-                        int split, cudaStream_t st, const char* label = "center_cast");
+                        int split, cudaStream_t st, const char* label = "center_cast", int max_blocks = 0);
+// Streaming multiprocessors of the current device.
+int device_sm_count();
 // Z[p][i] = sum_k xi[p][k] xc[i][k] on tensor cores (tcgen05, TMA), FP32 accumulate;
 // *absmax = max(*absmax, max |Z|) when absmax != NULL; timeouts set bits 8/16/32 of *err.
 void launch_project_umma(const void* xa, const void* xa_lo, int64_t n, const void* xib, const void* xib_lo, int P,
@@ -50,13 +52,14 @@ void launch_project_umma(const void* xa, const void* xa_lo, int64_t n, const voi
 
 // Fused target side of the Chebyshev evaluation: BF16 tensor-core projection of n
 // centred targets (xa) onto the P directions (xib) with, in the epilogue, the
-// Clenshaw sum t_p = sum_l beta[p][l] T_l(z/R) accumulated over the slices of each
-// tile; part receives umma_cheb_parts(P) x n FP64 partial sums (no projection is
+// sum t_p = sum_l coef[p][l] T_l(z/R) (Clenshaw; or sum_l coef[p][l] (z/R)^l by Horner
+// when horner) accumulated over the slices of each tile; part receives
+// umma_cheb_parts(P) rows of n FP64 partial sums, row stride ldp (no projection is
 // stored).  Targets outside [-R, R] set bit 4 of *err.
 int64_t umma_cheb_parts(int P);
 bool umma_cheb_fits(int P, int q);
 void launch_umma_cheb_target(const void* xa, int64_t n, const void* xib, int P, int d, const float* coef, int q,
-                             int horner, double R, double* part, unsigned* err, cudaStream_t st);
+                             int horner, double R, double* part, int64_t ldp, unsigned* err, cudaStream_t st);
 // s[i] = scale * sum_{r < parts} part[r * n + i] (fixed order).
 template <class T>
 void launch_sum_parts(const double* part, int parts, int64_t n, double scale, T* s, cudaStream_t st);

@@ -100,3 +100,26 @@ def test_f16x3_laplacian_and_gradient():
     ref, gref, _ = oracle.sliced_sum("laplacian", wl.param, wl.x, wl.y, wl.w, wl.xi, grad=True)
     assert rel_inf(s, ref, wl.w.sum()) <= 1e-5
     assert rel_inf(g, gref, wl.w.sum()) <= 2e-5
+
+
+@pytest.mark.parametrize("kernel,precision,method,tol", [("gaussian", "bf16", "cheb", 2e-3),
+                                                         ("gaussian", "bf16", "ndft", 2e-3),
+                                                         ("negdist", "f16x3", "auto", 1e-5)])
+def test_large_point_sets_sampled(kernel, precision, method, tol):
+    """Point sets of a few hundred thousand rows (many persistent-tile waves, ragged last
+    tile): sampled targets, including rows at multiples of 65536, against the oracle."""
+    dev = cuda_or_skip()
+    d, P = 64, 32
+    N, M = 2 * 65536 + 12345, 5 * 65536 + 7
+    rng = np.random.Generator(np.random.PCG64(31))
+    x = rng.standard_normal((N, d), dtype=np.float32)
+    y = (rng.standard_normal((M, d), dtype=np.float32) + 0.25).astype(np.float32)
+    w = rng.random(N).astype(np.float32)
+    xi = workloads.directions(P, d, seed=32)
+    param = math.sqrt(d) if kernel == "gaussian" else 0.0
+    plan = _plan(to_dev(x, dev), to_dev(w, dev), kernel, param, xi, precision, method=method)
+    s = plan.sum(to_dev(y, dev)).cpu().numpy()
+    edges = np.array([0, 65535, 65536, 131071, 131072, 196607, 196608, 262143, 262144, 327679, 327680, M - 1])
+    idx = np.unique(np.concatenate([edges, oracle.sampled_targets(M, 12)]))
+    ref, _ = oracle.sliced_sum(kernel, param, x, y[idx], w, xi)
+    assert rel_inf(s[idx], ref, w.sum()) <= tol
