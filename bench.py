@@ -189,6 +189,24 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest x over the ranks of the default process group (x itself when there is
+    none): the job's time is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: every rank processes units_per_rank per step (replicas, weak
+    scaling), the step takes the slowest rank's ms_per_step."""
+    return units_per_rank * world / (ms_per_step * 1e-3)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -256,12 +274,8 @@ def run_ours(args):
     slk.timing_reset()
     dev_ms = ev0.elapsed_time(ev1)
     # wall time includes the host work of plan creation (parameter selection is cached)
-    ms = max(dev_ms, t_wall * 1e3) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = (wl.N + wl.M) * wl.P * world / (ms * 1e-3)
+    ms = max_over_ranks(max(dev_ms, t_wall * 1e3) / args.steps, dev)
+    value = job_rate((wl.N + wl.M) * wl.P, world, ms)
 
     # ---------------- dominant kernel roofline
     peaks, peak_kind = _peaks()
@@ -317,11 +331,12 @@ def run_ours(args):
         for _ in range(e2e_steps):
             host_step()
         torch.cuda.synchronize()
-        te = (time.perf_counter() - t0) / e2e_steps
+        te = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dev)
         bi = xh.numel() * xh.element_size() + yh.numel() * yh.element_size() + wh.numel() * wh.element_size() + \
             wl.xi.size * 8
         bo = sh.numel() * sh.element_size() + (gh.numel() * gh.element_size() if args.grad else 0)
-        e2e = {"value": (wl.N + wl.M) * wl.P * world / te, "unit": "slice-points/s", "h2d_bytes_per_step": int(bi),
+        e2e = {"value": job_rate((wl.N + wl.M) * wl.P, world, te * 1e3), "unit": "slice-points/s",
+               "h2d_bytes_per_step": int(bi),
                "d2h_bytes_per_step": int(bo), "ms_per_step": te * 1e3}
 
     cpu = None
