@@ -110,6 +110,21 @@ def plan_kwargs(wl, args):
                 n_coeff=wl.n_coeff, method=args.method or wl.method, directions=wl.xi)
 
 
+# DRAM read + write per point of one launch, from one ncu capture of the d = 784, P = 512 BF16
+# workload at n = 2e5 points (profiles/umma_cheb_target_and_center_cast_d784_n200k.md); the
+# traffic of these kernels grows in proportion to the points.  An entry is valid only for the
+# kernel as captured and is removed when that kernel changes.
+NCU_TRAFFIC_PER_POINT = {("gauss_d784", "center_cast"): (627.233024e6 + 281.766400e6) / 2e5,
+                         ("gauss_d784", "umma_cheb_target"): (314.511616e6 + 7.280640e6) / 2e5}
+
+
+def measured_traffic(wl, kernel_name, launches_per_step):
+    key = (wl.name, kernel_name)
+    if key not in NCU_TRAFFIC_PER_POINT or wl.d != 784 or wl.P != 512 or wl.N != wl.M:
+        return None
+    return NCU_TRAFFIC_PER_POINT[key] * wl.N
+
+
 def algorithmic(wl, info, precision, kernel_name, launches_per_step):
     """(algorithmic amount per launch, unit, bound) of one launch of a library kernel.
 
@@ -301,7 +316,8 @@ def run_ours(args):
             achieved = amount / avg_s / 1e9
             runit = "GB/s"
         roofline = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": runit,
-                    "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                    "frac": achieved / peak, "traffic": measured_traffic(wl, name, per_step),
+                    "peak_source": peak_kind,
                     "launch_ms": tot_ms / n_launch,
                     "share": tot_ms / sum(v[1] for v in kernels.values())}
 
