@@ -106,7 +106,7 @@ struct slk_plan_s {
     bool sorting = false;
     double sort_scale = 1.0;
     DevBuf<unsigned char> kw;  // sorted (key, w) pairs, P x N
-    DevBuf<double2> AB;        // FP64 prefix sums of w and w*key at bucket starts, P x (NB + 1)
+    DevBuf<double2> AB;        // prefix sums of w and w*key at bucket starts, P x (NB + 1), 16 B per entry
     DevBuf<float> kmin, kscale;
     DevBuf<int32_t> tab;       // first sorted index of each bucket, P x (NB + 1)
     int NB = 0;
@@ -333,20 +333,18 @@ void plan_sort_source(slk_plan plan, const T* Zx, const T* w, cudaStream_t st) {
     int nb = 1;
     while (static_cast<int64_t>(nb) * 8 < N && nb < (1 << 22)) nb <<= 1;
     plan->NB = nb;
-    DevBuf<T> keys(static_cast<size_t>(P) * N, st);
-    DevBuf<int32_t> idx(static_cast<size_t>(P) * N, st);
-    {
-        size_t sb = segmented_sort_scratch<T>(P, N);
-        DevBuf<unsigned char> scratch(sb, st);
-        launch_segmented_sort<T>(Zx, P, N, N, keys.get(), idx.get(), scratch.get(), sb, st);
-    }
     plan->kw.alloc(sorted_pairs_bytes<T>(P, N), st);
+    {
+        const size_t sb = sort_pairs_scratch<T>(P, N);
+        DevBuf<unsigned char> scratch(sb, st);
+        launch_sort_pairs<T>(Zx, P, N, N, w, plan->kw.get(), scratch.get(), sb, st);
+    }
     plan->AB.alloc(static_cast<size_t>(P) * (nb + 1), st);
     plan->kmin.alloc(P, st);
     plan->kscale.alloc(P, st);
     plan->tab.alloc(static_cast<size_t>(P) * (nb + 1), st);
-    launch_sorted_pairs<T>(keys.get(), idx.get(), w, P, N, plan->kw.get(), nb, plan->kmin.get(), plan->kscale.get(),
-                           plan->tab.get(), plan->AB.get(), st);
+    launch_bucket_tables<T>(P, N, plan->kw.get(), nb, plan->kmin.get(), plan->kscale.get(), plan->tab.get(),
+                            plan->AB.get(), st);
 }
 
 template <class T>

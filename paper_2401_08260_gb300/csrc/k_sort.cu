@@ -33,37 +33,29 @@ __device__ inline double key_from_bits(unsigned long long u) {
     return __longlong_as_double(static_cast<long long>((u & 0x8000000000000000ull) ? (u & 0x7fffffffffffffffull) : ~u));
 }
 
-template <class T, class U>
-__global__ void k_to_bits(const T* __restrict__ in, int64_t n, int64_t ld, U* __restrict__ out, int32_t* __restrict__ idx) {
-    const int p = blockIdx.y;
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        out[static_cast<int64_t>(p) * n + i] = key_bits(in[static_cast<int64_t>(p) * ld + i]);
-        idx[static_cast<int64_t>(p) * n + i] = static_cast<int32_t>(i);
-    }
-}
+template <class T>
+struct KW {
+    T key, w;
+};
 
-template <class T, class U>
-__global__ void k_from_bits(const U* __restrict__ in, int64_t total, T* __restrict__ out) {
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        out[i] = key_from_bits(in[i]);
-}
-
-// digit histogram of one tile: hist[(p * 256 + digit) * tiles + tile]
-template <class U>
-__global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const U* __restrict__ keys, int64_t n, int shift, int tiles,
+// Digit histogram of one tile: hist[(p * 256 + digit) * tiles + tile].  FIRST: the keys are
+// the order-preserving bits of the projections z (row stride ldz), otherwise the bits array.
+template <class T, class U, bool FIRST>
+__global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const T* __restrict__ z, int64_t ldz,
+                                                          const U* __restrict__ keys, int64_t n, int shift, int tiles,
                                                           int32_t* __restrict__ hist) {
     __shared__ int32_t h[RS_BINS];
     const int p = blockIdx.y, tile = blockIdx.x;
     h[threadIdx.x] = 0;
     __syncthreads();
-    const U* seg = keys + static_cast<int64_t>(p) * n;
     const int64_t base = static_cast<int64_t>(tile) * RS_TILE;
 #pragma unroll
     for (int r = 0; r < RS_ITEMS; ++r) {
-        int64_t i = base + r * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[static_cast<int>((seg[i] >> shift) & 0xffu)], 1);
+        const int64_t i = base + r * RS_THREADS + threadIdx.x;
+        if (i < n) {
+            const U k = FIRST ? key_bits(z[static_cast<int64_t>(p) * ldz + i]) : keys[static_cast<int64_t>(p) * n + i];
+            atomicAdd(&h[static_cast<int>((k >> shift) & 0xffu)], 1);
+        }
     }
     __syncthreads();
     hist[(static_cast<int64_t>(p) * RS_BINS + threadIdx.x) * tiles + tile] = h[threadIdx.x];
@@ -108,69 +100,122 @@ __global__ void __launch_bounds__(1024) k_radix_scan(int32_t* __restrict__ hist,
     }
 }
 
-// stable scatter of one tile by the digit at `shift`
-template <class U>
-__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const U* __restrict__ kin, const int32_t* __restrict__ vin,
-                                                             int64_t n, int shift, int tiles,
-                                                             const int32_t* __restrict__ hist, U* __restrict__ kout,
-                                                             int32_t* __restrict__ vout) {
-    __shared__ int32_t off[RS_BINS];
-    __shared__ int32_t cnt[RS_THREADS / 32][RS_BINS];
-    __shared__ int32_t round_tot[RS_BINS];
+constexpr int RS_WARPS = RS_THREADS / 32;
+
+template <class T, class U>
+constexpr size_t radix_pass_smem() {
+    return static_cast<size_t>(RS_TILE) * (sizeof(U) + sizeof(T)) + (RS_WARPS + 2) * RS_BINS * sizeof(int32_t);
+}
+
+// One stable LSD pass over a tile of RS_TILE keys with their payload (the source weight).
+// Each warp ranks a contiguous run of RS_TILE / RS_WARPS keys with warp-private digit
+// counters (match_any per 32 keys); per-digit prefixes over the warps and over the digits
+// give every key its place in the tile's digit-sorted order, the tile is reordered in shared
+// memory, and each digit's run is written to its global offset (from the scanned histogram)
+// in contiguous stores.  FIRST reads the projections and the weights (source index order);
+// LAST writes (key, w) pairs instead of bits and payload.
+template <class T, class U, bool FIRST, bool LAST>
+__global__ void __launch_bounds__(RS_THREADS, 3) k_radix_pass(const T* __restrict__ z, int64_t ldz, const T* __restrict__ w,
+                                                          const U* __restrict__ kin, const T* __restrict__ vin,
+                                                          int64_t n, int shift, int tiles,
+                                                          const int32_t* __restrict__ hist, U* __restrict__ kout,
+                                                          T* __restrict__ vout, KW<T>* __restrict__ pout) {
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    U* sk = reinterpret_cast<U*>(rs_smem);
+    T* sv = reinterpret_cast<T*>(sk + RS_TILE);
+    int32_t* wcnt = reinterpret_cast<int32_t*>(sv + RS_TILE);  // [warp][digit]
+    int32_t* loc = wcnt + RS_WARPS * RS_BINS;                   // tile-local start of each digit
+    int32_t* glob = loc + RS_BINS;                              // global start of each digit for this tile
     const int p = blockIdx.y, tile = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t seg = static_cast<int64_t>(p) * n;
-    off[threadIdx.x] = hist[(static_cast<int64_t>(p) * RS_BINS + threadIdx.x) * tiles + tile];
-    for (int w = 0; w < RS_THREADS / 32; ++w) cnt[w][threadIdx.x] = 0;
-    const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t base = static_cast<int64_t>(tile) * RS_TILE;
+    for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) wcnt[i] = 0;
+    glob[threadIdx.x] = hist[(static_cast<int64_t>(p) * RS_BINS + threadIdx.x) * tiles + tile];
     __syncthreads();
+
+    constexpr int RUN = RS_TILE / RS_WARPS;  // keys per warp
+    U key[RS_ITEMS];
+    T val[RS_ITEMS];
+    int rank[RS_ITEMS];
+    int32_t* mycnt = wcnt + warp * RS_BINS;
+    const unsigned lt_mask = (1u << lane) - 1u;
+#pragma unroll
     for (int r = 0; r < RS_ITEMS; ++r) {
-        const int64_t i = base + r * RS_THREADS + threadIdx.x;
-        const bool valid = i < n;
-        U key = valid ? kin[seg + i] : U(0);
-        int32_t val = valid ? vin[seg + i] : 0;
-        const int digit = valid ? static_cast<int>((key >> shift) & 0xffu) : RS_BINS + lane;
+        const int64_t e = base + warp * RUN + r * 32 + lane;
+        const bool valid = e < n;
+        if (FIRST) {
+            key[r] = valid ? key_bits(z[static_cast<int64_t>(p) * ldz + e]) : U(0);
+            val[r] = valid ? w[e] : T(0);
+        } else {
+            key[r] = valid ? kin[seg + e] : U(0);
+            val[r] = valid ? vin[seg + e] : T(0);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const int64_t e = base + warp * RUN + r * 32 + lane;
+        const bool valid = e < n;
+        const int digit = valid ? static_cast<int>((key[r] >> shift) & 0xffu) : RS_BINS + lane;
         const unsigned peers = __match_any_sync(0xffffffffu, digit);
-        const int rank = __popc(peers & lt_mask);
-        if (valid && rank == 0) cnt[warp][digit] = __popc(peers);
-        __syncthreads();
-        {  // per digit: exclusive prefix over warps (warp order = stable order)
-            int32_t run = 0;
-            for (int w = 0; w < RS_THREADS / 32; ++w) {
-                int32_t c = cnt[w][threadIdx.x];
-                cnt[w][threadIdx.x] = run;
-                run += c;
-            }
-            round_tot[threadIdx.x] = run;
+        const int before = valid ? mycnt[digit] : 0;
+        rank[r] = before + __popc(peers & lt_mask);
+        __syncwarp();
+        if (valid && (peers & lt_mask) == 0u) mycnt[digit] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over the warps (warp order = input order), tile total
+    const int t = threadIdx.x;
+    int32_t run = 0;
+#pragma unroll
+    for (int q = 0; q < RS_WARPS; ++q) {
+        const int32_t c = wcnt[q * RS_BINS + t];
+        wcnt[q * RS_BINS + t] = run;
+        run += c;
+    }
+    // exclusive scan of the digit totals over the 256 digits
+    {
+        int32_t x = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
+        __shared__ int32_t wt[RS_WARPS];
+        if (lane == 31) wt[warp] = x;
         __syncthreads();
-        if (valid) {
-            const int32_t pos = off[digit] + cnt[warp][digit] + rank;
-            kout[seg + pos] = key;
-            vout[seg + pos] = val;
+        int32_t off = 0;
+        for (int q = 0; q < warp; ++q) off += wt[q];
+        loc[t] = off + x - run;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const int64_t e = base + warp * RUN + r * 32 + lane;
+        if (e < n) {
+            const int digit = static_cast<int>((key[r] >> shift) & 0xffu);
+            const int pos = loc[digit] + wcnt[warp * RS_BINS + digit] + rank[r];
+            sk[pos] = key[r];
+            sv[pos] = val[r];
         }
-        __syncthreads();
-        off[threadIdx.x] += round_tot[threadIdx.x];
-        for (int w = 0; w < RS_THREADS / 32; ++w) cnt[w][threadIdx.x] = 0;
-        __syncthreads();
+    }
+    __syncthreads();
+    const int cnt = static_cast<int>(n - base < RS_TILE ? n - base : RS_TILE);
+    for (int j = threadIdx.x; j < cnt; j += RS_THREADS) {
+        const U k = sk[j];
+        const int digit = static_cast<int>((k >> shift) & 0xffu);
+        const int64_t g = seg + glob[digit] + (j - loc[digit]);
+        if (LAST) {
+            pout[g] = KW<T>{key_from_bits(k), sv[j]};
+        } else {
+            kout[g] = k;
+            vout[g] = sv[j];
+        }
     }
 }
 
 // ------------------------------------------------------------ sorted pairs and bucket sums
-
-template <class T>
-struct KW {
-    T key, w;
-};
-
-template <class T>
-__global__ void k_gather_pairs(const T* __restrict__ keys, const int32_t* __restrict__ idx, const T* __restrict__ w,
-                               int64_t total, int64_t n, KW<T>* __restrict__ kw) {
-    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
-         e += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        kw[e] = KW<T>{keys[e], w[idx[e]]};
-}
 
 __device__ inline int bucket_of(float z, float kmin, float kscale, int NB) {
     float f = (z - kmin) * kscale;
@@ -188,44 +233,236 @@ __global__ void k_bucket_minmax(const KW<T>* __restrict__ kw, int P, int64_t n, 
     }
 }
 
-// tab[p][b] = first sorted index whose bucket is >= b (b = 0..NB)
+// Exact-enough sums without FP64 arithmetic in the hot loops (FP64 runs at a small
+// fraction of the FP32 rate on this GPU): a value is an unevaluated pair hi + lo of floats
+// ("double-float", about 44 significant bits).  TwoSum (Knuth) adds without rounding loss,
+// and a product w key is split exactly into p + e with an FMA, e = fma(w, key, -p).
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_norm(float hi, float lo) {
+    const float s = hi + lo;
+    return DF{s, lo - (s - hi)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = a.hi + b.hi, v = s - a.hi;
+    const float e = (a.hi - (s - v)) + (b.hi - v) + a.lo + b.lo;
+    return df_norm(s, e);
+}
+__device__ __forceinline__ DF df_shfl_up(DF a, int o) {
+    return DF{__shfl_up_sync(0xffffffffu, a.hi, o), __shfl_up_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ DF df_shfl_down(DF a, int o) {
+    return DF{__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ DF df_from(double d) {
+    const float hi = static_cast<float>(d);
+    return DF{hi, static_cast<float>(d - static_cast<double>(hi))};
+}
+__device__ __forceinline__ double df_value(DF a) { return static_cast<double>(a.hi) + static_cast<double>(a.lo); }
+
+// Prefix entry at a bucket start: sums of w and w key before it.  FP32 data: double-float
+// pairs (no FP64 arithmetic on the target side); FP64 data: doubles.  16 bytes either way.
 template <class T>
-__global__ void k_bucket_tab(const KW<T>* __restrict__ kw, int64_t n, int NB, const float* __restrict__ kmin,
-                             const float* __restrict__ kscale, int32_t* __restrict__ tab) {
-    const int p = blockIdx.y;
+struct Pre;
+template <>
+struct Pre<float> {
+    float ahi, alo, bhi, blo;
+};
+template <>
+struct Pre<double> {
+    double a, b;
+};
+
+// Running sums (w, w key) over sorted pairs, and their scan arithmetic.
+template <class T>
+struct PairSum;
+template <>
+struct PairSum<float> {
+    DF a{0.0f, 0.0f}, b{0.0f, 0.0f};
+    __device__ __forceinline__ void add(float w, float key) {
+        // TwoSum into (hi, lo) without renormalising every step
+        float s = a.hi + w, bp = s - a.hi;
+        a.lo += (a.hi - (s - bp)) + (w - bp);
+        a.hi = s;
+        const float pr = w * key;
+        s = b.hi + pr;
+        bp = s - b.hi;
+        b.lo += (b.hi - (s - bp)) + (pr - bp) + fmaf(w, key, -pr);
+        b.hi = s;
+    }
+    __device__ __forceinline__ void norm() {
+        a = df_norm(a.hi, a.lo);
+        b = df_norm(b.hi, b.lo);
+    }
+    __device__ __forceinline__ void plus(const PairSum& o) {
+        a = df_add(a, o.a);
+        b = df_add(b, o.b);
+    }
+    __device__ __forceinline__ PairSum shfl_up(int o) const {
+        PairSum r;
+        r.a = df_shfl_up(a, o);
+        r.b = df_shfl_up(b, o);
+        return r;
+    }
+    __device__ __forceinline__ PairSum shfl_down(int o) const {
+        PairSum r;
+        r.a = df_shfl_down(a, o);
+        r.b = df_shfl_down(b, o);
+        return r;
+    }
+    __device__ __forceinline__ double2 to_double2() const { return make_double2(df_value(a), df_value(b)); }
+    __device__ static PairSum from_double2(double2 v) {
+        PairSum r;
+        r.a = df_from(v.x);
+        r.b = df_from(v.y);
+        return r;
+    }
+    __device__ __forceinline__ Pre<float> entry() const { return Pre<float>{a.hi, a.lo, b.hi, b.lo}; }
+};
+template <>
+struct PairSum<double> {
+    double a = 0.0, b = 0.0;
+    __device__ __forceinline__ void add(double w, double key) {
+        a += w;
+        b = fma(w, key, b);
+    }
+    __device__ __forceinline__ void norm() {}
+    __device__ __forceinline__ void plus(const PairSum& o) {
+        a += o.a;
+        b += o.b;
+    }
+    __device__ __forceinline__ PairSum shfl_up(int o) const {
+        PairSum r;
+        r.a = __shfl_up_sync(0xffffffffu, a, o);
+        r.b = __shfl_up_sync(0xffffffffu, b, o);
+        return r;
+    }
+    __device__ __forceinline__ PairSum shfl_down(int o) const {
+        PairSum r;
+        r.a = __shfl_down_sync(0xffffffffu, a, o);
+        r.b = __shfl_down_sync(0xffffffffu, b, o);
+        return r;
+    }
+    __device__ __forceinline__ double2 to_double2() const { return make_double2(a, b); }
+    __device__ static PairSum from_double2(double2 v) {
+        PairSum r;
+        r.a = v.x;
+        r.b = v.y;
+        return r;
+    }
+    __device__ __forceinline__ Pre<double> entry() const { return Pre<double>{a, b}; }
+};
+
+constexpr int PS_THREADS = 256, PS_ITEMS = 8, PS_CHUNK = PS_THREADS * PS_ITEMS;
+
+// per chunk of PS_CHUNK sorted pairs: (sum w, sum w key) in FP64; cs[p][c], row length nchunk + 1
+template <class T>
+__global__ void __launch_bounds__(PS_THREADS) k_pair_chunk_sums(const KW<T>* __restrict__ kw, int64_t n, int nchunk,
+                                                               double2* __restrict__ cs) {
+    __shared__ PairSum<T> red[PS_THREADS / 32];
+    const int p = blockIdx.y, c = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const KW<T>* ks = kw + static_cast<int64_t>(p) * n;
+    const int64_t i0 = static_cast<int64_t>(c) * PS_CHUNK + threadIdx.x;
+    PairSum<T> acc;
+#pragma unroll
+    for (int r = 0; r < PS_ITEMS; ++r) {  // coalesced; a fixed order within the chunk
+        const int64_t i = i0 + r * PS_THREADS;
+        if (i < n) {
+            const KW<T> e = ks[i];
+            acc.add(e.w, e.key);
+        }
+    }
+    acc.norm();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc.plus(acc.shfl_down(o));
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        PairSum<T> t = red[0];
+        for (int q = 1; q < PS_THREADS / 32; ++q) t.plus(red[q]);
+        cs[static_cast<int64_t>(p) * (nchunk + 1) + c] = t.to_double2();
+    }
+}
+
+// Bucket tables from the sorted pairs and the scanned chunk sums (cs[p][c] = exclusive
+// prefix before chunk c): every sorted index i that starts buckets (b(i-1), b(i)] writes
+// tab[q] = i and AB[q] = the prefix of (w, w key) before i; the last index fills the
+// buckets above it (AB[NB] = the totals).  Each thread takes PS_ITEMS consecutive pairs.
+template <class T>
+__global__ void __launch_bounds__(PS_THREADS) k_pair_prefix_tab(const KW<T>* __restrict__ kw, int64_t n, int nchunk,
+                                                               const double2* __restrict__ cs, int NB,
+                                                               const float* __restrict__ kmin,
+                                                               const float* __restrict__ kscale,
+                                                               int32_t* __restrict__ tab, Pre<T>* __restrict__ AB) {
+    __shared__ PairSum<T> wsum[PS_THREADS / 32];
+    __shared__ PairSum<T> chunk_start;
+    const int p = blockIdx.y, c = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const KW<T>* ks = kw + static_cast<int64_t>(p) * n;
     int32_t* tb = tab + static_cast<int64_t>(p) * (NB + 1);
+    Pre<T>* ab = AB + static_cast<int64_t>(p) * (NB + 1);
     const float lo = kmin[p], sc = kscale[p];
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int b = bucket_of(static_cast<float>(ks[i].key), lo, sc, NB);
-        const int bp = i > 0 ? bucket_of(static_cast<float>(ks[i - 1].key), lo, sc, NB) : -1;
-        for (int q = bp + 1; q <= b; ++q) tb[q] = static_cast<int32_t>(i);
-        if (i == n - 1)
-            for (int q = b + 1; q <= NB; ++q) tb[q] = static_cast<int32_t>(n);
+    const int64_t i0 = static_cast<int64_t>(c) * PS_CHUNK + static_cast<int64_t>(threadIdx.x) * PS_ITEMS;
+    if (threadIdx.x == 0) chunk_start = PairSum<T>::from_double2(cs[static_cast<int64_t>(p) * (nchunk + 1) + c]);
+    KW<T> el[PS_ITEMS];
+    PairSum<T> own;
+#pragma unroll
+    for (int r = 0; r < PS_ITEMS; ++r) {
+        const int64_t i = i0 + r;
+        el[r] = i < n ? ks[i] : KW<T>{T(0), T(0)};
+        own.add(el[r].w, el[r].key);
     }
-}
-
-// per bucket sums of w and w z in FP64 (fixed order: the sorted order)
-template <class T>
-__global__ void k_bucket_sums(const KW<T>* __restrict__ kw, int64_t n, int NB, const int32_t* __restrict__ tab,
-                              double2* __restrict__ AB) {
-    const int p = blockIdx.y;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < NB; b += gridDim.x * blockDim.x) {
-        const int32_t* tb = tab + static_cast<int64_t>(p) * (NB + 1);
-        const KW<T>* ks = kw + static_cast<int64_t>(p) * n;
-        double a = 0.0, c = 0.0;
-        for (int32_t i = tb[b]; i < tb[b + 1]; ++i) {
-            const double wv = static_cast<double>(ks[i].w);
-            a += wv;
-            c += wv * static_cast<double>(ks[i].key);
+    own.norm();
+    // inclusive scan of the thread totals within the warp, then the warps in order
+    PairSum<T> x = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const PairSum<T> y = x.shfl_up(o);
+        if (lane >= o) {
+            PairSum<T> t = y;
+            t.plus(x);
+            x = t;
         }
-        AB[static_cast<int64_t>(p) * (NB + 1) + b] = make_double2(a, c);
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    PairSum<T> start = chunk_start;
+    for (int q = 0; q < warp; ++q) start.plus(wsum[q]);
+    // exclusive: the warp's inclusive value one lane up (zero in lane 0)
+    PairSum<T> prev = x.shfl_up(1);
+    if (lane > 0) start.plus(prev);
+    PairSum<T> run = start;
+    int bprev = i0 == 0 ? -1 : (i0 < n ? bucket_of(static_cast<float>(ks[i0 - 1].key), lo, sc, NB) : NB);
+#pragma unroll
+    for (int r = 0; r < PS_ITEMS; ++r) {
+        const int64_t i = i0 + r;
+        if (i >= n) break;
+        const int bi = bucket_of(static_cast<float>(el[r].key), lo, sc, NB);
+        if (bi > bprev) {
+            run.norm();
+            const Pre<T> pre = run.entry();
+            for (int q = bprev + 1; q <= bi; ++q) {
+                tb[q] = static_cast<int32_t>(i);
+                ab[q] = pre;
+            }
+            bprev = bi;
+        }
+        run.add(el[r].w, el[r].key);
+        if (i == n - 1) {
+            run.norm();
+            const Pre<T> tot = run.entry();
+            for (int q = bi + 1; q <= NB; ++q) {
+                tb[q] = static_cast<int32_t>(n);
+                ab[q] = tot;
+            }
+        }
     }
 }
 
-// exclusive FP64 scan of the bucket sums of one slice, in place; AB[NB] = totals
-__global__ void __launch_bounds__(1024) k_bucket_prefix(double2* __restrict__ AB, int NB) {
+// exclusive FP64 scan of one row of NB double2 values, in place; row[NB] = the totals
+__global__ void __launch_bounds__(1024) k_row_exclusive_scan(double2* __restrict__ AB, int NB) {
     __shared__ double wa[32], wb[32];
     __shared__ double ca_s, cb_s;
     double2* row = AB + static_cast<int64_t>(blockIdx.x) * (NB + 1);
@@ -282,23 +519,65 @@ __global__ void __launch_bounds__(1024) k_bucket_prefix(double2* __restrict__ AB
 
 // ------------------------------------------------------------ targets
 
-// Slices [p0, p1): for target m, bucket b of z; A_< and B_< from the bucket's FP64
-// prefix plus the sorted pairs of bucket b below z (and A_<= for the gradient).
+// Per-slice value and derivative at z from the prefix entry of z's bucket (e), the totals
+// (tot) and the sums over the bucket's sources below z (a_loc = sum w, b_loc = sum w key):
+//   t = -c_d [ z (2A_< - W) - (2B_< - S) ],   g = c_d (W - 2A_< - a_eq).
+// FP32 data: the differences 2A_< - W and 2B_< - S and the product with z are formed in
+// double-float arithmetic (TwoSum / exact FMA products), so the only rounding of size
+// 2^-24 is that of the result itself, whatever the cancellation between the terms.
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+    const float s = a + b, v = s - a;
+    return DF{s, (a - (s - v)) + (b - v)};
+}
+// 2 (hi + lo + loc) - (thi + tlo) as a double-float
+__device__ __forceinline__ DF df_twice_minus(float hi, float lo, float loc, float thi, float tlo) {
+    const DF h = df_two_sum(2.0f * hi, -thi);
+    const DF l = df_two_sum(2.0f * lo, 2.0f * loc);
+    return df_add(h, DF{l.hi, l.lo - tlo});
+}
+__device__ __forceinline__ float negdist_value(const Pre<float>& e, const Pre<float>& tot, float a_loc, float b_loc,
+                                               float z, float cd) {
+    const DF u = df_twice_minus(e.ahi, e.alo, a_loc, tot.ahi, tot.alo);  // 2A_< - W
+    const DF v = df_twice_minus(e.bhi, e.blo, b_loc, tot.bhi, tot.blo);  // 2B_< - S
+    const float p = z * u.hi;
+    const DF zu = df_norm(p, fmaf(z, u.hi, -p) + z * u.lo);
+    const DF d = df_add(zu, DF{-v.hi, -v.lo});
+    return -cd * (d.hi + d.lo);
+}
+__device__ __forceinline__ double negdist_value(const Pre<double>& e, const Pre<double>& tot, double a_loc,
+                                                double b_loc, double z, double cd) {
+    const double A = e.a + a_loc, B = e.b + b_loc;
+    return -cd * (z * (2.0 * A - tot.a) - (2.0 * B - tot.b));
+}
+__device__ __forceinline__ float negdist_slope(const Pre<float>& e, const Pre<float>& tot, float a_loc, float a_eq,
+                                               float cd) {
+    const DF u = df_twice_minus(e.ahi, e.alo, a_loc, tot.ahi, tot.alo);  // 2A_< - W
+    return cd * (-(u.hi + (u.lo + a_eq)));
+}
+__device__ __forceinline__ double negdist_slope(const Pre<double>& e, const Pre<double>& tot, double a_loc,
+                                                double a_eq, double cd) {
+    return cd * (tot.a - 2.0 * (e.a + a_loc) - a_eq);
+}
+
+// Slices [p0, p1): for target m, bucket b of z; A_< and B_< from the bucket's prefix entry
+// plus the sorted pairs of bucket b below z (and A_<= for the gradient), the value or
+// derivative by negdist_value / negdist_slope; per-slice values summed with Kahan
+// compensation, then added to the FP64 accumulator once per launch.
 template <class T>
 __global__ void __launch_bounds__(256) k_negdist_target(const T* __restrict__ Z, int P, int p0, int p1, int64_t n,
                                                        int64_t ldz, const KW<T>* __restrict__ kw, int64_t nx,
-                                                       const double2* __restrict__ AB, int NB,
+                                                       const Pre<T>* __restrict__ AB, int NB,
                                                        const float* __restrict__ kmin, const float* __restrict__ kscale,
-                                                       const int32_t* __restrict__ tab, double cd, double scale,
+                                                       const int32_t* __restrict__ tab, T cd, T scale,
                                                        double* __restrict__ acc, T* __restrict__ G, int accumulate_G) {
     const int64_t m = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (m >= n) return;
-    double sum = 0.0;
+    T sum = T(0), comp = T(0);  // Kahan
     for (int p = p0; p < p1; ++p) {
         const T z = Z[static_cast<int64_t>(p) * ldz + m];
         const KW<T>* ks = kw + static_cast<int64_t>(p) * nx;
         const int32_t* tb = tab + static_cast<int64_t>(p) * (NB + 1);
-        const double2* ab = AB + static_cast<int64_t>(p) * (NB + 1);
+        const Pre<T>* ab = AB + static_cast<int64_t>(p) * (NB + 1);
         const int b = bucket_of(static_cast<float>(z), kmin[p], kscale[p], NB);
         const int32_t hi = tb[b + 1];
         int32_t i = tb[b];
@@ -307,10 +586,9 @@ __global__ void __launch_bounds__(256) k_negdist_target(const T* __restrict__ Z,
             const KW<T> e = ks[i];
             if (!(e.key < z)) break;
             a += e.w;
-            bz += e.w * e.key;
+            bz = fma(e.w, e.key, bz);
         }
-        const double2 base = ab[b], tot = ab[NB];
-        const double Al = base.x + static_cast<double>(a);
+        const Pre<T> eb = ab[b], tot = ab[NB];
         if (G) {
             T aeq = T(0);
             for (; i < hi; ++i) {
@@ -318,16 +596,18 @@ __global__ void __launch_bounds__(256) k_negdist_target(const T* __restrict__ Z,
                 if (e.key != z) break;
                 aeq += e.w;
             }
-            const double g = scale * cd * (tot.x - 2.0 * Al - static_cast<double>(aeq));
+            const T g = scale * negdist_slope(eb, tot, a, aeq, cd);
             T* gp = G + m * P + p;
-            *gp = accumulate_G ? static_cast<T>(static_cast<double>(*gp) + g) : static_cast<T>(g);
+            *gp = accumulate_G ? *gp + g : g;
         } else {
-            const double Bl = base.y + static_cast<double>(bz);
-            const double zd = static_cast<double>(z);
-            sum += -cd * (zd * (2.0 * Al - tot.x) - (2.0 * Bl - tot.y));
+            const T t = negdist_value(eb, tot, a, bz, z, cd);
+            const T y = t - comp;
+            const T tt = sum + y;
+            comp = (tt - sum) - y;
+            sum = tt;
         }
     }
-    if (!G) acc[m] += scale * sum;
+    if (!G) acc[m] += static_cast<double>(scale) * (static_cast<double>(sum) - static_cast<double>(comp));
 }
 
 }  // namespace
@@ -335,45 +615,56 @@ __global__ void __launch_bounds__(256) k_negdist_target(const T* __restrict__ Z,
 // ------------------------------------------------------------ launchers
 
 template <class T>
-size_t segmented_sort_scratch(int P, int64_t n) {
+size_t sort_pairs_scratch(int P, int64_t n) {
     using U = typename KeyOf<T>::U;
-    int64_t tiles = ceil_div(n, RS_TILE);
-    size_t total = static_cast<size_t>(P) * n;
-    return 2 * total * sizeof(U) + total * sizeof(int32_t) + static_cast<size_t>(P) * RS_BINS * tiles * sizeof(int32_t) +
-           1024;
+    const int64_t tiles = ceil_div(n, RS_TILE);
+    const size_t total = static_cast<size_t>(P) * n;
+    return 2 * total * (sizeof(U) + sizeof(T)) + static_cast<size_t>(P) * RS_BINS * tiles * sizeof(int32_t) + 1024;
+}
+
+template <class T, class U, bool FIRST, bool LAST>
+void radix_pass(dim3 grid, const T* z, int64_t ldz, const T* w, const U* kin, const T* vin, int64_t n, int shift,
+                int tiles, const int32_t* hist, U* kout, T* vout, KW<T>* pout, cudaStream_t st) {
+    constexpr size_t smem = radix_pass_smem<T, U>();
+    static bool attr = false;
+    if (!attr) {
+        SLK_CHECK_CUDA(cudaFuncSetAttribute(k_radix_pass<T, U, FIRST, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            static_cast<int>(smem)));
+        attr = true;
+    }
+    k_radix_pass<T, U, FIRST, LAST><<<grid, RS_THREADS, smem, st>>>(z, ldz, w, kin, vin, n, shift, tiles, hist, kout,
+                                                                    vout, pout);
 }
 
 template <class T>
-void launch_segmented_sort(const T* keys_in, int P, int64_t n, int64_t ldk, T* keys_out, int32_t* idx_out,
-                           void* scratch, size_t scratch_bytes, cudaStream_t st) {
+void launch_sort_pairs(const T* z, int P, int64_t n, int64_t ldz, const T* w, void* kw, void* scratch,
+                       size_t scratch_bytes, cudaStream_t st) {
     using U = typename KeyOf<T>::U;
     SLK_REQUIRE(n < (int64_t(1) << 31), "segments longer than 2^31 are not supported");
-    SLK_REQUIRE(scratch_bytes >= segmented_sort_scratch<T>(P, n), "sort scratch too small");
+    SLK_REQUIRE(scratch_bytes >= sort_pairs_scratch<T>(P, n), "sort scratch too small");
     SLK_REQUIRE(P <= 65535, "too many segments for one sort launch");
+    if (n <= 0) return;
     const int tiles = static_cast<int>(ceil_div(n, RS_TILE));
     const size_t total = static_cast<size_t>(P) * n;
     unsigned char* s = static_cast<unsigned char*>(scratch);
-    U* kb0 = reinterpret_cast<U*>(s);
-    U* kb1 = kb0 + total;
-    int32_t* v1 = reinterpret_cast<int32_t*>(kb1 + total);
-    int32_t* hist = v1 + total;
-    int32_t* v0 = idx_out;
-    dim3 g1(static_cast<unsigned>(ceil_div(n, 256) < 1024 ? ceil_div(n, 256) : 1024), P);
-    {
-        SLK_TIMED("to_bits", st);
-        k_to_bits<T, U><<<g1, 256, 0, st>>>(keys_in, n, ldk, kb0, v0);
-    }
-    SLK_CHECK_LAUNCH();
+    U* k0 = reinterpret_cast<U*>(s);
+    U* k1 = k0 + total;
+    T* v0 = reinterpret_cast<T*>(k1 + total);
+    T* v1 = v0 + total;
+    int32_t* hist = reinterpret_cast<int32_t*>(v1 + total);
+    KW<T>* pairs = static_cast<KW<T>*>(kw);
+    constexpr int passes = KeyOf<T>::passes;
     dim3 gt(tiles, P);
-    U* kin = kb0;
-    U* kout = kb1;
-    int32_t* vin = v0;
-    int32_t* vout = v1;
-    for (int pass = 0; pass < KeyOf<T>::passes; ++pass) {
+    const U* kin = nullptr;
+    const T* vin = nullptr;
+    for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
+        U* kout = (pass & 1) ? k1 : k0;
+        T* vout = (pass & 1) ? v1 : v0;
         {
             SLK_TIMED("radix_hist", st);
-            k_radix_hist<U><<<gt, RS_THREADS, 0, st>>>(kin, n, shift, tiles, hist);
+            if (pass == 0) k_radix_hist<T, U, true><<<gt, RS_THREADS, 0, st>>>(z, ldz, nullptr, n, shift, tiles, hist);
+            else k_radix_hist<T, U, false><<<gt, RS_THREADS, 0, st>>>(nullptr, 0, kin, n, shift, tiles, hist);
         }
         SLK_CHECK_LAUNCH();
         {
@@ -383,24 +674,20 @@ void launch_segmented_sort(const T* keys_in, int P, int64_t n, int64_t ldk, T* k
         SLK_CHECK_LAUNCH();
         {
             SLK_TIMED("radix_scatter", st);
-            k_radix_scatter<U><<<gt, RS_THREADS, 0, st>>>(kin, vin, n, shift, tiles, hist, kout, vout);
+            if (pass == 0)
+                radix_pass<T, U, true, false>(gt, z, ldz, w, nullptr, nullptr, n, shift, tiles, hist, kout, vout, nullptr,
+                                              st);
+            else if (pass == passes - 1)
+                radix_pass<T, U, false, true>(gt, nullptr, 0, nullptr, kin, vin, n, shift, tiles, hist, nullptr, nullptr,
+                                              pairs, st);
+            else
+                radix_pass<T, U, false, false>(gt, nullptr, 0, nullptr, kin, vin, n, shift, tiles, hist, kout, vout,
+                                               nullptr, st);
         }
         SLK_CHECK_LAUNCH();
-        U* tk = kin;
         kin = kout;
-        kout = tk;
-        int32_t* tv = vin;
         vin = vout;
-        vout = tv;
     }
-    // an even number of passes leaves keys in kb0 and payload in idx_out
-    int64_t tot = static_cast<int64_t>(total);
-    {
-        SLK_TIMED("from_bits", st);
-        k_from_bits<T, U><<<static_cast<unsigned>(ceil_div(tot, 256) < 16384 ? ceil_div(tot, 256) : 16384), 256, 0, st>>>(
-            kin, tot, keys_out);
-    }
-    SLK_CHECK_LAUNCH();
 }
 
 template <class T>
@@ -409,42 +696,37 @@ int64_t sorted_pairs_bytes(int P, int64_t n) {
 }
 
 template <class T>
-void launch_sorted_pairs(const T* keys, const int32_t* idx, const T* w, int P, int64_t n, void* kw, int NB,
-                         float* kmin, float* kscale, int32_t* tab, double2* AB, cudaStream_t st) {
-    const int64_t total = static_cast<int64_t>(P) * n;
-    KW<T>* pairs = static_cast<KW<T>*>(kw);
-    {
-        SLK_TIMED("gather_pairs", st);
-        k_gather_pairs<T><<<static_cast<unsigned>(ceil_div(total, 256) < 16384 ? ceil_div(total, 256) : 16384), 256, 0,
-                            st>>>(keys, idx, w, total, n, pairs);
-    }
-    SLK_CHECK_LAUNCH();
+void launch_bucket_tables(int P, int64_t n, const void* kw, int NB, float* kmin, float* kscale, int32_t* tab,
+                          void* AB, cudaStream_t st) {
+    const KW<T>* pairs = static_cast<const KW<T>*>(kw);
     {
         SLK_TIMED("bucket_minmax", st);
         k_bucket_minmax<T><<<static_cast<unsigned>(ceil_div(P, 128)), 128, 0, st>>>(pairs, P, n, NB, kmin, kscale);
     }
     SLK_CHECK_LAUNCH();
+    const int nchunk = static_cast<int>(ceil_div(n, PS_CHUNK));
+    DevBuf<double2> cs(static_cast<size_t>(P) * (nchunk + 1), st);
+    dim3 g(static_cast<unsigned>(nchunk), P);
     {
-        SLK_TIMED("bucket_tab", st);
-        dim3 g(static_cast<unsigned>(ceil_div(n, 256) < 1024 ? ceil_div(n, 256) : 1024), P);
-        k_bucket_tab<T><<<g, 256, 0, st>>>(pairs, n, NB, kmin, kscale, tab);
+        SLK_TIMED("pair_chunk_sums", st);
+        k_pair_chunk_sums<T><<<g, PS_THREADS, 0, st>>>(pairs, n, nchunk, cs.get());
     }
     SLK_CHECK_LAUNCH();
     {
-        SLK_TIMED("bucket_sums", st);
-        dim3 g(static_cast<unsigned>(ceil_div(NB, 256)), P);
-        k_bucket_sums<T><<<g, 256, 0, st>>>(pairs, n, NB, tab, AB);
+        SLK_TIMED("chunk_scan", st);
+        k_row_exclusive_scan<<<P, 1024, 0, st>>>(cs.get(), nchunk);
     }
     SLK_CHECK_LAUNCH();
     {
-        SLK_TIMED("bucket_prefix", st);
-        k_bucket_prefix<<<P, 1024, 0, st>>>(AB, NB);
+        SLK_TIMED("pair_prefix_tab", st);
+        k_pair_prefix_tab<T><<<g, PS_THREADS, 0, st>>>(pairs, n, nchunk, cs.get(), NB, kmin, kscale, tab,
+                                                       static_cast<Pre<T>*>(AB));
     }
     SLK_CHECK_LAUNCH();
 }
 
 template <class T>
-void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const void* kw, int64_t nx, const double2* AB,
+void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const void* kw, int64_t nx, const void* AB,
                            int NB, const float* kmin, const float* kscale, const int32_t* tab, double cd, double scale,
                            double* acc, T* G, int accumulate_G, cudaStream_t st) {
     if (n <= 0) return;
@@ -457,19 +739,19 @@ void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const void
         const int p1 = p0 + batch < P ? p0 + batch : P;
         SLK_TIMED(G ? "negdist_target_grad" : "negdist_target", st);
         k_negdist_target<T><<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, st>>>(
-            Z, P, p0, p1, n, ldz, static_cast<const KW<T>*>(kw), nx, AB, NB, kmin, kscale, tab, cd, scale, acc, G,
-            accumulate_G);
+            Z, P, p0, p1, n, ldz, static_cast<const KW<T>*>(kw), nx, static_cast<const Pre<T>*>(AB), NB, kmin, kscale,
+            tab, static_cast<T>(cd), static_cast<T>(scale), acc, G, accumulate_G);
         SLK_CHECK_LAUNCH();
     }
 }
 
 #define SLK_INST(T)                                                                                                   \
-    template size_t segmented_sort_scratch<T>(int, int64_t);                                                          \
-    template void launch_segmented_sort<T>(const T*, int, int64_t, int64_t, T*, int32_t*, void*, size_t, cudaStream_t); \
+    template size_t sort_pairs_scratch<T>(int, int64_t);                                                              \
+    template void launch_sort_pairs<T>(const T*, int, int64_t, int64_t, const T*, void*, void*, size_t, cudaStream_t); \
     template int64_t sorted_pairs_bytes<T>(int, int64_t);                                                             \
-    template void launch_sorted_pairs<T>(const T*, const int32_t*, const T*, int, int64_t, void*, int, float*, float*, \
-                                         int32_t*, double2*, cudaStream_t);                                           \
-    template void launch_negdist_target<T>(const T*, int, int64_t, int64_t, const void*, int64_t, const double2*, int, \
+    template void launch_bucket_tables<T>(int, int64_t, const void*, int, float*, float*, int32_t*, void*,             \
+                                          cudaStream_t);                                                              \
+    template void launch_negdist_target<T>(const T*, int, int64_t, int64_t, const void*, int64_t, const void*, int,   \
                                            const float*, const float*, const int32_t*, double, double, double*, T*,   \
                                            int, cudaStream_t);
 SLK_INST(float)

@@ -136,31 +136,31 @@ void launch_nfft_target(const T* Z, int P, int64_t n, int64_t ldz, const Fourier
                         T* G, unsigned* err, cudaStream_t st);
 
 // ------------------------------------------------------------ k_sort.cu
-// Segmented LSD radix sort of P segments of n keys (row stride ldk) with an
-// int32 payload (the source index).  Output is P x n contiguous.
+// Per slice p < P, the n sources sorted by their projection z[p * ldz + i] into (key, w)
+// pairs (kw, P x n, sorted order), w the source weights: a segmented LSD radix sort on
+// order-preserving key bits (8-bit digits, stable) carrying the weight as payload.
 template <class T>
-void launch_segmented_sort(const T* keys_in, int P, int64_t n, int64_t ldk, T* keys_out, int32_t* idx_out,
-                           void* scratch, size_t scratch_bytes, cudaStream_t st);
+void launch_sort_pairs(const T* z, int P, int64_t n, int64_t ldz, const T* w, void* kw, void* scratch,
+                       size_t scratch_bytes, cudaStream_t st);
 template <class T>
-size_t segmented_sort_scratch(int P, int64_t n);
+size_t sort_pairs_scratch(int P, int64_t n);
 // Bytes of the sorted (key, w) pairs of P segments of n sources.
 template <class T>
 int64_t sorted_pairs_bytes(int P, int64_t n);
-// From sorted keys and their source indices: (key, w) pairs in sorted order
-// (kw), NB equal-width buckets per slice over [key_min, key_max] (kmin,
-// kscale; tab[p][b] = first sorted index of bucket >= b) and FP64 exclusive
-// prefix sums of w and w*key at the bucket starts (AB[p][b], AB[p][NB] =
-// totals).
+// From the sorted pairs: NB equal-width buckets per slice over [key_min, key_max] (kmin,
+// kscale; tab[p][b] = first sorted index of bucket >= b) and the exclusive prefix sums of
+// w and w*key at the bucket starts (AB[p][b], AB[p][NB] = totals; 16 bytes per entry:
+// two doubles for FP64 data, double-float pairs (hi, lo) for FP32 data).
 template <class T>
-void launch_sorted_pairs(const T* keys, const int32_t* idx, const T* w, int P, int64_t n, void* kw, int NB,
-                         float* kmin, float* kscale, int32_t* tab, double2* AB, cudaStream_t st);
+void launch_bucket_tables(int P, int64_t n, const void* kw, int NB, float* kmin, float* kscale, int32_t* tab,
+                          void* AB, cudaStream_t st);
 // Negative-distance 1-D sums at the targets (Section 3.2 in the range-free
 // form t = -c_d [z (2 A_< - W) - (2 B_< - S)]) summed over slices into acc[m],
 // times `scale`; with G != NULL writes g = scale c_d (W - A_< - A_<=) into
 // G[m][p] instead (the derivative, sign(0) = 0).  Slices are processed in
 // batches whose sorted pairs fit in L2.
 template <class T>
-void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const void* kw, int64_t nx, const double2* AB,
+void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const void* kw, int64_t nx, const void* AB,
                            int NB, const float* kmin, const float* kscale, const int32_t* tab, double cd, double scale,
                            double* acc, T* G, int accumulate_G, cudaStream_t st);
 
