@@ -232,15 +232,16 @@ const T* mu_of(slk_plan plan) {
     else return plan->mu32.get();
 }
 
-// Centre and cast n FP32 points to the 16-bit tensor-core operand (one pass), then run
-// tc_kernel(xa, xa_lo, rows, st) on it.
+// Centre and cast n FP32 points to the 16-bit tensor-core operand in one pass, then run
+// tc_kernel(xa, xa_lo, row0 = 0, n, st) on it.  (Running the two in L2-sized chunks was
+// measured slower: the shorter launches lose more than the L2 reuse of the copy gains.)
 template <class F>
 void cast_and_run(slk_plan plan, const float* x, int64_t n, int64_t ldx, cudaStream_t st, F&& tc_kernel) {
     const int split = plan->tc == 2;
     const size_t bytes = static_cast<size_t>(n) * umma_operand_ld(plan->d) * 2;
     DevBuf<unsigned char> xa(bytes, st), xl(split ? bytes : 0, st);
     launch_center_cast(x, n, plan->d, ldx, plan->mu32.get(), xa.get(), xl.get(), split, st);
-    tc_kernel(static_cast<const void*>(xa.get()), static_cast<const void*>(xl.get()), n, st);
+    tc_kernel(static_cast<const void*>(xa.get()), static_cast<const void*>(xl.get()), int64_t(0), n, st);
 }
 
 // Z (P x n, ldz = n) = projections of n points onto the plan's directions, centred;
@@ -249,10 +250,11 @@ template <class T>
 void project(slk_plan plan, const T* x, int64_t n, int64_t ldx, T* Z, float* absmax, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
         if (plan->tc) {
-            cast_and_run(plan, x, n, ldx, st, [&](const void* xa, const void* xl, int64_t rows, cudaStream_t s) {
-                launch_project_umma(xa, xl, rows, plan->xib.get(), plan->xib_lo.get(), plan->P, plan->d, plan->tc == 2,
-                                    Z, n, absmax, plan->err_dev.get(), s);
-            });
+            cast_and_run(plan, x, n, ldx, st,
+                         [&](const void* xa, const void* xl, int64_t r0, int64_t rows, cudaStream_t s) {
+                             launch_project_umma(xa, xl, rows, plan->xib.get(), plan->xib_lo.get(), plan->P, plan->d,
+                                                 plan->tc == 2, Z + r0, n, absmax, plan->err_dev.get(), s);
+                         });
             return;
         }
     }
@@ -420,9 +422,10 @@ bool sum_fused_cheb(slk_plan plan, const T* y, int64_t M, int64_t ldy, void* s_u
         const int parts = static_cast<int>(umma_cheb_parts(plan->P));
         DevBuf<double> part(static_cast<size_t>(parts) * M, st);
         const void* coef = plan->fd.horner ? plan->fd.mono : plan->beta.get();
-        cast_and_run(plan, y, M, ldy, st, [&](const void* ya, const void*, int64_t rows, cudaStream_t s) {
+        cast_and_run(plan, y, M, ldy, st, [&](const void* ya, const void*, int64_t r0, int64_t rows, cudaStream_t s) {
             launch_umma_cheb_target(ya, rows, plan->xib.get(), plan->P, plan->d, static_cast<const float*>(coef),
-                                    plan->fh.cheb_qp, plan->fd.horner, plan->R, part.get(), M, plan->err_dev.get(), s);
+                                    plan->fh.cheb_qp, plan->fd.horner, plan->R, part.get() + r0, M,
+                                    plan->err_dev.get(), s);
         });
         if (is_device_pointer(s_user)) {
             launch_sum_parts<T>(part.get(), parts, M, 1.0 / plan->P, static_cast<T*>(s_user), st);

@@ -20,7 +20,7 @@ namespace slk {
 
 namespace {
 
-constexpr int RS_THREADS = 256, RS_ITEMS = 16, RS_TILE = RS_THREADS * RS_ITEMS, RS_BINS = 256;
+constexpr int RS_THREADS = 256, RS_ITEMS = 8, RS_TILE = RS_THREADS * RS_ITEMS, RS_BINS = 256;
 
 template <class T> struct KeyOf;
 template <> struct KeyOf<float> { using U = uint32_t; static constexpr int passes = 4; };
@@ -49,55 +49,73 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const T* __restrict__
     h[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = static_cast<int64_t>(tile) * RS_TILE;
+    // all loads first (they are independent), then the shared-memory counts
+    U k[RS_ITEMS];
 #pragma unroll
     for (int r = 0; r < RS_ITEMS; ++r) {
         const int64_t i = base + r * RS_THREADS + threadIdx.x;
-        if (i < n) {
-            const U k = FIRST ? key_bits(z[static_cast<int64_t>(p) * ldz + i]) : keys[static_cast<int64_t>(p) * n + i];
-            atomicAdd(&h[static_cast<int>((k >> shift) & 0xffu)], 1);
-        }
+        if (i < n) k[r] = FIRST ? key_bits(z[static_cast<int64_t>(p) * ldz + i]) : keys[static_cast<int64_t>(p) * n + i];
+    }
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const int64_t i = base + r * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[static_cast<int>((k[r] >> shift) & 0xffu)], 1);
     }
     __syncthreads();
     hist[(static_cast<int64_t>(p) * RS_BINS + threadIdx.x) * tiles + tile] = h[threadIdx.x];
 }
 
-// exclusive scan of one segment's 256 x tiles counts (digit-major), in place
-__global__ void __launch_bounds__(1024) k_radix_scan(int32_t* __restrict__ hist, int tiles) {
-    __shared__ int32_t warp_tot[32];
-    __shared__ int32_t carry_s;
-    int32_t* h = hist + static_cast<int64_t>(blockIdx.x) * RS_BINS * tiles;
-    const int64_t total = static_cast<int64_t>(RS_BINS) * tiles;
+// Exclusive scan of one (slice, digit) row of per-tile counts, in place; the row total
+// goes to rt[p * 256 + digit].  Rows are independent (P x 256 blocks); each block walks its
+// row in coalesced 256-wide chunks, carrying the running total.
+__global__ void __launch_bounds__(256) k_radix_scan_rows(int32_t* __restrict__ hist, int tiles, int32_t* __restrict__ rt) {
+    __shared__ int32_t warp_tot[8];
+    const int row = blockIdx.y * RS_BINS + blockIdx.x;
+    int32_t* h = hist + static_cast<int64_t>(row) * tiles;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry_s = 0;
-    __syncthreads();
-    for (int64_t b = 0; b < total; b += 1024) {
-        int64_t i = b + threadIdx.x;
-        int32_t v = i < total ? h[i] : 0;
+    int32_t carry = 0;
+    for (int base = 0; base < tiles; base += 256) {
+        const int j = base + threadIdx.x;
+        const int32_t v = j < tiles ? h[j] : 0;
         int32_t x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
         if (lane == 31) warp_tot[warp] = x;
         __syncthreads();
-        if (warp == 0) {
-            int32_t t = warp_tot[lane];
+        int32_t before = carry, chunk = 0;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int32_t y = __shfl_up_sync(0xffffffffu, t, o);
-                if (lane >= o) t += y;
-            }
-            warp_tot[lane] = t;  // inclusive
+        for (int q = 0; q < 8; ++q) {
+            const int32_t t = warp_tot[q];
+            if (q < warp) before += t;
+            chunk += t;
         }
-        __syncthreads();
-        int32_t carry = carry_s;
-        int32_t excl = carry + (warp ? warp_tot[warp - 1] : 0) + x - v;
-        if (i < total) h[i] = excl;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry_s = excl + v;
+        if (j < tiles) h[j] = before + x - v;
+        carry += chunk;
         __syncthreads();
     }
+    if (threadIdx.x == 0) rt[row] = carry;
+}
+
+// Exclusive scan of the 256 digit totals of each slice, in place (digit bases).
+__global__ void __launch_bounds__(256) k_radix_scan_digits(int32_t* __restrict__ rt) {
+    __shared__ int32_t warp_tot[8];
+    int32_t* r = rt + static_cast<int64_t>(blockIdx.x) * RS_BINS;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t v = r[threadIdx.x];
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    int32_t base = 0;
+    for (int q = 0; q < warp; ++q) base += warp_tot[q];
+    r[threadIdx.x] = base + x - v;
 }
 
 constexpr int RS_WARPS = RS_THREADS / 32;
@@ -115,10 +133,11 @@ constexpr size_t radix_pass_smem() {
 // in contiguous stores.  FIRST reads the projections and the weights (source index order);
 // LAST writes (key, w) pairs instead of bits and payload.
 template <class T, class U, bool FIRST, bool LAST>
-__global__ void __launch_bounds__(RS_THREADS, 3) k_radix_pass(const T* __restrict__ z, int64_t ldz, const T* __restrict__ w,
+__global__ void __launch_bounds__(RS_THREADS, 5) k_radix_pass(const T* __restrict__ z, int64_t ldz, const T* __restrict__ w,
                                                           const U* __restrict__ kin, const T* __restrict__ vin,
                                                           int64_t n, int shift, int tiles,
-                                                          const int32_t* __restrict__ hist, U* __restrict__ kout,
+                                                          const int32_t* __restrict__ hist,
+                                                          const int32_t* __restrict__ dbase, U* __restrict__ kout,
                                                           T* __restrict__ vout, KW<T>* __restrict__ pout) {
     extern __shared__ __align__(16) unsigned char rs_smem[];
     U* sk = reinterpret_cast<U*>(rs_smem);
@@ -131,7 +150,8 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_radix_pass(const T* __restric
     const int64_t seg = static_cast<int64_t>(p) * n;
     const int64_t base = static_cast<int64_t>(tile) * RS_TILE;
     for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) wcnt[i] = 0;
-    glob[threadIdx.x] = hist[(static_cast<int64_t>(p) * RS_BINS + threadIdx.x) * tiles + tile];
+    glob[threadIdx.x] = hist[(static_cast<int64_t>(p) * RS_BINS + threadIdx.x) * tiles + tile] +
+                        dbase[p * RS_BINS + threadIdx.x];
     __syncthreads();
 
     constexpr int RUN = RS_TILE / RS_WARPS;  // keys per warp
@@ -619,12 +639,13 @@ size_t sort_pairs_scratch(int P, int64_t n) {
     using U = typename KeyOf<T>::U;
     const int64_t tiles = ceil_div(n, RS_TILE);
     const size_t total = static_cast<size_t>(P) * n;
-    return 2 * total * (sizeof(U) + sizeof(T)) + static_cast<size_t>(P) * RS_BINS * tiles * sizeof(int32_t) + 1024;
+    return 2 * total * (sizeof(U) + sizeof(T)) + static_cast<size_t>(P) * RS_BINS * (tiles + 1) * sizeof(int32_t) +
+           1024;
 }
 
 template <class T, class U, bool FIRST, bool LAST>
 void radix_pass(dim3 grid, const T* z, int64_t ldz, const T* w, const U* kin, const T* vin, int64_t n, int shift,
-                int tiles, const int32_t* hist, U* kout, T* vout, KW<T>* pout, cudaStream_t st) {
+                int tiles, const int32_t* hist, const int32_t* dbase, U* kout, T* vout, KW<T>* pout, cudaStream_t st) {
     constexpr size_t smem = radix_pass_smem<T, U>();
     static bool attr = false;
     if (!attr) {
@@ -632,8 +653,8 @@ void radix_pass(dim3 grid, const T* z, int64_t ldz, const T* w, const U* kin, co
                                             static_cast<int>(smem)));
         attr = true;
     }
-    k_radix_pass<T, U, FIRST, LAST><<<grid, RS_THREADS, smem, st>>>(z, ldz, w, kin, vin, n, shift, tiles, hist, kout,
-                                                                    vout, pout);
+    k_radix_pass<T, U, FIRST, LAST><<<grid, RS_THREADS, smem, st>>>(z, ldz, w, kin, vin, n, shift, tiles, hist, dbase,
+                                                                    kout, vout, pout);
 }
 
 template <class T>
@@ -652,6 +673,7 @@ void launch_sort_pairs(const T* z, int P, int64_t n, int64_t ldz, const T* w, vo
     T* v0 = reinterpret_cast<T*>(k1 + total);
     T* v1 = v0 + total;
     int32_t* hist = reinterpret_cast<int32_t*>(v1 + total);
+    int32_t* dbase = hist + static_cast<size_t>(P) * RS_BINS * tiles;  // P x 256 digit bases
     KW<T>* pairs = static_cast<KW<T>*>(kw);
     constexpr int passes = KeyOf<T>::passes;
     dim3 gt(tiles, P);
@@ -669,20 +691,22 @@ void launch_sort_pairs(const T* z, int P, int64_t n, int64_t ldz, const T* w, vo
         SLK_CHECK_LAUNCH();
         {
             SLK_TIMED("radix_scan", st);
-            k_radix_scan<<<P, 1024, 0, st>>>(hist, tiles);
+            k_radix_scan_rows<<<dim3(RS_BINS, P), 256, 0, st>>>(hist, tiles, dbase);
+            SLK_CHECK_LAUNCH();
+            k_radix_scan_digits<<<P, 256, 0, st>>>(dbase);
         }
         SLK_CHECK_LAUNCH();
         {
             SLK_TIMED("radix_scatter", st);
             if (pass == 0)
-                radix_pass<T, U, true, false>(gt, z, ldz, w, nullptr, nullptr, n, shift, tiles, hist, kout, vout, nullptr,
-                                              st);
+                radix_pass<T, U, true, false>(gt, z, ldz, w, nullptr, nullptr, n, shift, tiles, hist, dbase, kout, vout,
+                                              nullptr, st);
             else if (pass == passes - 1)
-                radix_pass<T, U, false, true>(gt, nullptr, 0, nullptr, kin, vin, n, shift, tiles, hist, nullptr, nullptr,
-                                              pairs, st);
+                radix_pass<T, U, false, true>(gt, nullptr, 0, nullptr, kin, vin, n, shift, tiles, hist, dbase, nullptr,
+                                              nullptr, pairs, st);
             else
-                radix_pass<T, U, false, false>(gt, nullptr, 0, nullptr, kin, vin, n, shift, tiles, hist, kout, vout,
-                                               nullptr, st);
+                radix_pass<T, U, false, false>(gt, nullptr, 0, nullptr, kin, vin, n, shift, tiles, hist, dbase, kout,
+                                               vout, nullptr, st);
         }
         SLK_CHECK_LAUNCH();
         kin = kout;
