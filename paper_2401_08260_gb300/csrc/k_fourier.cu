@@ -609,9 +609,18 @@ __global__ void __launch_bounds__(256) k_nfft_target(const T* __restrict__ Z, in
         for (int e = threadIdx.x; e < pc * W; e += blockDim.x) sh[e] = h[static_cast<int64_t>(p0) * W + e];
         __syncthreads();
         if (mi >= n) continue;
+        constexpr int U = 4;  // projections of four slices loaded together (memory-level parallelism)
+        T zq[U];
         for (int q = 0; q < pc; ++q) {
             const int p = p0 + q;
-            const T z = Z[static_cast<int64_t>(p) * ldz + mi];
+            if (q % U == 0) {
+#pragma unroll
+                for (int r = 0; r < U; ++r) zq[r] = q + r < pc ? Z[static_cast<int64_t>(p + r) * ldz + mi] : T(0);
+            }
+            T z = zq[0];
+#pragma unroll
+            for (int r = 1; r < U; ++r)
+                if (q % U == r) z = zq[r];
             if (!(z <= R && z >= -R)) bad = true;  // outside the certified window (or NaN)
             const T u = z * scale_u;
             const T c0 = ceil(u - half_m);
@@ -878,7 +887,9 @@ template <class T>
 void launch_nfft_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const T* h, double* acc,
                         T* G, unsigned* err, cudaStream_t st) {
     if (n <= 0) return;
-    int chunk = static_cast<int>((96 * 1024) / (sizeof(T) * fd.W));
+    // slices whose grid windows a block holds at once: about 24 KB, so that several blocks share
+    // an SM (the loop over slices is latency-bound; occupancy hides it)
+    int chunk = static_cast<int>((24 * 1024) / (sizeof(T) * fd.W));
     if (chunk > P) chunk = P;
     if (chunk < 1) chunk = 1;
     size_t smem = sizeof(T) * fd.W * chunk;
