@@ -105,7 +105,12 @@ typedef struct {
                                  relative to sum|w|; 0 = default for the precision */
     double radius;            /* half-width R of the certified window: every projected
                                  target must satisfy |<xi_p, y - mu>| <= R (mu = the plan's
-                                 centre); 0 = 1.25 x the largest projected source */
+                                 centre); 0 = automatic: 1.25 x the largest projected source,
+                                 except on the BF16 Gaussian path with the Chebyshev
+                                 evaluation, where the window is fixed before the sources are
+                                 projected: 1.5 x the largest projection over the sample of
+                                 (at most 4096) sources the centre is estimated from, or the
+                                 first rule when a source falls outside that */
     int32_t slice_batch;      /* slices processed per pass; 0 = all at once */
     int32_t reserved[7];
 } slk_plan_desc;

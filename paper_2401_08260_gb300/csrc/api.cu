@@ -262,10 +262,11 @@ void project(slk_plan plan, const T* x, int64_t n, int64_t ldx, T* Z, float* abs
     if (absmax) launch_absmax<T>(Z, plan->P, n, n, absmax, st);
 }
 
+// Device copy of the chosen Fourier parameters (plan->fh, plan->R) and the tables the
+// source side needs.
 template <class T>
-void plan_fourier_source(slk_plan plan, const T* Zx, const T* w, cudaStream_t st) {
+void fourier_setup(slk_plan plan, cudaStream_t st) {
     const int P = plan->P;
-    const int64_t N = plan->N;
     FourierHost& fh = plan->fh;
     FourierDev& fd = plan->fd;
     fd.L = fh.L;
@@ -279,29 +280,14 @@ void plan_fourier_source(slk_plan plan, const T* Zx, const T* w, cudaStream_t st
     fd.beta = fh.beta;
     fd.R = plan->R;
     fd.q = fh.cheb_qp;
+    fd.horner = 0;
+    fd.mono = nullptr;
     if (fh.method == SLK_FOURIER_CHEB) {
         plan->chebM.alloc(fh.cheb_M.size(), st);
         SLK_CHECK_CUDA(cudaMemcpyAsync(plan->chebM.get(), fh.cheb_M.data(), sizeof(double) * fh.cheb_M.size(),
                                        cudaMemcpyHostToDevice, st));
         plan->beta.alloc(sizeof(T) * P * fh.cheb_qp, st);
-        const bool try_mono = fh.cheb_qp <= 16;
-        if (try_mono) plan->mono.alloc(sizeof(T) * P * fh.cheb_qp, st);
-        DevBuf<unsigned> bad(1, st);
-        SLK_CHECK_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(unsigned), st));
-        int64_t ne = cheb_source_scratch(P, N, fd);
-        DevBuf<T> scratch(ne, st);
-        // Horner's rounding bound gamma_2q sum|a| against Clenshaw's scale sum|beta|: at most
-        // twice it for FP32 / FP64 evaluation; for BF16 projections (whose input rounding,
-        // 2^-9 of each coordinate, dominates) up to 8x, i.e. below 2^-16 sum|beta| for q <= 16
-        const double mono_ratio = plan->tc == 1 ? 8.0 : 2.0;
-        launch_cheb_source<T>(Zx, P, N, N, w, fd, plan->chebM.get(), reinterpret_cast<T*>(plan->beta.get()),
-                              try_mono ? reinterpret_cast<T*>(plan->mono.get()) : nullptr, bad.get(), mono_ratio,
-                              scratch.get(), ne, st);
-        unsigned bad_host = 1;
-        SLK_CHECK_CUDA(cudaMemcpyAsync(&bad_host, bad.get(), sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-        SLK_CHECK_CUDA(cudaStreamSynchronize(st));
-        fd.horner = try_mono && bad_host == 0;
-        fd.mono = fd.horner ? plan->mono.get() : nullptr;
+        if (fh.cheb_qp <= 16) plan->mono.alloc(sizeof(T) * P * fh.cheb_qp, st);
     } else if (fh.method == SLK_FOURIER_NDFT) {
         const int K = fh.k_hi - fh.k_lo + 1;
         plan->coef.alloc(fh.coef.size(), st);
@@ -309,15 +295,50 @@ void plan_fourier_source(slk_plan plan, const T* Zx, const T* w, cudaStream_t st
                                        cudaMemcpyHostToDevice, st));
         plan->cw.alloc(sizeof(Cplx<T>) * P * K, st);
         plan->cw0.alloc(sizeof(T) * P, st);
-        int64_t ne = ndft_source_scratch(P, N, fd);
-        DevBuf<T> scratch(ne, st);
-        launch_ndft_source<T>(Zx, P, N, N, w, fd, plan->coef.get(), reinterpret_cast<Cplx<T>*>(plan->cw.get()),
-                              reinterpret_cast<T*>(plan->cw0.get()), scratch.get(), ne, st);
     } else {
         plan->mult.alloc(fh.mult.size(), st);
         SLK_CHECK_CUDA(cudaMemcpyAsync(plan->mult.get(), fh.mult.data(), sizeof(double) * fh.mult.size(),
                                        cudaMemcpyHostToDevice, st));
         plan->hgrid.alloc(sizeof(T) * P * fh.W, st);
+    }
+}
+
+// Horner's rounding bound gamma_2q sum|a| against Clenshaw's scale sum|beta|: at most twice it
+// for FP32 / FP64 evaluation; for BF16 projections (whose input rounding, 2^-9 of each
+// coordinate, dominates) up to 8x, i.e. below 2^-16 sum|beta| for q <= 16.
+double mono_ratio_of(slk_plan plan) { return plan->tc == 1 ? 8.0 : 2.0; }
+
+// Reads the Horner check of the Chebyshev source side; also waits for the table uploads.
+void cheb_finish(slk_plan plan, const unsigned* bad_dev, cudaStream_t st) {
+    unsigned bad_host = 1;
+    SLK_CHECK_CUDA(cudaMemcpyAsync(&bad_host, bad_dev, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    SLK_CHECK_CUDA(cudaStreamSynchronize(st));
+    plan->fd.horner = plan->fh.cheb_qp <= 16 && bad_host == 0;
+    plan->fd.mono = plan->fd.horner ? plan->mono.get() : nullptr;
+}
+
+template <class T>
+void plan_fourier_source(slk_plan plan, const T* Zx, const T* w, cudaStream_t st) {
+    const int P = plan->P;
+    const int64_t N = plan->N;
+    FourierHost& fh = plan->fh;
+    FourierDev& fd = plan->fd;
+    fourier_setup<T>(plan, st);
+    if (fh.method == SLK_FOURIER_CHEB) {
+        DevBuf<unsigned> bad(1, st);
+        SLK_CHECK_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(unsigned), st));
+        int64_t ne = cheb_source_scratch(P, N, fd);
+        DevBuf<T> scratch(ne, st);
+        launch_cheb_source<T>(Zx, P, N, N, w, fd, plan->chebM.get(), reinterpret_cast<T*>(plan->beta.get()),
+                              fh.cheb_qp <= 16 ? reinterpret_cast<T*>(plan->mono.get()) : nullptr, bad.get(),
+                              mono_ratio_of(plan), scratch.get(), ne, st);
+        cheb_finish(plan, bad.get(), st);
+    } else if (fh.method == SLK_FOURIER_NDFT) {
+        int64_t ne = ndft_source_scratch(P, N, fd);
+        DevBuf<T> scratch(ne, st);
+        launch_ndft_source<T>(Zx, P, N, N, w, fd, plan->coef.get(), reinterpret_cast<Cplx<T>*>(plan->cw.get()),
+                              reinterpret_cast<T*>(plan->cw0.get()), scratch.get(), ne, st);
+    } else {
         int64_t ne = nfft_source_scratch(P, N, fd);
         DevBuf<T> scratch(ne, st);
         launch_nfft_source<T>(Zx, P, N, N, w, fd, fh.n_coeff, plan->mult.get(), reinterpret_cast<T*>(plan->hgrid.get()),
@@ -325,6 +346,74 @@ void plan_fourier_source(slk_plan plan, const T* Zx, const T* w, cudaStream_t st
     }
     // the host copies of the coefficient tables must outlive the async copies
     SLK_CHECK_CUDA(cudaStreamSynchronize(st));
+}
+
+// Largest |projection| over a sample of min(N, 4096) strided source rows (the rows the
+// centre is estimated from), on the BF16 tensor-core path.
+double sample_projection_max(slk_plan plan, const float* x, int64_t N, int64_t ldx, cudaStream_t st) {
+    const int d = plan->d, P = plan->P;
+    const int64_t S = N < 4096 ? N : 4096;
+    DevBuf<float> xs(static_cast<size_t>(S) * d, st);
+    launch_gather_rows(x, N, d, ldx, S, xs.get(), st);
+    DevBuf<float> zs(static_cast<size_t>(P) * S, st);
+    DevBuf<float> mx(1, st);
+    SLK_CHECK_CUDA(cudaMemsetAsync(mx.get(), 0, sizeof(float), st));
+    cast_and_run(plan, xs.get(), S, d, st, [&](const void* xa, const void*, int64_t, int64_t rows, cudaStream_t s) {
+        launch_project_umma(xa, nullptr, rows, plan->xib.get(), nullptr, P, d, 0, zs.get(), S, mx.get(),
+                            plan->err_dev.get(), s);
+    });
+    float m = 0.0f;
+    SLK_CHECK_CUDA(cudaMemcpyAsync(&m, mx.get(), sizeof(float), cudaMemcpyDeviceToHost, st));
+    SLK_CHECK_CUDA(cudaStreamSynchronize(st));
+    if (!std::isfinite(m)) fail(SLK_ERR_INVALID, "non-finite projected sources");
+    return m;
+}
+
+// Source side of the Chebyshev evaluation fused into the projection (BF16 path): the
+// Fourier parameters are chosen for a radius fixed before the projection (the caller's, or
+// 1.5 x the largest projection over the sample of sources), the moments come out of the
+// projection kernel itself and no projection is stored.  Returns false, with nothing kept,
+// when the method is not the Chebyshev one, its term count is not supported by the fused
+// kernel, or a projected source lies outside the radius (the caller then takes the
+// two-pass route, which sets the radius from all sources).
+bool fused_cheb_source(slk_plan plan, const float* x, int64_t ldx, const float* w, cudaStream_t st) {
+    const int P = plan->P, d = plan->d;
+    const int64_t N = plan->N;
+    const bool user_radius = plan->desc.radius > 0.0;
+    const double R = user_radius ? plan->desc.radius : 1.5 * sample_projection_max(plan, x, N, ldx, st) + 1e-6;
+    double tol = plan->desc.tol;
+    if (tol <= 0.0) tol = default_tol(SLK_GAUSSIAN, plan->desc.precision);
+    FourierHost fh = choose_gaussian(plan->desc.param, d, R, plan->desc.n_coeff, plan->desc.method, tol);
+    if (fh.method != SLK_FOURIER_CHEB || !umma_moments_fit(fh.cheb_qp)) return false;
+    plan->fh = fh;
+    plan->R = R;
+    fourier_setup<float>(plan, st);
+    const int64_t nchunk = umma_moments_chunks(P);
+    DevBuf<double> mom(static_cast<size_t>(nchunk) * P * fh.cheb_qp, st);
+    DevBuf<float> mx(1, st);
+    SLK_CHECK_CUDA(cudaMemsetAsync(mx.get(), 0, sizeof(float), st));
+    cast_and_run(plan, x, N, ldx, st, [&](const void* xa, const void*, int64_t, int64_t rows, cudaStream_t s) {
+        launch_umma_moments(xa, rows, plan->xib.get(), P, d, w, fh.cheb_qp, R, mom.get(), mx.get(),
+                            plan->err_dev.get(), s);
+    });
+    float rx = 0.0f;
+    SLK_CHECK_CUDA(cudaMemcpyAsync(&rx, mx.get(), sizeof(float), cudaMemcpyDeviceToHost, st));
+    SLK_CHECK_CUDA(cudaStreamSynchronize(st));
+    if (!std::isfinite(rx)) fail(SLK_ERR_INVALID, "non-finite projected sources");
+    if (rx > R) {
+        if (user_radius)
+            fail(SLK_ERR_INVALID, "radius %.6g is smaller than the largest projected source %.6g", R, rx);
+        return false;
+    }
+    DevBuf<unsigned> bad(1, st);
+    SLK_CHECK_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(unsigned), st));
+    launch_cheb_reduce_f64(mom.get(), static_cast<int>(nchunk), P, plan->fd, plan->chebM.get(),
+                           reinterpret_cast<float*>(plan->beta.get()),
+                           fh.cheb_qp <= 16 ? reinterpret_cast<float*>(plan->mono.get()) : nullptr, bad.get(),
+                           mono_ratio_of(plan), st);
+    cheb_finish(plan, bad.get(), st);
+    plan->fourier = true;
+    return true;
 }
 
 template <class T>
@@ -384,6 +473,9 @@ void create_impl(slk_plan plan, const void* x_user, int64_t ldx, const void* w_u
     }
     // project the sources (and find the largest |z| for the Fourier window)
     const int kernel = plan->desc.kernel;
+    if constexpr (sizeof(T) == 4) {
+        if (plan->tc == 1 && kernel == SLK_GAUSSIAN && fused_cheb_source(plan, xv.ptr, xv.ld, wv.ptr, st)) return;
+    }
     const bool need_fourier = kernel == SLK_GAUSSIAN || kernel == SLK_LAPLACIAN;
     DevBuf<T> Zx(static_cast<size_t>(P) * N, st);
     DevBuf<float> mx(1, st);

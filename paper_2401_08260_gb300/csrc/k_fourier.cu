@@ -316,8 +316,8 @@ __global__ void __launch_bounds__(256) k_cheb_moments(const T* __restrict__ Z, i
 
 // beta[p][l] = sum_j M[l][j] mu[p][j], mu summed over chunks in a fixed order (FP64);
 // optionally the monomial form of the same polynomial (q <= 16, see launch_cheb_source).
-template <class T>
-__global__ void k_cheb_reduce(const T* __restrict__ partial, int nchunk, int P, int q, const double* __restrict__ M,
+template <class T, class TP = T>
+__global__ void k_cheb_reduce(const TP* __restrict__ partial, int nchunk, int P, int q, const double* __restrict__ M,
                               T* __restrict__ beta, T* __restrict__ mono, unsigned* __restrict__ mono_bad,
                               double mono_ratio) {
     extern __shared__ double smu[];  // mu[q], then beta[q]
@@ -768,6 +768,15 @@ void launch_cheb_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, c
         k_cheb_reduce<T><<<P, 128, 2 * sizeof(double) * q, st>>>(scratch, static_cast<int>(nchunk), P, q, M, beta,
                                                                   q <= 16 ? mono : nullptr, mono_bad, mono_ratio);
     }
+    SLK_CHECK_LAUNCH();
+}
+
+void launch_cheb_reduce_f64(const double* partial, int nchunk, int P, const FourierDev& fd, const double* M,
+                            float* beta, float* mono, unsigned* mono_bad, double mono_ratio, cudaStream_t st) {
+    const int q = fd.q;
+    SLK_TIMED("cheb_reduce", st);
+    k_cheb_reduce<float, double><<<P, 128, 2 * sizeof(double) * q, st>>>(partial, nchunk, P, q, M, beta,
+                                                                         q <= 16 ? mono : nullptr, mono_bad, mono_ratio);
     SLK_CHECK_LAUNCH();
 }
 

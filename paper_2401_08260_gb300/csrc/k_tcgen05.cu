@@ -231,7 +231,11 @@ __device__ __forceinline__ void cheb_chunk(const float (&v)[8], const float* __r
 //             (target) and column (slice p) t_p = sum_l beta[p][l] T_l(z / R) by Clenshaw,
 //             summed over the tile's columns; Z receives the FP64 partial row sums
 //             Z_part[(col_tile * 2 + half) * n + row] (no projection is stored).
-enum { EPI_Z = 0, EPI_ROW = 1, EPI_CHEB = 2 };
+//   EPI_MOM:  the source side of the Chebyshev evaluation fused in, with the roles turned
+//             round: A = directions (rows = slices), B = points (columns); every thread
+//             keeps one slice's moments mu_j = sum_n w_n T_j(z / R) in registers over all the
+//             point tiles of its CTA and writes them once (no projection is stored).
+enum { EPI_Z = 0, EPI_ROW = 1, EPI_CHEB = 2, EPI_MOM = 3 };
 
 struct ChebEpi {
     const float* beta;  // P x q: Chebyshev coefficients, or monomial ones when horner
@@ -240,7 +244,41 @@ struct ChebEpi {
     float inv_R, R;
     double* part;  // (2 * col_tiles) x ldp
     int64_t ldp;
+    // EPI_MOM: weights of the npts points, moment partials mom[(chunk * P + slice) * q + j]
+    const float* w;
+    int npts;
+    double* mom;
 };
+
+// Moments of one slice over a 32-point accumulator chunk: z[j] for the chunk's points,
+// the lane-th point's weight in wl (zero beyond the points); t holds this tile's FP32 sums.
+template <int QP>
+__device__ __forceinline__ void mom_chunk(const float (&v)[32], float wl, float inv_R, int valid_pts, float (&t)[QP],
+                                          float& mx) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const float wj = __shfl_sync(0xffffffffu, wl, j);
+        const float z = v[j];
+        if (j < valid_pts) mx = fmaxf(mx, fabsf(z));
+        const float u = z * inv_R, u2 = u + u;
+        float tm1 = 1.0f, tc = u;  // T_0, T_1
+        t[0] += wj;
+#pragma unroll
+        for (int k = 1; k < QP; ++k) {
+            t[k] = fmaf(wj, tc, t[k]);
+            const float tn = fmaf(u2, tc, -tm1);
+            tm1 = tc;
+            tc = tn;
+        }
+    }
+}
+
+// Add a float into an unevaluated pair hi + lo without rounding loss (TwoSum).
+__device__ __forceinline__ void two_sum_into(float& hi, float& lo, float x) {
+    const float s = hi + x, bp = s - hi;
+    lo += (hi - (s - bp)) + (x - bp);
+    hi = s;
+}
 
 //
 // CL = 2: clusters of two CTAs work on neighbouring 128-point blocks against the same
@@ -250,17 +288,30 @@ struct ChebEpi {
 // released it (the MMA commit arrives on the empty barriers of both CTAs).
 // Work items: item -> slice tile (item % col_tiles), point blocks (item / col_tiles) * CL + rank.
 template <int EPI, int CL>
-__global__ void __launch_bounds__(EPI == EPI_CHEB ? 384 : 256, 1)
+__global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256, 1)
     k_umma_project(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int n, int P,
                    int d, int col_tiles, int tiles, float* __restrict__ Z, int64_t ldz, float* __restrict__ absmax,
                    unsigned* __restrict__ err, const float* __restrict__ rs, float scale, ChebEpi ce) {
     static_assert(CL == 1 || CL == 2, "cluster of one or two CTAs");
     constexpr bool ROWMAJOR = EPI == EPI_ROW;
     const int rank = CL > 1 ? static_cast<int>(blockIdx.x % CL) : 0;
-    const int unit = static_cast<int>(blockIdx.x / CL), nunits = static_cast<int>(gridDim.x / CL);
-    auto row_of = [&](int item) { return ((item / col_tiles) * CL + rank) * BM; };
-    auto col_of = [&](int item) { return (item % col_tiles) * BN; };
-    constexpr int EPI_WARPS = EPI == EPI_CHEB ? 8 : 4;
+    int unit = static_cast<int>(blockIdx.x / CL), nunits = static_cast<int>(gridDim.x / CL);
+    // EPI_MOM: a cluster keeps one group of CL slice blocks for all its point tiles, so its
+    // threads can accumulate their slices' moments across tiles
+    int mom_group = 0, mom_chunk_id = -1;
+    if (EPI == EPI_MOM) {
+        const int groups = (static_cast<int>((n + BM - 1) / BM) + CL - 1) / CL;
+        const int per_group = nunits / groups;
+        mom_group = unit % groups;
+        mom_chunk_id = unit / groups < per_group ? unit / groups : -1;
+        unit = mom_chunk_id >= 0 ? mom_chunk_id : tiles;  // idle units take no tile
+        nunits = per_group > 0 ? per_group : 1;
+    }
+    auto row_of = [&](int item) {
+        return EPI == EPI_MOM ? (mom_group * CL + rank) * BM : ((item / col_tiles) * CL + rank) * BM;
+    };
+    auto col_of = [&](int item) { return EPI == EPI_MOM ? item * BN : (item % col_tiles) * BN; };
+    constexpr int EPI_WARPS = EPI == EPI_CHEB || EPI == EPI_MOM ? 8 : 4;
     constexpr int STAGES = STAGES_1;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -370,6 +421,58 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB ? 384 : 256, 1)
             }
             umma_commit(&sm->acc_full[b]);
         }
+    } else if (warp >= 4 && EPI == EPI_MOM) {
+        // ---------------- fused source side: moments of one slice per thread
+        const int q4 = warp & 3, half = (warp - 4) >> 2;  // TMEM lane quarter (slices), column half (points)
+        const uint32_t lane_off = static_cast<uint32_t>(q4 * 32) << 16;
+        const int slice = row_of(0) + q4 * 32 + lane;
+        float mx = 0.0f;
+        bool ok = true;
+        auto run = [&](auto qp_tag) {
+            constexpr int QP = decltype(qp_tag)::value;
+            float hi[QP], lo[QP];
+#pragma unroll
+            for (int k = 0; k < QP; ++k) hi[k] = lo[k] = 0.0f;
+            int local = 0;
+            for (int tile = unit; tile < tiles; tile += nunits, ++local) {
+                const int b = local & 1;
+                if (!mbar_wait(&sm->acc_full[b], (local >> 1) & 1)) {
+                    atomicOr(err, 32u);
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                float t[QP];
+#pragma unroll
+                for (int k = 0; k < QP; ++k) t[k] = 0.0f;
+                for (int cc = 0; cc < BN / 2; cc += 32) {
+                    float v[32];
+                    tmem_ld32(tmem + lane_off + b * BN + half * (BN / 2) + cc, v);
+                    const int pt0 = col_of(tile) + half * (BN / 2) + cc;
+                    const float wl = pt0 + lane < ce.npts ? __ldg(ce.w + pt0 + lane) : 0.0f;
+                    mom_chunk<QP>(v, wl, ce.inv_R, ce.npts - pt0, t, mx);
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm->acc_empty[b]);
+                // a tile's FP32 sums (128 points) into the running double-float moments
+#pragma unroll
+                for (int k = 0; k < QP; ++k) two_sum_into(hi[k], lo[k], t[k]);
+            }
+            if (mom_chunk_id >= 0 && slice < n) {
+                double* out = ce.mom + (static_cast<int64_t>(mom_chunk_id * 2 + half) * n + slice) * QP;
+#pragma unroll
+                for (int k = 0; k < QP; ++k) out[k] = static_cast<double>(hi[k]) + static_cast<double>(lo[k]);
+            }
+        };
+        if (ce.q == 8) run(std::integral_constant<int, 8>{});
+        else if (ce.q == 12) run(std::integral_constant<int, 12>{});
+        else run(std::integral_constant<int, 16>{});
+        if (slice >= n) mx = 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0 && absmax) atomicMax(reinterpret_cast<unsigned int*>(absmax), __float_as_uint(mx));
+        (void)ok;
     } else if (warp >= 4 && EPI == EPI_CHEB) {
         // ---------------- fused target side: t_p(z) per (row, slice), row sums per tile
         const int q4 = warp & 3, half = (warp - 4) >> 2;  // TMEM lane quarter, column half
@@ -745,7 +848,7 @@ size_t epi_smem() {
 }
 template <int EPI>
 constexpr int epi_threads() {
-    return EPI == EPI_CHEB ? 384 : THREADS;
+    return EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : THREADS;
 }
 
 // Co-resident work units of the persistent kernel on the current device (SMs for CL = 1,
@@ -863,6 +966,53 @@ void launch_umma_cheb_target(const void* xa, int64_t n, const void* xib, int P, 
     SLK_TIMED("umma_cheb_target", st);
     launch_persistent<EPI_CHEB, kProjCluster>(ma, mb, n, P, d, col_tiles, nullptr, 0, nullptr, err, nullptr, 1.0f, ce,
                                               st);
+}
+
+bool umma_moments_fit(int q) { return q == 8 || q == 12 || q == 16; }
+
+int64_t umma_moments_chunks(int P) {
+    const int groups = static_cast<int>((ceil_div(P, BM) + kProjCluster - 1) / kProjCluster);
+    const int units = persistent_units<EPI_MOM, kProjCluster>();
+    SLK_REQUIRE(units >= groups, "too many slices for the fused moments kernel");
+    return 2 * static_cast<int64_t>(units / groups);
+}
+
+void launch_umma_moments(const void* xa, int64_t n, const void* xib, int P, int d, const float* w, int q, double R,
+                         double* mom, float* absmax, unsigned* err, cudaStream_t st) {
+    SLK_REQUIRE(umma_moments_fit(q), "Chebyshev term count unsupported by the fused moments kernel");
+    SLK_REQUIRE(n < (int64_t(1) << 31), "too many points for one projection");
+    const int64_t ld = umma_operand_ld(d);
+    // A = directions (slices as rows), B = points (this CTA's half of a 256-point tile)
+    CUtensorMap ma = make_map(xib, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, P, d, ld, BM);
+    CUtensorMap mb = make_map(xa, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, n, d, ld, BN / kProjCluster);
+    const int groups = static_cast<int>((ceil_div(P, BM) + kProjCluster - 1) / kProjCluster);
+    const int units = persistent_units<EPI_MOM, kProjCluster>();
+    const int per_group = units / groups;
+    const int point_tiles = static_cast<int>(ceil_div(n, BN));
+    ChebEpi ce{};
+    ce.q = q;
+    ce.inv_R = static_cast<float>(1.0 / R);
+    ce.R = static_cast<float>(R);
+    ce.w = w;
+    ce.npts = static_cast<int>(n);
+    ce.mom = mom;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kProjCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(static_cast<unsigned>(per_group * groups * kProjCluster));
+    cfg.blockDim = dim3(epi_threads<EPI_MOM>());
+    cfg.dynamicSmemBytes = epi_smem<EPI_MOM>();
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = kProjCluster > 1 ? 1 : 0;
+    SLK_TIMED("umma_cheb_moments", st);
+    // "n" of the kernel is the row count (slices), "P" the column count (points)
+    SLK_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_umma_project<EPI_MOM, kProjCluster>, ma, mb, P, static_cast<int>(n), d,
+                                      point_tiles, point_tiles, static_cast<float*>(nullptr), int64_t(0), absmax, err,
+                                      static_cast<const float*>(nullptr), 1.0f, ce));
 }
 
 void launch_grad_umma(const void* g16, int64_t M, int P, const void* xit16, int d, const float* gs, double scale,

@@ -209,6 +209,24 @@ void launch_sum_parts(const double* part, int parts, int64_t n, double scale, T*
 
 template void launch_sum_parts<float>(const double*, int, int64_t, double, float*, cudaStream_t);
 template void launch_sum_parts<double>(const double*, int, int64_t, double, double*, cudaStream_t);
+__global__ void k_gather_rows(const float* __restrict__ x, int64_t N, int d, int64_t ldx, int64_t S,
+                              float* __restrict__ out) {
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < S * d;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t s = e / d;
+        const int k = static_cast<int>(e - s * d);
+        out[e] = x[((s * N) / S) * ldx + k];
+    }
+}
+
+void launch_gather_rows(const float* x, int64_t N, int d, int64_t ldx, int64_t S, float* out, cudaStream_t st) {
+    if (S <= 0) return;
+    const int64_t blocks = ceil_div(S * d, 256);
+    SLK_TIMED("gather_rows", st);
+    k_gather_rows<<<static_cast<unsigned>(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(x, N, d, ldx, S, out);
+    SLK_CHECK_LAUNCH();
+}
+
 template void launch_sample_mean<float>(const float*, int64_t, int, int64_t, double*, cudaStream_t);
 template void launch_sample_mean<double>(const double*, int64_t, int, int64_t, double*, cudaStream_t);
 template void launch_convert<float>(const double*, float*, int64_t, cudaStream_t);

@@ -43,6 +43,8 @@ int64_t umma_operand_ld(int d);
 // label names the launch in the timing registry; max_blocks > 0 caps the grid.
 void launch_center_cast(const float* x, int64_t n, int d, int64_t ldx, const float* mu, void* out, void* out_lo,
                         int split, cudaStream_t st, const char* label = "center_cast", int max_blocks = 0);
+// out[s][k] = x[s * N / S][k] (the strided sample of S rows the centre is estimated from).
+void launch_gather_rows(const float* x, int64_t N, int d, int64_t ldx, int64_t S, float* out, cudaStream_t st);
 // Streaming multiprocessors of the current device.
 int device_sm_count();
 // Z[p][i] = sum_k xi[p][k] xc[i][k] on tensor cores (tcgen05, TMA), FP32 accumulate;
@@ -60,6 +62,15 @@ int64_t umma_cheb_parts(int P);
 bool umma_cheb_fits(int P, int q);
 void launch_umma_cheb_target(const void* xa, int64_t n, const void* xib, int P, int d, const float* coef, int q,
                              int horner, double R, double* part, int64_t ldp, unsigned* err, cudaStream_t st);
+// Fused source side of the Chebyshev evaluation (BF16 tensor cores): projections of n
+// centred points (xa, BF16) onto the P directions (xib) with the moments
+// mu_j = sum_n w_n T_j(z / R), j < q, accumulated in the epilogue (double-float per thread,
+// no projection stored); mom receives umma_moments_chunks(P) x P x q FP64 partials
+// (mom[(c * P + p) * q + j]), *absmax the largest |z| over the points.  q is 8, 12 or 16.
+bool umma_moments_fit(int q);
+int64_t umma_moments_chunks(int P);
+void launch_umma_moments(const void* xa, int64_t n, const void* xib, int P, int d, const float* w, int q, double R,
+                         double* mom, float* absmax, unsigned* err, cudaStream_t st);
 // s[i] = scale * sum_{r < parts} part[r * n + i] (fixed order).
 template <class T>
 void launch_sum_parts(const double* part, int parts, int64_t n, double scale, T* s, cudaStream_t st);
@@ -104,6 +115,10 @@ void launch_cheb_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, c
                         const double* M, T* beta, T* mono, unsigned* mono_bad, double mono_ratio, T* scratch,
                         int64_t scratch_elems, cudaStream_t st);
 int64_t cheb_source_scratch(int P, int64_t n, const FourierDev& fd);
+// beta (and the monomial form, as launch_cheb_source) from FP64 moment partials
+// partial[(c * P + p) * q + j], c < nchunk, summed in a fixed order.
+void launch_cheb_reduce_f64(const double* partial, int nchunk, int P, const FourierDev& fd, const double* M,
+                            float* beta, float* mono, unsigned* mono_bad, double mono_ratio, cudaStream_t st);
 template <class T>
 void launch_cheb_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const T* beta, double* acc,
                         T* G, unsigned* err, cudaStream_t st);

@@ -123,3 +123,30 @@ def test_large_point_sets_sampled(kernel, precision, method, tol):
     idx = np.unique(np.concatenate([edges, oracle.sampled_targets(M, 12)]))
     ref, _ = oracle.sliced_sum(kernel, param, x, y[idx], w, xi)
     assert rel_inf(s[idx], ref, w.sum()) <= tol
+
+
+def test_bf16_fused_moments_radius_fallback():
+    """The fused source side fixes its radius before projecting (1.5 x the largest projection
+    over a sample of sources).  A source outside it (an outlier on an unsampled row) sends the
+    plan down the two-pass route, whose radius covers every source; both agree with the oracle."""
+    dev = cuda_or_skip()
+    from paper_2401_08260_gb300.slk import Plan
+    d, N, M, P = 64, 20000, 257, 48
+    rng = np.random.Generator(np.random.PCG64(41))
+    x = rng.random((N, d), dtype=np.float32)
+    y = rng.random((M, d), dtype=np.float32)
+    w = rng.random(N).astype(np.float32)
+    xi = workloads.directions(P, d, seed=42)
+    sigma = math.sqrt(d)
+    sigma_ok = _plan(to_dev(x, dev), to_dev(w, dev), "gaussian", sigma, xi, "bf16", method="cheb")
+    r_plain = sigma_ok.info()["radius"]
+    x_out = x.copy()
+    x_out[1] += 6.0  # row 1 is not among the sampled rows s * N / 4096
+    plan = _plan(to_dev(x_out, dev), to_dev(w, dev), "gaussian", sigma, xi, "bf16", method="cheb")
+    r_out = plan.info()["radius"]
+    z_max = np.abs((x_out - x_out[[int(s * N / 4096) for s in range(4096)]].mean(axis=0)) @ xi.T).max()
+    assert r_out >= z_max and r_out > 2.0 * r_plain
+    for xx, pl in ((x, sigma_ok), (x_out, plan)):
+        s = pl.sum(to_dev(y, dev))
+        ref, _ = oracle.sliced_sum("gaussian", sigma, xx, y, w, xi)
+        assert rel_inf(s, ref, w.sum()) <= 2e-3
