@@ -110,12 +110,14 @@ def plan_kwargs(wl, args):
                 n_coeff=wl.n_coeff, method=args.method or wl.method, directions=wl.xi)
 
 
-# DRAM read + write per point of one launch, from one ncu capture of the d = 784, P = 512 BF16
-# workload at n = 2e5 points (profiles/umma_cheb_target_and_center_cast_d784_n200k.md); the
+# DRAM read + write per point of one launch, from ncu captures of the d = 784, P = 512 BF16
+# workload at n = 2e5 points (profiles/umma_cheb_target_and_center_cast_d784_n200k.md,
+# profiles/umma_cheb_moments_d784_n200k.md); the
 # traffic of these kernels grows in proportion to the points.  An entry is valid only for the
 # kernel as captured and is removed when that kernel changes.
 NCU_TRAFFIC_PER_POINT = {("gauss_d784", "center_cast"): (627.233024e6 + 281.766400e6) / 2e5,
-                         ("gauss_d784", "umma_cheb_target"): (314.511616e6 + 7.280640e6) / 2e5}
+                         ("gauss_d784", "umma_cheb_target"): (314.612992e6 + 7.674368e6) / 2e5,
+                         ("gauss_d784", "umma_cheb_moments"): (315.320832e6 + 3.245568e6) / 2e5}
 
 
 def measured_traffic(wl, kernel_name, launches_per_step):
