@@ -159,25 +159,43 @@ def algorithmic(wl, info, precision, kernel_name, launches_per_step):
 
 def cpu_sample(wl, budget_s: float):
     """Time the oracle's sliced sum on a bounded sample: k targets against all N
-    sources and all P slices.  Returns (slice-points/s extrapolated, seconds, sample text)."""
+    sources and all P slices.  Returns (slice-points/s extrapolated, seconds, sample text,
+    the sampled target indices, the oracle's sliced sums there)."""
     import oracle
     oracle.build()
     idx = oracle.sampled_targets(wl.M, 1)
     t0 = time.perf_counter()
-    oracle.sliced_sum(wl.kernel, wl.param, wl.x, wl.y[idx[:1]], wl.w, wl.xi)
+    ref, _ = oracle.sliced_sum(wl.kernel, wl.param, wl.x, wl.y[idx[:1]], wl.w, wl.xi)
     t1 = time.perf_counter() - t0
     k = max(1, min(wl.M, int(budget_s / max(t1, 1e-3))))
     if k > 1:
         idx = oracle.sampled_targets(wl.M, k)
         t0 = time.perf_counter()
-        oracle.sliced_sum(wl.kernel, wl.param, wl.x, wl.y[idx], wl.w, wl.xi)
+        ref, _ = oracle.sliced_sum(wl.kernel, wl.param, wl.x, wl.y[idx], wl.w, wl.xi)
         t1 = time.perf_counter() - t0
         k = len(idx)
+    else:
+        idx = idx[:1]
     full = t1 * wl.M / k
     rate = (wl.N + wl.M) * wl.P / full
     sample = (f"{k} target(s) x all {wl.N} sources x {wl.P} slices (FP64 exact 1-D sums, projections by numpy); "
               f"{t1:.2f} s measured, full job extrapolated to {full:.3g} s")
-    return rate, t1, sample
+    return rate, t1, sample, idx, ref
+
+
+def sampled_errors(wl, s_dev, idx, ref_sliced, model_error):
+    """Errors of the device result at the oracle's sampled targets: l_inf / sum|w| against the
+    sliced oracle (same directions, exact 1-D sums: the parity error) and against the direct
+    d-dimensional sum (parity plus the slicing error)."""
+    import numpy as np
+    import oracle
+    got = s_dev[idx].double().cpu().numpy()
+    wsum = float(np.abs(wl.w.astype(np.float64)).sum())
+    direct = oracle.direct_sum(wl.kernel, wl.param, wl.x, wl.y[idx], wl.w)
+    return {"linf_over_sum_w_vs_sliced_oracle": float(np.max(np.abs(got - ref_sliced)) / wsum),
+            "linf_over_sum_w_vs_direct_sum": float(np.max(np.abs(got - direct)) / wsum),
+            "l1_over_sum_w_vs_sliced_oracle": float(np.mean(np.abs(got - ref_sliced)) / wsum),
+            "certified_model_error": model_error, "targets": int(len(idx))}
 
 
 def run_reference(args):
@@ -190,7 +208,7 @@ def run_reference(args):
     rates = []
     sample = ""
     for i in range(warm + steps):
-        r, _, sample = cpu_sample(wl, budget)
+        r, _, sample, _, _ = cpu_sample(wl, budget)
         if i >= warm:
             rates.append(r)
     value = statistics.median(rates)
@@ -358,10 +376,12 @@ def run_ours(args):
                "d2h_bytes_per_step": int(bo), "ms_per_step": te * 1e3}
 
     cpu = None
+    errors = None
     if rank == 0 and not args.no_cpu and world == 1:
-        r, secs, sample = cpu_sample(wl, args.cpu_budget)
+        r, secs, sample, idx, ref = cpu_sample(wl, args.cpu_budget)
         cpu = {"value": r, "unit": "slice-points/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
                "sample": sample}
+        errors = sampled_errors(wl, s, idx, ref, info["model_error"])
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "slice-points/s", "n_gpus": world, "steps": args.steps,
@@ -372,7 +392,8 @@ def run_ours(args):
                            "parallelism": f"replicas{world}" if world > 1 else "single",
                            "l2": "inputs larger than L2 (no flush needed)",
                            "model_error": info["model_error"], "backward": bool(args.grad)},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+                "roofline": roofline, "cpu_baseline": cpu, "errors": errors, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": launches,
                 "kernels_ms_per_step": {k: v[1] / args.steps for k, v in kernels.items()}}
         print(json.dumps(line), flush=True)
     if world > 1:
