@@ -339,6 +339,12 @@ struct PairSum<float> {
         return r;
     }
     __device__ __forceinline__ Pre<float> entry() const { return Pre<float>{a.hi, a.lo, b.hi, b.lo}; }
+    __device__ static PairSum from_pair(float sa, float sb) {
+        PairSum r;
+        r.a = DF{sa, 0.0f};
+        r.b = DF{sb, 0.0f};
+        return r;
+    }
 };
 template <>
 struct PairSum<double> {
@@ -372,6 +378,12 @@ struct PairSum<double> {
         return r;
     }
     __device__ __forceinline__ Pre<double> entry() const { return Pre<double>{a, b}; }
+    __device__ static PairSum from_pair(double sa, double sb) {
+        PairSum r;
+        r.a = sa;
+        r.b = sb;
+        return r;
+    }
 };
 
 constexpr int PS_THREADS = 256, PS_ITEMS = 8, PS_CHUNK = PS_THREADS * PS_ITEMS;
@@ -385,16 +397,19 @@ __global__ void __launch_bounds__(PS_THREADS) k_pair_chunk_sums(const KW<T>* __r
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const KW<T>* ks = kw + static_cast<int64_t>(p) * n;
     const int64_t i0 = static_cast<int64_t>(c) * PS_CHUNK + threadIdx.x;
-    PairSum<T> acc;
+    // a thread's PS_ITEMS pairs in plain arithmetic (their rounding is ~2^-24 of a sum of
+    // eight terms, negligible against the prefixes); double-float from there on
+    T sa = T(0), sb = T(0);
 #pragma unroll
     for (int r = 0; r < PS_ITEMS; ++r) {  // coalesced; a fixed order within the chunk
         const int64_t i = i0 + r * PS_THREADS;
         if (i < n) {
             const KW<T> e = ks[i];
-            acc.add(e.w, e.key);
+            sa += e.w;
+            sb = fma(e.w, e.key, sb);
         }
     }
-    acc.norm();
+    PairSum<T> acc = PairSum<T>::from_pair(sa, sb);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc.plus(acc.shfl_down(o));
     if (lane == 0) red[warp] = acc;
@@ -427,14 +442,15 @@ __global__ void __launch_bounds__(PS_THREADS) k_pair_prefix_tab(const KW<T>* __r
     const int64_t i0 = static_cast<int64_t>(c) * PS_CHUNK + static_cast<int64_t>(threadIdx.x) * PS_ITEMS;
     if (threadIdx.x == 0) chunk_start = PairSum<T>::from_double2(cs[static_cast<int64_t>(p) * (nchunk + 1) + c]);
     KW<T> el[PS_ITEMS];
-    PairSum<T> own;
+    T sa = T(0), sb = T(0);  // this thread's PS_ITEMS pairs in plain arithmetic
 #pragma unroll
     for (int r = 0; r < PS_ITEMS; ++r) {
         const int64_t i = i0 + r;
         el[r] = i < n ? ks[i] : KW<T>{T(0), T(0)};
-        own.add(el[r].w, el[r].key);
+        sa += el[r].w;
+        sb = fma(el[r].w, el[r].key, sb);
     }
-    own.norm();
+    const PairSum<T> own = PairSum<T>::from_pair(sa, sb);
     // inclusive scan of the thread totals within the warp, then the warps in order
     PairSum<T> x = own;
 #pragma unroll
@@ -453,7 +469,8 @@ __global__ void __launch_bounds__(PS_THREADS) k_pair_prefix_tab(const KW<T>* __r
     // exclusive: the warp's inclusive value one lane up (zero in lane 0)
     PairSum<T> prev = x.shfl_up(1);
     if (lane > 0) start.plus(prev);
-    PairSum<T> run = start;
+    start.norm();
+    T la = T(0), lb = T(0);  // the run within this thread's pairs, plain arithmetic
     int bprev = i0 == 0 ? -1 : (i0 < n ? bucket_of(static_cast<float>(ks[i0 - 1].key), lo, sc, NB) : NB);
 #pragma unroll
     for (int r = 0; r < PS_ITEMS; ++r) {
@@ -461,21 +478,24 @@ __global__ void __launch_bounds__(PS_THREADS) k_pair_prefix_tab(const KW<T>* __r
         if (i >= n) break;
         const int bi = bucket_of(static_cast<float>(el[r].key), lo, sc, NB);
         if (bi > bprev) {
-            run.norm();
-            const Pre<T> pre = run.entry();
+            PairSum<T> pre = start;
+            pre.plus(PairSum<T>::from_pair(la, lb));
+            const Pre<T> e = pre.entry();
             for (int q = bprev + 1; q <= bi; ++q) {
                 tb[q] = static_cast<int32_t>(i);
-                ab[q] = pre;
+                ab[q] = e;
             }
             bprev = bi;
         }
-        run.add(el[r].w, el[r].key);
+        la += el[r].w;
+        lb = fma(el[r].w, el[r].key, lb);
         if (i == n - 1) {
-            run.norm();
-            const Pre<T> tot = run.entry();
+            PairSum<T> tot = start;
+            tot.plus(PairSum<T>::from_pair(la, lb));
+            const Pre<T> e = tot.entry();
             for (int q = bi + 1; q <= NB; ++q) {
                 tb[q] = static_cast<int32_t>(n);
-                ab[q] = tot;
+                ab[q] = e;
             }
         }
     }
