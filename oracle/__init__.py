@@ -33,8 +33,8 @@ import threading
 
 import numpy as np
 
-GAUSSIAN, LAPLACIAN, NEGDIST = 0, 1, 2
-KERNELS = {"gaussian": GAUSSIAN, "laplacian": LAPLACIAN, "negdist": NEGDIST}
+GAUSSIAN, LAPLACIAN, NEGDIST, MATERN32 = 0, 1, 2, 3
+KERNELS = {"gaussian": GAUSSIAN, "laplacian": LAPLACIAN, "negdist": NEGDIST, "matern32": MATERN32}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "slk_oracle.c")
@@ -90,7 +90,8 @@ def cd(d: int) -> float:
 
 
 def F(kernel, param: float, r) -> np.ndarray:
-    """Radial basis function F(r) of Table 1 (param = sigma or the paper's alpha)."""
+    """Radial basis function F(r) of Table 1 (param = sigma, the paper's alpha, or the
+    Matern length scale beta)."""
     r = np.asarray(r, dtype=np.float64)
     lib = _load()
     k = _kid(kernel)

@@ -30,15 +30,22 @@
 #define ORC_GAUSSIAN 0
 #define ORC_LAPLACIAN 1
 #define ORC_NEGDIST 2
+#define ORC_MATERN32 3
 
 
 /* F(r): Gaussian exp(-r^2/(2 sigma^2)), Laplacian exp(-alpha r), negative
- * distance -r  (Table 1, first column; param = sigma or alpha). */
+ * distance -r, Matern nu = 3/2 (1 + a r) exp(-a r) with a = sqrt(3) / beta
+ * (Table 1, first column, and the Appendix's formula for nu = p + 1/2 at p = 1;
+ * param = sigma, alpha or beta). */
 double orc_F(int kernel, double param, double r) {
     switch (kernel) {
     case ORC_GAUSSIAN: return exp(-r * r / (2.0 * param * param));
     case ORC_LAPLACIAN: return exp(-param * r);
     case ORC_NEGDIST: return -r;
+    case ORC_MATERN32: {
+        double a = sqrt(3.0) / param;
+        return (1.0 + a * r) * exp(-a * r);
+    }
     }
     return NAN;
 }
@@ -49,6 +56,10 @@ double orc_dF(int kernel, double param, double r) {
     case ORC_GAUSSIAN: return -r / (param * param) * exp(-r * r / (2.0 * param * param));
     case ORC_LAPLACIAN: return -param * exp(-param * r);
     case ORC_NEGDIST: return -1.0;
+    case ORC_MATERN32: {
+        double a = sqrt(3.0) / param;
+        return -a * a * r * exp(-a * r);
+    }
     }
     return NAN;
 }
@@ -236,6 +247,73 @@ static double f_laplace_d(int d, double alpha, double x, double* df, double* err
     return s;
 }
 
+/*
+ * Matern nu = 3/2 1-D counterpart.  F(r) = (1 + a r) exp(-a r) = G(r) - r G'(r) for the
+ * Laplacian G(r) = exp(-a r), so its power-series coefficients are G's times (1 - n);
+ * Theorem 2.3 maps every power r^n to a multiple of x^n, hence
+ *   f(x) = sum_n (1 - n) b_n x^n,  b_n the Laplacian coefficients above (alpha = a),
+ * with the same two recurrences (the n = 1 term vanishes: f is C^1 at 0).
+ */
+static double f_matern_dd(int d, double a, double x, double* df, double* err) {
+    dd ax = dd_mul(dd_from(a), dd_from(x));
+    dd ax2 = dd_mul(ax, ax);
+    dd cdd = cd_dd(d);
+    dd s = dd_from(0.0), ds = dd_from(0.0);
+    double tmax = 0.0;
+    int nterms = 0;
+    for (int parity = 0; parity < 2; ++parity) {
+        dd term = parity == 0 ? dd_from(1.0) : dd_mul(ax, (dd){-cdd.hi, -cdd.lo});
+        int n = parity;
+        for (int j = 0; j < 200000; ++j) {
+            dd t = dd_mul_d(term, 1.0 - n);
+            s = dd_add(s, t);
+            ds = dd_add(ds, dd_mul_d(t, (double)n));
+            if (fabs(t.hi) > tmax) tmax = fabs(t.hi);
+            ++nterms;
+            double den = (n + 1.0) * (n + 1.0) * (n + 2.0);
+            if (ax2.hi * (n + d) < den && n > 1 && fabs(t.hi) < 1e-34 * (tmax > 0 ? tmax : 1.0)) break;
+            term = dd_div_d(dd_mul_d(dd_mul(term, ax2), (double)(n + d)), den);
+            n += 2;
+            if (term.hi == 0.0) break;
+        }
+    }
+    if (df) *df = (x != 0.0) ? (ds.hi + ds.lo) / x : 0.0;
+    if (err) *err = tmax * (nterms + 2) * ldexp(1.0, -100) + fabs(s.hi) * DBL_EPSILON;
+    return s.hi + s.lo;
+}
+
+static double f_matern_d(int d, double a, double x, double* df, double* err) {
+    double ax2 = (a * x) * (a * x), cd = orc_cd(d);
+    double s = 0.0, ds = 0.0, tmax = 0.0;
+    int nterms = 0;
+    for (int parity = 0; parity < 2; ++parity) {
+        double term = parity == 0 ? 1.0 : -cd * a * x;
+        int n = parity;
+        for (int j = 0; j < 200000; ++j) {
+            double t = (1.0 - n) * term;
+            s += t;
+            ds += n * t;
+            if (fabs(t) > tmax) tmax = fabs(t);
+            ++nterms;
+            double den = (n + 1.0) * (n + 1.0) * (n + 2.0);
+            if (ax2 * (n + d) < den && n > 1 && fabs(t) < 1e-18 * (tmax > 0 ? tmax : 1.0)) break;
+            term *= ax2 * (n + d) / den;
+            n += 2;
+            if (term == 0.0) break;
+        }
+    }
+    *df = (x != 0.0) ? ds / x : 0.0;
+    *err = tmax * (nterms + 2) * 4.0 * DBL_EPSILON;
+    return s;
+}
+
+static double f_matern(int d, double beta, double x, double* df, double* err) {
+    double a = sqrt(3.0) / beta;
+    double v = f_matern_d(d, a, x, df, err);
+    if (*err <= 1e-12) return v;
+    return f_matern_dd(d, a, x, df, err);
+}
+
 static double f_gauss(int d, double sigma, double x, double* df, double* err) {
     double v = f_gauss_d(d, sigma, x, df, err);
     if (*err <= 1e-12) return v;
@@ -336,6 +414,7 @@ double orc_f(int kernel, int d, double param, double x, double* df, double* err)
     }
     case ORC_LAPLACIAN: return f_laplace(d, param, x, df, err);
     case ORC_NEGDIST: return f_negdist(d, x, df, err);
+    case ORC_MATERN32: return f_matern(d, param, x, df, err);
     }
     return NAN;
 }

@@ -45,7 +45,8 @@ def test_cd_kershaw_bound_and_asymptotics():
 # ------------------------------------------------- special dimensions (Thm 2.3, Cor 2.4)
 
 @pytest.mark.parametrize("kernel,param", [("gaussian", 0.7), ("gaussian", 3.0), ("laplacian", 0.5),
-                                          ("laplacian", 2.0), ("negdist", 0.0)])
+                                          ("laplacian", 2.0), ("negdist", 0.0), ("matern32", 1.0),
+                                          ("matern32", 0.4)])
 def test_d1_counterpart_equals_F(kernel, param):
     """d = 1: b_n = a_n (Theorem 2.3), so f = F."""
     x = np.linspace(0.0, 6.0, 97)
@@ -54,6 +55,9 @@ def test_d1_counterpart_equals_F(kernel, param):
         ref = np.exp(-x ** 2 / (2 * param ** 2))
     elif kernel == "laplacian":
         ref = np.exp(-param * x)
+    elif kernel == "matern32":
+        a = math.sqrt(3.0) / param  # Matern nu = 3/2 (Appendix, nu = p + 1/2 with p = 1)
+        ref = (1 + a * x) * np.exp(-a * x)
     else:
         ref = -x
     np.testing.assert_allclose(fx, ref, rtol=1e-12, atol=2e-12)
@@ -70,6 +74,11 @@ def test_d3_closed_forms(param):
     np.testing.assert_allclose(lap, np.exp(-param * t) * (1 - param * t), rtol=1e-11, atol=2e-12)
     nd = oracle.f("negdist", 3, 0.0, t)
     np.testing.assert_allclose(nd, -2.0 * t, rtol=1e-15)
+    # Matern nu = 3/2 with beta = param: F = (1 + a t) e^{-a t}, a = sqrt(3)/beta, so
+    # F + t F' = e^{-a t} (1 + a t - a^2 t^2)
+    a = math.sqrt(3.0) / param
+    mt = oracle.f("matern32", 3, param, t)
+    np.testing.assert_allclose(mt, np.exp(-a * t) * (1 + a * t - a * a * t * t), rtol=1e-10, atol=2e-12)
 
 
 def test_gaussian_matches_library_hypergeometric():
@@ -127,6 +136,9 @@ def _Sd(kernel, d, param, s):
     ("laplacian", 50, 1 / math.sqrt(50), [1.0, 7.0, 20.0]),
     ("negdist", 4, 0.0, [0.5, 2.0]),
     ("negdist", 50, 0.0, [0.5, 2.0]),
+    ("matern32", 2, 1.0, [0.3, 1.0, 3.0]),
+    ("matern32", 7, 1.0, [0.3, 1.0, 3.0]),
+    ("matern32", 50, math.sqrt(50), [2.0, 7.0, 20.0]),
 ])
 def test_transform_Sd_returns_F(kernel, d, param, svals):
     """Proposition 2.2: S_d(f) = F, by independent adaptive quadrature of Eq. (2.2)."""
@@ -178,7 +190,8 @@ def test_gaussian_bounded_by_one():
 
 
 @pytest.mark.parametrize("kernel,d,param", [("gaussian", 16, 4.0), ("gaussian", 784, 28.0),
-                                            ("laplacian", 50, 1 / math.sqrt(50)), ("negdist", 3072, 0.0)])
+                                            ("laplacian", 50, 1 / math.sqrt(50)), ("negdist", 3072, 0.0),
+                                            ("matern32", 50, math.sqrt(50))])
 def test_derivative_matches_finite_differences(kernel, d, param):
     x = np.linspace(0.3, 12.0, 25)
     h = 1e-5
@@ -198,17 +211,23 @@ def _small(kernel, d, N, M, P, seed, scale=1.0):
     return X, Y, w, xi
 
 
-@pytest.mark.parametrize("kernel,param", [("gaussian", 1.3), ("laplacian", 0.7), ("negdist", 0.0)])
+@pytest.mark.parametrize("kernel,param", [("gaussian", 1.3), ("laplacian", 0.7), ("negdist", 0.0),
+                                          ("matern32", 1.1)])
 def test_direct_sum_against_cdist(kernel, param):
     """O-direct against scipy's pairwise distances."""
     from scipy.spatial.distance import cdist
     X, Y, w, _ = _small(kernel, 5, 37, 23, 1, 1)
     r = cdist(Y, X)
-    Fr = {"gaussian": np.exp(-r ** 2 / (2 * param ** 2)), "laplacian": np.exp(-param * r), "negdist": -r}[kernel]
+    if kernel == "matern32":
+        a = math.sqrt(3.0) / param
+        Fr = (1 + a * r) * np.exp(-a * r)
+    else:
+        Fr = {"gaussian": np.exp(-r ** 2 / (2 * param ** 2)), "laplacian": np.exp(-param * r), "negdist": -r}[kernel]
     np.testing.assert_allclose(oracle.direct_sum(kernel, param, X, Y, w), Fr @ w, rtol=1e-13, atol=1e-13)
 
 
-@pytest.mark.parametrize("kernel,param", [("gaussian", 1.3), ("laplacian", 0.7), ("negdist", 0.0)])
+@pytest.mark.parametrize("kernel,param", [("gaussian", 1.3), ("laplacian", 0.7), ("negdist", 0.0),
+                                          ("matern32", 0.9)])
 def test_sliced_d1_is_exact(kernel, param):
     """d = 1: every direction is +-1 and f = F, so the sliced sum equals the direct sum."""
     X, Y, w, xi = _small(kernel, 1, 50, 20, 7, 2)
@@ -321,7 +340,8 @@ def test_invariances():
         np.testing.assert_allclose(s12, 2 * s - 3 * s2, rtol=1e-10, atol=1e-10)
 
 
-@pytest.mark.parametrize("kernel,param", [("gaussian", 1.2), ("laplacian", 0.8), ("negdist", 0.0)])
+@pytest.mark.parametrize("kernel,param", [("gaussian", 1.2), ("laplacian", 0.8), ("negdist", 0.0),
+                                          ("matern32", 1.0)])
 def test_sliced_gradient_matches_finite_differences(kernel, param):
     """O-grad against central differences of O-sliced (piecewise smooth; h below the
     smallest projected gap)."""
