@@ -69,7 +69,9 @@ typedef enum {
 typedef enum {
     SLK_GAUSSIAN = 0,         /* param = sigma > 0 */
     SLK_LAPLACIAN = 1,        /* param = alpha > 0 (F = exp(-alpha r)) */
-    SLK_NEGDIST = 2           /* param ignored */
+    SLK_NEGDIST = 2,          /* param ignored */
+    SLK_MATERN32 = 3          /* Matern nu = 3/2, param = beta > 0:
+                                 F = (1 + sqrt(3) r / beta) exp(-sqrt(3) r / beta) */
 } slk_kernel;
 
 typedef enum {

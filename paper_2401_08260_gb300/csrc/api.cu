@@ -135,12 +135,22 @@ struct slk_plan_s {
 
 namespace {
 
+// Coefficients for the NFFT kernels: the Laplacian's smooth part (alpha = param) or the
+// Matern nu = 3/2 counterpart (a = sqrt(3) / beta, beta = param).
+FourierHost fourier_smooth(const slk_plan_desc& desc, int d, double R, double tol) {
+    const int max_nc = desc.precision == SLK_PREC_F64 ? 4096 : 8192;
+    if (desc.kernel == SLK_MATERN32)
+        return choose_laplace_smooth(std::sqrt(3.0) / desc.param, d, R, desc.n_coeff, tol, max_nc, true);
+    return choose_laplace_smooth(desc.param, d, R, desc.n_coeff, tol, max_nc);
+}
+
 // Default model-error target per precision, well below the accuracy bar of the
 // arithmetic (FP64 1e-12 for the Gaussian).  The Laplacian's smooth part has
 // coefficients decaying only like k^-4 (its |x|^3 term at 0), so it asks for
-// 1e-7 (FP64) and 2e-6 (FP32) to keep the grid at a few thousand coefficients.
+// 1e-7 (FP64) and 2e-6 (FP32) to keep the grid at a few thousand coefficients; so does the
+// Matern nu = 3/2 counterpart (also an |x|^3 term).
 double default_tol(int kernel, int precision) {
-    if (kernel == SLK_LAPLACIAN) return precision == SLK_PREC_F64 ? 1e-7 : 2e-6;
+    if (kernel == SLK_LAPLACIAN || kernel == SLK_MATERN32) return precision == SLK_PREC_F64 ? 1e-7 : 2e-6;
     if (precision == SLK_PREC_F64) return 1e-12;
     if (precision == SLK_PREC_BF16) return 1e-5;
     return 2e-7;
@@ -476,7 +486,7 @@ void create_impl(slk_plan plan, const void* x_user, int64_t ldx, const void* w_u
     if constexpr (sizeof(T) == 4) {
         if (plan->tc == 1 && kernel == SLK_GAUSSIAN && fused_cheb_source(plan, xv.ptr, xv.ld, wv.ptr, st)) return;
     }
-    const bool need_fourier = kernel == SLK_GAUSSIAN || kernel == SLK_LAPLACIAN;
+    const bool need_fourier = kernel != SLK_NEGDIST;
     DevBuf<T> Zx(static_cast<size_t>(P) * N, st);
     DevBuf<float> mx(1, st);
     SLK_CHECK_CUDA(cudaMemsetAsync(mx.get(), 0, sizeof(float), st));
@@ -492,7 +502,7 @@ void create_impl(slk_plan plan, const void* x_user, int64_t ldx, const void* w_u
         double tol = plan->desc.tol;
         if (tol <= 0.0) tol = default_tol(kernel, plan->desc.precision);
         if (kernel == SLK_GAUSSIAN) plan->fh = choose_gaussian(plan->desc.param, d, R, plan->desc.n_coeff, plan->desc.method, tol);
-        else plan->fh = choose_laplace_smooth(plan->desc.param, d, R, plan->desc.n_coeff, tol, plan->f64 ? 4096 : 8192);
+        else plan->fh = fourier_smooth(plan->desc, d, R, tol);
         plan->fourier = true;
         plan_fourier_source<T>(plan, Zx.get(), wv.ptr, st);
     }
@@ -637,14 +647,15 @@ void grad_impl(slk_plan plan, const void* y_user, int64_t M, int64_t ldy, const 
 
 void validate_desc(const slk_plan_desc* desc) {
     SLK_REQUIRE(desc, "descriptor is NULL");
-    SLK_REQUIRE(desc->kernel >= SLK_GAUSSIAN && desc->kernel <= SLK_NEGDIST, "unknown kernel %d", desc->kernel);
+    SLK_REQUIRE(desc->kernel >= SLK_GAUSSIAN && desc->kernel <= SLK_MATERN32, "unknown kernel %d", desc->kernel);
     SLK_REQUIRE(desc->precision >= SLK_PREC_F64 && desc->precision <= SLK_PREC_F16X3, "unknown precision %d",
                 desc->precision);
     SLK_REQUIRE(desc->d >= 1, "d must be >= 1");
     SLK_REQUIRE(desc->P >= 1 && desc->P <= 65535, "P must be in [1, 65535]");
     SLK_REQUIRE(desc->method >= SLK_FOURIER_AUTO && desc->method <= SLK_FOURIER_CHEB, "unknown Fourier method");
-    if (desc->kernel == SLK_LAPLACIAN && desc->method == SLK_FOURIER_CHEB)
-        fail(SLK_ERR_UNSUPPORTED, "the Chebyshev evaluation serves the Gaussian kernel; the Laplacian uses the NFFT");
+    if ((desc->kernel == SLK_LAPLACIAN || desc->kernel == SLK_MATERN32) && desc->method != SLK_FOURIER_AUTO &&
+        desc->method != SLK_FOURIER_NFFT)
+        fail(SLK_ERR_UNSUPPORTED, "the Laplacian and Matern kernels use the NFFT (their coefficients decay like k^-4)");
     SLK_REQUIRE(desc->n_coeff >= 0 && desc->n_coeff <= (1 << 14) && desc->n_coeff % 2 == 0,
                 "n_coeff must be even and in [0, 16384]");
     if (desc->kernel != SLK_NEGDIST)
@@ -856,9 +867,10 @@ slk_status slk_fourier_params(const slk_plan_desc* desc, double radius, slk_plan
         const bool f64 = desc->precision == SLK_PREC_F64;
         double tol = desc->tol;
         if (tol <= 0.0) tol = default_tol(desc->kernel, desc->precision);
+        (void)f64;
         FourierHost fh = desc->kernel == SLK_GAUSSIAN
                              ? choose_gaussian(desc->param, desc->d, radius, desc->n_coeff, desc->method, tol)
-                             : choose_laplace_smooth(desc->param, desc->d, radius, desc->n_coeff, tol, f64 ? 4096 : 8192);
+                             : fourier_smooth(*desc, desc->d, radius, tol);
         std::memset(info, 0, sizeof(*info));
         info->kernel = desc->kernel;
         info->precision = desc->precision;

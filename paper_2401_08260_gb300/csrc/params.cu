@@ -227,7 +227,7 @@ inline DD dd_div(DD a, double b) {
 // derivatives of the series, in double-double.  Returns k1; der[q] receives
 // the q-th derivative (q = 0..3) when der != NULL; *err receives a rounding
 // bound.  cd must carry c_d to double-double accuracy.
-double k1_laplace(double alpha, int d, DD cd, double x, double* der, double* err) {
+double k1_laplace(double alpha, int d, DD cd, double x, double* der, double* err, bool matern = false) {
     DD ax = dd_mul({alpha, 0.0}, {x, 0.0});
     DD ax2 = dd_mul(ax, ax);
     DD s[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
@@ -237,20 +237,22 @@ double k1_laplace(double alpha, int d, DD cd, double x, double* der, double* err
         DD term = parity == 0 ? DD{1.0, 0.0} : dd_mul(ax, {-cd.hi, -cd.lo});
         int n = parity;
         for (int j = 0; j < 100000; ++j) {
+            // the Matern nu = 3/2 series weighs the x^n term by 1 - n (which also drops n = 1)
+            const DD tw = matern ? dd_scale(term, 1.0 - n) : term;
             if (n != 1 && x != 0.0) {
                 // d^q/dx^q x^n = n (n-1) ... (n-q+1) x^(n-q)
-                DD f = term;
+                DD f = tw;
                 for (int q = 0; q < 4; ++q) {
                     s[q] = dd_add(s[q], f);
                     f = dd_div(dd_scale(f, static_cast<double>(n - q)), x);
                 }
             } else if (n == 0) {
-                s[0] = dd_add(s[0], term);
+                s[0] = dd_add(s[0], tw);
             }
-            tmax = std::max(tmax, std::fabs(term.hi));
+            tmax = std::max(tmax, std::fabs(tw.hi));
             ++terms;
             double den = (n + 1.0) * (n + 1.0) * (n + 2.0);
-            if (ax2.hi * (n + d) < den && std::fabs(term.hi) < 1e-34 * std::max(tmax, 1e-300)) break;
+            if (ax2.hi * (n + d) < den && n > 1 && std::fabs(tw.hi) < 1e-34 * std::max(tmax, 1e-300)) break;
             term = dd_div(dd_scale(dd_mul(term, ax2), static_cast<double>(n + d)), den);
             n += 2;
             if (term.hi == 0.0) break;
@@ -500,10 +502,12 @@ FourierHost choose_gaussian(double sigma, int d, double R, int n_coeff_req, int 
     return fp;
 }
 
-FourierHost choose_laplace_smooth(double alpha, int d, double R, int n_coeff_req, double tol, int max_nc) {
+FourierHost choose_laplace_smooth(double alpha, int d, double R, int n_coeff_req, double tol, int max_nc,
+                                  bool matern) {
+    const int key = matern ? 2 : 1;
     {
         std::lock_guard<std::mutex> g(cache_mu);
-        auto it = cache.find({1, alpha, d, R, tol, n_coeff_req, max_nc});
+        auto it = cache.find({key, alpha, d, R, tol, n_coeff_req, max_nc});
         if (it != cache.end()) return it->second;
     }
     const double D = 2.0 * R;
@@ -524,13 +528,13 @@ FourierHost choose_laplace_smooth(double alpha, int d, double R, int n_coeff_req
         //     phi1 = B T + (1 - B) k1(x0)
         const double x0 = rho * fp.L;
         double t0[4];
-        k1_laplace(alpha, d, cd, x0, t0, &emax);
+        k1_laplace(alpha, d, cd, x0, t0, &emax, matern);
         for (int j = 0; j < nf; ++j) {
             double u = (j < nf / 2 ? j : j - nf) / static_cast<double>(nf);  // in [-1/2, 1/2)
             double au = std::fabs(u), e = 0.0;
             double v;
             if (au <= rho) {
-                v = k1_laplace(alpha, d, cd, au * fp.L, nullptr, &e);
+                v = k1_laplace(alpha, d, cd, au * fp.L, nullptr, &e, matern);
             } else {
                 double h = (au - rho) * fp.L;
                 double T = t0[0] + h * (t0[1] + h * (0.5 * t0[2] + h * t0[3] / 6.0));
@@ -568,8 +572,8 @@ FourierHost choose_laplace_smooth(double alpha, int d, double R, int n_coeff_req
         }
     }
     if (!have)
-        fail(SLK_ERR_ACCURACY, "Laplacian smooth part: no grid of at most %d coefficients meets %.3g (alpha*R = %.3g)",
-             max_nc, tol_t, alpha * R);
+        fail(SLK_ERR_ACCURACY, "%s: no grid of at most %d coefficients meets %.3g (alpha*R = %.3g)",
+             matern ? "Matern kernel" : "Laplacian smooth part", max_nc, tol_t, alpha * R);
     choose_window(&best, 0.25 * tol);
     set_active_window(&best);
     best.mult.resize(best.n_coeff / 2);
@@ -581,7 +585,7 @@ FourierHost choose_laplace_smooth(double alpha, int d, double R, int n_coeff_req
     best.model_err = best.trunc_err + best.window_err;
     {
         std::lock_guard<std::mutex> g(cache_mu);
-        cache[{1, alpha, d, R, tol, n_coeff_req, max_nc}] = best;
+        cache[{key, alpha, d, R, tol, n_coeff_req, max_nc}] = best;
     }
     return best;
 }

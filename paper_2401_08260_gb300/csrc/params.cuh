@@ -31,6 +31,11 @@ struct FourierHost {
 double cd_host(int d);
 FourierHost choose_gaussian(double sigma, int d, double R, int n_coeff_req, int method, double tol);
 // max_nc: largest N_c whose grid (2 N_c complex values) fits one block's shared memory
-FourierHost choose_laplace_smooth(double alpha, int d, double R, int n_coeff_req, double tol, int max_nc);
+// Fourier coefficients of a Laplacian-type counterpart on the window: the Laplacian's
+// smooth part k1 = f_lap + alpha c_d |x| (matern = false), or, with matern, the whole
+// Matern nu = 3/2 counterpart (its series is the Laplacian one, alpha = sqrt(3) / beta,
+// with the x^n term scaled by 1 - n; no |x| term).
+FourierHost choose_laplace_smooth(double alpha, int d, double R, int n_coeff_req, double tol, int max_nc,
+                                  bool matern = false);
 
 }  // namespace slk

@@ -90,7 +90,7 @@ extern "C" int64_t slk_request_bytes(const slk_plan_desc* desc, int64_t N, int64
         create += grids + P * e * 256 * (N / 32768 + 2);
         persist += grids;
     }
-    if (desc->kernel != SLK_GAUSSIAN) {
+    if (desc->kernel == SLK_NEGDIST || desc->kernel == SLK_LAPLACIAN) {
         const int64_t NB = N / 8 + 2;
         const int64_t sort = P * N * (e + 4) + 2 * P * N * e + P * N * 4 + P * 256 * (N / 4096 + 1) * 4;
         const int64_t keep = P * N * 2 * e + P * NB * 20;

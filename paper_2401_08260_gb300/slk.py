@@ -21,7 +21,7 @@ except ImportError:  # pragma: no cover
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libslk.so")
 
-KERNELS = {"gaussian": 0, "laplacian": 1, "negdist": 2}
+KERNELS = {"gaussian": 0, "laplacian": 1, "negdist": 2, "matern32": 3}
 PRECISIONS = {"f64": 0, "f32": 1, "bf16": 2, "f16x3": 3}
 METHODS = {"auto": 0, "nfft": 1, "ndft": 2, "cheb": 3}
 STATUS = {0: "SLK_OK", 1: "SLK_ERR_INVALID", 2: "SLK_ERR_OOM", 3: "SLK_ERR_CUDA", 4: "SLK_ERR_ACCURACY",
@@ -154,7 +154,7 @@ class Plan:
     """A sliced kernel-summation plan over the sources x (N x d) with weights w.
 
     kernel: "gaussian" (param = sigma), "laplacian" (param = alpha, F = exp(-alpha r))
-    or "negdist".  precision: "f64", "f32", "bf16" or "f16x3".  directions: optional
+    or "negdist" or "matern32" (param = beta).  precision: "f64", "f32", "bf16" or "f16x3".  directions: optional
     P x d unit directions (FP64); otherwise the library draws them from ``seed``."""
 
     def __init__(self, x, w, kernel: str, param: float = 0.0, P: int = 256, precision: str = "f32",

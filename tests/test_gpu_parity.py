@@ -149,9 +149,34 @@ def test_laplace_fp64():
     assert err <= 1e-6 and err <= 4 * info["model_error"] + 1e-12, (err, info)
 
 
+@pytest.mark.parametrize("precision,tol", [("f32", 1e-5), ("f16x3", 1e-5), ("f64", 5e-6), ("bf16", 2e-3)])
+def test_matern32(precision, tol):
+    """Matern nu = 3/2 (the paper's fourth experiment kernel) through the NFFT with the
+    regularised coefficients of its C^2 counterpart: sums and gradient against the oracle."""
+    dev = cuda_or_skip()
+    d, N, M, P = 50, 20011, 333, 24
+    wl = workloads.make("laplace_d50", N=N, M=M, P=P)  # the d = 50 mixture data
+    beta = math.sqrt(d)
+    dt = np.float64 if precision == "f64" else np.float32
+    x, y, w = wl.x.astype(dt), wl.y.astype(dt), wl.w.astype(dt)
+    # FP64: a certified model error of 1e-6 (the default 1e-7 would need more than the
+    # 4096 coefficients an FP64 grid holds at this radius)
+    plan = _plan(to_dev(x, dev), to_dev(w, dev), "matern32", beta, wl.xi, precision,
+                 tol=1e-6 if precision == "f64" else 0.0)
+    info = plan.info()
+    assert info["method"] == 1 and info["model_error"] > 0.0, info
+    s = plan.sum(to_dev(y, dev))
+    ref, gref, _ = oracle.sliced_sum("matern32", beta, x, y, w, wl.xi, grad=True)
+    assert rel_inf(s, ref, w.sum()) <= tol, (rel_inf(s, ref, w.sum()), info)
+    g = plan.grad(to_dev(y, dev))
+    # the tensor-core paths (bf16, f16x3) form the backward product G xi in BF16
+    gtol = 2 * tol if precision in ("f32", "f64") else max(2 * tol, 1e-4)
+    assert rel_inf(g, gref, w.sum()) <= gtol
+
+
 @pytest.mark.parametrize("kernel,param,method", [("gaussian", None, "ndft"), ("gaussian", None, "nfft"),
                                                  ("gaussian", None, "cheb"), ("negdist", 0.0, "auto"),
-                                                 ("laplacian", None, "auto")])
+                                                 ("laplacian", None, "auto"), ("matern32", None, "auto")])
 def test_gradient_fp32(kernel, param, method):
     dev = cuda_or_skip()
     d, N, M, P = 40, 6007, 129, 29
@@ -162,7 +187,7 @@ def test_gradient_fp32(kernel, param, method):
     gs = rng.standard_normal(M).astype(np.float32)
     xi = workloads.directions(P, d, seed=22)
     if param is None:
-        param = math.sqrt(d) if kernel == "gaussian" else 1.0 / math.sqrt(d)
+        param = math.sqrt(d) if kernel in ("gaussian", "matern32") else 1.0 / math.sqrt(d)
     plan = _plan(to_dev(x, dev), to_dev(w, dev), kernel, param, xi, "f32", method=method)
     gy = plan.grad(to_dev(y, dev), gs=to_dev(gs, dev))
     _, g_ref, _ = oracle.sliced_sum(kernel, param, x, y, w, xi, grad=True)
@@ -181,7 +206,7 @@ def test_gradient_fp64_gradcheck():
     x = to_dev(rng.standard_normal((200, d)), dev)
     w = to_dev(rng.random(200), dev)
     xi = workloads.directions(11, d, seed=1)
-    for kernel, param in [("gaussian", 1.3), ("laplacian", 0.6), ("negdist", 0.0)]:
+    for kernel, param in [("gaussian", 1.3), ("laplacian", 0.6), ("negdist", 0.0), ("matern32", 10.0)]:
         plan = Plan(x, w, kernel, param, P=11, precision="f64", directions=xi, radius=12.0)
         y = to_dev(rng.standard_normal((6, d)), dev).requires_grad_(True)
         assert torch.autograd.gradcheck(lambda yy: sliced_kernel_sum(yy, plan), (y,), eps=1e-6, atol=1e-6, rtol=1e-4)
