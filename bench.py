@@ -120,41 +120,64 @@ NCU_TRAFFIC_PER_POINT = {("gauss_d784", "center_cast"): (627.233024e6 + 281.7664
                          ("gauss_d784", "umma_cheb_moments"): (315.320832e6 + 3.245568e6) / 2e5}
 
 
-def measured_traffic(wl, kernel_name, launches_per_step):
+def step_points(wl, kernel_name, kernels):
+    """Rows that one step's launches of a kernel process together.  The fused Chebyshev path
+    (the one that gathers a radius sample, `gather_rows`) also centres, casts and projects that
+    sample of min(4096, N) source rows; source-side kernels see the N sources, target-side
+    kernels the M targets, the rest both."""
+    S = min(4096, wl.N) if "gather_rows" in kernels else 0
+    if kernel_name.startswith("center_cast"):
+        return wl.N + wl.M + S
+    if kernel_name.startswith(("umma_cheb_moments", "cheb_moments", "ndft_source", "spread")):
+        return wl.N
+    if kernel_name.startswith(("umma_cheb_target", "umma_grad", "cheb_target", "ndft_target", "nfft_target",
+                               "negdist_target")):
+        return wl.M
+    if kernel_name.startswith(("umma_project", "gemm")) and S:
+        return S
+    return wl.N + wl.M
+
+
+def measured_traffic(wl, kernel_name, launches_per_step, kernels):
+    """DRAM bytes of an average launch, from the per-point ncu figure (None without one)."""
     key = (wl.name, kernel_name)
     if key not in NCU_TRAFFIC_PER_POINT or wl.d != 784 or wl.P != 512 or wl.N != wl.M:
         return None
-    return NCU_TRAFFIC_PER_POINT[key] * wl.N
+    return NCU_TRAFFIC_PER_POINT[key] * step_points(wl, kernel_name, kernels) / max(1.0, launches_per_step)
 
 
-def algorithmic(wl, info, precision, kernel_name, launches_per_step):
-    """(algorithmic amount per launch, unit, bound) of one launch of a library kernel.
+def algorithmic(wl, info, precision, kernel_name, launches_per_step, kernels, P=None, grad=False):
+    """(algorithmic amount of an average launch, unit, bound) of a library kernel: the amount
+    of one step's launches (their points from `step_points`) over the launches per step.
 
     Units of work: a point (row of x or y) and a slice-point (one point on one slice).
-    The projection, centring, Fourier and Chebyshev kernels run once per point set
-    (the N sources or the M targets; N = M in every workload here), so one launch
-    covers N points; other kernels (sort passes, batched lookups) split the N + M
-    points of a step over their launches.
     Projection: 2 d P flop per point (tensor for BF16 / FP16x3, FP32 ALU otherwise;
     the fused Chebyshev target kernel is counted by its contraction alone).
     NDFT source / target: one complex multiply-add per band coefficient, 8 K flop per
     slice-point (FP32 ALU).  Chebyshev moments / Clenshaw: two FMAs per term, 4 q flop
     per slice-point (FP32 ALU).  Centring cast: 4 d bytes read + 2 ld16 (x2 for the
-    hi/lo split) written per point.  Other kernels: the 4-byte projections they read."""
-    per_set = kernel_name.startswith(("gemm", "umma", "ndft", "nfft", "cheb", "center_cast")) and "reduce" not in kernel_name
-    pts = 0.5 * (wl.N + wl.M) if per_set else (wl.N + wl.M) / max(1.0, launches_per_step)
+    hi/lo split) written per point, plus, with the gradient, the same for the M x P
+    per-slice derivatives it casts.  Other kernels: the 4-byte projections they read.
+    P: the slices one launch covers (this rank's share when the slices are sharded)."""
+    P = wl.P if P is None else P
+    pts = step_points(wl, kernel_name, kernels) / max(1.0, launches_per_step)
+    per = 1.0 / max(1.0, launches_per_step)
     if kernel_name.startswith(("gemm", "umma")):
         bound = "tensor" if kernel_name.startswith("umma") else "alu"
-        return 2.0 * pts * wl.d * wl.P, "flop", bound
+        return 2.0 * pts * wl.d * P, "flop", bound
     if kernel_name.startswith("ndft_source") or kernel_name.startswith("ndft_target"):
         K = info["k_hi"] - info["k_lo"] + 1
-        return 8.0 * K * pts * wl.P, "flop", "alu"
+        return 8.0 * K * pts * P, "flop", "alu"
     if kernel_name.startswith(("cheb_moments", "cheb_target")):
-        return 4.0 * info["cheb_terms"] * pts * wl.P, "flop", "alu"
+        return 4.0 * info["cheb_terms"] * pts * P, "flop", "alu"
     if kernel_name.startswith("center_cast"):
+        k = 2 if precision == "f16x3" else 1
         ld16 = (wl.d + 7) // 8 * 8
-        return pts * (4.0 * wl.d + 2.0 * ld16 * (2 if precision == "f16x3" else 1)), "byte", "hbm"
-    return 4.0 * pts * wl.P, "byte", "hbm"
+        amount = pts * (4.0 * wl.d + 2.0 * ld16 * k)
+        if grad:
+            amount += per * wl.M * (4.0 * P + 2.0 * ((P + 7) // 8 * 8))
+        return amount, "byte", "hbm"
+    return 4.0 * pts * P, "byte", "hbm"
 
 
 def cpu_sample(wl, budget_s: float):
@@ -238,7 +261,8 @@ def max_over_ranks(x: float, device=None) -> float:
 
 def job_rate(units_per_rank: float, world: int, ms_per_step: float) -> float:
     """Whole-job throughput: every rank processes units_per_rank per step (replicas, weak
-    scaling), the step takes the slowest rank's ms_per_step."""
+    scaling; for a slice-sharded sum the caller passes the whole job's units with world = 1),
+    the step takes the slowest rank's ms_per_step."""
     return units_per_rank * world / (ms_per_step * 1e-3)
 
 
@@ -268,8 +292,24 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     gy = torch.empty_like(y) if args.grad else None
+    sharded = args.parallel == "slices"
+    if sharded:
+        from paper_2401_08260_gb300.shard import ShardedPlan, SliceShard
+        P_local = SliceShard(wl.P).count
+        if P_local == 0:
+            raise SystemExit("--parallel slices needs P >= the number of GPUs")
+    else:
+        P_local = wl.P
 
     def step():
+        if sharded:
+            # this rank's slices of the plan, then one all-reduce of the M sums (and of the gradient)
+            sp = ShardedPlan(x, w, **kw)
+            s.copy_(sp.sum(y))
+            if args.grad:
+                gy.copy_(sp.grad(y))
+            sp.close()
+            return
         plan = slk.Plan(x, w, **kw)
         plan.sum(y, out=s, sync=False)
         if args.grad:
@@ -278,9 +318,14 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         step()
-    plan = slk.Plan(x, w, **kw)
-    info = plan.info()
-    plan.close()
+    if sharded:
+        sp = ShardedPlan(x, w, **kw)
+        info = sp.plan.info()
+        sp.close()
+    else:
+        plan = slk.Plan(x, w, **kw)
+        info = plan.info()
+        plan.close()
     torch.cuda.synchronize()
 
     # ---------------- device-resident timed region
@@ -310,7 +355,9 @@ def run_ours(args):
     dev_ms = ev0.elapsed_time(ev1)
     # wall time includes the host work of plan creation (parameter selection is cached)
     ms = max_over_ranks(max(dev_ms, t_wall * 1e3) / args.steps, dev)
-    value = job_rate((wl.N + wl.M) * wl.P, world, ms)
+    # replicas: every rank sums all P slices; sharded: the ranks share one sum's P slices
+    job_world = 1 if sharded else world
+    value = job_rate((wl.N + wl.M) * wl.P, job_world, ms)
 
     # ---------------- dominant kernel roofline
     peaks, peak_kind = _peaks()
@@ -319,7 +366,7 @@ def run_ours(args):
     if top:
         name, (n_launch, tot_ms) = top
         per_step = n_launch / args.steps
-        amount, unit, bound = algorithmic(wl, info, precision, name, per_step)
+        amount, unit, bound = algorithmic(wl, info, precision, name, per_step, kernels, P=P_local, grad=args.grad)
         avg_s = tot_ms / n_launch * 1e-3
         if bound == "tensor":
             # a kernel timed inside a long step: the sustained dense BF16 figure (FP16 runs at the same rate)
@@ -336,7 +383,7 @@ def run_ours(args):
             achieved = amount / avg_s / 1e9
             runit = "GB/s"
         roofline = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": runit,
-                    "frac": achieved / peak, "traffic": measured_traffic(wl, name, per_step),
+                    "frac": achieved / peak, "traffic": measured_traffic(wl, name, per_step, kernels),
                     "peak_source": peak_kind,
                     "launch_ms": tot_ms / n_launch,
                     "share": tot_ms / sum(v[1] for v in kernels.values())}
@@ -353,6 +400,13 @@ def run_ours(args):
         gh = torch.empty_like(yh).pin_memory() if args.grad else None
 
         def host_step():
+            if sharded:
+                sp = ShardedPlan(xh, wh, **kw)
+                sh.copy_(sp.sum(yh))
+                if args.grad:
+                    gh.copy_(sp.grad(yh))
+                sp.close()
+                return
             plan = slk.Plan(xh, wh, **kw)
             plan.sum(yh, out=sh, sync=True)
             if args.grad:
@@ -369,9 +423,11 @@ def run_ours(args):
         torch.cuda.synchronize()
         te = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dev)
         bi = xh.numel() * xh.element_size() + yh.numel() * yh.element_size() + wh.numel() * wh.element_size() + \
-            wl.xi.size * 8
+            P_local * wl.d * 8
         bo = sh.numel() * sh.element_size() + (gh.numel() * gh.element_size() if args.grad else 0)
-        e2e = {"value": job_rate((wl.N + wl.M) * wl.P, world, te * 1e3), "unit": "slice-points/s",
+        if sharded and world > 1:  # the combined results are staged through the GPU for the all-reduce
+            bi, bo = bi + bo, bo + bo
+        e2e = {"value": job_rate((wl.N + wl.M) * wl.P, job_world, te * 1e3), "unit": "slice-points/s",
                "h2d_bytes_per_step": int(bi),
                "d2h_bytes_per_step": int(bo), "ms_per_step": te * 1e3}
 
@@ -385,11 +441,13 @@ def run_ours(args):
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "slice-points/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "strong" if sharded else "weak",
                 "vs_baseline": None, "dtype": precision, "data": "synthetic",
                 "config": {"workload": args.workload, "kernel": wl.kernel, "N": wl.N, "M": wl.M, "d": wl.d,
                            "P": wl.P, "n_coeff": info["n_coeff"], "method": {1: "nfft", 2: "ndft"}.get(info["method"]),
-                           "parallelism": f"replicas{world}" if world > 1 else "single",
+                           "parallelism": (f"slices{world}" if sharded else f"replicas{world}") if world > 1
+                           else "single",
                            "l2": "inputs larger than L2 (no flush needed)",
                            "model_error": info["model_error"], "backward": bool(args.grad)},
                 "roofline": roofline, "cpu_baseline": cpu, "errors": errors, "e2e": e2e, "clocks": clocks,
@@ -565,6 +623,9 @@ def main():
     ap.add_argument("--M", type=int, default=None)
     ap.add_argument("--P", type=int, default=None)
     ap.add_argument("--grad", action="store_true", help="include the y-gradient (backward) in every step")
+    ap.add_argument("--parallel", choices=["replicas", "slices"], default="replicas",
+                    help="N > 1: independent replicas of the workload (default), or one workload whose "
+                         "slices are split over the GPUs with one all-reduce of the sums per step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

@@ -113,8 +113,18 @@ typedef struct {
                                  projected: 1.5 x the largest projection over the sample of
                                  (at most 4096) sources the centre is estimated from, or the
                                  first rule when a source falls outside that */
-    int32_t slice_batch;      /* slices processed per pass; 0 = all at once */
-    int32_t reserved[7];
+    int32_t slice_batch;      /* slk_kernel_sum only: build and run plans of at most slice_batch
+                                 slices one after another and combine their sums, so that the
+                                 working memory is one batch's plan (Sec. 5.4, remark on
+                                 memory and batching); 0 = all at once.  A plan from
+                                 slk_plan_create holds every slice and ignores the field. */
+    int32_t slice_offset;     /* first slice of the library's draw: the plan draws the rows
+                                 slice_offset .. slice_offset + P - 1 of the direction sequence
+                                 of `seed`, so that plans over disjoint slice ranges (GPUs of a
+                                 sharded sum, batches) together use the same directions as one
+                                 plan over all slices; >= 0, slice_offset + P <= 2^31 - 1;
+                                 ignored when directions != NULL */
+    int32_t reserved[6];
 } slk_plan_desc;
 
 /* What a plan chose (filled by slk_plan_get_info). */
@@ -216,7 +226,14 @@ slk_status slk_fourier_params(const slk_plan_desc* desc, double radius, slk_plan
 
 /*
  * One-shot convenience: plan, sum and destroy in one call (same arguments and
- * errors as the three calls).
+ * errors as the three calls).  With 0 < desc->slice_batch < desc->P the P
+ * slices are processed in batches of at most slice_batch (Sec. 5.4, remark on
+ * memory and batching): batch b covers the slices [p0, p0 + P_b) of the draw
+ * (slice_offset + p0 onwards) or the rows p0 .. p0 + P_b - 1 of
+ * desc->directions, is planned and summed on its own, and the result is
+ * s = sum_b (P_b / P) s_b, accumulated in FP64 on the device; the device
+ * memory held at once is one batch's plan plus 12 M bytes (20 M for FP64).
+ * Each batch chooses its own window and Fourier parameters from its slices.
  */
 slk_status slk_kernel_sum(const slk_plan_desc* desc, const void* x, int64_t N, int64_t ldx, const void* w,
                           const void* y, int64_t M, int64_t ldy, void* s, void* stream);

@@ -1,4 +1,5 @@
 // C ABI: plans, sums and gradients (Algorithm 1 with the 1-D methods of Section 3).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -461,7 +462,7 @@ void create_impl(slk_plan plan, const void* x_user, int64_t ldx, const void* w_u
                                        cudaMemcpyDefault, st));
         SLK_CHECK_CUDA(cudaStreamSynchronize(st));  // the caller may free a host copy after we return
     } else {
-        launch_draw_directions(plan->xi64.get(), P, d, plan->desc.seed, st);
+        launch_draw_directions(plan->xi64.get(), P, d, plan->desc.seed, plan->desc.slice_offset, st);
     }
     plan->mu64.alloc(d, st);
     launch_sample_mean<T>(xv.ptr, N, d, xv.ld, plan->mu64.get(), st);
@@ -661,7 +662,17 @@ void validate_desc(const slk_plan_desc* desc) {
     if (desc->kernel != SLK_NEGDIST)
         SLK_REQUIRE(desc->param > 0.0 && std::isfinite(desc->param), "kernel parameter must be positive");
     SLK_REQUIRE(desc->tol >= 0.0 && desc->radius >= 0.0, "tol and radius must be >= 0");
+    SLK_REQUIRE(desc->slice_batch >= 0, "slice_batch must be >= 0");
+    SLK_REQUIRE(desc->slice_offset >= 0 && desc->slice_offset <= INT32_MAX - desc->P,
+                "slice_offset must be in [0, 2^31 - 1 - P]");
 }
+
+// slk_kernel_sum over slice batches (Sec. 5.4, remark on memory and batching): batch b plans
+// the slices [p0, p0 + P_b) on its own, sums into a device buffer, and adds (P_b / P) times that
+// into an FP64 accumulator; one batch's plan is alive at a time.
+template <class T>
+void batched_kernel_sum(const slk_plan_desc& desc, const void* x, int64_t N, int64_t ldx, const void* w,
+                        const void* y, int64_t M, int64_t ldy, void* s, cudaStream_t st);
 
 }  // namespace
 
@@ -892,6 +903,18 @@ slk_status slk_fourier_params(const slk_plan_desc* desc, double radius, slk_plan
 
 slk_status slk_kernel_sum(const slk_plan_desc* desc, const void* x, int64_t N, int64_t ldx, const void* w,
                           const void* y, int64_t M, int64_t ldy, void* s, void* stream) {
+    if (desc && desc->slice_batch > 0 && desc->slice_batch < desc->P) {
+        set_last_error("");
+        return guarded([&] {
+            validate_desc(desc);
+            SLK_REQUIRE(M >= 0, "M must be >= 0");
+            if (M == 0) return;
+            SLK_REQUIRE(y && s, "y and s must not be NULL");
+            cudaStream_t st = static_cast<cudaStream_t>(stream);
+            if (desc->precision == SLK_PREC_F64) batched_kernel_sum<double>(*desc, x, N, ldx, w, y, M, ldy, s, st);
+            else batched_kernel_sum<float>(*desc, x, N, ldx, w, y, M, ldy, s, st);
+        });
+    }
     slk_plan plan = nullptr;
     slk_status st = slk_plan_create(&plan, desc, x, N, ldx, w, stream);
     if (st != SLK_OK) return st;
@@ -907,6 +930,39 @@ slk_status slk_kernel_sum(const slk_plan_desc* desc, const void* x, int64_t N, i
 }
 
 }  // extern "C"
+
+namespace {
+
+template <class T>
+void batched_kernel_sum(const slk_plan_desc& desc, const void* x, int64_t N, int64_t ldx, const void* w,
+                        const void* y, int64_t M, int64_t ldy, void* s, cudaStream_t st) {
+    const int P = desc.P, B = desc.slice_batch, d = desc.d;
+    DevBuf<T> sb(static_cast<size_t>(M), st);
+    DevBuf<double> acc(static_cast<size_t>(M), st);
+    for (int p0 = 0; p0 < P; p0 += B) {
+        slk_plan_desc b = desc;
+        b.P = std::min(B, P - p0);
+        b.slice_batch = 0;
+        if (desc.directions) b.directions = desc.directions + static_cast<size_t>(p0) * d;
+        else b.slice_offset = desc.slice_offset + p0;
+        slk_plan plan = nullptr;
+        slk_status r = slk_plan_create(&plan, &b, x, N, ldx, w, st);
+        if (r != SLK_OK) throw Error{r, slk_last_error()};
+        r = slk_sum(plan, y, M, ldy, sb.get(), st);
+        if (r == SLK_OK) r = slk_plan_sync(plan);
+        std::string keep = slk_last_error();
+        slk_plan_destroy(plan);
+        if (r != SLK_OK) throw Error{r, keep};
+        launch_accumulate_scaled<T>(acc.get(), sb.get(), static_cast<double>(b.P) / P, M, p0 == 0, st);
+    }
+    T* out = is_device_pointer(s) ? static_cast<T*>(s) : sb.get();
+    launch_sum_parts<T>(acc.get(), 1, M, 1.0, out, st);
+    if (out != s)
+        SLK_CHECK_CUDA(cudaMemcpyAsync(s, out, sizeof(T) * static_cast<size_t>(M), cudaMemcpyDeviceToHost, st));
+    SLK_CHECK_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace
 
 // ------------------------------------------------------------ sums without device allocation
 //

@@ -30,11 +30,13 @@ __device__ inline double u01(uint32_t hi, uint32_t lo) {
     return (static_cast<double>(v >> 11) + 0.5) * 0x1.0p-53;
 }
 
-__global__ void k_draw_directions(double* xi, int P, int d, uint32_t k0, uint32_t k1) {
+// Row p of xi is row p0 + p of the seed's sequence: the counter holds the global slice index,
+// so plans over disjoint slice ranges reproduce the rows of one plan over all of them.
+__global__ void k_draw_directions(double* xi, int P, int d, uint32_t p0, uint32_t k0, uint32_t k1) {
     int p = blockIdx.y;
     int pairs = (d + 1) / 2;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < pairs; j += gridDim.x * blockDim.x) {
-        uint32_t c[4] = {static_cast<uint32_t>(j), static_cast<uint32_t>(p), 0x736c6b31u, 0u};
+        uint32_t c[4] = {static_cast<uint32_t>(j), p0 + static_cast<uint32_t>(p), 0x736c6b31u, 0u};
         philox4x32_10(c, k0, k1);
         double u1 = u01(c[0], c[1]), u2 = u01(c[2], c[3]);
         double r = sqrt(-2.0 * log(u1));
@@ -63,12 +65,13 @@ __global__ void k_normalize_rows(double* xi, int d) {
     for (int k = threadIdx.x; k < d; k += blockDim.x) row[k] *= inv;
 }
 
-void launch_draw_directions(double* xi, int P, int d, uint64_t seed, cudaStream_t st) {
+void launch_draw_directions(double* xi, int P, int d, uint64_t seed, int p0, cudaStream_t st) {
     int pairs = (d + 1) / 2;
     dim3 grid(static_cast<unsigned>(ceil_div(pairs, 256)), P);
     {
         SLK_TIMED("draw_directions", st);
-        k_draw_directions<<<grid, 256, 0, st>>>(xi, P, d, static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+        k_draw_directions<<<grid, 256, 0, st>>>(xi, P, d, static_cast<uint32_t>(p0), static_cast<uint32_t>(seed),
+                                                static_cast<uint32_t>(seed >> 32));
     }
     SLK_CHECK_LAUNCH();
     launch_normalize_rows(xi, P, d, st);
@@ -209,6 +212,30 @@ void launch_sum_parts(const double* part, int parts, int64_t n, double scale, T*
 
 template void launch_sum_parts<float>(const double*, int, int64_t, double, float*, cudaStream_t);
 template void launch_sum_parts<double>(const double*, int, int64_t, double, double*, cudaStream_t);
+// acc = (first ? 0 : acc) + a t: one batch's sums weighted by its share of the slices
+template <class T>
+__global__ void k_accumulate_scaled(double* __restrict__ acc, const T* __restrict__ t, double a, int64_t n,
+                                    int first) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const double v = a * static_cast<double>(t[i]);
+        acc[i] = first ? v : acc[i] + v;
+    }
+}
+
+template <class T>
+void launch_accumulate_scaled(double* acc, const T* t, double a, int64_t n, bool first, cudaStream_t st) {
+    if (n <= 0) return;
+    const int64_t blocks = ceil_div(n, 256);
+    SLK_TIMED("accumulate_scaled", st);
+    k_accumulate_scaled<T><<<static_cast<unsigned>(blocks < 8192 ? blocks : 8192), 256, 0, st>>>(acc, t, a, n,
+                                                                                                 first ? 1 : 0);
+    SLK_CHECK_LAUNCH();
+}
+
+template void launch_accumulate_scaled<float>(double*, const float*, double, int64_t, bool, cudaStream_t);
+template void launch_accumulate_scaled<double>(double*, const double*, double, int64_t, bool, cudaStream_t);
+
 __global__ void k_gather_rows(const float* __restrict__ x, int64_t N, int d, int64_t ldx, int64_t S,
                               float* __restrict__ out) {
     for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < S * d;

@@ -8,7 +8,8 @@ namespace slk {
 // ------------------------------------------------------------ k_util.cu
 // Draw P directions uniform on S^{d-1} (Algorithm 1, first step): Philox4x32-10
 // counter-based generator (Salmon et al. 2011), Box-Muller, row normalisation.
-void launch_draw_directions(double* xi, int P, int d, uint64_t seed, cudaStream_t st);
+// rows p0 .. p0 + P - 1 of the direction sequence of `seed` (Philox4x32-10, Box-Muller, normalised)
+void launch_draw_directions(double* xi, int P, int d, uint64_t seed, int p0, cudaStream_t st);
 // Row-normalise a P x d FP64 matrix in place.
 void launch_normalize_rows(double* xi, int P, int d, cudaStream_t st);
 // mu[k] = mean over up to 4096 evenly strided rows of x (the centre subtracted
@@ -74,6 +75,9 @@ void launch_umma_moments(const void* xa, int64_t n, const void* xib, int P, int 
 // s[i] = scale * sum_{r < parts} part[r * n + i] (fixed order).
 template <class T>
 void launch_sum_parts(const double* part, int parts, int64_t n, double scale, T* s, cudaStream_t st);
+// acc[i] = (first ? 0 : acc[i]) + a * t[i] in FP64 (the slice batches of a one-shot sum)
+template <class T>
+void launch_accumulate_scaled(double* acc, const T* t, double a, int64_t n, bool first, cudaStream_t st);
 // dst[c][r] = BF16(src[r][c]) (rows x cols FP32 in; cols x ld16(rows) out, zero padded).
 void launch_transpose_bf16(const float* src, int rows, int cols, void* dst, cudaStream_t st);
 // Backward product on tensor cores: gy[m][k] = scale * gs[m] * sum_p G[m][p] xi[p][k] with G (M x P)

@@ -40,7 +40,7 @@ class PlanDesc(ctypes.Structure):
                 ("d", ctypes.c_int32), ("P", ctypes.c_int32), ("n_coeff", ctypes.c_int32),
                 ("method", ctypes.c_int32), ("seed", ctypes.c_uint64), ("directions", ctypes.c_void_p),
                 ("tol", ctypes.c_double), ("radius", ctypes.c_double), ("slice_batch", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("slice_offset", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -150,43 +150,55 @@ class _Arr:
             self.rows = a.shape[0]
 
 
+def _plan_desc(kernel: str, param: float, d: int, P: int, precision: str, n_coeff: int = 0, method: str = "auto",
+               seed: int = 0, directions=None, tol: float = 0.0, radius: float = 0.0, slice_offset: int = 0,
+               slice_batch: int = 0):
+    """A filled PlanDesc and the FP64 copy of `directions` it points to (keep it alive)."""
+    desc = PlanDesc()
+    desc.kernel = KERNELS[kernel]
+    desc.precision = PRECISIONS[precision]
+    desc.param = float(param)
+    desc.d = int(d)
+    desc.P = int(P)
+    desc.n_coeff = int(n_coeff)
+    desc.method = METHODS[method]
+    desc.seed = int(seed)
+    dirs = None
+    if directions is not None:
+        if torch is not None and isinstance(directions, torch.Tensor):
+            dirs = directions.to(torch.float64).contiguous()
+            desc.directions = dirs.data_ptr()
+        else:
+            dirs = np.ascontiguousarray(np.asarray(directions, dtype=np.float64))
+            desc.directions = dirs.ctypes.data
+        if tuple(dirs.shape) != (int(P), int(d)):
+            raise ValueError("directions must be P x d")
+    desc.tol = float(tol)
+    desc.radius = float(radius)
+    desc.slice_offset = int(slice_offset)
+    desc.slice_batch = int(slice_batch)
+    return desc, dirs
+
+
 class Plan:
     """A sliced kernel-summation plan over the sources x (N x d) with weights w.
 
     kernel: "gaussian" (param = sigma), "laplacian" (param = alpha, F = exp(-alpha r))
     or "negdist" or "matern32" (param = beta).  precision: "f64", "f32", "bf16" or "f16x3".  directions: optional
-    P x d unit directions (FP64); otherwise the library draws them from ``seed``."""
+    P x d unit directions (FP64); otherwise the library draws rows slice_offset .. slice_offset + P - 1 of
+    the direction sequence of ``seed``."""
 
     def __init__(self, x, w, kernel: str, param: float = 0.0, P: int = 256, precision: str = "f32",
                  n_coeff: int = 0, method: str = "auto", seed: int = 0, directions=None, tol: float = 0.0,
-                 radius: float = 0.0):
+                 radius: float = 0.0, slice_offset: int = 0):
         lib = load()
         self.precision = precision
         self.dtype = _dtype_for(precision)
         xa = _Arr(x, self.dtype, 2)
         wa = _Arr(w, self.dtype, 1)
         d = int(x.shape[1])
-        desc = PlanDesc()
-        desc.kernel = KERNELS[kernel]
-        desc.precision = PRECISIONS[precision]
-        desc.param = float(param)
-        desc.d = d
-        desc.P = int(P)
-        desc.n_coeff = int(n_coeff)
-        desc.method = METHODS[method]
-        desc.seed = int(seed)
-        self._dirs = None
-        if directions is not None:
-            if torch is not None and isinstance(directions, torch.Tensor):
-                self._dirs = directions.to(torch.float64).contiguous()
-                desc.directions = self._dirs.data_ptr()
-            else:
-                self._dirs = np.ascontiguousarray(np.asarray(directions, dtype=np.float64))
-                desc.directions = self._dirs.ctypes.data
-            if tuple(self._dirs.shape) != (P, d):
-                raise ValueError("directions must be P x d")
-        desc.tol = float(tol)
-        desc.radius = float(radius)
+        desc, self._dirs = _plan_desc(kernel, param, d, P, precision, n_coeff, method, seed, directions, tol,
+                                      radius, slice_offset)
         self.kernel, self.param, self.d, self.P = kernel, param, d, int(P)
         self.N = int(x.shape[0])
         self._desc = desc
@@ -310,13 +322,26 @@ def timing_read() -> dict:
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(n.value, cap))}
 
 
-def kernel_sum(x, w, y, kernel: str, param: float = 0.0, P: int = 256, precision: str = "f32", **kw):
-    """One-shot s = sum_n w_n F(|x_n - y_m|) via slicing (plan, sum, destroy)."""
-    plan = Plan(x, w, kernel, param, P, precision, **kw)
-    try:
-        return plan.sum(y)
-    finally:
-        plan.close()
+def kernel_sum(x, w, y, kernel: str, param: float = 0.0, P: int = 256, precision: str = "f32",
+               slice_batch: int = 0, out=None, **kw):
+    """One-shot s = sum_n w_n F(|x_n - y_m|) via slicing (slk_kernel_sum: plan, sum, destroy).
+
+    slice_batch: 0 < B < P processes the slices in batches of at most B, one batch's plan in
+    device memory at a time; the other keywords are those of `Plan`."""
+    lib = load()
+    dtype = _dtype_for(precision)
+    xa, wa, ya = _Arr(x, dtype, 2), _Arr(w, dtype, 1), _Arr(y, dtype, 2)
+    desc, dirs = _plan_desc(kernel, param, int(x.shape[1]), P, precision, slice_batch=slice_batch, **kw)
+    if out is None:
+        if torch is not None and isinstance(y, torch.Tensor):
+            out = torch.empty(ya.rows, dtype=ya.keep.dtype, device=ya.keep.device)
+        else:
+            out = np.empty(ya.rows, dtype=dtype)
+    oa = _Arr(out, dtype, 1)
+    _check(lib.slk_kernel_sum(ctypes.byref(desc), xa.ptr, xa.rows, xa.ld, wa.ptr, ya.ptr, ya.rows, ya.ld, oa.ptr,
+                              _stream_of(x)))
+    del dirs
+    return out
 
 
 if torch is not None:

@@ -57,3 +57,22 @@ def test_single_process_is_unchanged():
     bench = _bench()
     assert bench.max_over_ranks(7.5) == 7.5
     assert bench.job_rate(2.0e9, 1, 10.0) == pytest.approx(2.0e11)
+
+
+def test_roofline_amount_covers_every_launch_of_a_step():
+    """The per-launch amount is one step's work over the step's launches: three centring
+    launches (sources, targets, the 4096-row radius sample) share N + M + 4096 rows."""
+    from types import SimpleNamespace
+    bench = _bench()
+    wl = SimpleNamespace(name="gauss_d784", N=10 ** 6, M=10 ** 6, d=784, P=512)
+    kernels = {"center_cast": (3, 1.0), "gather_rows": (1, 0.01), "umma_cheb_moments": (1, 1.0)}
+    amount, unit, bound = bench.algorithmic(wl, {}, "bf16", "center_cast", 3, kernels)
+    assert (unit, bound) == ("byte", "hbm")
+    assert amount * 3 == pytest.approx((2 * 10 ** 6 + 4096) * (4 * 784 + 2 * 784))
+    amount, unit, bound = bench.algorithmic(wl, {}, "bf16", "umma_cheb_moments", 1, kernels)
+    assert (unit, bound) == ("flop", "tensor") and amount == pytest.approx(2.0 * 10 ** 6 * 784 * 512)
+    # a rank of a slice-sharded sum projects onto its own slices only
+    amount, _, _ = bench.algorithmic(wl, {}, "bf16", "umma_cheb_moments", 1, kernels, P=256)
+    assert amount == pytest.approx(2.0 * 10 ** 6 * 784 * 256)
+    traffic = bench.measured_traffic(wl, "center_cast", 3, kernels)
+    assert traffic * 3 == pytest.approx(bench.NCU_TRAFFIC_PER_POINT[("gauss_d784", "center_cast")] * (2 * 10 ** 6 + 4096))
