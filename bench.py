@@ -110,24 +110,30 @@ def plan_kwargs(wl, args):
                 n_coeff=wl.n_coeff, method=args.method or wl.method, directions=wl.xi)
 
 
-# DRAM read + write per point of one launch, from ncu captures of the d = 784, P = 512 BF16
-# workload at n = 2e5 points (profiles/umma_cheb_target_and_center_cast_d784_n200k.md,
-# profiles/umma_cheb_moments_d784_n200k.md); the
-# traffic of these kernels grows in proportion to the points.  An entry is valid only for the
+# DRAM read + write per point of one launch, from the ncu captures (summarised under
+# profiles/) of the d = 784, P = 512 BF16 workload at n = 2e5 points: the centring cast and
+# the target kernel that reads the FP32 targets itself; the traffic of these kernels grows
+# in proportion to the points.  An entry is valid only for the
 # kernel as captured and is removed when that kernel changes.
 NCU_TRAFFIC_PER_POINT = {("gauss_d784", "center_cast"): (627.233024e6 + 281.766400e6) / 2e5,
-                         ("gauss_d784", "umma_cheb_target"): (314.612992e6 + 7.674368e6) / 2e5,
-                         ("gauss_d784", "umma_cheb_moments"): (315.320832e6 + 3.245568e6) / 2e5}
+                         ("gauss_d784", "umma_cheb_target"): (628.103936e6 + 8.866048e6) / 2e5}
+
+
+def f32_direct(wl, kernels):
+    """The fused Chebyshev path (the one that gathers a radius sample, `gather_rows`) hands
+    contiguous FP32 target rows with d a multiple of four straight to its tensor-core target
+    kernel, which centres and rounds them in shared memory; the sources (and otherwise the
+    targets too) go through a centring cast first."""
+    return "gather_rows" in kernels and wl.d % 4 == 0
 
 
 def step_points(wl, kernel_name, kernels):
     """Rows that one step's launches of a kernel process together.  The fused Chebyshev path
-    (the one that gathers a radius sample, `gather_rows`) also centres, casts and projects that
-    sample of min(4096, N) source rows; source-side kernels see the N sources, target-side
-    kernels the M targets, the rest both."""
+    also centres, casts and projects a sample of min(4096, N) source rows; source-side
+    kernels see the N sources, target-side kernels the M targets, the rest both."""
     S = min(4096, wl.N) if "gather_rows" in kernels else 0
     if kernel_name.startswith("center_cast"):
-        return wl.N + wl.M + S
+        return wl.N + S if f32_direct(wl, kernels) else wl.N + wl.M + S
     if kernel_name.startswith(("umma_cheb_moments", "cheb_moments", "ndft_source", "spread")):
         return wl.N
     if kernel_name.startswith(("umma_cheb_target", "umma_grad", "cheb_target", "ndft_target", "nfft_target",
@@ -146,7 +152,7 @@ def measured_traffic(wl, kernel_name, launches_per_step, kernels):
     return NCU_TRAFFIC_PER_POINT[key] * step_points(wl, kernel_name, kernels) / max(1.0, launches_per_step)
 
 
-def algorithmic(wl, info, precision, kernel_name, launches_per_step, kernels, P=None, grad=False):
+def algorithmic(wl, info, precision, kernel_name, launches_per_step, kernels, P=None, grad=False, peaks=None):
     """(algorithmic amount of an average launch, unit, bound) of a library kernel: the amount
     of one step's launches (their points from `step_points`) over the launches per step.
 
@@ -158,10 +164,22 @@ def algorithmic(wl, info, precision, kernel_name, launches_per_step, kernels, P=
     per slice-point (FP32 ALU).  Centring cast: 4 d bytes read + 2 ld16 (x2 for the
     hi/lo split) written per point, plus, with the gradient, the same for the M x P
     per-slice derivatives it casts.  Other kernels: the 4-byte projections they read.
+    The fused Chebyshev target kernel that reads the FP32 rows itself moves 4 d bytes per
+    target plus 16 bytes per 256-slice tile of FP64 partial sums beside its 2 d P flop; at
+    d = 784, P = 512 the two minimum times are within 5% of each other, and the bound
+    reported is the one with the longer minimum time under `peaks` (HBM copy bandwidth,
+    sustained BF16).
     P: the slices one launch covers (this rank's share when the slices are sharded)."""
     P = wl.P if P is None else P
     pts = step_points(wl, kernel_name, kernels) / max(1.0, launches_per_step)
     per = 1.0 / max(1.0, launches_per_step)
+    if kernel_name.startswith("umma_cheb_target") and f32_direct(wl, kernels):
+        flops = 2.0 * pts * wl.d * P
+        nbytes = pts * (4.0 * wl.d + 16.0 * ((P + 255) // 256))
+        pk = peaks or {}
+        t_hbm = nbytes / (pk.get("hbm_gbs", 6689.8) * 1e9)
+        t_tc = flops / (pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1772.1)) * 1e12)
+        return (nbytes, "byte", "hbm") if t_hbm >= t_tc else (flops, "flop", "tensor")
     if kernel_name.startswith(("gemm", "umma")):
         bound = "tensor" if kernel_name.startswith("umma") else "alu"
         return 2.0 * pts * wl.d * P, "flop", bound
@@ -289,6 +307,10 @@ def run_ours(args):
     y = torch.from_numpy(wl.y).to(dev)
     w = torch.from_numpy(wl.w).to(dev)
     s = torch.empty(wl.M, dtype=x.dtype, device=dev)
+    # the directions are an input like x, y and w: resident on the device for the timed steps
+    # (the end-to-end run below passes the host copy)
+    kw_host = kw
+    kw = dict(kw, directions=torch.from_numpy(wl.xi).to(dev))
     stream = torch.cuda.current_stream(dev)
 
     gy = torch.empty_like(y) if args.grad else None
@@ -366,7 +388,8 @@ def run_ours(args):
     if top:
         name, (n_launch, tot_ms) = top
         per_step = n_launch / args.steps
-        amount, unit, bound = algorithmic(wl, info, precision, name, per_step, kernels, P=P_local, grad=args.grad)
+        amount, unit, bound = algorithmic(wl, info, precision, name, per_step, kernels, P=P_local, grad=args.grad,
+                                          peaks=peaks)
         avg_s = tot_ms / n_launch * 1e-3
         if bound == "tensor":
             # a kernel timed inside a long step: the sustained dense BF16 figure (FP16 runs at the same rate)
@@ -401,13 +424,13 @@ def run_ours(args):
 
         def host_step():
             if sharded:
-                sp = ShardedPlan(xh, wh, **kw)
+                sp = ShardedPlan(xh, wh, **kw_host)
                 sh.copy_(sp.sum(yh))
                 if args.grad:
                     gh.copy_(sp.grad(yh))
                 sp.close()
                 return
-            plan = slk.Plan(xh, wh, **kw)
+            plan = slk.Plan(xh, wh, **kw_host)
             plan.sum(yh, out=sh, sync=True)
             if args.grad:
                 plan.grad(yh, out=gh, sync=True)

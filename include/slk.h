@@ -212,7 +212,11 @@ slk_status slk_plan_get_directions(slk_plan plan, double* xi_host);
 /* Report the parameters the plan chose.  Synchronises the plan's stream. */
 slk_status slk_plan_get_info(slk_plan plan, slk_plan_info* info);
 
-/* Release the plan and its device memory (waits for its pending work). */
+/* Release the plan.  Does not wait: its device memory is freed in stream order
+ * after the plan's last call (on that call's stream), so the caller must not
+ * use the plan's results on another stream without ordering that stream after
+ * it.  A device-side status of the last call that was not yet collected (by
+ * slk_plan_sync or a later call) is dropped. */
 slk_status slk_plan_destroy(slk_plan plan);
 
 /*

@@ -73,6 +73,36 @@ using namespace slk;
 
 // ------------------------------------------------------------ plan object
 
+// Pinned host words that receive the plans' deferred device status.  They are handed out
+// from blocks of 256 (never returned to the driver) and come back through a host callback
+// queued on the plan's last stream, so a word is reused only after the last copy into it
+// has landed; creating and destroying a plan thus neither allocates nor frees pinned
+// memory, which would synchronise the device.
+struct PinnedWords {
+    std::mutex mu;
+    std::vector<unsigned*> free;
+    unsigned* get() {
+        std::lock_guard<std::mutex> g(mu);
+        if (free.empty()) {
+            unsigned* blk = nullptr;
+            SLK_CHECK_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&blk), 256 * sizeof(unsigned), cudaHostAllocPortable));
+            for (int i = 0; i < 256; ++i) free.push_back(blk + i);
+        }
+        unsigned* p = free.back();
+        free.pop_back();
+        return p;
+    }
+    void put(unsigned* p) {
+        std::lock_guard<std::mutex> g(mu);
+        free.push_back(p);
+    }
+};
+PinnedWords& pinned_words() {
+    static PinnedWords* w = new PinnedWords();  // outlives every plan (host callbacks may run late)
+    return *w;
+}
+void CUDART_CB return_pinned_word(void* p) { pinned_words().put(static_cast<unsigned*>(p)); }
+
 struct slk_plan_s {
     slk_plan_desc desc{};
     int device = 0;
@@ -118,12 +148,19 @@ struct slk_plan_s {
     cudaEvent_t done = nullptr;
     bool pending = false;
 
+    // Releases in stream order after the last call (stream): every device buffer is freed
+    // on that stream, the event is destroyed (its resources go once it completes) and the
+    // status word returns to the pool through a host callback on the same stream.
     ~slk_plan_s() {
-        if (done) {
-            cudaEventSynchronize(done);
-            cudaEventDestroy(done);
-        }
-        if (err_host) cudaFreeHost(err_host);
+        for (DevBuf<double>* b : {&xi64, &mu64, &coef, &mult, &chebM}) b->stream = stream;
+        for (DevBuf<float>* b : {&xi32, &mu32, &kmin, &kscale}) b->stream = stream;
+        for (DevBuf<unsigned char>* b : {&xib, &xib_lo, &xit16, &beta, &mono, &cw, &cw0, &hgrid, &kw}) b->stream = stream;
+        AB.stream = stream;
+        tab.stream = stream;
+        err_dev.stream = stream;
+        if (done) cudaEventDestroy(done);
+        if (err_host && cudaLaunchHostFunc(stream, return_pinned_word, err_host) != cudaSuccess)
+            cudaGetLastError();  // the word is then not reused
     }
     int64_t device_bytes() const {
         return static_cast<int64_t>(xi64.bytes() + xi32.bytes() + mu64.bytes() + mu32.bytes() + xib.bytes() +
@@ -224,8 +261,14 @@ struct InView {
             ld = ld_user;
         } else {
             staged.alloc(static_cast<size_t>(n) * d, st);
-            SLK_CHECK_CUDA(cudaMemcpy2DAsync(staged.get(), sizeof(T) * d, user, sizeof(T) * ld_user, sizeof(T) * d, n,
-                                             cudaMemcpyHostToDevice, st));
+            // contiguous rows: one linear copy (a pitched copy of n rows runs far below the
+            // link's bandwidth)
+            if (ld_user == d)
+                SLK_CHECK_CUDA(cudaMemcpyAsync(staged.get(), user, sizeof(T) * static_cast<size_t>(n) * d,
+                                               cudaMemcpyHostToDevice, st));
+            else
+                SLK_CHECK_CUDA(cudaMemcpy2DAsync(staged.get(), sizeof(T) * d, user, sizeof(T) * ld_user,
+                                                 sizeof(T) * d, n, cudaMemcpyHostToDevice, st));
             ptr = staged.get();
             ld = d;
         }
@@ -407,22 +450,23 @@ bool fused_cheb_source(slk_plan plan, const float* x, int64_t ldx, const float* 
         launch_umma_moments(xa, rows, plan->xib.get(), P, d, w, fh.cheb_qp, R, mom.get(), mx.get(),
                             plan->err_dev.get(), s);
     });
-    float rx = 0.0f;
-    SLK_CHECK_CUDA(cudaMemcpyAsync(&rx, mx.get(), sizeof(float), cudaMemcpyDeviceToHost, st));
-    SLK_CHECK_CUDA(cudaStreamSynchronize(st));
-    if (!std::isfinite(rx)) fail(SLK_ERR_INVALID, "non-finite projected sources");
-    if (rx > R) {
-        if (user_radius)
-            fail(SLK_ERR_INVALID, "radius %.6g is smaller than the largest projected source %.6g", R, rx);
-        return false;
-    }
+    // the reduction runs before the range check, so one wait covers both; its output is
+    // discarded when a source lies outside the radius
     DevBuf<unsigned> bad(1, st);
     SLK_CHECK_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(unsigned), st));
     launch_cheb_reduce_f64(mom.get(), static_cast<int>(nchunk), P, plan->fd, plan->chebM.get(),
                            reinterpret_cast<float*>(plan->beta.get()),
                            fh.cheb_qp <= 16 ? reinterpret_cast<float*>(plan->mono.get()) : nullptr, bad.get(),
                            mono_ratio_of(plan), st);
+    float rx = 0.0f;
+    SLK_CHECK_CUDA(cudaMemcpyAsync(&rx, mx.get(), sizeof(float), cudaMemcpyDeviceToHost, st));
     cheb_finish(plan, bad.get(), st);
+    if (!std::isfinite(rx)) fail(SLK_ERR_INVALID, "non-finite projected sources");
+    if (rx > R) {
+        if (user_radius)
+            fail(SLK_ERR_INVALID, "radius %.6g is smaller than the largest projected source %.6g", R, rx);
+        return false;
+    }
     plan->fourier = true;
     return true;
 }
@@ -460,7 +504,8 @@ void create_impl(slk_plan plan, const void* x_user, int64_t ldx, const void* w_u
     if (plan->desc.directions) {
         SLK_CHECK_CUDA(cudaMemcpyAsync(plan->xi64.get(), plan->desc.directions, sizeof(double) * P * d,
                                        cudaMemcpyDefault, st));
-        SLK_CHECK_CUDA(cudaStreamSynchronize(st));  // the caller may free a host copy after we return
+        // the caller may free a host copy after we return; a device copy is ordered on st
+        if (!is_device_pointer(plan->desc.directions)) SLK_CHECK_CUDA(cudaStreamSynchronize(st));
     } else {
         launch_draw_directions(plan->xi64.get(), P, d, plan->desc.seed, plan->desc.slice_offset, st);
     }
@@ -525,11 +570,18 @@ bool sum_fused_cheb(slk_plan plan, const T* y, int64_t M, int64_t ldy, void* s_u
         const int parts = static_cast<int>(umma_cheb_parts(plan->P));
         DevBuf<double> part(static_cast<size_t>(parts) * M, st);
         const void* coef = plan->fd.horner ? plan->fd.mono : plan->beta.get();
-        cast_and_run(plan, y, M, ldy, st, [&](const void* ya, const void*, int64_t r0, int64_t rows, cudaStream_t s) {
-            launch_umma_cheb_target(ya, rows, plan->xib.get(), plan->P, plan->d, static_cast<const float*>(coef),
-                                    plan->fh.cheb_qp, plan->fd.horner, plan->R, part.get() + r0, M,
-                                    plan->err_dev.get(), s);
-        });
+        if (umma_f32_operand_ok(y, ldy))  // aligned FP32 rows: centred and rounded in the kernel
+            launch_umma_cheb_target_f32(y, ldy, plan->mu32.get(), M, plan->xib.get(), plan->P, plan->d,
+                                        static_cast<const float*>(coef), plan->fh.cheb_qp, plan->fd.horner, plan->R,
+                                        part.get(), M, plan->err_dev.get(), st);
+        else
+            cast_and_run(plan, y, M, ldy, st,
+                         [&](const void* ya, const void*, int64_t r0, int64_t rows, cudaStream_t s) {
+                             launch_umma_cheb_target(ya, rows, plan->xib.get(), plan->P, plan->d,
+                                                     static_cast<const float*>(coef), plan->fh.cheb_qp,
+                                                     plan->fd.horner, plan->R, part.get() + r0, M,
+                                                     plan->err_dev.get(), s);
+                         });
         if (is_device_pointer(s_user)) {
             launch_sum_parts<T>(part.get(), parts, M, 1.0 / plan->P, static_cast<T*>(s_user), st);
         } else {
@@ -722,7 +774,7 @@ slk_status slk_plan_create(slk_plan* out, const slk_plan_desc* desc, const void*
         plan->stream = st;
         plan->err_dev.alloc(1, st);
         SLK_CHECK_CUDA(cudaMemsetAsync(plan->err_dev.get(), 0, sizeof(unsigned), st));
-        SLK_CHECK_CUDA(cudaMallocHost(&plan->err_host, sizeof(unsigned)));
+        plan->err_host = pinned_words().get();
         *plan->err_host = 0;
         SLK_CHECK_CUDA(cudaEventCreateWithFlags(&plan->done, cudaEventDisableTiming));
         if (plan->f64) create_impl<double>(plan.get(), x, ldx, w, st);
@@ -864,8 +916,7 @@ slk_status slk_plan_destroy(slk_plan plan) {
     set_last_error("");
     return guarded([&] {
         if (!plan) return;
-        cudaStreamSynchronize(plan->stream);
-        delete plan;
+        delete plan;  // stream-ordered release after the plan's last call (no wait)
     });
 }
 

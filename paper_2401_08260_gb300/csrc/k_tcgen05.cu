@@ -10,6 +10,14 @@
 // with tcgen05.ld and store Z slice-major (coalesced along points), keeping
 // the largest |z| on the way.
 //
+// The fused Chebyshev target kernel also comes in a variant that reads the
+// targets as FP32 rows straight from the caller's array: TMA brings each
+// 64-column stage in as two 32-column halves, three converter warps centre and
+// round them to BF16 in shared memory, in place, in the swizzled layout the
+// tensor core reads, and only then release the stage to the MMA issuer.  This
+// removes the separate centring pass over the targets (an FP32 read and a BF16
+// write and re-read of every target) and leaves bit-identical operands.
+//
 // The FP16 "x3" variant (k_umma_project_x3) splits both operands into a high
 // and a scaled low FP16 part (a = a_hi + 2^-11 a_lo') and forms
 // a_hi b_hi + 2^-11 (a_hi b_lo' + a_lo' b_hi) (error ~ 2^-22 relative per
@@ -73,6 +81,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
             smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
         : "memory");
+}
+
+// bring a tile of the tensor into L2 only (no shared memory, no barrier)
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int c0, int c1) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1)
+                 : "memory");
 }
 
 // UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
@@ -166,9 +181,22 @@ struct Smem {
     // follows the stage buffers (each stage: A tile then B tile, 1024-byte aligned)
     uint64_t full[STAGES_1];
     uint64_t empty[STAGES_1];
+    uint64_t raw_full[STAGES_1];  // FP32-input variant: the TMA bytes of a stage have landed
     uint64_t acc_full[2];
     uint64_t acc_empty[2];
     uint32_t tmem_base;
+};
+
+// Stage geometry of the persistent projection.  CVT (target side only): the targets
+// arrive as FP32 rows (two 32-column halves of 128 bytes per row, unswizzled) and are
+// centred and rounded to BF16 in shared memory, in place over the first half, by the
+// converter warps; three stages of 64 KB.
+template <bool CVT>
+struct Geo {
+    static constexpr int A_BYTES = CVT ? BM * BK * 4 : BM * BK * 2;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int STAGES = CVT ? 3 : STAGES_1;
 };
 
 // BF16 projection, persistent: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
@@ -248,6 +276,8 @@ struct ChebEpi {
     const float* w;
     int npts;
     double* mom;
+    // FP32-target variant: the centre subtracted from the targets (d values)
+    const float* mu;
 };
 
 // Moments of one slice over a 32-point accumulator chunk: z[j] for the chunk's points,
@@ -287,12 +317,14 @@ __device__ __forceinline__ void two_sum_into(float& hi, float& lo, float x) {
 // cluster instead of once per CTA.  A stage is refilled only after both CTAs' MMAs have
 // released it (the MMA commit arrives on the empty barriers of both CTAs).
 // Work items: item -> slice tile (item % col_tiles), point blocks (item / col_tiles) * CL + rank.
-template <int EPI, int CL>
+template <int EPI, int CL, bool CVT>
 __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256, 1)
     k_umma_project(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int n, int P,
                    int d, int col_tiles, int tiles, float* __restrict__ Z, int64_t ldz, float* __restrict__ absmax,
                    unsigned* __restrict__ err, const float* __restrict__ rs, float scale, ChebEpi ce) {
     static_assert(CL == 1 || CL == 2, "cluster of one or two CTAs");
+    static_assert(!CVT || (EPI == EPI_CHEB && CL == 2), "FP32 targets: fused target epilogue, CTA pairs");
+    using G = Geo<CVT>;
     constexpr bool ROWMAJOR = EPI == EPI_ROW;
     const int rank = CL > 1 ? static_cast<int>(blockIdx.x % CL) : 0;
     int unit = static_cast<int>(blockIdx.x / CL), nunits = static_cast<int>(gridDim.x / CL);
@@ -312,11 +344,11 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256,
     };
     auto col_of = [&](int item) { return EPI == EPI_MOM ? item * BN : (item % col_tiles) * BN; };
     constexpr int EPI_WARPS = EPI == EPI_CHEB || EPI == EPI_MOM ? 8 : 4;
-    constexpr int STAGES = STAGES_1;
+    constexpr int STAGES = G::STAGES;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
-    constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    constexpr int A_BYTES = G::A_BYTES, B_BYTES = G::B_BYTES;
+    constexpr int STAGE_BYTES = G::STAGE_BYTES;
     Smem* sm = reinterpret_cast<Smem*>(base + STAGES * STAGE_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kblocks = (d + BK - 1) / BK;
@@ -324,8 +356,9 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256,
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&sm->full[s], 1);
+            mbar_init(&sm->full[s], CVT ? 96 : 1);  // CVT: one arrival per converter thread
             mbar_init(&sm->empty[s], CL);  // one MMA commit per CTA of the cluster
+            mbar_init(&sm->raw_full[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sm->acc_full[b], 1);
@@ -355,7 +388,7 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256,
     if (CL > 1) cluster_sync();
     const uint32_t tmem = sm->tmem_base;
 
-    if (warp == 0 && lane == 0) {
+    if (!CVT && warp == 0 && lane == 0) {
         // ---------------- TMA producer: one ring across all tiles of this CTA
         int g = 0;
         bool ok = true;
@@ -388,7 +421,7 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256,
                     atomicOr(err, 8u);
                     break;
                 }
-    } else if (warp == 1 && lane == 0) {
+    } else if (!CVT && warp == 1 && lane == 0) {
         // ---------------- MMA issuer
         const uint32_t idesc = instr_desc(1u, BM, BN);
         int g = 0, local = 0;
@@ -420,6 +453,133 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256,
                 else umma_commit_mc(&sm->empty[s], static_cast<uint16_t>(0x3));
             }
             umma_commit(&sm->acc_full[b]);
+        }
+    } else if (CVT && warp == 0) {
+        // ---------------- control of the FP32-target variant (one thread): TMA loads, L2
+        // prefetches and MMA issue in one loop over this CTA's stages g = (tile, k block).
+        // Stage g + STAGES - 1 is loaded right after the MMAs of stage g are issued (its
+        // buffer is the one stage g - 1 used, released once those MMAs, issued one step
+        // earlier, complete); the points of stage g + PF are prefetched into L2 so that the
+        // loads find them there.
+        if (lane == 0) {
+            constexpr int PF = 8;
+            int ntile = 0;
+            for (int t = unit; t < tiles; t += nunits) ++ntile;
+            const int total = ntile * kblocks;
+            auto issue = [&](int gg) {
+                const int tile = unit + (gg / kblocks) * nunits, kb = gg % kblocks, s = gg % STAGES;
+                const int r0 = row_of(tile), c0 = col_of(tile);
+                unsigned char* st = base + s * STAGE_BYTES;
+                uint64_t* tb = &sm->raw_full[s];
+                mbar_expect_tx(tb, STAGE_BYTES);
+                // the two 32-column halves of this CTA's FP32 targets, and its half of the
+                // directions delivered to both CTAs
+                tma_load_2d(st, &map_a, tb, kb * BK, r0);
+                tma_load_2d(st + BM * 128, &map_a, tb, kb * BK + 32, r0);
+                tma_load_2d_mc(st + A_BYTES + rank * (B_BYTES / 2), &map_b, tb, kb * BK, c0 + rank * (BN / 2),
+                               static_cast<uint16_t>(0x3));
+            };
+            auto prefetch = [&](int gg) {
+                const int tile = unit + (gg / kblocks) * nunits, kb = gg % kblocks;
+                tma_prefetch_2d(&map_a, kb * BK, row_of(tile));
+                tma_prefetch_2d(&map_a, kb * BK + 32, row_of(tile));
+            };
+            const uint32_t idesc = instr_desc(1u, BM, BN);
+            for (int gg = 0; gg < total && gg < PF; ++gg) prefetch(gg);
+            for (int gg = 0; gg < total && gg < STAGES - 1; ++gg) issue(gg);
+            bool ok = true;
+            for (int g = 0; g < total; ++g) {
+                const int kb = g % kblocks, local = g / kblocks, b = local & 1, s = g % STAGES;
+                if (kb == 0 && local >= 2 && !mbar_wait(&sm->acc_empty[b], ((local >> 1) - 1) & 1)) {
+                    atomicOr(err, 16u);
+                    ok = false;
+                    break;
+                }
+                if (!mbar_wait(&sm->full[s], (g / STAGES) & 1)) {
+                    atomicOr(err, 16u);
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                unsigned char* st = base + s * STAGE_BYTES;
+#pragma unroll
+                for (int k = 0; k < BK / 16; ++k)
+                    umma_f16(tmem + b * BN, smem_desc(st + k * 32), smem_desc(st + A_BYTES + k * 32), idesc,
+                             (kb > 0 || k > 0) ? 1u : 0u);
+                umma_commit_mc(&sm->empty[s], static_cast<uint16_t>(0x3));
+                if (kb == kblocks - 1) umma_commit(&sm->acc_full[b]);
+                const int gn = g + STAGES - 1;
+                if (gn < total) {
+                    if (gn >= STAGES && !mbar_wait(&sm->empty[gn % STAGES], ((gn / STAGES) - 1) & 1)) {
+                        atomicOr(err, 8u);
+                        ok = false;
+                        break;
+                    }
+                    issue(gn);
+                }
+                if (g + PF < total) prefetch(g + PF);
+            }
+            // every stage filled released by both MMAs before exit (no commit of the peer in flight)
+            if (ok)
+                for (int j = total > STAGES ? total - STAGES : 0; j < total; ++j)
+                    if (!mbar_wait(&sm->empty[j % STAGES], (j / STAGES) & 1)) {
+                        atomicOr(err, 8u);
+                        break;
+                    }
+        }
+    } else if (CVT && warp <= 3) {
+        // ---------------- converters (warps 1-3): FP32 targets -> centred BF16 operand, in place
+        // Lane l takes columns 4j..4j+3 (j = l % 16) of one row of a pair (l / 16): it reads
+        // them from the first (j < 8) or second 32-column half and writes their BF16 values,
+        // x - mu rounded to nearest (the same arithmetic as the separate centring cast), to
+        // the row's 128-byte line with the 128-byte swizzle (16-byte chunk c at c ^ (row % 8)).
+        // A row's BF16 line is its own line of the first half, so each row is converted by
+        // one warp: all of a batch's loads precede its stores (__syncwarp), and rows beyond
+        // the targets are written as zeros.  Batches of 16 rows go round the three warps.
+        constexpr int HALF = BM * 128, NB = BM / 16;
+        const int j = lane & 15, rr = lane >> 4, cw = warp - 1;
+        const int npts = n;
+        int g = 0;
+        bool ok = true;
+        for (int tile = unit; tile < tiles && ok; tile += nunits) {
+            const int p0 = row_of(tile);
+            for (int kb = 0; kb < kblocks; ++kb, ++g) {
+                const int s = g % STAGES;
+                // every lane waits (and so observes the TMA bytes); the vote keeps the warp together
+                const bool got = mbar_wait(&sm->raw_full[s], (g / STAGES) & 1);
+                if (!__all_sync(0xffffffffu, got)) {
+                    if (lane == 0) atomicOr(err, 8u);
+                    ok = false;
+                    break;
+                }
+                unsigned char* cv = base + s * STAGE_BYTES;
+                const unsigned char* src = cv + (j >> 3) * HALF + (j & 7) * 16;
+                float m[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int k = kb * BK + 4 * j + e;
+                    m[e] = k < d ? __ldg(ce.mu + k) : 0.0f;
+                }
+                for (int bi = cw; bi < NB; bi += 3) {
+                    const int r0 = bi * 16;
+                    float4 v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[u] = *reinterpret_cast<const float4*>(src + (r0 + 2 * u + rr) * 128);
+                    __syncwarp();
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int r = r0 + 2 * u + rr;
+                        union { __nv_bfloat162 h[2]; uint2 u2; } pk;
+                        pk.h[0] = __floats2bfloat162_rn(v[u].x - m[0], v[u].y - m[1]);
+                        pk.h[1] = __floats2bfloat162_rn(v[u].z - m[2], v[u].w - m[3]);
+                        if (p0 + r >= npts) pk.u2 = make_uint2(0u, 0u);
+                        *reinterpret_cast<uint2*>(cv + r * 128 + (((j >> 1) ^ (r & 7)) << 4) + ((j & 1) << 3)) = pk.u2;
+                    }
+                }
+                // generic-proxy writes, read next by the tensor core (async proxy)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&sm->full[s]);
+            }
         }
     } else if (warp >= 4 && EPI == EPI_MOM) {
         // ---------------- fused source side: moments of one slice per thread
@@ -834,17 +994,34 @@ CUtensorMap make_map(const void* ptr, CUtensorMapDataType dt, int64_t rows, int 
     return m;
 }
 
+// 2-D tensor map over row-major [rows][ld] FP32 points, box = 32 columns (128 bytes) x
+// box_rows, no swizzle: the FP32 input of the converting projection (two boxes per
+// 64-column stage); columns >= cols and rows >= rows read as zeros.
+CUtensorMap make_map_f32(const float* ptr, int64_t rows, int cols, int64_t ld, int box_rows) {
+    CUtensorMap m;
+    cuuint64_t gdim[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+    cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ld * 4)};
+    cuuint32_t box[2] = {32u, static_cast<cuuint32_t>(box_rows)};
+    cuuint32_t estride[2] = {1, 1};
+    CUresult r = get_encode()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), gdim, gstride, box,
+                              estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) fail(SLK_ERR_CUDA, "cuTensorMapEncodeTiled (FP32) failed (%d)", static_cast<int>(r));
+    return m;
+}
+
+template <bool CVT>
 size_t umma_smem_bytes(size_t extra = 0) {
-    constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
-    return 1024 + STAGES_1 * (A_BYTES + B_BYTES) + ((sizeof(Smem) + 15) & ~size_t(15)) + extra;
+    using G = Geo<CVT>;
+    return 1024 + static_cast<size_t>(G::STAGES) * G::STAGE_BYTES + ((sizeof(Smem) + 15) & ~size_t(15)) + extra;
 }
 // room for beta (padded P x q floats) in the fused kernel; kept a few KB under the SM's
 // capacity so that small kernels of another stream can share the SM
 constexpr size_t kChebSmem = 28 * 1024;
 
-template <int EPI>
+template <int EPI, bool CVT>
 size_t epi_smem() {
-    return umma_smem_bytes(EPI == EPI_CHEB ? kChebSmem : 0);
+    return umma_smem_bytes<CVT>(EPI == EPI_CHEB ? kChebSmem : 0);
 }
 template <int EPI>
 constexpr int epi_threads() {
@@ -853,15 +1030,15 @@ constexpr int epi_threads() {
 
 // Co-resident work units of the persistent kernel on the current device (SMs for CL = 1,
 // clusters of two CTAs for CL = 2); sets the kernel's shared-memory limit once.
-template <int EPI, int CL>
+template <int EPI, int CL, bool CVT = false>
 int persistent_units() {
     static int units[128] = {};
     int dev = 0;
     SLK_CHECK_CUDA(cudaGetDevice(&dev));
     SLK_REQUIRE(dev >= 0 && dev < 128, "device index out of range");
     if (!units[dev]) {
-        SLK_CHECK_CUDA(cudaFuncSetAttribute(k_umma_project<EPI, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            static_cast<int>(epi_smem<EPI>())));
+        SLK_CHECK_CUDA(cudaFuncSetAttribute(k_umma_project<EPI, CL, CVT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            static_cast<int>(epi_smem<EPI, CVT>())));
         int sms = 0;
         SLK_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         if (CL == 1) {
@@ -875,11 +1052,11 @@ int persistent_units() {
             attr[0].val.clusterDim.z = 1;
             cfg.gridDim = dim3(static_cast<unsigned>(sms / CL * CL));
             cfg.blockDim = dim3(epi_threads<EPI>());
-            cfg.dynamicSmemBytes = epi_smem<EPI>();
+            cfg.dynamicSmemBytes = epi_smem<EPI, CVT>();
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             int clusters = 0;
-            SLK_CHECK_CUDA(cudaOccupancyMaxActiveClusters(&clusters, k_umma_project<EPI, CL>, &cfg));
+            SLK_CHECK_CUDA(cudaOccupancyMaxActiveClusters(&clusters, k_umma_project<EPI, CL, CVT>, &cfg));
             SLK_REQUIRE(clusters > 0, "no cluster of the projection kernel fits on this device");
             units[dev] = clusters;
         }
@@ -889,13 +1066,13 @@ int persistent_units() {
 
 // Launch the persistent projection over n rows (A) and col_tiles 256-wide column tiles
 // (B); for CL = 2, map_b must have 128-row boxes (each CTA loads one half of a tile).
-template <int EPI, int CL>
+template <int EPI, int CL, bool CVT = false>
 void launch_persistent(const CUtensorMap& ma, const CUtensorMap& mb, int64_t n, int P, int d, int col_tiles, float* Z,
                        int64_t ldz, float* absmax, unsigned* err, const float* rs, float scale, const ChebEpi& ce,
                        cudaStream_t st) {
     const int64_t items = ceil_div(ceil_div(n, BM), CL) * col_tiles;
     SLK_REQUIRE(items < (int64_t(1) << 31) && n < (int64_t(1) << 31), "too many points for one projection");
-    const int64_t units = persistent_units<EPI, CL>();
+    const int64_t units = persistent_units<EPI, CL, CVT>();
     const int64_t grid = (items < units ? items : units) * CL;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -905,11 +1082,11 @@ void launch_persistent(const CUtensorMap& ma, const CUtensorMap& mb, int64_t n, 
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(static_cast<unsigned>(grid));
     cfg.blockDim = dim3(epi_threads<EPI>());
-    cfg.dynamicSmemBytes = epi_smem<EPI>();
+    cfg.dynamicSmemBytes = epi_smem<EPI, CVT>();
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = CL > 1 ? 1 : 0;
-    SLK_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_umma_project<EPI, CL>, ma, mb, static_cast<int>(n), P, d, col_tiles,
+    SLK_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_umma_project<EPI, CL, CVT>, ma, mb, static_cast<int>(n), P, d, col_tiles,
                                       static_cast<int>(items), Z, ldz, absmax, err, rs, scale, ce));
 }
 
@@ -968,6 +1145,27 @@ void launch_umma_cheb_target(const void* xa, int64_t n, const void* xib, int P, 
                                               st);
 }
 
+bool umma_f32_operand_ok(const float* x, int64_t ld) {
+    return reinterpret_cast<uintptr_t>(x) % 16 == 0 && ld % 4 == 0;
+}
+
+void launch_umma_cheb_target_f32(const float* y, int64_t ldy, const float* mu, int64_t n, const void* xib, int P, int d,
+                                 const float* coef, int q, int horner, double R, double* part, int64_t ldp,
+                                 unsigned* err, cudaStream_t st) {
+    if (n <= 0) return;
+    SLK_REQUIRE(umma_cheb_fits(P, q), "Chebyshev coefficients do not fit the fused kernel");
+    SLK_REQUIRE(umma_f32_operand_ok(y, ldy), "FP32 targets need 16-byte aligned rows");
+    const int64_t ld = umma_operand_ld(d);
+    CUtensorMap ma = make_map_f32(y, n, d, ldy, BM);
+    CUtensorMap mb = make_map(xib, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, P, d, ld, BN / kProjCluster);
+    const int col_tiles = static_cast<int>(ceil_div(P, BN));
+    ChebEpi ce{coef, q, horner, static_cast<float>(1.0 / R), static_cast<float>(R), part, ldp};
+    ce.mu = mu;
+    SLK_TIMED("umma_cheb_target", st);
+    launch_persistent<EPI_CHEB, kProjCluster, true>(ma, mb, n, P, d, col_tiles, nullptr, 0, nullptr, err, nullptr,
+                                                    1.0f, ce, st);
+}
+
 bool umma_moments_fit(int q) { return q == 8 || q == 12 || q == 16; }
 
 int64_t umma_moments_chunks(int P) {
@@ -1004,15 +1202,15 @@ void launch_umma_moments(const void* xa, int64_t n, const void* xib, int P, int 
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(static_cast<unsigned>(per_group * groups * kProjCluster));
     cfg.blockDim = dim3(epi_threads<EPI_MOM>());
-    cfg.dynamicSmemBytes = epi_smem<EPI_MOM>();
+    cfg.dynamicSmemBytes = epi_smem<EPI_MOM, false>();
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = kProjCluster > 1 ? 1 : 0;
     SLK_TIMED("umma_cheb_moments", st);
     // "n" of the kernel is the row count (slices), "P" the column count (points)
-    SLK_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_umma_project<EPI_MOM, kProjCluster>, ma, mb, P, static_cast<int>(n), d,
-                                      point_tiles, point_tiles, static_cast<float*>(nullptr), int64_t(0), absmax, err,
-                                      static_cast<const float*>(nullptr), 1.0f, ce));
+    SLK_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_umma_project<EPI_MOM, kProjCluster, false>, ma, mb, P,
+                                      static_cast<int>(n), d, point_tiles, point_tiles, static_cast<float*>(nullptr),
+                                      int64_t(0), absmax, err, static_cast<const float*>(nullptr), 1.0f, ce));
 }
 
 void launch_grad_umma(const void* g16, int64_t M, int P, const void* xit16, int d, const float* gs, double scale,

@@ -63,6 +63,14 @@ int64_t umma_cheb_parts(int P);
 bool umma_cheb_fits(int P, int q);
 void launch_umma_cheb_target(const void* xa, int64_t n, const void* xib, int P, int d, const float* coef, int q,
                              int horner, double R, double* part, int64_t ldp, unsigned* err, cudaStream_t st);
+// The same with the FP32 targets y (row stride ldy) read directly: the kernel centres
+// them (y - mu) and rounds them to BF16 in shared memory, bit for bit the operand that
+// launch_center_cast followed by launch_umma_cheb_target uses.  Needs
+// umma_f32_operand_ok(y, ldy).
+bool umma_f32_operand_ok(const float* x, int64_t ld);
+void launch_umma_cheb_target_f32(const float* y, int64_t ldy, const float* mu, int64_t n, const void* xib, int P, int d,
+                                 const float* coef, int q, int horner, double R, double* part, int64_t ldp,
+                                 unsigned* err, cudaStream_t st);
 // Fused source side of the Chebyshev evaluation (BF16 tensor cores): projections of n
 // centred points (xa, BF16) onto the P directions (xib) with the moments
 // mu_j = sum_n w_n T_j(z / R), j < q, accumulated in the epilogue (double-float per thread,

@@ -60,19 +60,37 @@ def test_single_process_is_unchanged():
 
 
 def test_roofline_amount_covers_every_launch_of_a_step():
-    """The per-launch amount is one step's work over the step's launches: three centring
-    launches (sources, targets, the 4096-row radius sample) share N + M + 4096 rows."""
+    """The per-launch amount is one step's work over the step's launches.  On the fused
+    Chebyshev path with d a multiple of four the target kernel reads the FP32 rows itself, so
+    two centring launches (sources, the 4096-row radius sample) share N + 4096 rows;
+    otherwise three (targets too) share N + M + 4096."""
     from types import SimpleNamespace
     bench = _bench()
+    peaks = {"hbm_gbs": 6689.8, "bf16_tflops_sustained": 1772.1}
+    kernels = {"center_cast": (2, 1.0), "gather_rows": (1, 0.01), "umma_cheb_moments": (1, 1.0),
+               "umma_cheb_target": (1, 1.0)}
     wl = SimpleNamespace(name="gauss_d784", N=10 ** 6, M=10 ** 6, d=784, P=512)
-    kernels = {"center_cast": (3, 1.0), "gather_rows": (1, 0.01), "umma_cheb_moments": (1, 1.0)}
-    amount, unit, bound = bench.algorithmic(wl, {}, "bf16", "center_cast", 3, kernels)
+    amount, unit, bound = bench.algorithmic(wl, {}, "bf16", "center_cast", 2, kernels)
     assert (unit, bound) == ("byte", "hbm")
-    assert amount * 3 == pytest.approx((2 * 10 ** 6 + 4096) * (4 * 784 + 2 * 784))
-    amount, unit, bound = bench.algorithmic(wl, {}, "bf16", "umma_cheb_moments", 1, kernels)
+    assert amount * 2 == pytest.approx((10 ** 6 + 4096) * (4 * 784 + 2 * 784))
+    # the sources' projection: 2 d P flop per source on the tensor cores
+    amount, unit, bound = bench.algorithmic(wl, {}, "bf16", "umma_cheb_moments", 1, kernels, peaks=peaks)
     assert (unit, bound) == ("flop", "tensor") and amount == pytest.approx(2.0 * 10 ** 6 * 784 * 512)
+    # 3136 + 32 bytes per target at 6.69 TB/s outlast 2 d P flop at 1.77 PFLOP/s: HBM-bound
+    amount, unit, bound = bench.algorithmic(wl, {}, "bf16", "umma_cheb_target", 1, kernels, peaks=peaks)
+    assert (unit, bound) == ("byte", "hbm") and amount == pytest.approx(10 ** 6 * (4 * 784 + 32))
     # a rank of a slice-sharded sum projects onto its own slices only
     amount, _, _ = bench.algorithmic(wl, {}, "bf16", "umma_cheb_moments", 1, kernels, P=256)
     assert amount == pytest.approx(2.0 * 10 ** 6 * 784 * 256)
-    traffic = bench.measured_traffic(wl, "center_cast", 3, kernels)
-    assert traffic * 3 == pytest.approx(bench.NCU_TRAFFIC_PER_POINT[("gauss_d784", "center_cast")] * (2 * 10 ** 6 + 4096))
+    amount, unit, bound = bench.algorithmic(wl, {}, "bf16", "umma_cheb_target", 1, kernels, P=256, peaks=peaks)
+    assert (unit, bound) == ("byte", "hbm") and amount == pytest.approx(10 ** 6 * (4 * 784 + 16))
+    # d not a multiple of four: the cast route for the targets too, three centring launches
+    wl3 = SimpleNamespace(name="gauss_d786", N=10 ** 6, M=10 ** 6, d=786, P=512)
+    kernels3 = dict(kernels, center_cast=(3, 1.0))
+    amount, unit, bound = bench.algorithmic(wl3, {}, "bf16", "center_cast", 3, kernels3)
+    ld16 = (786 + 7) // 8 * 8
+    assert amount * 3 == pytest.approx((2 * 10 ** 6 + 4096) * (4 * 786 + 2 * ld16))
+    amount, unit, bound = bench.algorithmic(wl3, {}, "bf16", "umma_cheb_target", 1, kernels3, peaks=peaks)
+    assert (unit, bound) == ("flop", "tensor") and amount == pytest.approx(2.0 * 10 ** 6 * 786 * 512)
+    traffic = bench.measured_traffic(wl, "center_cast", 2, kernels)
+    assert traffic * 2 == pytest.approx(bench.NCU_TRAFFIC_PER_POINT[("gauss_d784", "center_cast")] * (10 ** 6 + 4096))

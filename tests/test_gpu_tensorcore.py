@@ -150,3 +150,45 @@ def test_bf16_fused_moments_radius_fallback():
         s = pl.sum(to_dev(y, dev))
         ref, _ = oracle.sliced_sum("gaussian", sigma, xx, y, w, xi)
         assert rel_inf(s, ref, w.sum()) <= 2e-3
+
+
+@pytest.mark.parametrize("d,N,M,P", [(784, 5000, 1153, 512), (200, 4099, 700, 300)])
+def test_bf16_fused_f32_targets_match_cast_route(d, N, M, P):
+    """Aligned FP32 target rows go straight into the fused tensor-core target kernel, which
+    centres them and rounds them to BF16 in shared memory; rows whose stride is not a
+    multiple of four take the separate centring cast first.  Both routes hand the tensor
+    core the same BF16 operands and run the same epilogue: the sums are bit-identical, also
+    for plans built from the two layouts of the sources, and agree with the oracle."""
+    dev = cuda_or_skip()
+    from paper_2401_08260_gb300.slk import Plan
+    rng = np.random.Generator(np.random.PCG64(51))
+    x = rng.random((N, d), dtype=np.float32)
+    y = rng.random((M, d), dtype=np.float32)
+    w = rng.random(N).astype(np.float32)
+    xi = workloads.directions(P, d, seed=52)
+    sigma = math.sqrt(d)
+
+    def strided(a):
+        # same values, row stride d + 1 (not a multiple of four): the centring-cast route
+        buf = torch.zeros((a.shape[0], d + 1), dtype=torch.float32, device=dev)
+        buf[:, :d] = torch.from_numpy(a).to(dev)
+        v = buf[:, :d]
+        assert v.stride(0) == d + 1 and (d + 1) % 4 != 0
+        return v
+
+    p_a = Plan(to_dev(x, dev), to_dev(w, dev), "gaussian", sigma, P=P, precision="bf16", directions=xi,
+               method="cheb")
+    p_b = Plan(strided(x), to_dev(w, dev), "gaussian", sigma, P=P, precision="bf16", directions=xi, method="cheb")
+    assert p_a.info()["radius"] == p_b.info()["radius"]
+    s_direct = p_a.sum(to_dev(y, dev)).cpu().numpy()
+    np.testing.assert_array_equal(s_direct, p_a.sum(strided(y)).cpu().numpy())
+    np.testing.assert_array_equal(s_direct, p_b.sum(to_dev(y, dev)).cpu().numpy())
+    ref, _ = oracle.sliced_sum("gaussian", sigma, x, y, w, xi)
+    assert rel_inf(s_direct, ref, w.sum()) <= 2e-3
+    # targets beyond the window are still reported on the direct route
+    far = y.copy()
+    far[M // 2] += 60.0
+    from paper_2401_08260_gb300.slk import SlkError
+    with pytest.raises(SlkError) as e:
+        p_a.sum(to_dev(far, dev))
+    assert e.value.status == 4
