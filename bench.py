@@ -116,7 +116,7 @@ def plan_kwargs(wl, args):
 # in proportion to the points.  An entry is valid only for the
 # kernel as captured and is removed when that kernel changes.
 NCU_TRAFFIC_PER_POINT = {("gauss_d784", "center_cast"): (627.233024e6 + 281.766400e6) / 2e5,
-                         ("gauss_d784", "umma_cheb_target"): (628.103936e6 + 8.866048e6) / 2e5}
+                         ("gauss_d784", "umma_cheb_target"): (628.377600e6 + 8.614912e6) / 2e5}
 
 
 def f32_direct(wl, kernels):

@@ -403,8 +403,10 @@ void plan_fourier_source(slk_plan plan, const T* Zx, const T* w, cudaStream_t st
 }
 
 // Largest |projection| over a sample of min(N, 4096) strided source rows (the rows the
-// centre is estimated from), on the BF16 tensor-core path.
-double sample_projection_max(slk_plan plan, const float* x, int64_t N, int64_t ldx, cudaStream_t st) {
+// centre is estimated from), on the BF16 tensor-core path: launched here, the value is copied
+// into the pinned word *out and ev is recorded after the copy (read it once ev completes).
+void sample_projection_max_async(slk_plan plan, const float* x, int64_t N, int64_t ldx, float* out, cudaEvent_t ev,
+                                 cudaStream_t st) {
     const int d = plan->d, P = plan->P;
     const int64_t S = N < 4096 ? N : 4096;
     DevBuf<float> xs(static_cast<size_t>(S) * d, st);
@@ -416,25 +418,48 @@ double sample_projection_max(slk_plan plan, const float* x, int64_t N, int64_t l
         launch_project_umma(xa, nullptr, rows, plan->xib.get(), nullptr, P, d, 0, zs.get(), S, mx.get(),
                             plan->err_dev.get(), s);
     });
-    float m = 0.0f;
-    SLK_CHECK_CUDA(cudaMemcpyAsync(&m, mx.get(), sizeof(float), cudaMemcpyDeviceToHost, st));
-    SLK_CHECK_CUDA(cudaStreamSynchronize(st));
-    if (!std::isfinite(m)) fail(SLK_ERR_INVALID, "non-finite projected sources");
-    return m;
+    SLK_CHECK_CUDA(cudaMemcpyAsync(out, mx.get(), sizeof(float), cudaMemcpyDeviceToHost, st));
+    SLK_CHECK_CUDA(cudaEventRecord(ev, st));
 }
+
+struct EventGuard {
+    cudaEvent_t ev = nullptr;
+    EventGuard() { SLK_CHECK_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)); }
+    ~EventGuard() { cudaEventDestroy(ev); }
+};
+struct PinnedWordGuard {
+    unsigned* w = pinned_words().get();
+    ~PinnedWordGuard() { pinned_words().put(w); }  // only after the copy into it has been waited for
+};
 
 // Source side of the Chebyshev evaluation fused into the projection (BF16 path): the
 // Fourier parameters are chosen for a radius fixed before the projection (the caller's, or
 // 1.5 x the largest projection over the sample of sources), the moments come out of the
-// projection kernel itself and no projection is stored.  Returns false, with nothing kept,
+// projection kernel itself and no projection is stored.  The centring cast of the sources
+// does not depend on the radius, so it is queued before the host waits for the sample's
+// largest projection and keeps the GPU busy meanwhile.  Returns false, with nothing kept,
 // when the method is not the Chebyshev one, its term count is not supported by the fused
-// kernel, or a projected source lies outside the radius (the caller then takes the
-// two-pass route, which sets the radius from all sources).
+// kernel, or a projected source lies outside the radius (the caller then takes the two-pass
+// route, which sets the radius from all sources).
 bool fused_cheb_source(slk_plan plan, const float* x, int64_t ldx, const float* w, cudaStream_t st) {
     const int P = plan->P, d = plan->d;
     const int64_t N = plan->N;
+    const int m = plan->desc.method;
+    if (m != SLK_FOURIER_AUTO && m != SLK_FOURIER_CHEB) return false;
     const bool user_radius = plan->desc.radius > 0.0;
-    const double R = user_radius ? plan->desc.radius : 1.5 * sample_projection_max(plan, x, N, ldx, st) + 1e-6;
+    EventGuard sample_done;
+    PinnedWordGuard sample_max;
+    if (!user_radius)
+        sample_projection_max_async(plan, x, N, ldx, reinterpret_cast<float*>(sample_max.w), sample_done.ev, st);
+    DevBuf<unsigned char> xa(static_cast<size_t>(N) * umma_operand_ld(d) * 2, st);
+    launch_center_cast(x, N, d, ldx, plan->mu32.get(), xa.get(), nullptr, 0, st);
+    double R = plan->desc.radius;
+    if (!user_radius) {
+        SLK_CHECK_CUDA(cudaEventSynchronize(sample_done.ev));
+        const float ms = *reinterpret_cast<const float*>(sample_max.w);
+        if (!std::isfinite(ms)) fail(SLK_ERR_INVALID, "non-finite projected sources");
+        R = 1.5 * ms + 1e-6;
+    }
     double tol = plan->desc.tol;
     if (tol <= 0.0) tol = default_tol(SLK_GAUSSIAN, plan->desc.precision);
     FourierHost fh = choose_gaussian(plan->desc.param, d, R, plan->desc.n_coeff, plan->desc.method, tol);
@@ -446,10 +471,8 @@ bool fused_cheb_source(slk_plan plan, const float* x, int64_t ldx, const float* 
     DevBuf<double> mom(static_cast<size_t>(nchunk) * P * fh.cheb_qp, st);
     DevBuf<float> mx(1, st);
     SLK_CHECK_CUDA(cudaMemsetAsync(mx.get(), 0, sizeof(float), st));
-    cast_and_run(plan, x, N, ldx, st, [&](const void* xa, const void*, int64_t, int64_t rows, cudaStream_t s) {
-        launch_umma_moments(xa, rows, plan->xib.get(), P, d, w, fh.cheb_qp, R, mom.get(), mx.get(),
-                            plan->err_dev.get(), s);
-    });
+    launch_umma_moments(xa.get(), N, plan->xib.get(), P, d, w, fh.cheb_qp, R, mom.get(), mx.get(), plan->err_dev.get(),
+                        st);
     // the reduction runs before the range check, so one wait covers both; its output is
     // discarded when a source lies outside the radius
     DevBuf<unsigned> bad(1, st);

@@ -727,6 +727,7 @@ void launch_ndft_target(const T* Z, int P, int64_t n, int64_t ldz, const Fourier
     do {                                                                                  \
         switch (QV) {                                                                     \
             case 8: { constexpr int QM = 8; __VA_ARGS__; } break;                         \
+            case 10: { constexpr int QM = 10; __VA_ARGS__; } break;                       \
             case 12: { constexpr int QM = 12; __VA_ARGS__; } break;                       \
             case 16: { constexpr int QM = 16; __VA_ARGS__; } break;                       \
             case 24: { constexpr int QM = 24; __VA_ARGS__; } break;                       \

@@ -241,13 +241,11 @@ __device__ __forceinline__ void cheb_chunk(const float (&v)[8], const float* __r
                 }
             }
         }
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const float y = b1[r] - c;
-            const float tt = s + y;
-            c = (tt - s) - y;
-            s = tt;
-        }
+        // the group's four values added plainly, the group sum with Kahan compensation
+        const float y = ((b1[0] + b1[1]) + (b1[2] + b1[3])) - c;
+        const float tt = s + y;
+        c = (tt - s) - y;
+        s = tt;
     }
 }
 
@@ -626,6 +624,7 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256,
             }
         };
         if (ce.q == 8) run(std::integral_constant<int, 8>{});
+        else if (ce.q == 10) run(std::integral_constant<int, 10>{});
         else if (ce.q == 12) run(std::integral_constant<int, 12>{});
         else run(std::integral_constant<int, 16>{});
         if (slice >= n) mx = 0.0f;
@@ -657,6 +656,9 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256,
                 if (qn == 12) {
                     if (ce.horner) cheb_chunk<12, true>(v, bt, ppad, ce.R, ce.inv_R, s, c, bad);
                     else cheb_chunk<12, false>(v, bt, ppad, ce.R, ce.inv_R, s, c, bad);
+                } else if (qn == 10) {
+                    if (ce.horner) cheb_chunk<10, true>(v, bt, ppad, ce.R, ce.inv_R, s, c, bad);
+                    else cheb_chunk<10, false>(v, bt, ppad, ce.R, ce.inv_R, s, c, bad);
                 } else if (qn == 8) {
                     if (ce.horner) cheb_chunk<8, true>(v, bt, ppad, ce.R, ce.inv_R, s, c, bad);
                     else cheb_chunk<8, false>(v, bt, ppad, ce.R, ce.inv_R, s, c, bad);
@@ -1128,7 +1130,8 @@ void launch_transpose_bf16(const float* src, int rows, int cols, void* dst, cuda
 int64_t umma_cheb_parts(int P) { return 2 * ceil_div(P, BN); }
 
 bool umma_cheb_fits(int P, int q) {
-    return (q == 8 || q == 12 || q == 16) && static_cast<size_t>(ceil_div(P, BN) * BN) * q * sizeof(float) <= kChebSmem;
+    return (q == 8 || q == 10 || q == 12 || q == 16) &&
+           static_cast<size_t>(ceil_div(P, BN) * BN) * q * sizeof(float) <= kChebSmem;
 }
 
 void launch_umma_cheb_target(const void* xa, int64_t n, const void* xib, int P, int d, const float* coef, int q,
@@ -1166,7 +1169,7 @@ void launch_umma_cheb_target_f32(const float* y, int64_t ldy, const float* mu, i
                                                     1.0f, ce, st);
 }
 
-bool umma_moments_fit(int q) { return q == 8 || q == 12 || q == 16; }
+bool umma_moments_fit(int q) { return q == 8 || q == 10 || q == 12 || q == 16; }
 
 int64_t umma_moments_chunks(int P) {
     const int groups = static_cast<int>((ceil_div(P, BM) + kProjCluster - 1) / kProjCluster);

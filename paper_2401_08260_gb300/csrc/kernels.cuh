@@ -75,7 +75,7 @@ void launch_umma_cheb_target_f32(const float* y, int64_t ldy, const float* mu, i
 // centred points (xa, BF16) onto the P directions (xib) with the moments
 // mu_j = sum_n w_n T_j(z / R), j < q, accumulated in the epilogue (double-float per thread,
 // no projection stored); mom receives umma_moments_chunks(P) x P x q FP64 partials
-// (mom[(c * P + p) * q + j]), *absmax the largest |z| over the points.  q is 8, 12 or 16.
+// (mom[(c * P + p) * q + j]), *absmax the largest |z| over the points.  q is 8, 10, 12 or 16.
 bool umma_moments_fit(int q);
 int64_t umma_moments_chunks(int P);
 void launch_umma_moments(const void* xa, int64_t n, const void* xib, int P, int d, const float* w, int q, double R,

@@ -364,7 +364,7 @@ void choose_chebyshev(FourierHost* fp, double tol_c) {
         return;
     }
     int qp = 96;
-    for (int b : {8, 12, 16, 24, 32, 48, 64, 96})
+    for (int b : {8, 10, 12, 16, 24, 32, 48, 64, 96})
         if (q <= b) {
             qp = b;
             break;

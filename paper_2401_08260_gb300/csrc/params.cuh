@@ -20,7 +20,7 @@ struct FourierHost {
     std::vector<double> psi;   // Psi(k / n_g), k < N_c / 2
     std::vector<double> mult;  // c_k / Psi(k / n_g)^2, k < N_c / 2
     // Chebyshev evaluation (Jacobi-Anger): q terms, certified error; the device works with
-    // qp >= q terms (qp one of 8, 12, 16, 24, 32, 48, 64, 96, so its loops have fixed
+    // qp >= q terms (qp one of 8, 10, 12, 16, 24, 32, 48, 64, 96, so its loops have fixed
     // length), M is qp x qp (row-major) and zero outside the leading q x q block
     int cheb_q = 0, cheb_qp = 0;
     std::vector<double> cheb_M;
