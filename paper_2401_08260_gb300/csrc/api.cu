@@ -137,9 +137,8 @@ struct slk_plan_s {
     bool sorting = false;
     double sort_scale = 1.0;
     DevBuf<unsigned char> kw;  // sorted (key, w) pairs, P x N
-    DevBuf<double2> AB;        // prefix sums of w and w*key at bucket starts, P x (NB + 1), 16 B per entry
+    DevBuf<unsigned char> rec;  // bucket records (prefix sums of w and w*key, pair range), P x (NB + 1) x 32 B
     DevBuf<float> kmin, kscale;
-    DevBuf<int32_t> tab;       // first sorted index of each bucket, P x (NB + 1)
     int NB = 0;
 
     // deferred device-side status
@@ -154,9 +153,8 @@ struct slk_plan_s {
     ~slk_plan_s() {
         for (DevBuf<double>* b : {&xi64, &mu64, &coef, &mult, &chebM}) b->stream = stream;
         for (DevBuf<float>* b : {&xi32, &mu32, &kmin, &kscale}) b->stream = stream;
-        for (DevBuf<unsigned char>* b : {&xib, &xib_lo, &xit16, &beta, &mono, &cw, &cw0, &hgrid, &kw}) b->stream = stream;
-        AB.stream = stream;
-        tab.stream = stream;
+        for (DevBuf<unsigned char>* b : {&xib, &xib_lo, &xit16, &beta, &mono, &cw, &cw0, &hgrid, &kw, &rec})
+            b->stream = stream;
         err_dev.stream = stream;
         if (done) cudaEventDestroy(done);
         if (err_host && cudaLaunchHostFunc(stream, return_pinned_word, err_host) != cudaSuccess)
@@ -166,8 +164,7 @@ struct slk_plan_s {
         return static_cast<int64_t>(xi64.bytes() + xi32.bytes() + mu64.bytes() + mu32.bytes() + xib.bytes() +
                                     xib_lo.bytes() + xit16.bytes() + coef.bytes() +
                                     mult.bytes() + chebM.bytes() + beta.bytes() + mono.bytes() + cw.bytes() + cw0.bytes() + hgrid.bytes() + kw.bytes() +
-                                    AB.bytes() +
-                                    kmin.bytes() + kscale.bytes() + tab.bytes());
+                                    rec.bytes() + kmin.bytes() + kscale.bytes());
     }
 };
 
@@ -508,12 +505,10 @@ void plan_sort_source(slk_plan plan, const T* Zx, const T* w, cudaStream_t st) {
         DevBuf<unsigned char> scratch(sb, st);
         launch_sort_pairs<T>(Zx, P, N, N, w, plan->kw.get(), scratch.get(), sb, st);
     }
-    plan->AB.alloc(static_cast<size_t>(P) * (nb + 1), st);
+    plan->rec.alloc(static_cast<size_t>(P) * (nb + 1) * kBucketRecordBytes, st);
     plan->kmin.alloc(P, st);
     plan->kscale.alloc(P, st);
-    plan->tab.alloc(static_cast<size_t>(P) * (nb + 1), st);
-    launch_bucket_tables<T>(P, N, plan->kw.get(), nb, plan->kmin.get(), plan->kscale.get(), plan->tab.get(),
-                            plan->AB.get(), st);
+    launch_bucket_tables<T>(P, N, plan->kw.get(), nb, plan->kmin.get(), plan->kscale.get(), plan->rec.get(), st);
 }
 
 template <class T>
@@ -640,8 +635,8 @@ void sum_impl(slk_plan plan, const void* y_user, int64_t M, int64_t ldy, void* s
                                   nullptr, plan->err_dev.get(), st);
     }
     if (plan->sorting)
-        launch_negdist_target<T>(Zy.get(), P, M, M, plan->kw.get(), plan->N, plan->AB.get(), plan->NB,
-                                 plan->kmin.get(), plan->kscale.get(), plan->tab.get(), plan->cd,
+        launch_negdist_target<T>(Zy.get(), P, M, M, plan->kw.get(), plan->N, plan->rec.get(), plan->NB,
+                                 plan->kmin.get(), plan->kscale.get(), plan->cd,
                                  plan->sort_scale, acc.get(), nullptr, 0, st);
     const bool s_dev = is_device_pointer(s_user);
     if (s_dev) {
@@ -686,8 +681,8 @@ void grad_impl(slk_plan plan, const void* y_user, int64_t M, int64_t ldy, const 
                                   G.get(), plan->err_dev.get(), st);
     }
     if (plan->sorting)
-        launch_negdist_target<T>(Zy.get(), P, M, M, plan->kw.get(), plan->N, plan->AB.get(), plan->NB,
-                                 plan->kmin.get(), plan->kscale.get(), plan->tab.get(), plan->cd,
+        launch_negdist_target<T>(Zy.get(), P, M, M, plan->kw.get(), plan->N, plan->rec.get(), plan->NB,
+                                 plan->kmin.get(), plan->kscale.get(), plan->cd,
                                  plan->sort_scale, nullptr, G.get(), plan->fourier ? 1 : 0, st);
     InView<T> gsv(gs_user, gs_user ? M : 0, 1, 1, st);
     const bool g_dev = is_device_pointer(gy_user);
@@ -1117,8 +1112,8 @@ void sum_noalloc_impl(slk_plan plan, const T* y, int64_t M, int64_t ldy, T* s, u
                                   plan->err_dev.get(), st);
     }
     if (plan->sorting)
-        launch_negdist_target<T>(Zy, P, M, M, plan->kw.get(), plan->N, plan->AB.get(), plan->NB,
-                                 plan->kmin.get(), plan->kscale.get(), plan->tab.get(), plan->cd,
+        launch_negdist_target<T>(Zy, P, M, M, plan->kw.get(), plan->N, plan->rec.get(), plan->NB,
+                                 plan->kmin.get(), plan->kscale.get(), plan->cd,
                                  plan->sort_scale, acc, nullptr, 0, st);
     launch_finalize<T>(acc, s, M, 1.0 / P, st);
 }

@@ -231,6 +231,56 @@ __global__ void __launch_bounds__(256) k_ndft_target(const T* __restrict__ Z, in
     if (!GRAD && m < n) acc[m] += sum.value();
 }
 
+// The same evaluation for few targets, where one thread per target would occupy only a
+// handful of SMs: one warp per target, lane l taking the slices p = l, l + 32, ...; each
+// lane sums its slices (compensated for FP32), then the 32 lane sums are added in a fixed
+// butterfly order, so the result does not depend on scheduling.
+template <class T, int KMAX, bool GRAD>
+__global__ void __launch_bounds__(256) k_ndft_target_warp(const T* __restrict__ Z, int P, int64_t n, int64_t ldz,
+                                                          T two_over_L, int k_lo, int K,
+                                                          const Cplx<T>* __restrict__ cw, const T* __restrict__ cw0,
+                                                          T R, double* __restrict__ acc, T* __restrict__ G,
+                                                          unsigned* __restrict__ err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t m = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    if (m >= n) return;  // m is the same for the whole warp
+    const T two_pi_over_L = two_over_L * T(3.141592653589793238462643383279);
+    typename Acc<T>::type sum;
+    bool bad = false;
+    for (int p = lane; p < P; p += 32) {
+        const T z = Z[static_cast<int64_t>(p) * ldz + m];
+        if (!(z <= R && z >= -R)) bad = true;  // outside the certified window (or NaN)
+        const T s = z * two_over_L;
+        T sb, cb, s1, c1;
+        sincospi_t(T(k_lo) * s, &sb, &cb);
+        sincospi_t(s, &s1, &c1);
+        T cr = cb, ci = sb;  // e^{+i k th}
+        T t = T(0), dt = T(0);
+        const Cplx<T>* row = cw + static_cast<int64_t>(p) * K;
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) {
+            if (j < K) {
+                const Cplx<T> a = row[j];
+                if (GRAD) dt -= T(k_lo + j) * (a.re * ci + a.im * cr);
+                else t += a.re * cr - a.im * ci;
+                const T nr = cr * c1 - ci * s1;
+                const T ni = ci * c1 + cr * s1;
+                cr = nr;
+                ci = ni;
+            }
+        }
+        if (GRAD) G[m * P + p] = T(2) * dt * two_pi_over_L;
+        else sum.add(T(2) * t + cw0[p]);
+    }
+    if (bad) atomicOr(err, 4u);
+    if (!GRAD) {
+        double v = sum.value();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) acc[m] += v;
+    }
+}
+
 // ------------------------------------------------------------ Chebyshev evaluation
 
 // One source's contribution w T_j(u), j < QMAX, to the moments (Chebyshev recurrence
@@ -691,6 +741,9 @@ void launch_ndft_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, c
     SLK_CHECK_LAUNCH();
 }
 
+// Below this many targets the NDFT target side runs one warp per target (see k_ndft_target_warp).
+constexpr int64_t kNdftWarpTargets = 32768;
+
 template <class T>
 void launch_ndft_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const Cplx<T>* cw,
                         const T* cw0, double* acc, T* G, unsigned* err, cudaStream_t st) {
@@ -705,6 +758,18 @@ void launch_ndft_target(const T* Z, int P, int64_t n, int64_t ldz, const Fourier
     const T two_over_L = static_cast<T>(2.0 / fd.L);
     const unsigned blocks = static_cast<unsigned>(ceil_div(n, 256));
     SLK_TIMED(G ? "ndft_target_grad" : "ndft_target", st);
+    if (n < kNdftWarpTargets) {
+        // few targets: one warp per target (eight per block) keeps every SM busy
+        const unsigned wblocks = static_cast<unsigned>(ceil_div(n, 8));
+        if (G)
+            SLK_NDFT_DISPATCH(K, (k_ndft_target_warp<T, KM, true><<<wblocks, 256, 0, st>>>(
+                                     Z, P, n, ldz, two_over_L, fd.k_lo, K, cw, cw0, static_cast<T>(fd.R), acc, G, err)));
+        else
+            SLK_NDFT_DISPATCH(K, (k_ndft_target_warp<T, KM, false><<<wblocks, 256, 0, st>>>(
+                                     Z, P, n, ldz, two_over_L, fd.k_lo, K, cw, cw0, static_cast<T>(fd.R), acc, G, err)));
+        SLK_CHECK_LAUNCH();
+        return;
+    }
     if (G) {
         SLK_NDFT_DISPATCH(K, {
             cudaFuncSetAttribute(k_ndft_target<T, KM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);

@@ -294,6 +294,17 @@ struct Pre<double> {
     double a, b;
 };
 
+// One bucket of one slice: the prefix entry at its first sorted index, that index and the
+// first index of the next bucket, in one 32-byte (one-sector) record.
+template <class T>
+struct alignas(32) BucketRec {
+    Pre<T> e;
+    int32_t start, end;
+    int32_t pad[2];
+};
+static_assert(sizeof(BucketRec<float>) == kBucketRecordBytes && sizeof(BucketRec<double>) == kBucketRecordBytes,
+              "bucket records are 32 bytes");
+
 // Running sums (w, w key) over sorted pairs, and their scan arithmetic.
 template <class T>
 struct PairSum;
@@ -421,23 +432,24 @@ __global__ void __launch_bounds__(PS_THREADS) k_pair_chunk_sums(const KW<T>* __r
     }
 }
 
-// Bucket tables from the sorted pairs and the scanned chunk sums (cs[p][c] = exclusive
+// Bucket records from the sorted pairs and the scanned chunk sums (cs[p][c] = exclusive
 // prefix before chunk c): every sorted index i that starts buckets (b(i-1), b(i)] writes
-// tab[q] = i and AB[q] = the prefix of (w, w key) before i; the last index fills the
-// buckets above it (AB[NB] = the totals).  Each thread takes PS_ITEMS consecutive pairs.
+// their start i and prefix entry (the prefix of (w, w key) before i), and i as the end of
+// bucket b(i-1) and of the empty buckets between; the last index ends its bucket and fills
+// the buckets above it (record NB holds the totals).  Each thread takes PS_ITEMS
+// consecutive pairs.
 template <class T>
 __global__ void __launch_bounds__(PS_THREADS) k_pair_prefix_tab(const KW<T>* __restrict__ kw, int64_t n, int nchunk,
                                                                const double2* __restrict__ cs, int NB,
                                                                const float* __restrict__ kmin,
                                                                const float* __restrict__ kscale,
-                                                               int32_t* __restrict__ tab, Pre<T>* __restrict__ AB) {
+                                                               BucketRec<T>* __restrict__ rec) {
     __shared__ PairSum<T> wsum[PS_THREADS / 32];
     __shared__ PairSum<T> chunk_start;
     const int p = blockIdx.y, c = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const KW<T>* ks = kw + static_cast<int64_t>(p) * n;
-    int32_t* tb = tab + static_cast<int64_t>(p) * (NB + 1);
-    Pre<T>* ab = AB + static_cast<int64_t>(p) * (NB + 1);
+    BucketRec<T>* rb = rec + static_cast<int64_t>(p) * (NB + 1);
     const float lo = kmin[p], sc = kscale[p];
     const int64_t i0 = static_cast<int64_t>(c) * PS_CHUNK + static_cast<int64_t>(threadIdx.x) * PS_ITEMS;
     if (threadIdx.x == 0) chunk_start = PairSum<T>::from_double2(cs[static_cast<int64_t>(p) * (nchunk + 1) + c]);
@@ -478,12 +490,16 @@ __global__ void __launch_bounds__(PS_THREADS) k_pair_prefix_tab(const KW<T>* __r
         if (i >= n) break;
         const int bi = bucket_of(static_cast<float>(el[r].key), lo, sc, NB);
         if (bi > bprev) {
+            // bucket bprev ends here, the empty buckets between start and end here, bucket bi
+            // starts here (each field is written by exactly one thread)
             PairSum<T> pre = start;
             pre.plus(PairSum<T>::from_pair(la, lb));
             const Pre<T> e = pre.entry();
+            if (bprev >= 0) rb[bprev].end = static_cast<int32_t>(i);
             for (int q = bprev + 1; q <= bi; ++q) {
-                tb[q] = static_cast<int32_t>(i);
-                ab[q] = e;
+                rb[q].e = e;
+                rb[q].start = static_cast<int32_t>(i);
+                if (q < bi) rb[q].end = static_cast<int32_t>(i);
             }
             bprev = bi;
         }
@@ -493,9 +509,11 @@ __global__ void __launch_bounds__(PS_THREADS) k_pair_prefix_tab(const KW<T>* __r
             PairSum<T> tot = start;
             tot.plus(PairSum<T>::from_pair(la, lb));
             const Pre<T> e = tot.entry();
+            rb[bi].end = static_cast<int32_t>(n);
             for (int q = bi + 1; q <= NB; ++q) {
-                tb[q] = static_cast<int32_t>(n);
-                ab[q] = e;
+                rb[q].e = e;
+                rb[q].start = static_cast<int32_t>(n);
+                rb[q].end = static_cast<int32_t>(n);
             }
         }
     }
@@ -606,9 +624,9 @@ __device__ __forceinline__ double negdist_slope(const Pre<double>& e, const Pre<
 template <class T>
 __global__ void __launch_bounds__(256) k_negdist_target(const T* __restrict__ Z, int P, int p0, int p1, int64_t n,
                                                        int64_t ldz, const KW<T>* __restrict__ kw, int64_t nx,
-                                                       const Pre<T>* __restrict__ AB, int NB,
+                                                       const BucketRec<T>* __restrict__ rec, int NB,
                                                        const float* __restrict__ kmin, const float* __restrict__ kscale,
-                                                       const int32_t* __restrict__ tab, T cd, T scale,
+                                                       T cd, T scale,
                                                        double* __restrict__ acc, T* __restrict__ G, int accumulate_G) {
     const int64_t m = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (m >= n) return;
@@ -616,11 +634,11 @@ __global__ void __launch_bounds__(256) k_negdist_target(const T* __restrict__ Z,
     for (int p = p0; p < p1; ++p) {
         const T z = Z[static_cast<int64_t>(p) * ldz + m];
         const KW<T>* ks = kw + static_cast<int64_t>(p) * nx;
-        const int32_t* tb = tab + static_cast<int64_t>(p) * (NB + 1);
-        const Pre<T>* ab = AB + static_cast<int64_t>(p) * (NB + 1);
+        const BucketRec<T>* rb = rec + static_cast<int64_t>(p) * (NB + 1);
         const int b = bucket_of(static_cast<float>(z), kmin[p], kscale[p], NB);
-        const int32_t hi = tb[b + 1];
-        int32_t i = tb[b];
+        const BucketRec<T> r = rb[b];  // one sector: prefix entry and the bucket's pair range
+        const int32_t hi = r.end;
+        int32_t i = r.start;
         T a = T(0), bz = T(0);
         for (; i < hi; ++i) {
             const KW<T> e = ks[i];
@@ -628,7 +646,7 @@ __global__ void __launch_bounds__(256) k_negdist_target(const T* __restrict__ Z,
             a += e.w;
             bz = fma(e.w, e.key, bz);
         }
-        const Pre<T> eb = ab[b], tot = ab[NB];
+        const Pre<T> eb = r.e, tot = rb[NB].e;
         if (G) {
             T aeq = T(0);
             for (; i < hi; ++i) {
@@ -740,8 +758,8 @@ int64_t sorted_pairs_bytes(int P, int64_t n) {
 }
 
 template <class T>
-void launch_bucket_tables(int P, int64_t n, const void* kw, int NB, float* kmin, float* kscale, int32_t* tab,
-                          void* AB, cudaStream_t st) {
+void launch_bucket_tables(int P, int64_t n, const void* kw, int NB, float* kmin, float* kscale, void* rec,
+                          cudaStream_t st) {
     const KW<T>* pairs = static_cast<const KW<T>*>(kw);
     {
         SLK_TIMED("bucket_minmax", st);
@@ -763,19 +781,19 @@ void launch_bucket_tables(int P, int64_t n, const void* kw, int NB, float* kmin,
     SLK_CHECK_LAUNCH();
     {
         SLK_TIMED("pair_prefix_tab", st);
-        k_pair_prefix_tab<T><<<g, PS_THREADS, 0, st>>>(pairs, n, nchunk, cs.get(), NB, kmin, kscale, tab,
-                                                       static_cast<Pre<T>*>(AB));
+        k_pair_prefix_tab<T><<<g, PS_THREADS, 0, st>>>(pairs, n, nchunk, cs.get(), NB, kmin, kscale,
+                                                       static_cast<BucketRec<T>*>(rec));
     }
     SLK_CHECK_LAUNCH();
 }
 
 template <class T>
-void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const void* kw, int64_t nx, const void* AB,
-                           int NB, const float* kmin, const float* kscale, const int32_t* tab, double cd, double scale,
-                           double* acc, T* G, int accumulate_G, cudaStream_t st) {
+void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const void* kw, int64_t nx, const void* rec,
+                           int NB, const float* kmin, const float* kscale, double cd, double scale, double* acc, T* G,
+                           int accumulate_G, cudaStream_t st) {
     if (n <= 0) return;
     // slices per launch: keep one batch's pairs (the randomly accessed state) within ~64 MB of L2
-    const int64_t per_slice = static_cast<int64_t>(sizeof(KW<T>)) * nx + static_cast<int64_t>(NB + 1) * 20;
+    const int64_t per_slice = static_cast<int64_t>(sizeof(KW<T>)) * nx + static_cast<int64_t>(NB + 1) * kBucketRecordBytes;
     int batch = static_cast<int>((int64_t(64) << 20) / (per_slice > 0 ? per_slice : 1));
     if (batch < 1) batch = 1;
     if (batch > P) batch = P;
@@ -783,8 +801,8 @@ void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const void
         const int p1 = p0 + batch < P ? p0 + batch : P;
         SLK_TIMED(G ? "negdist_target_grad" : "negdist_target", st);
         k_negdist_target<T><<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, st>>>(
-            Z, P, p0, p1, n, ldz, static_cast<const KW<T>*>(kw), nx, static_cast<const Pre<T>*>(AB), NB, kmin, kscale,
-            tab, static_cast<T>(cd), static_cast<T>(scale), acc, G, accumulate_G);
+            Z, P, p0, p1, n, ldz, static_cast<const KW<T>*>(kw), nx, static_cast<const BucketRec<T>*>(rec), NB, kmin,
+            kscale, static_cast<T>(cd), static_cast<T>(scale), acc, G, accumulate_G);
         SLK_CHECK_LAUNCH();
     }
 }
@@ -793,11 +811,10 @@ void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const void
     template size_t sort_pairs_scratch<T>(int, int64_t);                                                              \
     template void launch_sort_pairs<T>(const T*, int, int64_t, int64_t, const T*, void*, void*, size_t, cudaStream_t); \
     template int64_t sorted_pairs_bytes<T>(int, int64_t);                                                             \
-    template void launch_bucket_tables<T>(int, int64_t, const void*, int, float*, float*, int32_t*, void*,             \
-                                          cudaStream_t);                                                              \
+    template void launch_bucket_tables<T>(int, int64_t, const void*, int, float*, float*, void*, cudaStream_t);       \
     template void launch_negdist_target<T>(const T*, int, int64_t, int64_t, const void*, int64_t, const void*, int,   \
-                                           const float*, const float*, const int32_t*, double, double, double*, T*,   \
-                                           int, cudaStream_t);
+                                           const float*, const float*, double, double, double*, T*, int,             \
+                                           cudaStream_t);
 SLK_INST(float)
 SLK_INST(double)
 #undef SLK_INST

@@ -175,20 +175,22 @@ size_t sort_pairs_scratch(int P, int64_t n);
 template <class T>
 int64_t sorted_pairs_bytes(int P, int64_t n);
 // From the sorted pairs: NB equal-width buckets per slice over [key_min, key_max] (kmin,
-// kscale; tab[p][b] = first sorted index of bucket >= b) and the exclusive prefix sums of
-// w and w*key at the bucket starts (AB[p][b], AB[p][NB] = totals; 16 bytes per entry:
-// two doubles for FP64 data, double-float pairs (hi, lo) for FP32 data).
+// kscale) and one 32-byte record per bucket b <= NB, rec[p][b]: the exclusive prefix sums
+// of w and w*key at the bucket's first sorted index (16 bytes: two doubles for FP64 data,
+// double-float pairs (hi, lo) for FP32 data), that index and the first index of the next
+// bucket (a target's lookup reads one record); rec[p][NB] holds the totals.
+constexpr int64_t kBucketRecordBytes = 32;
 template <class T>
-void launch_bucket_tables(int P, int64_t n, const void* kw, int NB, float* kmin, float* kscale, int32_t* tab,
-                          void* AB, cudaStream_t st);
+void launch_bucket_tables(int P, int64_t n, const void* kw, int NB, float* kmin, float* kscale, void* rec,
+                          cudaStream_t st);
 // Negative-distance 1-D sums at the targets (Section 3.2 in the range-free
 // form t = -c_d [z (2 A_< - W) - (2 B_< - S)]) summed over slices into acc[m],
 // times `scale`; with G != NULL writes g = scale c_d (W - A_< - A_<=) into
 // G[m][p] instead (the derivative, sign(0) = 0).  Slices are processed in
 // batches whose sorted pairs fit in L2.
 template <class T>
-void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const void* kw, int64_t nx, const void* AB,
-                           int NB, const float* kmin, const float* kscale, const int32_t* tab, double cd, double scale,
-                           double* acc, T* G, int accumulate_G, cudaStream_t st);
+void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const void* kw, int64_t nx, const void* rec,
+                           int NB, const float* kmin, const float* kscale, double cd, double scale, double* acc, T* G,
+                           int accumulate_G, cudaStream_t st);
 
 }  // namespace slk

@@ -91,9 +91,9 @@ extern "C" int64_t slk_request_bytes(const slk_plan_desc* desc, int64_t N, int64
         persist += grids;
     }
     if (desc->kernel == SLK_NEGDIST || desc->kernel == SLK_LAPLACIAN) {
-        const int64_t NB = N / 8 + 2;
+        const int64_t NB = N / 4 + 2;  // the plan's bucket count: a power of two >= N / 8
         const int64_t sort = P * N * (e + 4) + 2 * P * N * e + P * N * 4 + P * 256 * (N / 4096 + 1) * 4;
-        const int64_t keep = P * N * 2 * e + P * NB * 20;
+        const int64_t keep = P * N * 2 * e + P * NB * 32;  // 32-byte bucket records
         create += sort + keep;
         persist += keep;
     }
