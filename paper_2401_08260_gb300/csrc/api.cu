@@ -424,9 +424,18 @@ struct EventGuard {
     EventGuard() { SLK_CHECK_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)); }
     ~EventGuard() { cudaEventDestroy(ev); }
 };
+// A pinned word for one readback; back to the pool only once the copy into it (recorded
+// by `after`) has landed, also when an error leaves the call early.
 struct PinnedWordGuard {
     unsigned* w = pinned_words().get();
-    ~PinnedWordGuard() { pinned_words().put(w); }  // only after the copy into it has been waited for
+    cudaEvent_t after = nullptr;
+    ~PinnedWordGuard() {
+        if (after && cudaEventSynchronize(after) != cudaSuccess) {
+            cudaGetLastError();
+            return;  // not reused
+        }
+        pinned_words().put(w);
+    }
 };
 
 // Source side of the Chebyshev evaluation fused into the projection (BF16 path): the
@@ -446,8 +455,10 @@ bool fused_cheb_source(slk_plan plan, const float* x, int64_t ldx, const float* 
     const bool user_radius = plan->desc.radius > 0.0;
     EventGuard sample_done;
     PinnedWordGuard sample_max;
-    if (!user_radius)
+    if (!user_radius) {
         sample_projection_max_async(plan, x, N, ldx, reinterpret_cast<float*>(sample_max.w), sample_done.ev, st);
+        sample_max.after = sample_done.ev;
+    }
     DevBuf<unsigned char> xa(static_cast<size_t>(N) * umma_operand_ld(d) * 2, st);
     launch_center_cast(x, N, d, ldx, plan->mu32.get(), xa.get(), nullptr, 0, st);
     double R = plan->desc.radius;
