@@ -266,7 +266,10 @@ slk_status slk_kernel_sum(const slk_plan_desc* desc, const void* x, int64_t N, i
  *    (the accumulator is cleared at the start of each call).  Calls whose work
  *    overlaps on the GPU (other streams, other threads, several plans on the
  *    same device) race on the array: order them on one stream or synchronise.
- *  - Results equal slk_sum's; errors as slk_sum, plus SLK_ERR_INVALID for
+ *  - Results agree with slk_sum's to rounding: the same projections and 1-D
+ *    method, run as separate projection and target kernels (on the BF16
+ *    Chebyshev path slk_sum evaluates inside the projection kernel instead,
+ *    summing in another order); errors as slk_sum, plus SLK_ERR_INVALID for
  *    host pointers or sizes beyond the array.
  */
 slk_status slk_sum_noalloc(slk_plan plan, const void* y, int64_t M, int64_t ldy, void* s, void* stream);
