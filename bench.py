@@ -636,7 +636,10 @@ def run_serve(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)  # about 0.8 s timed at the default workload: several clock samples
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 200 for this library, about 0.8 s at the default workload so that "
+                         "the clock sampler sees several samples; 10 for the reference arm, whose steps are oracle "
+                         "samples of seconds each)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="gauss_d784")
@@ -661,6 +664,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
+    if args.steps is None:
+        args.steps = 10 if args.impl == "reference" else 200
     if args.serve:
         run_serve(args)
     elif args.impl == "reference":
