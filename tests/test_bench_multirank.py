@@ -94,3 +94,21 @@ def test_roofline_amount_covers_every_launch_of_a_step():
     assert (unit, bound) == ("flop", "tensor") and amount == pytest.approx(2.0 * 10 ** 6 * 786 * 512)
     traffic = bench.measured_traffic(wl, "center_cast", 2, kernels)
     assert traffic * 2 == pytest.approx(bench.NCU_TRAFFIC_PER_POINT[("gauss_d784", "center_cast")] * (10 ** 6 + 4096))
+
+
+def test_default_steps_per_arm(monkeypatch):
+    """Without --steps the library's arm times 200 steps (several clock samples at about 4 ms a
+    step) and the oracle's reference arm 10 (its steps are oracle samples of seconds each, and
+    the whole run must stay within minutes); an explicit --steps applies to either arm."""
+    import sys
+    bench = _bench()
+    seen = {}
+    monkeypatch.setattr(bench, "run_ours", lambda a: seen.update(ours=a.steps))
+    monkeypatch.setattr(bench, "run_reference", lambda a: seen.update(reference=a.steps))
+    for argv in (["bench.py"], ["bench.py", "--impl", "reference"], ["bench.py", "--impl", "reference", "--steps", "4"]):
+        monkeypatch.setattr(sys, "argv", argv)
+        bench.main()
+    assert seen == {"ours": 200, "reference": 4}
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference"])
+    bench.main()
+    assert seen["reference"] == 10
