@@ -62,7 +62,7 @@ typedef enum {
     SLK_ERR_ACCURACY = 4,     /* the requested accuracy cannot be certified */
     SLK_ERR_TIMEOUT = 5,      /* a bounded wait ran out */
     SLK_ERR_BUSY = 6,         /* no slot or memory free right now; retry later */
-    SLK_ERR_UNSUPPORTED = 7,  /* valid request this build does not implement */
+    SLK_ERR_UNSUPPORTED = 7,  /* valid request the library does not implement */
     SLK_ERR_NOT_FOUND = 8     /* unknown request id */
 } slk_status;
 
