@@ -48,3 +48,25 @@ def test_chebyshev_is_chosen_for_the_benchmark_window():
     info = slk.fourier_params("gaussian", 28.0, 784, 3.0, precision="bf16")
     assert info["method"] == 3 and 1 <= info["cheb_terms"] <= 16
     assert info["model_error"] <= 1e-5
+
+
+@pytest.mark.parametrize("sigma,d,R,precision,tol", [
+    (4.0, 16, 5.0, "f64", 0.0),       # the d = 16 workload: FP64 default target
+    (28.0, 784, 3.0, "f32", 0.0),
+])
+def test_ndft_band_reproduces_f_within_the_certified_error(sigma, d, R, precision, tol):
+    """The NDFT keeps the band k_lo <= |k| <= k_hi (it drops coefficients from both ends while
+    the dropped mass stays within a share of the target); for d > 1 the k = 0 coefficient is
+    f^(0) / L = 0 (f^ grows like omega^(d-1) at 0).  The band's cosine sum reproduces f on the
+    window within the certified error."""
+    info = slk.fourier_params("gaussian", sigma, d, R, precision=precision, method="ndft", tol=tol)
+    L, k_lo, k_hi, err = info["period"], info["k_lo"], info["k_hi"], info["model_error"]
+    assert info["method"] == 2 and 1 <= k_lo <= k_hi
+    assert oracle.fhat_gauss(d, sigma, 0.0) == 0.0
+    k = np.arange(k_lo, k_hi + 1)
+    ck = oracle.fhat_gauss(d, sigma, k / L) / L
+    u = np.linspace(-2 * R, 2 * R, 401)
+    phi = 2.0 * (ck[None, :] * np.cos(2 * np.pi * np.outer(u, k) / L)).sum(axis=1)
+    exact = oracle.f("gaussian", d, sigma, np.abs(u))
+    dev = np.abs(phi - exact).max()
+    assert dev <= err
