@@ -70,3 +70,34 @@ def test_ndft_band_reproduces_f_within_the_certified_error(sigma, d, R, precisio
     exact = oracle.f("gaussian", d, sigma, np.abs(u))
     dev = np.abs(phi - exact).max()
     assert dev <= err
+
+
+@pytest.mark.parametrize("precision", ["bf16", "f32"])
+def test_chebyshev_form_reproduces_f_within_the_certified_error(precision):
+    """The Chebyshev form of the truncated Fourier sum (Jacobi-Anger expansion on the window
+    [-R, R]): with the band and term count the host chooses, the separable approximation
+    sum_{l,j<q} M_lj T_l(z/R) T_j(s/R), M_lj = 2 e_l e_j cos(pi (l - j) / 2) sum_k c_k
+    J_l(w_k) J_j(w_k) (e_0 = 1, e_j = 2, w_k = 2 pi k R / L, Bessel values from scipy),
+    reproduces the oracle's f(|z - s|) over the whole window square within the certified
+    model error."""
+    jv = pytest.importorskip("scipy.special").jv
+    sigma, d = 28.0, 784
+    info = slk.fourier_params("gaussian", sigma, d, 3.0, precision=precision)
+    assert info["method"] == 3
+    L, R, q = info["period"], info["radius"], info["cheb_terms"]
+    k = np.arange(info["k_lo"], info["k_hi"] + 1)
+    ck = oracle.fhat_gauss(d, sigma, k / L) / L
+    om = 2 * np.pi * k * R / L
+    ll = np.arange(q)
+    e = np.where(ll == 0, 1.0, 2.0)
+    J = jv(ll[:, None], om[None, :])
+    M = 2 * e[:, None] * e[None, :] * np.cos(np.pi * (ll[:, None] - ll[None, :]) / 2) * ((J * ck) @ J.T)
+    u = np.linspace(-1.0, 1.0, 121)
+    T = np.cos(np.outer(np.arccos(u), ll))
+    approx = T @ M @ T.T
+    exact = oracle.f("gaussian", d, sigma, np.abs(R * (u[:, None] - u[None, :])))
+    dev = np.abs(approx - exact).max()
+    assert dev <= info["model_error"]
+    # one term fewer is visibly worse: the certified count is not padded generously
+    approx_short = T[:, :-1] @ M[:-1, :-1] @ T[:, :-1].T
+    assert np.abs(approx_short - exact).max() > dev
