@@ -468,7 +468,7 @@ def run_ours(args):
                 "scaling": "strong" if sharded else "weak",
                 "vs_baseline": None, "dtype": precision, "data": "synthetic",
                 "config": {"workload": args.workload, "kernel": wl.kernel, "N": wl.N, "M": wl.M, "d": wl.d,
-                           "P": wl.P, "n_coeff": info["n_coeff"], "method": {1: "nfft", 2: "ndft"}.get(info["method"]),
+                           "P": wl.P, "n_coeff": info["n_coeff"], "method": {1: "nfft", 2: "ndft", 3: "cheb"}.get(info["method"]),
                            "parallelism": (f"slices{world}" if sharded else f"replicas{world}") if world > 1
                            else "single",
                            "l2": "inputs larger than L2 (no flush needed)",

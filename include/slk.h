@@ -160,8 +160,10 @@ const char* slk_last_error(void);
  * Build a plan: draw or copy the directions, project the sources x (N x d,
  * row stride ldx) onto them and precompute the x-side of every slice
  * (Algorithm 1, first step, and the source half of the 1-D method:
- * Fourier coefficients w_hat (Sec. 3.1), or sorted keys with FP64 prefix
- * sums (Sec. 3.2)).  w holds N weights.  N >= 1.
+ * Fourier coefficients w_hat or Chebyshev moments (Sec. 3.1), or the sorted
+ * (key, w) pairs with per-bucket prefix sums of w and w * key (Sec. 3.2),
+ * kept exact as double-float values with FP64 totals per chunk and bucket).
+ * w holds N weights.  N >= 1.
  * Errors: SLK_ERR_INVALID (bad descriptor, N < 1, ldx < d), SLK_ERR_OOM,
  * SLK_ERR_ACCURACY (no Fourier parameters meet desc->tol), SLK_ERR_CUDA.
  */
@@ -279,6 +281,9 @@ slk_status slk_sum_noalloc(slk_plan plan, const void* y, int64_t M, int64_t ldy,
  * the library is counted; while timing is enabled, each launch is also
  * bracketed by CUDA events recorded on the stream it is launched on.
  *   slk_launch_count   kernels launched by this process so far.
+ *   slk_device_alloc_count  device allocations the library has made in this
+ *                      process so far (stream-ordered allocations of plans,
+ *                      workspaces and staging buffers).
  *   slk_timing_enable  on != 0 starts recording events for later launches.
  *   slk_timing_read    waits for the recorded events and writes, per kernel
  *                      name in first-launch order, the launch count and the
@@ -293,6 +298,7 @@ typedef struct {
 } slk_kernel_time;
 
 int64_t slk_launch_count(void);
+int64_t slk_device_alloc_count(void);
 slk_status slk_timing_enable(int32_t on);
 slk_status slk_timing_read(slk_kernel_time* out, int32_t cap, int32_t* count);
 slk_status slk_timing_reset(void);

@@ -1,5 +1,6 @@
 // C ABI: plans, sums and gradients (Algorithm 1 with the 1-D methods of Section 3).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -28,7 +29,10 @@ void fail(slk_status st, const char* fmt, ...) {
     throw Error{st, std::string(buf)};
 }
 
+std::atomic<int64_t> g_dev_allocs{0};
+
 void* dev_alloc(size_t bytes, cudaStream_t st) {
+    g_dev_allocs.fetch_add(1, std::memory_order_relaxed);
     void* p = nullptr;
     cudaError_t e = cudaMallocAsync(&p, bytes, st);
     if (e != cudaSuccess) {
@@ -1162,3 +1166,5 @@ extern "C" slk_status slk_sum_noalloc(slk_plan plan, const void* y, int64_t M, i
         plan->stream = st;
     });
 }
+
+extern "C" int64_t slk_device_alloc_count(void) { return slk::g_dev_allocs.load(); }

@@ -90,6 +90,14 @@ __device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int c0, 
                  : "memory");
 }
 
+// Wait (bounded) for the last fill of each stage of a ring filled `fills` times, in the
+// order they were issued: fill j completes phase j / stages of barrier j % stages.  The
+// TMA bytes of those fills have then landed in this CTA's shared memory.
+__device__ __forceinline__ void drain_fills(uint64_t* bars, int stages, int fills) {
+    for (int j = fills > stages ? fills - stages : 0; j < fills; ++j)
+        if (!mbar_wait(&bars[j % stages], (j / stages) & 1)) break;
+}
+
 // UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t smem_desc(const void* p) {
     const uint64_t addr = smem_u32(p);
@@ -121,29 +129,13 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                  : "memory");
 }
 
-// the same arrival on the barrier at this offset in every CTA of mask (cluster)
-__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
-        "h"(mask)
-        : "memory");
+// One more commit by the MMA-issuing thread and a bounded wait for it: every tcgen05.mma
+// this thread issued has completed (tensor memory may then be freed).
+__device__ __forceinline__ void drain_mma(uint64_t* bar, unsigned* err) {
+    umma_commit(bar);
+    if (!mbar_wait(bar, 0)) atomicOr(err, 16u);
 }
 
-// TMA load delivered to this shared-memory offset (and mbarrier) in every CTA of mask
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
-                                               uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
-        "%3}], [%4], %5;" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "h"(mask)
-        : "memory");
-}
-
-// all threads of every CTA in the cluster
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     uint32_t r[32];
@@ -184,6 +176,7 @@ struct Smem {
     uint64_t raw_full[STAGES_1];  // FP32-input variant: the TMA bytes of a stage have landed
     uint64_t acc_full[2];
     uint64_t acc_empty[2];
+    uint64_t drain;  // the MMA issuer's last commit (all its MMAs complete)
     uint32_t tmem_base;
 };
 
@@ -309,28 +302,23 @@ __device__ __forceinline__ void two_sum_into(float& hi, float& lo, float x) {
 }
 
 //
-// CL = 2: clusters of two CTAs work on neighbouring 128-point blocks against the same
-// 256-slice tile; each CTA loads its own A tile and one half of the B tile, the B halves
-// multicast into both CTAs' shared memory, so the directions are read from L2 once per
-// cluster instead of once per CTA.  A stage is refilled only after both CTAs' MMAs have
-// released it (the MMA commit arrives on the empty barriers of both CTAs).
-// Work items: item -> slice tile (item % col_tiles), point blocks (item / col_tiles) * CL + rank.
-template <int EPI, int CL, bool CVT>
+// Work items: item -> slice tile (item % col_tiles), point block (item / col_tiles).
+// Each CTA loads its own A and B tiles into its own shared memory (no loads are shared
+// between CTAs).
+template <int EPI, bool CVT>
 __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256, 1)
     k_umma_project(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int n, int P,
                    int d, int col_tiles, int tiles, float* __restrict__ Z, int64_t ldz, float* __restrict__ absmax,
                    unsigned* __restrict__ err, const float* __restrict__ rs, float scale, ChebEpi ce) {
-    static_assert(CL == 1 || CL == 2, "cluster of one or two CTAs");
-    static_assert(!CVT || (EPI == EPI_CHEB && CL == 2), "FP32 targets: fused target epilogue, CTA pairs");
+    static_assert(!CVT || EPI == EPI_CHEB, "FP32 targets: fused target epilogue only");
     using G = Geo<CVT>;
     constexpr bool ROWMAJOR = EPI == EPI_ROW;
-    const int rank = CL > 1 ? static_cast<int>(blockIdx.x % CL) : 0;
-    int unit = static_cast<int>(blockIdx.x / CL), nunits = static_cast<int>(gridDim.x / CL);
-    // EPI_MOM: a cluster keeps one group of CL slice blocks for all its point tiles, so its
-    // threads can accumulate their slices' moments across tiles
+    int unit = static_cast<int>(blockIdx.x), nunits = static_cast<int>(gridDim.x);
+    // EPI_MOM: a CTA keeps one slice block for all its point tiles, so its threads can
+    // accumulate their slices' moments across tiles
     int mom_group = 0, mom_chunk_id = -1;
     if (EPI == EPI_MOM) {
-        const int groups = (static_cast<int>((n + BM - 1) / BM) + CL - 1) / CL;
+        const int groups = static_cast<int>((n + BM - 1) / BM);
         const int per_group = nunits / groups;
         mom_group = unit % groups;
         mom_chunk_id = unit / groups < per_group ? unit / groups : -1;
@@ -338,7 +326,7 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256,
         nunits = per_group > 0 ? per_group : 1;
     }
     auto row_of = [&](int item) {
-        return EPI == EPI_MOM ? (mom_group * CL + rank) * BM : ((item / col_tiles) * CL + rank) * BM;
+        return EPI == EPI_MOM ? mom_group * BM : (item / col_tiles) * BM;
     };
     auto col_of = [&](int item) { return EPI == EPI_MOM ? item * BN : (item % col_tiles) * BN; };
     constexpr int EPI_WARPS = EPI == EPI_CHEB || EPI == EPI_MOM ? 8 : 4;
@@ -355,13 +343,14 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256,
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&sm->full[s], CVT ? 96 : 1);  // CVT: one arrival per converter thread
-            mbar_init(&sm->empty[s], CL);  // one MMA commit per CTA of the cluster
+            mbar_init(&sm->empty[s], 1);  // one MMA commit
             mbar_init(&sm->raw_full[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sm->acc_full[b], 1);
             mbar_init(&sm->acc_empty[b], EPI_WARPS);  // one arrival per epilogue warp
         }
+        mbar_init(&sm->drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // Chebyshev coefficients in shared memory (after the Smem struct), degree-major
@@ -382,8 +371,6 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256,
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // the peer's barriers must be initialised before anything is multicast into them
-    if (CL > 1) cluster_sync();
     const uint32_t tmem = sm->tmem_base;
 
     if (!CVT && warp == 0 && lane == 0) {
@@ -402,23 +389,13 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256,
                 unsigned char* st = base + s * STAGE_BYTES;
                 mbar_expect_tx(&sm->full[s], STAGE_BYTES);
                 tma_load_2d(st, &map_a, &sm->full[s], kb * BK, row0);
-                if constexpr (CL == 1) {
-                    tma_load_2d(st + A_BYTES, &map_b, &sm->full[s], kb * BK, col0);
-                } else {
-                    // this CTA's half of the directions, delivered to both CTAs
-                    tma_load_2d_mc(st + A_BYTES + rank * (B_BYTES / 2), &map_b, &sm->full[s], kb * BK,
-                                   col0 + rank * (BN / 2), static_cast<uint16_t>(0x3));
-                }
+                tma_load_2d(st + A_BYTES, &map_b, &sm->full[s], kb * BK, col0);
             }
         }
-        // wait until every stage this CTA filled has been released by both MMAs, so that
-        // no commit of the peer is still on its way to this CTA's barriers at exit
-        if (CL > 1 && ok)
-            for (int j = g > STAGES ? g - STAGES : 0; j < g; ++j)
-                if (!mbar_wait(&sm->empty[j % STAGES], (j / STAGES) & 1)) {
-                    atomicOr(err, 8u);
-                    break;
-                }
+        // Before the CTA may exit, the bytes of every stage it filled have landed: the
+        // last fill of each stage completed its full barrier (at once on the normal path,
+        // where the MMA issuer waited on them; bounded after an error on either side).
+        drain_fills(sm->full, STAGES, g);
     } else if (!CVT && warp == 1 && lane == 0) {
         // ---------------- MMA issuer
         const uint32_t idesc = instr_desc(1u, BM, BN);
@@ -447,11 +424,12 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256,
                     umma_f16(acc_t, smem_desc(st + k * 32), smem_desc(st + A_BYTES + k * 32), idesc,
                              (kb > 0 || k > 0) ? 1u : 0u);
                 }
-                if constexpr (CL == 1) umma_commit(&sm->empty[s]);
-                else umma_commit_mc(&sm->empty[s], static_cast<uint16_t>(0x3));
+                umma_commit(&sm->empty[s]);
             }
             umma_commit(&sm->acc_full[b]);
         }
+        // no MMA of this CTA may still write tensor memory when it is freed
+        drain_mma(&sm->drain, err);
     } else if (CVT && warp == 0) {
         // ---------------- control of the FP32-target variant (one thread): TMA loads, L2
         // prefetches and MMA issue in one loop over this CTA's stages g = (tile, k block).
@@ -464,18 +442,18 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256,
             int ntile = 0;
             for (int t = unit; t < tiles; t += nunits) ++ntile;
             const int total = ntile * kblocks;
+            int issued = 0;
             auto issue = [&](int gg) {
+                ++issued;
                 const int tile = unit + (gg / kblocks) * nunits, kb = gg % kblocks, s = gg % STAGES;
                 const int r0 = row_of(tile), c0 = col_of(tile);
                 unsigned char* st = base + s * STAGE_BYTES;
                 uint64_t* tb = &sm->raw_full[s];
                 mbar_expect_tx(tb, STAGE_BYTES);
-                // the two 32-column halves of this CTA's FP32 targets, and its half of the
-                // directions delivered to both CTAs
+                // the two 32-column halves of the FP32 targets, and the directions
                 tma_load_2d(st, &map_a, tb, kb * BK, r0);
                 tma_load_2d(st + BM * 128, &map_a, tb, kb * BK + 32, r0);
-                tma_load_2d_mc(st + A_BYTES + rank * (B_BYTES / 2), &map_b, tb, kb * BK, c0 + rank * (BN / 2),
-                               static_cast<uint16_t>(0x3));
+                tma_load_2d(st + A_BYTES, &map_b, tb, kb * BK, c0);
             };
             auto prefetch = [&](int gg) {
                 const int tile = unit + (gg / kblocks) * nunits, kb = gg % kblocks;
@@ -504,7 +482,7 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256,
                 for (int k = 0; k < BK / 16; ++k)
                     umma_f16(tmem + b * BN, smem_desc(st + k * 32), smem_desc(st + A_BYTES + k * 32), idesc,
                              (kb > 0 || k > 0) ? 1u : 0u);
-                umma_commit_mc(&sm->empty[s], static_cast<uint16_t>(0x3));
+                umma_commit(&sm->empty[s]);
                 if (kb == kblocks - 1) umma_commit(&sm->acc_full[b]);
                 const int gn = g + STAGES - 1;
                 if (gn < total) {
@@ -517,13 +495,11 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256,
                 }
                 if (g + PF < total) prefetch(g + PF);
             }
-            // every stage filled released by both MMAs before exit (no commit of the peer in flight)
-            if (ok)
-                for (int j = total > STAGES ? total - STAGES : 0; j < total; ++j)
-                    if (!mbar_wait(&sm->empty[j % STAGES], (j / STAGES) & 1)) {
-                        atomicOr(err, 8u);
-                        break;
-                    }
+            (void)ok;
+            // before exit: the TMA bytes of every issued stage have landed and no MMA still
+            // writes tensor memory (immediate on the normal path, bounded after an error)
+            drain_fills(sm->raw_full, STAGES, issued);
+            drain_mma(&sm->drain, err);
         }
     } else if (CVT && warp <= 3) {
         // ---------------- converters (warps 1-3): FP32 targets -> centred BF16 operand, in place
@@ -728,8 +704,6 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256,
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    // neither CTA leaves while the other may still deliver into its shared memory
-    if (CL > 1) cluster_sync();
     if (warp == 2) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
@@ -760,6 +734,7 @@ struct SmemX3 {
     uint64_t d1_full[X3_BUF];
     uint64_t d1_empty[X3_BUF];
     uint64_t accum;
+    uint64_t drain;
     uint32_t tmem_base;
 };
 
@@ -790,6 +765,7 @@ __global__ void __launch_bounds__(X3_THREADS, 1)
             mbar_init(&sm->d1_empty[b], 8);  // one arrival per epilogue warp
         }
         mbar_init(&sm->accum, 1);
+        mbar_init(&sm->drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 2) {
@@ -804,7 +780,8 @@ __global__ void __launch_bounds__(X3_THREADS, 1)
     const uint32_t tmem = sm->tmem_base;
 
     if (warp == 0 && lane == 0) {
-        for (int kb = 0; kb < kblocks; ++kb) {
+        int fills = 0;
+        for (int kb = 0; kb < kblocks; ++kb, ++fills) {
             const int s = kb % X3_STAGES;
             if (kb >= X3_STAGES && !mbar_wait(&sm->empty[s], ((kb / X3_STAGES) - 1) & 1)) {
                 atomicOr(err, 8u);
@@ -817,6 +794,7 @@ __global__ void __launch_bounds__(X3_THREADS, 1)
             tma_load_2d(st + A_BYTES + B_BYTES, &map_a2, &sm->full[s], kb * BK, row0);
             tma_load_2d(st + 2 * A_BYTES + B_BYTES, &map_b2, &sm->full[s], kb * BK, col0);
         }
+        drain_fills(sm->full, X3_STAGES, fills);
     } else if (warp == 1 && lane == 0) {
         const uint32_t idesc = instr_desc(0u, BM, X3_BN);
         const uint32_t d2 = tmem + X3_BUF * X3_BN;
@@ -849,6 +827,7 @@ __global__ void __launch_bounds__(X3_THREADS, 1)
             umma_commit(&sm->empty[s]);
         }
         umma_commit(&sm->accum);
+        drain_mma(&sm->drain, err);
     } else if (warp >= 4) {
         const int q = warp & 3, h = (warp - 4) >> 2;
         const int row = row0 + q * 32 + lane;
@@ -1030,70 +1009,37 @@ constexpr int epi_threads() {
     return EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : THREADS;
 }
 
-// Co-resident work units of the persistent kernel on the current device (SMs for CL = 1,
-// clusters of two CTAs for CL = 2); sets the kernel's shared-memory limit once.
-template <int EPI, int CL, bool CVT = false>
+// Co-resident CTAs of the persistent kernel on the current device (one per SM); sets the
+// kernel's shared-memory limit once.
+template <int EPI, bool CVT = false>
 int persistent_units() {
     static int units[128] = {};
     int dev = 0;
     SLK_CHECK_CUDA(cudaGetDevice(&dev));
     SLK_REQUIRE(dev >= 0 && dev < 128, "device index out of range");
     if (!units[dev]) {
-        SLK_CHECK_CUDA(cudaFuncSetAttribute(k_umma_project<EPI, CL, CVT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        SLK_CHECK_CUDA(cudaFuncSetAttribute(k_umma_project<EPI, CVT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             static_cast<int>(epi_smem<EPI, CVT>())));
         int sms = 0;
         SLK_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        if (CL == 1) {
-            units[dev] = sms;
-        } else {
-            cudaLaunchConfig_t cfg = {};
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = CL;
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            cfg.gridDim = dim3(static_cast<unsigned>(sms / CL * CL));
-            cfg.blockDim = dim3(epi_threads<EPI>());
-            cfg.dynamicSmemBytes = epi_smem<EPI, CVT>();
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            int clusters = 0;
-            SLK_CHECK_CUDA(cudaOccupancyMaxActiveClusters(&clusters, k_umma_project<EPI, CL, CVT>, &cfg));
-            SLK_REQUIRE(clusters > 0, "no cluster of the projection kernel fits on this device");
-            units[dev] = clusters;
-        }
+        units[dev] = sms;
     }
     return units[dev];
 }
 
-// Launch the persistent projection over n rows (A) and col_tiles 256-wide column tiles
-// (B); for CL = 2, map_b must have 128-row boxes (each CTA loads one half of a tile).
-template <int EPI, int CL, bool CVT = false>
+// Launch the persistent projection over n rows (A) and col_tiles 256-wide column tiles (B).
+template <int EPI, bool CVT = false>
 void launch_persistent(const CUtensorMap& ma, const CUtensorMap& mb, int64_t n, int P, int d, int col_tiles, float* Z,
                        int64_t ldz, float* absmax, unsigned* err, const float* rs, float scale, const ChebEpi& ce,
                        cudaStream_t st) {
-    const int64_t items = ceil_div(ceil_div(n, BM), CL) * col_tiles;
+    const int64_t items = ceil_div(n, BM) * col_tiles;
     SLK_REQUIRE(items < (int64_t(1) << 31) && n < (int64_t(1) << 31), "too many points for one projection");
-    const int64_t units = persistent_units<EPI, CL, CVT>();
-    const int64_t grid = (items < units ? items : units) * CL;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(static_cast<unsigned>(grid));
-    cfg.blockDim = dim3(epi_threads<EPI>());
-    cfg.dynamicSmemBytes = epi_smem<EPI, CVT>();
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = CL > 1 ? 1 : 0;
-    SLK_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_umma_project<EPI, CL, CVT>, ma, mb, static_cast<int>(n), P, d, col_tiles,
-                                      static_cast<int>(items), Z, ldz, absmax, err, rs, scale, ce));
+    const int64_t units = persistent_units<EPI, CVT>();
+    const int64_t grid = items < units ? items : units;
+    k_umma_project<EPI, CVT><<<static_cast<unsigned>(grid), epi_threads<EPI>(), epi_smem<EPI, CVT>(), st>>>(
+        ma, mb, static_cast<int>(n), P, d, col_tiles, static_cast<int>(items), Z, ldz, absmax, err, rs, scale, ce);
+    SLK_CHECK_LAUNCH();
 }
-
-// Clusters of two for the forward projections (B multicast); 1 = one CTA per tile.
-constexpr int kProjCluster = 2;
 
 int sm_count_dev() {
     static int sms[128] = {};
@@ -1140,11 +1086,11 @@ void launch_umma_cheb_target(const void* xa, int64_t n, const void* xib, int P, 
     SLK_REQUIRE(umma_cheb_fits(P, q), "Chebyshev coefficients do not fit the fused kernel");
     const int64_t ld = umma_operand_ld(d);
     CUtensorMap ma = make_map(xa, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, n, d, ld, BM);
-    CUtensorMap mb = make_map(xib, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, P, d, ld, BN / kProjCluster);
+    CUtensorMap mb = make_map(xib, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, P, d, ld, BN);
     const int col_tiles = static_cast<int>(ceil_div(P, BN));
     ChebEpi ce{coef, q, horner, static_cast<float>(1.0 / R), static_cast<float>(R), part, ldp};
     SLK_TIMED("umma_cheb_target", st);
-    launch_persistent<EPI_CHEB, kProjCluster>(ma, mb, n, P, d, col_tiles, nullptr, 0, nullptr, err, nullptr, 1.0f, ce,
+    launch_persistent<EPI_CHEB>(ma, mb, n, P, d, col_tiles, nullptr, 0, nullptr, err, nullptr, 1.0f, ce,
                                               st);
 }
 
@@ -1160,20 +1106,20 @@ void launch_umma_cheb_target_f32(const float* y, int64_t ldy, const float* mu, i
     SLK_REQUIRE(umma_f32_operand_ok(y, ldy), "FP32 targets need 16-byte aligned rows");
     const int64_t ld = umma_operand_ld(d);
     CUtensorMap ma = make_map_f32(y, n, d, ldy, BM);
-    CUtensorMap mb = make_map(xib, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, P, d, ld, BN / kProjCluster);
+    CUtensorMap mb = make_map(xib, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, P, d, ld, BN);
     const int col_tiles = static_cast<int>(ceil_div(P, BN));
     ChebEpi ce{coef, q, horner, static_cast<float>(1.0 / R), static_cast<float>(R), part, ldp};
     ce.mu = mu;
     SLK_TIMED("umma_cheb_target", st);
-    launch_persistent<EPI_CHEB, kProjCluster, true>(ma, mb, n, P, d, col_tiles, nullptr, 0, nullptr, err, nullptr,
+    launch_persistent<EPI_CHEB, true>(ma, mb, n, P, d, col_tiles, nullptr, 0, nullptr, err, nullptr,
                                                     1.0f, ce, st);
 }
 
 bool umma_moments_fit(int q) { return q == 8 || q == 10 || q == 12 || q == 16; }
 
 int64_t umma_moments_chunks(int P) {
-    const int groups = static_cast<int>((ceil_div(P, BM) + kProjCluster - 1) / kProjCluster);
-    const int units = persistent_units<EPI_MOM, kProjCluster>();
+    const int groups = static_cast<int>(ceil_div(P, BM));
+    const int units = persistent_units<EPI_MOM>();
     SLK_REQUIRE(units >= groups, "too many slices for the fused moments kernel");
     return 2 * static_cast<int64_t>(units / groups);
 }
@@ -1183,11 +1129,11 @@ void launch_umma_moments(const void* xa, int64_t n, const void* xib, int P, int 
     SLK_REQUIRE(umma_moments_fit(q), "Chebyshev term count unsupported by the fused moments kernel");
     SLK_REQUIRE(n < (int64_t(1) << 31), "too many points for one projection");
     const int64_t ld = umma_operand_ld(d);
-    // A = directions (slices as rows), B = points (this CTA's half of a 256-point tile)
+    // A = directions (slices as rows), B = points (256-point tiles)
     CUtensorMap ma = make_map(xib, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, P, d, ld, BM);
-    CUtensorMap mb = make_map(xa, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, n, d, ld, BN / kProjCluster);
-    const int groups = static_cast<int>((ceil_div(P, BM) + kProjCluster - 1) / kProjCluster);
-    const int units = persistent_units<EPI_MOM, kProjCluster>();
+    CUtensorMap mb = make_map(xa, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, n, d, ld, BN);
+    const int groups = static_cast<int>(ceil_div(P, BM));
+    const int units = persistent_units<EPI_MOM>();
     const int per_group = units / groups;
     const int point_tiles = static_cast<int>(ceil_div(n, BN));
     ChebEpi ce{};
@@ -1197,23 +1143,13 @@ void launch_umma_moments(const void* xa, int64_t n, const void* xib, int P, int 
     ce.w = w;
     ce.npts = static_cast<int>(n);
     ce.mom = mom;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kProjCluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(static_cast<unsigned>(per_group * groups * kProjCluster));
-    cfg.blockDim = dim3(epi_threads<EPI_MOM>());
-    cfg.dynamicSmemBytes = epi_smem<EPI_MOM, false>();
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = kProjCluster > 1 ? 1 : 0;
     SLK_TIMED("umma_cheb_moments", st);
     // "n" of the kernel is the row count (slices), "P" the column count (points)
-    SLK_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_umma_project<EPI_MOM, kProjCluster, false>, ma, mb, P,
-                                      static_cast<int>(n), d, point_tiles, point_tiles, static_cast<float*>(nullptr),
-                                      int64_t(0), absmax, err, static_cast<const float*>(nullptr), 1.0f, ce));
+    k_umma_project<EPI_MOM, false><<<static_cast<unsigned>(per_group * groups), epi_threads<EPI_MOM>(),
+                                     epi_smem<EPI_MOM, false>(), st>>>(
+        ma, mb, P, static_cast<int>(n), d, point_tiles, point_tiles, static_cast<float*>(nullptr), int64_t(0), absmax,
+        err, static_cast<const float*>(nullptr), 1.0f, ce);
+    SLK_CHECK_LAUNCH();
 }
 
 void launch_grad_umma(const void* g16, int64_t M, int P, const void* xit16, int d, const float* gs, double scale,
@@ -1225,7 +1161,7 @@ void launch_grad_umma(const void* g16, int64_t M, int P, const void* xit16, int 
     CUtensorMap mb = make_map(xit16, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, d, P, ld, BN);
     const int col_tiles = static_cast<int>(ceil_div(d, BN));
     SLK_TIMED("umma_grad_bf16", st);
-    launch_persistent<EPI_ROW, 1>(ma, mb, M, d, P, col_tiles, gy, ldg, nullptr, err, gs, static_cast<float>(scale),
+    launch_persistent<EPI_ROW>(ma, mb, M, d, P, col_tiles, gy, ldg, nullptr, err, gs, static_cast<float>(scale),
                                   ChebEpi{}, st);
 }
 
@@ -1275,9 +1211,8 @@ void launch_project_umma(const void* xa, const void* xa_lo, int64_t n, const voi
         k_umma_project_x3<<<grid, X3_THREADS, x3_smem_bytes(), st>>>(ma, mb, ma2, mb2, static_cast<int>(n), P, d,
                                                                      col_tiles, Z, ldz, absmax, err);
     } else {
-        CUtensorMap mbh = kProjCluster > 1 ? make_map(xib, dt, P, d, ld, BN / kProjCluster) : mb;
         SLK_TIMED("umma_project_bf16", st);
-        launch_persistent<EPI_Z, kProjCluster>(ma, mbh, n, P, d, col_tiles, Z, ldz, absmax, err, nullptr, 1.0f,
+        launch_persistent<EPI_Z>(ma, mb, n, P, d, col_tiles, Z, ldz, absmax, err, nullptr, 1.0f,
                                                ChebEpi{}, st);
     }
     SLK_CHECK_LAUNCH();

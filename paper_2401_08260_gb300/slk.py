@@ -81,6 +81,7 @@ _SIGNATURES = {
     "slk_sum_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "slk_launch_count": (ctypes.c_int64, []),
+    "slk_device_alloc_count": (ctypes.c_int64, []),
     "slk_timing_enable": (ctypes.c_int, [ctypes.c_int32]),
     "slk_timing_read": (ctypes.c_int, [ctypes.POINTER(KernelTime), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "slk_timing_reset": (ctypes.c_int, []),

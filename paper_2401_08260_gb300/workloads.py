@@ -18,7 +18,8 @@ Named workloads (sizes at full scale):
                      BF16 projection.
 * ``negdist_d3072``  negative distance, N = M = 2e5, d = 3072, x ~ N(0, I),
                      y ~ N(0.5 * 1, I), w ~ U[0,1], P = 1000, FP32 (tensor-core
-                     projection with FP32-level accuracy), FP64 prefix sums.
+                     projection with FP32-level accuracy), exact prefix sums
+                     (double-float within chunks, FP64 per chunk and bucket).
 * ``laplace_d50``    Laplacian exp(-alpha r) with alpha = 1/sqrt(50) (length scale
                      sqrt(d)), 10-component Gaussian mixture (means ~ N(0, 4I),
                      unit covariance, equal weights) for x and y, d = 50,
