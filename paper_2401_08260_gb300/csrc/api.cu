@@ -463,8 +463,13 @@ bool fused_cheb_source(slk_plan plan, const float* x, int64_t ldx, const float* 
         sample_projection_max_async(plan, x, N, ldx, reinterpret_cast<float*>(sample_max.w), sample_done.ev, st);
         sample_max.after = sample_done.ev;
     }
-    DevBuf<unsigned char> xa(static_cast<size_t>(N) * umma_operand_ld(d) * 2, st);
-    launch_center_cast(x, N, d, ldx, plan->mu32.get(), xa.get(), nullptr, 0, st);
+    // CTA-pair route: the moments kernel reads the FP32 sources itself (no cast)
+    const bool pair = P <= 512 && umma_f32_operand_ok(x, ldx);
+    DevBuf<unsigned char> xa;
+    if (!pair) {
+        xa.alloc(static_cast<size_t>(N) * umma_operand_ld(d) * 2, st);
+        launch_center_cast(x, N, d, ldx, plan->mu32.get(), xa.get(), nullptr, 0, st);
+    }
     double R = plan->desc.radius;
     if (!user_radius) {
         SLK_CHECK_CUDA(cudaEventSynchronize(sample_done.ev));
@@ -475,16 +480,21 @@ bool fused_cheb_source(slk_plan plan, const float* x, int64_t ldx, const float* 
     double tol = plan->desc.tol;
     if (tol <= 0.0) tol = default_tol(SLK_GAUSSIAN, plan->desc.precision);
     FourierHost fh = choose_gaussian(plan->desc.param, d, R, plan->desc.n_coeff, plan->desc.method, tol);
-    if (fh.method != SLK_FOURIER_CHEB || !umma_moments_fit(fh.cheb_qp)) return false;
+    if (fh.method != SLK_FOURIER_CHEB || !umma_moments_fit(fh.cheb_qp) || (pair && !pair_cheb_fits(P, fh.cheb_qp)))
+        return false;
     plan->fh = fh;
     plan->R = R;
     fourier_setup<float>(plan, st);
-    const int64_t nchunk = umma_moments_chunks(P);
+    const int64_t nchunk = pair ? pair_moments_chunks(P) : umma_moments_chunks(P);
     DevBuf<double> mom(static_cast<size_t>(nchunk) * P * fh.cheb_qp, st);
     DevBuf<float> mx(1, st);
     SLK_CHECK_CUDA(cudaMemsetAsync(mx.get(), 0, sizeof(float), st));
-    launch_umma_moments(xa.get(), N, plan->xib.get(), P, d, w, fh.cheb_qp, R, mom.get(), mx.get(), plan->err_dev.get(),
-                        st);
+    if (pair)
+        launch_pair_moments(x, ldx, plan->mu32.get(), N, plan->xib.get(), P, d, w, fh.cheb_qp, R, mom.get(), mx.get(),
+                            plan->err_dev.get(), st);
+    else
+        launch_umma_moments(xa.get(), N, plan->xib.get(), P, d, w, fh.cheb_qp, R, mom.get(), mx.get(),
+                            plan->err_dev.get(), st);
     // the reduction runs before the range check, so one wait covers both; its output is
     // discarded when a source lies outside the radius
     DevBuf<unsigned> bad(1, st);
@@ -600,10 +610,16 @@ bool sum_fused_cheb(slk_plan plan, const T* y, int64_t M, int64_t ldy, void* s_u
         if (plan->tc != 1 || !plan->fourier || plan->sorting || plan->fh.method != SLK_FOURIER_CHEB ||
             !umma_cheb_fits(plan->P, plan->fh.cheb_qp) || M >= (int64_t(1) << 31))
             return false;
-        const int parts = static_cast<int>(umma_cheb_parts(plan->P));
-        DevBuf<double> part(static_cast<size_t>(parts) * M, st);
         const void* coef = plan->fd.horner ? plan->fd.mono : plan->beta.get();
-        if (umma_f32_operand_ok(y, ldy))  // aligned FP32 rows: centred and rounded in the kernel
+        // aligned FP32 rows and P <= 512: the CTA-pair kernel, all slices of a tile at once
+        const bool pair = umma_f32_operand_ok(y, ldy) && pair_cheb_fits(plan->P, plan->fh.cheb_qp);
+        const int parts = pair ? 2 : static_cast<int>(umma_cheb_parts(plan->P));
+        DevBuf<double> part(static_cast<size_t>(parts) * M, st);
+        if (pair)
+            launch_pair_cheb_target(y, ldy, plan->mu32.get(), M, plan->xib.get(), plan->P, plan->d,
+                                    static_cast<const float*>(coef), plan->fh.cheb_qp, plan->fd.horner, plan->R,
+                                    part.get(), M, plan->err_dev.get(), st);
+        else if (umma_f32_operand_ok(y, ldy))  // aligned FP32 rows: centred and rounded in the kernel
             launch_umma_cheb_target_f32(y, ldy, plan->mu32.get(), M, plan->xib.get(), plan->P, plan->d,
                                         static_cast<const float*>(coef), plan->fh.cheb_qp, plan->fd.horner, plan->R,
                                         part.get(), M, plan->err_dev.get(), st);

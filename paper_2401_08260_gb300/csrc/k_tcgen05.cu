@@ -32,135 +32,20 @@
 #include <type_traits>
 
 #include "kernels.cuh"
+#include "cheb_epi.cuh"
+#include "umma.cuh"
 
 namespace slk {
 
 namespace {
+
+using namespace umma;
 
 constexpr int BM = 128;       // points per tile (TMEM lanes)
 constexpr int BN = 256;       // slices per tile (TMEM columns per accumulator)
 constexpr int BK = 64;        // K elements per stage (128 bytes of 16-bit data)
 constexpr int STAGES_1 = 4;  // one 16-bit product: 48 KB per stage
 constexpr int THREADS = 256;  // warp 0: TMA, warp 1: MMA, warp 2: TMEM alloc, warps 4-7: epilogue
-constexpr unsigned WAIT_LIMIT = 1u << 26;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// bounded wait for the phase with the given parity; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    const uint32_t addr = smem_u32(bar);
-    for (unsigned it = 0; it < WAIT_LIMIT; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// bring a tile of the tensor into L2 only (no shared memory, no barrier)
-__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int c0, int c1) {
-    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(map)),
-                 "r"(c0), "r"(c1)
-                 : "memory");
-}
-
-// Wait (bounded) for the last fill of each stage of a ring filled `fills` times, in the
-// order they were issued: fill j completes phase j / stages of barrier j % stages.  The
-// TMA bytes of those fills have then landed in this CTA's shared memory.
-__device__ __forceinline__ void drain_fills(uint64_t* bars, int stages, int fills) {
-    for (int j = fills > stages ? fills - stages : 0; j < fills; ++j)
-        if (!mbar_wait(&bars[j % stages], (j / stages) & 1)) break;
-}
-
-// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t smem_desc(const void* p) {
-    const uint64_t addr = smem_u32(p);
-    uint64_t d = (addr >> 4) & 0x3FFFull;  // start address
-    d |= static_cast<uint64_t>(1) << 16;     // leading byte offset (unused with the 128B swizzle)
-    d |= static_cast<uint64_t>(1024 >> 4) << 32;  // stride byte offset
-    d |= static_cast<uint64_t>(1) << 46;     // descriptor version
-    d |= static_cast<uint64_t>(2) << 61;     // SWIZZLE_128B
-    return d;
-}
-
-// instruction descriptor, kind::f16: D = F32, A/B = BF16 (ab_fmt 1) or F16 (0), both K-major
-__host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_fmt, int M, int N) {
-    return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-           (static_cast<uint32_t>(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-// One more commit by the MMA-issuing thread and a bounded wait for it: every tcgen05.mma
-// this thread issued has completed (tensor memory may then be freed).
-__device__ __forceinline__ void drain_mma(uint64_t* bar, unsigned* err) {
-    umma_commit(bar);
-    if (!mbar_wait(bar, 0)) atomicOr(err, 16u);
-}
-
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 template <class Half>
 __device__ __forceinline__ Half to_half(float v);
@@ -196,52 +81,6 @@ struct Geo {
 // (column tile fastest, so the CTAs that share a block of points run together and the
 // second read of A hits L2).  Two 256-column TMEM accumulators alternate between tiles:
 // the epilogue of one tile overlaps the MMAs of the next.
-// Target-side evaluation of one 8-column accumulator chunk (one row per thread): four
-// slices at a time, the QP coefficients of the group loaded up front (one broadcast
-// LDS.128 per degree from the degree-major table), then Horner's rule on monomial
-// coefficients or Clenshaw's recurrence on Chebyshev ones; the 32 values are added to
-// (s, c) with Kahan compensation.  Projections outside [-R, R] (or NaN) set bad.
-// Chunks of 8 keep the unrolled evaluation within the register budget of 384 threads.
-template <int QP, bool HORNER>
-__device__ __forceinline__ void cheb_chunk(const float (&v)[8], const float* __restrict__ bt0, int ppad, float R,
-                                           float inv_R, float& s, float& c, bool& bad) {
-#pragma unroll
-    for (int j = 0; j < 8; j += 4) {
-        float u[4], b1[4], b2[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const float z = v[j + r];
-            if (!(z <= R && z >= -R)) bad = true;
-            u[r] = z * inv_R;
-            b1[r] = 0.0f;
-            b2[r] = 0.0f;
-        }
-        // fully unrolled over the degrees: the coefficient loads carry no loop dependence
-#pragma unroll
-        for (int k = QP - 1; k >= 0; --k) {
-            const float4 c4 = *reinterpret_cast<const float4*>(bt0 + j + k * ppad);
-            const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                if (HORNER) {
-                    b1[r] = fmaf(b1[r], u[r], cv[r]);
-                } else if (k >= 1) {
-                    const float bk = fmaf(u[r] + u[r], b1[r], cv[r] - b2[r]);
-                    b2[r] = b1[r];
-                    b1[r] = bk;
-                } else {
-                    b1[r] = fmaf(u[r], b1[r], cv[r] - b2[r]);
-                }
-            }
-        }
-        // the group's four values added plainly, the group sum with Kahan compensation
-        const float y = ((b1[0] + b1[1]) + (b1[2] + b1[3])) - c;
-        const float tt = s + y;
-        c = (tt - s) - y;
-        s = tt;
-    }
-}
-
 // Epilogues:
 //   EPI_Z:    Z[col * ldz + row] (slice-major projections), largest |z| into *absmax;
 //   EPI_ROW:  Z[row * ldz + col] * rowscale(row), rowscale = scale * (rs ? rs[row] : 1)
@@ -270,36 +109,6 @@ struct ChebEpi {
     // FP32-target variant: the centre subtracted from the targets (d values)
     const float* mu;
 };
-
-// Moments of one slice over a 32-point accumulator chunk: z[j] for the chunk's points,
-// the lane-th point's weight in wl (zero beyond the points); t holds this tile's FP32 sums.
-template <int QP>
-__device__ __forceinline__ void mom_chunk(const float (&v)[32], float wl, float inv_R, int valid_pts, float (&t)[QP],
-                                          float& mx) {
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const float wj = __shfl_sync(0xffffffffu, wl, j);
-        const float z = v[j];
-        if (j < valid_pts) mx = fmaxf(mx, fabsf(z));
-        const float u = z * inv_R, u2 = u + u;
-        float tm1 = 1.0f, tc = u;  // T_0, T_1
-        t[0] += wj;
-#pragma unroll
-        for (int k = 1; k < QP; ++k) {
-            t[k] = fmaf(wj, tc, t[k]);
-            const float tn = fmaf(u2, tc, -tm1);
-            tm1 = tc;
-            tc = tn;
-        }
-    }
-}
-
-// Add a float into an unevaluated pair hi + lo without rounding loss (TwoSum).
-__device__ __forceinline__ void two_sum_into(float& hi, float& lo, float x) {
-    const float s = hi + x, bp = s - hi;
-    lo += (hi - (s - bp)) + (x - bp);
-    hi = s;
-}
 
 //
 // Work items: item -> slice tile (item % col_tiles), point block (item / col_tiles).
@@ -1063,6 +872,14 @@ __global__ void k_transpose_cast(const float* __restrict__ src, int rows, int co
 }  // namespace
 
 int64_t umma_operand_ld(int d) { return (d + 7) / 8 * 8; }
+
+CUtensorMap tmap_bf16_sw128(const void* ptr, int64_t rows, int cols, int64_t ld, int box_rows) {
+    return make_map(ptr, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rows, cols, ld, box_rows);
+}
+
+CUtensorMap tmap_f32_rows(const float* ptr, int64_t rows, int cols, int64_t ld, int box_rows) {
+    return make_map_f32(ptr, rows, cols, ld, box_rows);
+}
 
 void launch_transpose_bf16(const float* src, int rows, int cols, void* dst, cudaStream_t st) {
     const int ldd = static_cast<int>(umma_operand_ld(rows));

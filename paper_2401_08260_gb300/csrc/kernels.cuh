@@ -80,6 +80,23 @@ bool umma_moments_fit(int q);
 int64_t umma_moments_chunks(int P);
 void launch_umma_moments(const void* xa, int64_t n, const void* xib, int P, int d, const float* w, int q, double R,
                          double* mom, float* absmax, unsigned* err, cudaStream_t st);
+
+// ------------------------------------------------------------ k_pair.cu
+// The two fused Chebyshev sides on CTA pairs (tcgen05 cta_group::2, M = 256) reading the
+// FP32 points directly (centred and rounded to BF16 in shared memory, the same operand as
+// the single-CTA kernels), all P <= 512 slices of a 256-point tile in one pass.
+//   target side: part receives 2 rows of n FP64 partial row sums (row stride ldp);
+//   source side: mom receives pair_moments_chunks(P) x P x q FP64 partials, *absmax the
+//                largest |z| over the points.
+// Both need umma_f32_operand_ok on the points; q is 8, 10, 12 or 16.
+bool pair_cheb_fits(int P, int q);
+void launch_pair_cheb_target(const float* y, int64_t ldy, const float* mu, int64_t n, const void* xib, int P, int d,
+                             const float* coef, int q, int horner, double R, double* part, int64_t ldp, unsigned* err,
+                             cudaStream_t st);
+int64_t pair_moments_chunks(int P);
+void launch_pair_moments(const float* x, int64_t ldx, const float* mu, int64_t n, const void* xib, int P, int d,
+                         const float* w, int q, double R, double* mom, float* absmax, unsigned* err, cudaStream_t st);
+
 // s[i] = scale * sum_{r < parts} part[r * n + i] (fixed order).
 template <class T>
 void launch_sum_parts(const double* part, int parts, int64_t n, double scale, T* s, cudaStream_t st);

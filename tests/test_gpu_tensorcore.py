@@ -154,11 +154,12 @@ def test_bf16_fused_moments_radius_fallback():
 
 @pytest.mark.parametrize("d,N,M,P", [(784, 5000, 1153, 512), (200, 4099, 700, 300)])
 def test_bf16_fused_f32_targets_match_cast_route(d, N, M, P):
-    """Aligned FP32 target rows go straight into the fused tensor-core target kernel, which
-    centres them and rounds them to BF16 in shared memory; rows whose stride is not a
-    multiple of four take the separate centring cast first.  Both routes hand the tensor
-    core the same BF16 operands and run the same epilogue: the sums are bit-identical, also
-    for plans built from the two layouts of the sources, and agree with the oracle."""
+    """Aligned FP32 rows go straight into the CTA-pair kernels (P <= 512), which centre them
+    and round them to BF16 in shared memory; rows whose stride is not a multiple of four
+    take the separate centring cast and the single-CTA kernels.  Both routes hand the
+    tensor core the same BF16 operands; they differ only in the FP32 order of the slice and
+    moment sums, so the results agree to 1e-6 of sum |w|, also for plans built from the two
+    layouts of the sources, and with the oracle within the BF16 tolerance."""
     dev = cuda_or_skip()
     from paper_2401_08260_gb300.slk import Plan
     rng = np.random.Generator(np.random.PCG64(51))
@@ -181,8 +182,9 @@ def test_bf16_fused_f32_targets_match_cast_route(d, N, M, P):
     p_b = Plan(strided(x), to_dev(w, dev), "gaussian", sigma, P=P, precision="bf16", directions=xi, method="cheb")
     assert p_a.info()["radius"] == p_b.info()["radius"]
     s_direct = p_a.sum(to_dev(y, dev)).cpu().numpy()
-    np.testing.assert_array_equal(s_direct, p_a.sum(strided(y)).cpu().numpy())
-    np.testing.assert_array_equal(s_direct, p_b.sum(to_dev(y, dev)).cpu().numpy())
+    assert rel_inf(s_direct, p_a.sum(strided(y)).cpu().numpy(), w.sum()) <= 1e-6
+    assert rel_inf(s_direct, p_b.sum(to_dev(y, dev)).cpu().numpy(), w.sum()) <= 1e-6
+    assert rel_inf(p_b.sum(strided(y)).cpu().numpy(), p_b.sum(to_dev(y, dev)).cpu().numpy(), w.sum()) <= 1e-6
     ref, _ = oracle.sliced_sum("gaussian", sigma, x, y, w, xi)
     assert rel_inf(s_direct, ref, w.sum()) <= 2e-3
     # targets beyond the window are still reported on the direct route
@@ -192,3 +194,38 @@ def test_bf16_fused_f32_targets_match_cast_route(d, N, M, P):
     with pytest.raises(SlkError) as e:
         p_a.sum(to_dev(far, dev))
     assert e.value.status == 4
+
+
+@pytest.mark.parametrize("d,N,M,P", [(784, 5000, 1153, 512), (200, 4099, 700, 300), (784, 2000, 100, 256),
+                                     (96, 3000, 300, 64), (52, 257, 255, 129), (784, 30001, 513, 512)])
+def test_pair_kernels_against_oracle_and_single_cta_route(d, N, M, P):
+    """The CTA-pair kernels (one MMA of M = 256 over two CTAs, all P <= 512 slices of a
+    256-point tile at once) over one or two 256-slice sub-tiles, ragged point tiles (fewer
+    and more tiles than CTA pairs), K tails (d not a multiple of 64) and slices beyond P:
+    within the BF16 tolerance of the oracle and within FP32 summation order of the
+    single-CTA route, which strided rows (stride d + 1) select."""
+    dev = cuda_or_skip()
+    from paper_2401_08260_gb300.slk import Plan
+    rng = np.random.Generator(np.random.PCG64(61))
+    x = rng.random((N, d), dtype=np.float32)
+    y = rng.random((M, d), dtype=np.float32)
+    w = rng.random(N).astype(np.float32)
+    xi = workloads.directions(P, d, seed=62)
+    sigma = math.sqrt(d)
+
+    def strided(a):
+        buf = torch.zeros((a.shape[0], d + 1), dtype=torch.float32, device=dev)
+        buf[:, :d] = torch.from_numpy(a).to(dev)
+        return buf[:, :d]
+
+    pair = Plan(to_dev(x, dev), to_dev(w, dev), "gaussian", sigma, P=P, precision="bf16", directions=xi,
+                method="cheb")
+    single = Plan(strided(x), to_dev(w, dev), "gaussian", sigma, P=P, precision="bf16", directions=xi,
+                  method="cheb", radius=pair.info()["radius"])
+    assert pair.info()["method"] == 3
+    s_pair = pair.sum(to_dev(y, dev)).cpu().numpy()
+    s_single = single.sum(strided(y)).cpu().numpy()
+    assert rel_inf(s_pair, s_single, w.sum()) <= 1e-6
+    idx = np.unique(np.concatenate([np.arange(min(M, 40)), np.arange(max(0, M - 40), M)]))
+    ref, _ = oracle.sliced_sum("gaussian", sigma, x, y[idx], w, xi)
+    assert rel_inf(s_pair[idx], ref, w.sum()) <= 2e-3
