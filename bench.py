@@ -111,12 +111,10 @@ def plan_kwargs(wl, args):
 
 
 # DRAM read + write per point of one launch, from the ncu captures (summarised under
-# profiles/) of the d = 784, P = 512 BF16 workload at n = 2e5 points: the centring cast and
-# the target kernel that reads the FP32 targets itself; the traffic of these kernels grows
-# in proportion to the points.  An entry is valid only for the
-# kernel as captured and is removed when that kernel changes.
-NCU_TRAFFIC_PER_POINT = {("gauss_d784", "center_cast"): (627.233024e6 + 281.766400e6) / 2e5,
-                         ("gauss_d784", "umma_cheb_target"): (628.377600e6 + 8.614912e6) / 2e5}
+# profiles/) of the d = 784, P = 512 BF16 workload at n = 2e5 points; the traffic of these
+# kernels grows in proportion to the points.  An entry is valid only for the kernel as
+# captured and is removed when that kernel changes.
+NCU_TRAFFIC_PER_POINT = {}
 
 
 def f32_direct(wl, kernels):
@@ -134,10 +132,10 @@ def step_points(wl, kernel_name, kernels):
     S = min(4096, wl.N) if "gather_rows" in kernels else 0
     if kernel_name.startswith("center_cast"):
         return wl.N + S if f32_direct(wl, kernels) else wl.N + wl.M + S
-    if kernel_name.startswith(("umma_cheb_moments", "cheb_moments", "ndft_source", "spread")):
+    if kernel_name.startswith(("umma_cheb_moments", "pair_cheb_moments", "cheb_moments", "ndft_source", "spread")):
         return wl.N
-    if kernel_name.startswith(("umma_cheb_target", "umma_grad", "cheb_target", "ndft_target", "nfft_target",
-                               "negdist_target")):
+    if kernel_name.startswith(("umma_cheb_target", "pair_cheb_target", "umma_grad", "cheb_target", "ndft_target",
+                               "nfft_target", "negdist_target")):
         return wl.M
     if kernel_name.startswith(("umma_project", "gemm")) and S:
         return S
@@ -164,18 +162,24 @@ def algorithmic(wl, info, precision, kernel_name, launches_per_step, kernels, P=
     per slice-point (FP32 ALU).  Centring cast: 4 d bytes read + 2 ld16 (x2 for the
     hi/lo split) written per point, plus, with the gradient, the same for the M x P
     per-slice derivatives it casts.  Other kernels: the 4-byte projections they read.
-    The fused Chebyshev target kernel that reads the FP32 rows itself moves 4 d bytes per
-    target plus 16 bytes per 256-slice tile of FP64 partial sums beside its 2 d P flop; at
-    d = 784, P = 512 the two minimum times are within 5% of each other, and the bound
-    reported is the one with the longer minimum time under `peaks` (HBM copy bandwidth,
-    sustained BF16).
+    The fused Chebyshev kernels that read the FP32 rows themselves move 4 d bytes per point
+    (plus 16 bytes of FP64 partial sums per target, or the 4-byte weight per source) beside
+    their 2 d P flop; at d = 784, P = 512 the two minimum times are within 5% of each other,
+    and the bound reported is the one with the longer minimum time under `peaks` (HBM copy
+    bandwidth, sustained BF16).
     P: the slices one launch covers (this rank's share when the slices are sharded)."""
     P = wl.P if P is None else P
     pts = step_points(wl, kernel_name, kernels) / max(1.0, launches_per_step)
     per = 1.0 / max(1.0, launches_per_step)
-    if kernel_name.startswith("umma_cheb_target") and f32_direct(wl, kernels):
+    if kernel_name.startswith(("pair_cheb_target", "pair_cheb_moments")) or \
+            (kernel_name.startswith("umma_cheb_target") and f32_direct(wl, kernels)):
         flops = 2.0 * pts * wl.d * P
-        nbytes = pts * (4.0 * wl.d + 16.0 * ((P + 255) // 256))
+        if kernel_name.startswith("pair_cheb_target"):
+            nbytes = pts * (4.0 * wl.d + 16.0)  # FP32 rows in, two FP64 partial sums out
+        elif kernel_name.startswith("pair_cheb_moments"):
+            nbytes = pts * (4.0 * wl.d + 4.0)  # FP32 rows and weights in (moment partials: per CTA pair)
+        else:
+            nbytes = pts * (4.0 * wl.d + 16.0 * ((P + 255) // 256))
         pk = peaks or {}
         t_hbm = nbytes / (pk.get("hbm_gbs", 6689.8) * 1e9)
         t_tc = flops / (pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1772.1)) * 1e12)

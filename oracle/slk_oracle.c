@@ -372,9 +372,13 @@ double orc_fhat_gauss(int d, double sigma, double omega);
  *   f'(x) = -2 int_0^inf fhat(w) 2 pi w sin(2 pi w x) dw.
  * fhat ~ exp(-u) u^((d-1)/2) with u = 2 pi^2 sigma^2 w^2 is integrated over the
  * band where it exceeds e^-45 of its peak, composite 16-point Gauss-Legendre
- * with >= 4 panels per period of the cosine.  Absolute error ~ 1e-15.
+ * with >= 4 panels per period of the cosine.  Rounding bound (*err; the integral of
+ * |fhat| is 1/2, so a relative error e of every fhat value costs at most e): fhat is
+ * evaluated in log space, where the terms of the exponent reach L = |log(d pi sigma)|
+ * + u_max + ((d-1)/2) |log u_max| + lgamma((d+2)/2), each rounded to eps relative, and the
+ * cosine's argument reaches 2 pi w_max x; together 4 eps (L + 2 pi w_max x + 4).
  */
-static double f_gauss_fourier(int d, double sigma, double x, double* df) {
+static double f_gauss_fourier(int d, double sigma, double x, double* df, double* err) {
     gl_init();
     double a = 0.5 * (d - 1);
     double umax = a + 55.0 + 12.0 * sqrt(a + 1.0);
@@ -395,6 +399,10 @@ static double f_gauss_fourier(int d, double sigma, double x, double* df) {
         }
     }
     if (df) *df = 2.0 * (ds + dcs);
+    if (err) {
+        const double L = fabs(log(d * M_PI * sigma)) + umax + a * fabs(log(umax)) + lgamma(0.5 * (d + 2));
+        *err = 4.0 * DBL_EPSILON * (L + 2.0 * M_PI * whi * fabs(x) + 4.0);
+    }
     return 2.0 * (s + cs);
 }
 
@@ -406,10 +414,7 @@ double orc_f(int kernel, int d, double param, double x, double* df, double* err)
     switch (kernel) {
     case ORC_GAUSSIAN: {
         double v = f_gauss(d, param, x, df, err);
-        if (*err > 1e-12) {
-            v = f_gauss_fourier(d, param, x, df);
-            *err = 1e-14;
-        }
+        if (*err > 1e-12) v = f_gauss_fourier(d, param, x, df, err);
         return v;
     }
     case ORC_LAPLACIAN: return f_laplace(d, param, x, df, err);

@@ -6,8 +6,10 @@
 //   source side  mom[p][j] = sum_n w_n T_j(<xi_p, x_n - mu> / R)          (moments per slice)
 // The pair of CTAs of a cluster of two forms one 256-point tile.  Each CTA brings in,
 // per 64-wide K stage, its own 128 FP32 point rows (two 32-column TMA boxes, converted
-// in place to centred BF16 in the tensor core's 128-byte-swizzled layout by three
-// converter warps) and its own 128 rows of each 256-direction sub-tile.  The even CTA
+// in place to centred BF16 in the tensor core's 128-byte-swizzled layout by two
+// converter warps) and its own 128 rows of each 256-direction sub-tile; while it works on
+// a tile its producer streams the rows of its next tile into L2, one contiguous chunk per
+// stage.  The even CTA
 // issues M = 256, N = 256 MMAs (kind::f16, FP32 accumulate) for up to two sub-tiles,
 // i.e. all P <= 512 slices of the tile at once, into two 256-column accumulators of each
 // CTA's tensor memory:
@@ -17,9 +19,9 @@
 // pair shares the tile through the pair MMA, not through any shared load).
 //
 // Signals between the two CTAs are remote mbarrier arrivals at cluster scope:
-//   converters of both CTAs  -> full[s] of the even CTA  (stage converted, 192 arrivals)
-//   even CTA's MMA commit    -> its own empty[s]; its control thread forwards the release
-//                               to the odd CTA's empty[s] when it refills that stage
+//   converters of both CTAs  -> full[s] of the even CTA  (stage converted, 128 arrivals)
+//   even CTA's MMA commit    -> its own empty[s]; its producer forwards the release to the
+//                               odd CTA's empty[s] when it refills that stage
 //   even CTA's MMA commit    -> its own acc_full; one epilogue thread forwards it
 //   epilogue warps of both   -> acc_empty of the even CTA (16 arrivals)
 // Every wait is bounded; on a timeout the CTA records an error bit and skips the rest.
@@ -44,7 +46,9 @@ constexpr int QM = 128;                      // rows per CTA (TMEM lanes); pair 
 constexpr int QN = 256;                      // MMA N (128 rows of B from each CTA)
 constexpr int QK = 64;                       // K elements per stage
 constexpr int QSTAGES = 3;
-constexpr int QTHREADS = 384;                // warp 0 control, 1-3 converters, 4-11 epilogue
+constexpr int QTHREADS = 384;                // warp 0 TMA, 1 MMA, 2-3 converters, 4-11 epilogue
+constexpr int CVT_WARPS = 2;
+constexpr int CVT_THREADS = 32 * CVT_WARPS;
 constexpr int CVT_BYTES = QM * QK * 4;       // 128 FP32 rows x 64 (two 32-column boxes)
 constexpr int DIR_BYTES = QM * QK * 2;       // 128 BF16 direction rows x 64, one sub-tile
 constexpr int QSTAGE_BYTES = CVT_BYTES + 2 * DIR_BYTES;
@@ -75,6 +79,8 @@ struct PairArgs {
     const float* beta;  // target side: P x q coefficients
     double* part;       // target side: 2 x ldp FP64 row sums
     int64_t ldp;
+    const float* pts;   // the FP32 points (for the L2 prefetch), row stride ldpts
+    int64_t ldpts;
     const float* w;     // source side: weights of the n points
     double* mom;        // source side: moment partials [(pair * halves + h) * P + p][q]
     float* absmax;      // source side: max |z| over the points
@@ -91,9 +97,9 @@ constexpr size_t kPairSmemMax = pair_smem_bytes(16);
 
 // Convert one stage's 128 FP32 rows (two unswizzled 32-column boxes of 128 bytes per
 // row) to centred BF16 in place over the first box, 128-byte swizzle (16-byte chunk c of
-// row r at c ^ (r % 8)); rows at or beyond n are written as zeros.  Warp cw (0..2) of the
-// three converter warps takes 16-row batches cw, cw + 3, ...  (the same arithmetic as the
-// single-CTA converting kernel).
+// row r at c ^ (r % 8)); rows at or beyond n are written as zeros.  Converter warp cw
+// takes 16-row batches cw, cw + CVT_WARPS, ...  (the same arithmetic as the single-CTA
+// converting kernel).
 __device__ __forceinline__ void convert_stage(unsigned char* cv, int lane, int cw, int kb, int d, const float* mu,
                                               int row0, int n) {
     constexpr int HALF = QM * 128, NB = QM / 16;
@@ -105,7 +111,7 @@ __device__ __forceinline__ void convert_stage(unsigned char* cv, int lane, int c
         const int k = kb * QK + 4 * j + e;
         m[e] = k < d ? __ldg(mu + k) : 0.0f;
     }
-    for (int bi = cw; bi < NB; bi += 3) {
+    for (int bi = cw; bi < NB; bi += CVT_WARPS) {
         const int r0 = bi * 16;
         float4 v[8];
 #pragma unroll
@@ -140,7 +146,7 @@ __global__ void __launch_bounds__(QTHREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < QSTAGES; ++s) {
             mbar_init(&sm->raw[s], 1);
-            mbar_init(&sm->full[s], 2 * 96);
+            mbar_init(&sm->full[s], 2 * CVT_THREADS);
             mbar_init(&sm->empty[s], 1);
         }
         mbar_init(&sm->acc_full, 1);
@@ -166,11 +172,38 @@ __global__ void __launch_bounds__(QTHREADS, 1)
     const int total = ntile * kblocks;
 
     if (warp == 0) {
-        // ---------------- control: TMA loads of this CTA; on the even CTA also the MMAs
+        // ---------------- producer: TMA loads of this CTA's stages, L2 prefetch of its next tile
         if (lane == 0) {
             int issued = 0;
-            auto issue = [&](int gg) {
+            // rows of the next tile brought into L2 a chunk per stage (contiguous bytes of
+            // the row-major points), so that the TMA loads of a tile find it there
+            const int chunk = (QM + kblocks - 1) / kblocks;
+            auto prefetch_rows = [&](int tile, int kb) {
+                const int rbase = tile * (2 * QM) + static_cast<int>(rank) * QM;
+                const int r0 = rbase + kb * chunk;
+                int r1 = r0 + chunk;
+                if (r1 > rbase + QM) r1 = rbase + QM;
+                if (r1 > a.n) r1 = a.n;
+                if (tile >= a.tiles || r0 >= r1) return;
+                // from the first element of row r0 to the last element of row r1 - 1, rounded
+                // down to 16 bytes (never past the caller's rows)
+                const int64_t bytes = ((static_cast<int64_t>(r1 - r0 - 1) * a.ldpts + a.d) * 4) & ~int64_t(15);
+                if (bytes > 0)
+                    bulk_prefetch_l2(a.pts + static_cast<int64_t>(r0) * a.ldpts, static_cast<uint32_t>(bytes));
+            };
+            for (int gg = 0; gg < total; ++gg) {
                 const int tile = pair + (gg / kblocks) * npairs, kb = gg % kblocks, s = gg % QSTAGES;
+                if (gg >= QSTAGES) {
+                    // released by the pair's MMAs: on the even CTA by their commit, on the odd
+                    // CTA by the even CTA's producer forwarding that release
+                    const bool ok = rank == 0 ? mbar_wait(&sm->empty[s], ((gg / QSTAGES) - 1) & 1)
+                                              : mbar_wait_cluster(&sm->empty[s], ((gg / QSTAGES) - 1) & 1);
+                    if (!ok) {
+                        atomicOr(a.err, 8u);
+                        break;
+                    }
+                    if (rank == 0) mbar_arrive_cluster(cluster_addr(&sm->empty[s], 1));
+                }
                 const int prow = tile * (2 * QM) + static_cast<int>(rank) * QM;
                 unsigned char* st = base + s * QSTAGE_BYTES;
                 mbar_expect_tx(&sm->raw[s], stage_tx);
@@ -180,71 +213,43 @@ __global__ void __launch_bounds__(QTHREADS, 1)
                     tma_load_2d(st + CVT_BYTES + j * DIR_BYTES, &map_dir, &sm->raw[s], kb * QK,
                                 j * QN + static_cast<int>(rank) * QM);
                 ++issued;
-            };
-            auto prefetch = [&](int gg) {
-                const int tile = pair + (gg / kblocks) * npairs, kb = gg % kblocks;
-                const int prow = tile * (2 * QM) + static_cast<int>(rank) * QM;
-                tma_prefetch_2d(&map_pts, kb * QK, prow);
-                tma_prefetch_2d(&map_pts, kb * QK + 32, prow);
-            };
-            constexpr int PF = 8;
-            for (int gg = 0; gg < total && gg < PF; ++gg) prefetch(gg);
-            for (int gg = 0; gg < total && gg < QSTAGES; ++gg) issue(gg);
-            if (rank == 0) {
-                const uint32_t idesc = instr_desc(1u, 2 * QM, QN);
-                for (int g = 0; g < total; ++g) {
-                    const int kb = g % kblocks, t = g / kblocks, s = g % QSTAGES;
-                    if (kb == 0 && t >= 1 && !mbar_wait_cluster(&sm->acc_empty, (t - 1) & 1)) {
-                        atomicOr(a.err, 16u);
-                        break;
-                    }
-                    if (!mbar_wait_cluster(&sm->full[s], (g / QSTAGES) & 1)) {
-                        atomicOr(a.err, 16u);
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    unsigned char* st = base + s * QSTAGE_BYTES;
-#pragma unroll
-                    for (int k = 0; k < QK / 16; ++k)
-                        for (int j = 0; j < nsub; ++j) {
-                            const uint64_t dp = smem_desc(st + k * 32);
-                            const uint64_t dd = smem_desc(st + CVT_BYTES + j * DIR_BYTES + k * 32);
-                            if (SIDE == SIDE_TARGET)
-                                umma_f16_pair(tmem + j * QN, dp, dd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
-                            else
-                                umma_f16_pair(tmem + j * QN, dd, dp, idesc, (kb > 0 || k > 0) ? 1u : 0u);
-                        }
-                    umma_commit_pair(&sm->empty[s]);
-                    if (kb == kblocks - 1) umma_commit_pair(&sm->acc_full);
-                    // refill the stage of g - 1 (its MMAs were issued one step earlier) in
-                    // both CTAs: the odd CTA learns of the release through its own barrier
-                    const int gp = g - 1, gn = gp + QSTAGES;
-                    if (gp >= 0 && gn < total) {
-                        if (!mbar_wait(&sm->empty[gp % QSTAGES], (gp / QSTAGES) & 1)) {
-                            atomicOr(a.err, 8u);
-                            break;
-                        }
-                        mbar_arrive_cluster(cluster_addr(&sm->empty[gp % QSTAGES], 1));
-                        issue(gn);
-                    }
-                    if (g + PF < total) prefetch(g + PF);
-                }
-                drain_fills(sm->raw, QSTAGES, issued);
-                drain_mma_pair(&sm->drain, a.err, 16u);
-            } else {
-                for (int gn = QSTAGES; gn < total; ++gn) {
-                    if (!mbar_wait_cluster(&sm->empty[gn % QSTAGES], ((gn / QSTAGES) - 1) & 1)) {
-                        atomicOr(a.err, 8u);
-                        break;
-                    }
-                    issue(gn);
-                    if (gn - QSTAGES + PF < total) prefetch(gn - QSTAGES + PF);
-                }
-                drain_fills(sm->raw, QSTAGES, issued);
+                prefetch_rows(tile + npairs, kb);
             }
+            drain_fills(sm->raw, QSTAGES, issued);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (even CTA): M = 256 over the pair, one or two sub-tiles
+        if (rank == 0 && lane == 0) {
+            const uint32_t idesc = instr_desc(1u, 2 * QM, QN);
+            for (int g = 0; g < total; ++g) {
+                const int kb = g % kblocks, t = g / kblocks, s = g % QSTAGES;
+                if (kb == 0 && t >= 1 && !mbar_wait_cluster(&sm->acc_empty, (t - 1) & 1)) {
+                    atomicOr(a.err, 16u);
+                    break;
+                }
+                if (!mbar_wait_cluster(&sm->full[s], (g / QSTAGES) & 1)) {
+                    atomicOr(a.err, 16u);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                unsigned char* st = base + s * QSTAGE_BYTES;
+#pragma unroll
+                for (int k = 0; k < QK / 16; ++k)
+                    for (int j = 0; j < nsub; ++j) {
+                        const uint64_t dp = smem_desc(st + k * 32);
+                        const uint64_t dd = smem_desc(st + CVT_BYTES + j * DIR_BYTES + k * 32);
+                        if (SIDE == SIDE_TARGET)
+                            umma_f16_pair(tmem + j * QN, dp, dd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                        else
+                            umma_f16_pair(tmem + j * QN, dd, dp, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                    }
+                umma_commit_pair(&sm->empty[s]);
+                if (kb == kblocks - 1) umma_commit_pair(&sm->acc_full);
+            }
+            drain_mma_pair(&sm->drain, a.err, 16u);
         }
     } else if (warp <= 3) {
-        // ---------------- converters (warps 1-3) of this CTA's points
+        // ---------------- converters (warps 2-3) of this CTA's points
         const uint32_t full0 = cluster_addr(&sm->full[0], 0);
         for (int g = 0; g < total; ++g) {
             const int s = g % QSTAGES, kb = g % kblocks, tile = pair + (g / kblocks) * npairs;
@@ -253,7 +258,7 @@ __global__ void __launch_bounds__(QTHREADS, 1)
                 if (lane == 0) atomicOr(a.err, 8u);
                 break;
             }
-            convert_stage(base + s * QSTAGE_BYTES, lane, warp - 1, kb, a.d, a.mu,
+            convert_stage(base + s * QSTAGE_BYTES, lane, warp - 2, kb, a.d, a.mu,
                           tile * (2 * QM) + static_cast<int>(rank) * QM, a.n);
             // generic-proxy writes, read next by the tensor core (async proxy)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -456,6 +461,8 @@ void launch_pair_cheb_target(const float* y, int64_t ldy, const float* mu, int64
     const CUtensorMap mp = tmap_f32_rows(y, n, d, ldy, QM);
     const CUtensorMap md = tmap_bf16_sw128(xib, P, d, umma_operand_ld(d), QM);
     PairArgs a = pair_args(n, P, d, q, R, mu, err);
+    a.pts = y;
+    a.ldpts = ldy;
     a.horner = horner;
     a.beta = coef;
     a.part = part;
@@ -479,6 +486,8 @@ void launch_pair_moments(const float* x, int64_t ldx, const float* mu, int64_t n
     const CUtensorMap mp = tmap_f32_rows(x, n, d, ldx, QM);
     const CUtensorMap md = tmap_bf16_sw128(xib, P, d, umma_operand_ld(d), QM);
     PairArgs a = pair_args(n, P, d, q, R, mu, err);
+    a.pts = x;
+    a.ldpts = ldx;
     a.w = w;
     a.mom = mom;
     a.absmax = absmax;

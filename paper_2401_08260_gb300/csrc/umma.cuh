@@ -61,6 +61,12 @@ __device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int c0, 
                  : "memory");
 }
 
+// bring `bytes` contiguous bytes at p into L2 (16-byte aligned start and size)
+__device__ __forceinline__ void bulk_prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(p)), "r"(bytes)
+                 : "memory");
+}
+
 // Wait (bounded) for the last fill of each stage of a ring filled `fills` times, in the
 // order they were issued: fill j completes phase j / stages of barrier j % stages.  The
 // TMA bytes of those fills have then landed in this CTA's shared memory.
