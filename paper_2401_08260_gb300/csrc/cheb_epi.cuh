@@ -54,6 +54,60 @@ __device__ __forceinline__ void cheb_chunk(const float (&v)[8], const float* __r
     }
 }
 
+
+// Target-side evaluation of one 32-column accumulator chunk (one row per thread, raw
+// TMEM words in r): 32 independent Horner (monomial coefficients) or Clenshaw (Chebyshev
+// coefficients) chains over the degrees, the coefficients of the chunk's 32 slices read as
+// eight broadcast LDS.128 per degree from the degree-major table bt0[k * ppad + p]; the
+// values are added to (s, c) four at a time, each group sum with Kahan compensation.
+// Projections outside [-R, R] (or NaN) set bad.
+template <int QP, bool HORNER>
+__device__ __forceinline__ void cheb_chunk32(const uint32_t (&r)[32], const float* __restrict__ bt0, int ppad,
+                                             float R, float inv_R, float& s, float& c, bool& bad) {
+    // Horner keeps one value per chain, Clenshaw two: the latter runs in two halves of 16
+    constexpr int W = HORNER ? 32 : 16;
+#pragma unroll
+    for (int h = 0; h < 32; h += W) {
+        float u[W], b1[W], b2[HORNER ? 1 : W];
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            const float z = __uint_as_float(r[h + i]);
+            if (!(z <= R && z >= -R)) bad = true;
+            u[i] = z * inv_R;
+            b1[i] = 0.0f;
+            if (!HORNER) b2[i] = 0.0f;
+        }
+#pragma unroll
+        for (int k = QP - 1; k >= 0; --k) {
+#pragma unroll
+            for (int g = 0; g < W / 4; ++g) {
+                const float4 c4 = *reinterpret_cast<const float4*>(bt0 + h + 4 * g + k * ppad);
+                const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int i = 4 * g + e;
+                    if (HORNER) {
+                        b1[i] = fmaf(b1[i], u[i], cv[e]);
+                    } else if (k >= 1) {
+                        const float bk = fmaf(u[i] + u[i], b1[i], cv[e] - b2[i]);
+                        b2[i] = b1[i];
+                        b1[i] = bk;
+                    } else {
+                        b1[i] = fmaf(u[i], b1[i], cv[e] - b2[i]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < W / 4; ++g) {
+            const float y = ((b1[4 * g] + b1[4 * g + 1]) + (b1[4 * g + 2] + b1[4 * g + 3])) - c;
+            const float tt = s + y;
+            c = (tt - s) - y;
+            s = tt;
+        }
+    }
+}
+
 // Moments of one slice over a 32-point accumulator chunk: z[j] for the chunk's points,
 // the lane-th point's weight in wl (zero beyond the points); t holds this tile's FP32 sums.
 template <int QP>

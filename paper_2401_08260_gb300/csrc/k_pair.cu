@@ -6,9 +6,9 @@
 //   source side  mom[p][j] = sum_n w_n T_j(<xi_p, x_n - mu> / R)          (moments per slice)
 // The pair of CTAs of a cluster of two forms one 256-point tile.  Each CTA brings in,
 // per 64-wide K stage, its own 128 FP32 point rows (two 32-column TMA boxes, converted
-// in place to centred BF16 in the tensor core's 128-byte-swizzled layout by two
-// converter warps) and its own 128 rows of each 256-direction sub-tile; while it works on
-// a tile its producer streams the rows of its next tile into L2, one contiguous chunk per
+// in place to centred BF16 in the tensor core's 128-byte-swizzled layout by its eight
+// worker warps) and its own 128 rows of each 256-direction sub-tile; while it works on a
+// tile its producer streams the rows of its next tile into L2, one contiguous chunk per
 // stage.  The even CTA
 // issues M = 256, N = 256 MMAs (kind::f16, FP32 accumulate) for up to two sub-tiles,
 // i.e. all P <= 512 slices of the tile at once, into two 256-column accumulators of each
@@ -19,11 +19,15 @@
 // pair shares the tile through the pair MMA, not through any shared load).
 //
 // Signals between the two CTAs are remote mbarrier arrivals at cluster scope:
-//   converters of both CTAs  -> full[s] of the even CTA  (stage converted, 128 arrivals)
+//   workers of both CTAs     -> full[s] of the even CTA  (stage converted, 16 arrivals)
 //   even CTA's MMA commit    -> its own empty[s]; its producer forwards the release to the
 //                               odd CTA's empty[s] when it refills that stage
-//   even CTA's MMA commit    -> its own acc_full; one epilogue thread forwards it
-//   epilogue warps of both   -> acc_empty of the even CTA (16 arrivals)
+//   even CTA's MMA commit    -> its own acc_full; one worker thread forwards it
+//   workers of both CTAs     -> acc_empty of the even CTA (16 arrivals)
+// The worker warps alternate between converting the stages of a tile and reading its
+// accumulators back once the MMAs are done (the 512 TMEM columns hold one tile's two
+// accumulators); each reads 32 columns at a time, the next load in flight while it
+// evaluates the current one.
 // Every wait is bounded; on a timeout the CTA records an error bit and skips the rest.
 // Before exit each CTA waits for its own TMA fills, the even CTA for its last MMAs, and
 // both meet at a cluster barrier before tensor memory is freed.
@@ -46,9 +50,8 @@ constexpr int QM = 128;                      // rows per CTA (TMEM lanes); pair 
 constexpr int QN = 256;                      // MMA N (128 rows of B from each CTA)
 constexpr int QK = 64;                       // K elements per stage
 constexpr int QSTAGES = 3;
-constexpr int QTHREADS = 384;                // warp 0 TMA, 1 MMA, 2-3 converters, 4-11 epilogue
-constexpr int CVT_WARPS = 2;
-constexpr int CVT_THREADS = 32 * CVT_WARPS;
+constexpr int QTHREADS = 320;                // warp 0 TMA, 1 MMA, 2-9 workers (convert + epilogue)
+constexpr int WORKER_WARPS = 8;              // each converts 16 of the 128 rows of a stage
 constexpr int CVT_BYTES = QM * QK * 4;       // 128 FP32 rows x 64 (two 32-column boxes)
 constexpr int DIR_BYTES = QM * QK * 2;       // 128 BF16 direction rows x 64, one sub-tile
 constexpr int QSTAGE_BYTES = CVT_BYTES + 2 * DIR_BYTES;
@@ -95,42 +98,34 @@ __host__ __device__ constexpr size_t pair_smem_bytes(int beta_terms) {
 }
 constexpr size_t kPairSmemMax = pair_smem_bytes(16);
 
-// Convert one stage's 128 FP32 rows (two unswizzled 32-column boxes of 128 bytes per
-// row) to centred BF16 in place over the first box, 128-byte swizzle (16-byte chunk c of
-// row r at c ^ (r % 8)); rows at or beyond n are written as zeros.  Converter warp cw
-// takes 16-row batches cw, cw + CVT_WARPS, ...  (the same arithmetic as the single-CTA
-// converting kernel).
-__device__ __forceinline__ void convert_stage(unsigned char* cv, int lane, int cw, int kb, int d, const float* mu,
-                                              int row0, int n) {
-    constexpr int HALF = QM * 128, NB = QM / 16;
+// Convert 16 of one stage's 128 FP32 rows (rows 16 wi .. 16 wi + 15; the stage holds two
+// unswizzled 32-column boxes of 128 bytes per row) to centred BF16 in place over the first
+// box, 128-byte swizzle (16-byte chunk c of row r at c ^ (r % 8)); rows at or beyond n are
+// written as zeros.  Lane l takes columns 4j..4j+3 (j = l % 16) of rows 2u + l / 16; m holds
+// the centre at those columns (the same arithmetic as the single-CTA converting kernel).
+__device__ __forceinline__ void convert_rows16(unsigned char* cv, int lane, int wi, const float (&m)[4], int row0,
+                                               int n) {
+    constexpr int HALF = QM * 128;
     const int j = lane & 15, rr = lane >> 4;
     const unsigned char* src = cv + (j >> 3) * HALF + (j & 7) * 16;
-    float m[4];
+    const int r0 = wi * 16;
+    float4 v[8];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const int k = kb * QK + 4 * j + e;
-        m[e] = k < d ? __ldg(mu + k) : 0.0f;
-    }
-    for (int bi = cw; bi < NB; bi += CVT_WARPS) {
-        const int r0 = bi * 16;
-        float4 v[8];
+    for (int u = 0; u < 8; ++u) v[u] = *reinterpret_cast<const float4*>(src + (r0 + 2 * u + rr) * 128);
+    __syncwarp();
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = *reinterpret_cast<const float4*>(src + (r0 + 2 * u + rr) * 128);
-        __syncwarp();
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int r = r0 + 2 * u + rr;
-            union { __nv_bfloat162 h[2]; uint2 u2; } pk;
-            pk.h[0] = __floats2bfloat162_rn(v[u].x - m[0], v[u].y - m[1]);
-            pk.h[1] = __floats2bfloat162_rn(v[u].z - m[2], v[u].w - m[3]);
-            if (row0 + r >= n) pk.u2 = make_uint2(0u, 0u);
-            *reinterpret_cast<uint2*>(cv + r * 128 + (((j >> 1) ^ (r & 7)) << 4) + ((j & 1) << 3)) = pk.u2;
-        }
+    for (int u = 0; u < 8; ++u) {
+        const int r = r0 + 2 * u + rr;
+        union { __nv_bfloat162 h[2]; uint2 u2; } pk;
+        pk.h[0] = __floats2bfloat162_rn(v[u].x - m[0], v[u].y - m[1]);
+        pk.h[1] = __floats2bfloat162_rn(v[u].z - m[2], v[u].w - m[3]);
+        if (row0 + r >= n) pk.u2 = make_uint2(0u, 0u);
+        *reinterpret_cast<uint2*>(cv + r * 128 + (((j >> 1) ^ (r & 7)) << 4) + ((j & 1) << 3)) = pk.u2;
     }
 }
 
 template <int SIDE>
-__global__ void __launch_bounds__(QTHREADS, 1)
+__global__ void __maxnreg__(200)
     k_pair_cheb(const __grid_constant__ CUtensorMap map_pts, const __grid_constant__ CUtensorMap map_dir, PairArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -146,11 +141,11 @@ __global__ void __launch_bounds__(QTHREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < QSTAGES; ++s) {
             mbar_init(&sm->raw[s], 1);
-            mbar_init(&sm->full[s], 2 * CVT_THREADS);
+            mbar_init(&sm->full[s], 2 * WORKER_WARPS);  // one arrival per worker warp of each CTA
             mbar_init(&sm->empty[s], 1);
         }
         mbar_init(&sm->acc_full, 1);
-        mbar_init(&sm->acc_empty, 2 * 8);
+        mbar_init(&sm->acc_empty, 2 * WORKER_WARPS);
         mbar_init(&sm->drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -248,126 +243,169 @@ __global__ void __launch_bounds__(QTHREADS, 1)
             }
             drain_mma_pair(&sm->drain, a.err, 16u);
         }
-    } else if (warp <= 3) {
-        // ---------------- converters (warps 2-3) of this CTA's points
-        const uint32_t full0 = cluster_addr(&sm->full[0], 0);
-        for (int g = 0; g < total; ++g) {
-            const int s = g % QSTAGES, kb = g % kblocks, tile = pair + (g / kblocks) * npairs;
-            const bool got = mbar_wait(&sm->raw[s], (g / QSTAGES) & 1);
-            if (!__all_sync(0xffffffffu, got)) {
-                if (lane == 0) atomicOr(a.err, 8u);
-                break;
-            }
-            convert_stage(base + s * QSTAGE_BYTES, lane, warp - 2, kb, a.d, a.mu,
-                          tile * (2 * QM) + static_cast<int>(rank) * QM, a.n);
-            // generic-proxy writes, read next by the tensor core (async proxy)
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive_cluster(full0 + static_cast<uint32_t>(s * sizeof(uint64_t)));
-        }
-    } else if (SIDE == SIDE_TARGET) {
-        // ---------------- target epilogue: row sums of t_p(z) over this CTA's 128 points
-        const int q4 = warp & 3, grp = (warp - 4) >> 2;  // TMEM lane quarter, warp group
+    } else {
+        // ---------------- workers (warps 2-9): for each tile, convert this warp's 16 rows of
+        // every stage as it lands, then read the finished accumulators back (TMEM lane
+        // quarter warp % 4, column group (warp - 2) / 4)
+        const int wi = warp - 2, q4 = warp & 3, grp = wi >> 2;
         const uint32_t lane_off = static_cast<uint32_t>(q4 * 32) << 16;
+        const uint32_t full0 = cluster_addr(&sm->full[0], 0);
         const uint32_t acc_empty0 = cluster_addr(&sm->acc_empty, 0);
         const uint32_t peer_full = cluster_addr(&sm->acc_full, 1);
-        // two sub-tiles: group j takes accumulator j; one sub-tile: its two column halves
-        const uint32_t col0 = nsub == 2 ? grp * QN : grp * (QN / 2);
-        const int ncols = nsub == 2 ? QN : QN / 2;
-        bool bad = false;
-        for (int t = 0; t < ntile; ++t) {
+        const bool forwarder = rank == 0 && wi == 0 && lane == 0;
+        // the centre's four columns of this lane for the next stage, loaded a stage ahead
+        float mnext[4];
+        auto load_mu = [&](int kb) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int k = kb * QK + 4 * (lane & 15) + e;
+                mnext[e] = k < a.d ? __ldg(a.mu + k) : 0.0f;
+            }
+        };
+        load_mu(0);
+        bool ok = true;
+        // convert the stages of local tile t; false on a timeout
+        auto convert_tile = [&](int t) {
             const int tile = pair + t * npairs;
-            const int row = tile * (2 * QM) + static_cast<int>(rank) * QM + q4 * 32 + lane;
+            for (int kb = 0; kb < kblocks; ++kb) {
+                const int g = t * kblocks + kb, s = g % QSTAGES;
+                float m[4] = {mnext[0], mnext[1], mnext[2], mnext[3]};
+                load_mu(kb + 1 < kblocks ? kb + 1 : 0);
+                const bool got = mbar_wait(&sm->raw[s], (g / QSTAGES) & 1);
+                if (!__all_sync(0xffffffffu, got)) {
+                    if (lane == 0) atomicOr(a.err, 8u);
+                    return false;
+                }
+                convert_rows16(base + s * QSTAGE_BYTES, lane, wi, m, tile * (2 * QM) + static_cast<int>(rank) * QM,
+                               a.n);
+                // generic-proxy writes, read next by the tensor core (async proxy)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(full0 + static_cast<uint32_t>(s * sizeof(uint64_t)));
+            }
+            return true;
+        };
+        auto wait_acc = [&](int t) {
             if (!mbar_wait_cluster(&sm->acc_full, t & 1)) {
                 atomicOr(a.err, 32u);
-                break;
+                return false;
             }
-            if (rank == 0 && warp == 4 && lane == 0) mbar_arrive_cluster(peer_full);
+            if (forwarder) mbar_arrive_cluster(peer_full);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            float s = 0.0f, c = 0.0f;  // Kahan
-            for (int cc = 0; cc < ncols; cc += 8) {
-                float v[8];
-                tmem_ld8(tmem + lane_off + col0 + cc, v);
-                const float* bt = sbeta + col0 + cc;
-                if (a.q == 10) {
-                    if (a.horner) cheb_chunk<10, true>(v, bt, QMAX_P, a.R, a.inv_R, s, c, bad);
-                    else cheb_chunk<10, false>(v, bt, QMAX_P, a.R, a.inv_R, s, c, bad);
-                } else if (a.q == 12) {
-                    if (a.horner) cheb_chunk<12, true>(v, bt, QMAX_P, a.R, a.inv_R, s, c, bad);
-                    else cheb_chunk<12, false>(v, bt, QMAX_P, a.R, a.inv_R, s, c, bad);
-                } else if (a.q == 8) {
-                    if (a.horner) cheb_chunk<8, true>(v, bt, QMAX_P, a.R, a.inv_R, s, c, bad);
-                    else cheb_chunk<8, false>(v, bt, QMAX_P, a.R, a.inv_R, s, c, bad);
-                } else {
-                    if (a.horner) cheb_chunk<16, true>(v, bt, QMAX_P, a.R, a.inv_R, s, c, bad);
-                    else cheb_chunk<16, false>(v, bt, QMAX_P, a.R, a.inv_R, s, c, bad);
-                }
-            }
+            return true;
+        };
+        auto release_acc = [&]() {
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive_cluster(acc_empty0);
-            if (row < a.n) a.part[static_cast<int64_t>(grp) * a.ldp + row] = static_cast<double>(s) - static_cast<double>(c);
-        }
-        if (bad) atomicOr(a.err, 4u);
-    } else {
-        // ---------------- source epilogue: one slice's moments per thread over all tiles
-        const int q4 = warp & 3, grp = (warp - 4) >> 2;
-        const uint32_t lane_off = static_cast<uint32_t>(q4 * 32) << 16;
-        const uint32_t acc_empty0 = cluster_addr(&sm->acc_empty, 0);
-        const uint32_t peer_full = cluster_addr(&sm->acc_full, 1);
-        // two sub-tiles: group j owns the slices of accumulator j (all 256 points);
-        // one sub-tile: both groups own the same slices, each over half of the points
-        const uint32_t col0 = nsub == 2 ? grp * QN : 0;
-        const int pt_off = nsub == 2 ? 0 : grp * (QN / 2);
-        const int ncols = nsub == 2 ? QN : QN / 2;
-        const int slice = (nsub == 2 ? grp * QN : 0) + static_cast<int>(rank) * QM + q4 * 32 + lane;
-        float mx = 0.0f;
-        auto run = [&](auto qp_tag) {
-            constexpr int QP = decltype(qp_tag)::value;
-            float hi[QP], lo[QP];
-#pragma unroll
-            for (int k = 0; k < QP; ++k) hi[k] = lo[k] = 0.0f;
-            for (int t = 0; t < ntile; ++t) {
-                const int tile = pair + t * npairs;
-                if (!mbar_wait_cluster(&sm->acc_full, t & 1)) {
-                    atomicOr(a.err, 32u);
-                    break;
+        };
+        if (SIDE == SIDE_TARGET) {
+            // row sums of t_p(z) over the slices of this warp's column group
+            const uint32_t col0 = nsub == 2 ? grp * QN : grp * (QN / 2);
+            const int ncols = nsub == 2 ? QN : QN / 2;
+            bool bad = false;
+            auto run = [&](auto qp_tag, auto horner_tag) {
+                constexpr int QP = decltype(qp_tag)::value;
+                constexpr bool HORNER = decltype(horner_tag)::value;
+                for (int t = 0; t < ntile && ok; ++t) {
+                    if (!convert_tile(t) || !wait_acc(t)) {
+                        ok = false;
+                        break;
+                    }
+                    const int tile = pair + t * npairs;
+                    const int row = tile * (2 * QM) + static_cast<int>(rank) * QM + q4 * 32 + lane;
+                    float sum = 0.0f, comp = 0.0f;  // Kahan
+                    uint32_t ra[32], rb[32];
+                    const uint32_t tbase = tmem + lane_off + col0;
+                    tmem_ld32_issue(tbase, ra);
+                    tmem_wait32(ra);
+                    for (int cc = 0; cc < ncols; cc += 64) {
+                        tmem_ld32_issue(tbase + cc + 32, rb);
+                        cheb_chunk32<QP, HORNER>(ra, sbeta + col0 + cc, QMAX_P, a.R, a.inv_R, sum, comp, bad);
+                        tmem_wait32(rb);
+                        if (cc + 64 < ncols) tmem_ld32_issue(tbase + cc + 64, ra);
+                        cheb_chunk32<QP, HORNER>(rb, sbeta + col0 + cc + 32, QMAX_P, a.R, a.inv_R, sum, comp, bad);
+                        if (cc + 64 < ncols) tmem_wait32(ra);
+                    }
+                    release_acc();
+                    if (row < a.n)
+                        a.part[static_cast<int64_t>(grp) * a.ldp + row] =
+                            static_cast<double>(sum) - static_cast<double>(comp);
                 }
-                if (rank == 0 && warp == 4 && lane == 0) mbar_arrive_cluster(peer_full);
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                float tt[QP];
+            };
+            using T_ = std::true_type;
+            using F_ = std::false_type;
+            if (a.q == 10) a.horner ? run(std::integral_constant<int, 10>{}, T_{}) : run(std::integral_constant<int, 10>{}, F_{});
+            else if (a.q == 12) a.horner ? run(std::integral_constant<int, 12>{}, T_{}) : run(std::integral_constant<int, 12>{}, F_{});
+            else if (a.q == 8) a.horner ? run(std::integral_constant<int, 8>{}, T_{}) : run(std::integral_constant<int, 8>{}, F_{});
+            else a.horner ? run(std::integral_constant<int, 16>{}, T_{}) : run(std::integral_constant<int, 16>{}, F_{});
+            if (bad) atomicOr(a.err, 4u);
+        } else {
+            // one slice's moments per thread over all tiles: two sub-tiles, group j owns the
+            // slices of accumulator j (all 256 points); one sub-tile, both groups own the same
+            // slices, each over half of the points
+            const uint32_t col0 = nsub == 2 ? grp * QN : 0;
+            const int pt_off = nsub == 2 ? 0 : grp * (QN / 2);
+            const int ncols = nsub == 2 ? QN : QN / 2;
+            const int slice = (nsub == 2 ? grp * QN : 0) + static_cast<int>(rank) * QM + q4 * 32 + lane;
+            float mx = 0.0f;
+            auto run = [&](auto qp_tag) {
+                constexpr int QP = decltype(qp_tag)::value;
+                float hi[QP], lo[QP];
 #pragma unroll
-                for (int k = 0; k < QP; ++k) tt[k] = 0.0f;
-                for (int cc = 0; cc < ncols; cc += 32) {
-                    float v[32];
-                    tmem_ld32(tmem + lane_off + col0 + pt_off + cc, v);
+                for (int k = 0; k < QP; ++k) hi[k] = lo[k] = 0.0f;
+                auto chunk = [&](const uint32_t (&r)[32], int tile, int cc, float (&tt)[QP]) {
                     // accumulator column c holds point tile * 256 + c (columns 0-127 from the
                     // even CTA's rows of B, 128-255 from the odd CTA's)
                     const int pt0 = tile * (2 * QM) + pt_off + cc;
                     const float wl = pt0 + lane < a.n ? __ldg(a.w + pt0 + lane) : 0.0f;
+                    float v[32];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
                     mom_chunk<QP>(v, wl, a.inv_R, a.n - pt0, tt, mx);
+                };
+                for (int t = 0; t < ntile && ok; ++t) {
+                    if (!convert_tile(t) || !wait_acc(t)) {
+                        ok = false;
+                        break;
+                    }
+                    const int tile = pair + t * npairs;
+                    float tt[QP];
+#pragma unroll
+                    for (int k = 0; k < QP; ++k) tt[k] = 0.0f;
+                    uint32_t ra[32], rb[32];
+                    const uint32_t tbase = tmem + lane_off + col0 + pt_off;
+                    tmem_ld32_issue(tbase, ra);
+                    tmem_wait32(ra);
+                    for (int cc = 0; cc < ncols; cc += 64) {
+                        tmem_ld32_issue(tbase + cc + 32, rb);
+                        chunk(ra, tile, cc, tt);
+                        tmem_wait32(rb);
+                        if (cc + 64 < ncols) tmem_ld32_issue(tbase + cc + 64, ra);
+                        chunk(rb, tile, cc + 32, tt);
+                        if (cc + 64 < ncols) tmem_wait32(ra);
+                    }
+                    release_acc();
+#pragma unroll
+                    for (int k = 0; k < QP; ++k) two_sum_into(hi[k], lo[k], tt[k]);
                 }
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive_cluster(acc_empty0);
+                if (slice < a.P) {
+                    const int halves = nsub == 2 ? 1 : 2;
+                    const int h = nsub == 2 ? 0 : grp;
+                    double* out = a.mom + (static_cast<int64_t>(pair * halves + h) * a.P + slice) * QP;
 #pragma unroll
-                for (int k = 0; k < QP; ++k) two_sum_into(hi[k], lo[k], tt[k]);
-            }
-            if (slice < a.P) {
-                const int halves = nsub == 2 ? 1 : 2;
-                const int h = nsub == 2 ? 0 : grp;
-                double* out = a.mom + (static_cast<int64_t>(pair * halves + h) * a.P + slice) * QP;
+                    for (int k = 0; k < QP; ++k) out[k] = static_cast<double>(hi[k]) + static_cast<double>(lo[k]);
+                }
+            };
+            if (a.q == 10) run(std::integral_constant<int, 10>{});
+            else if (a.q == 12) run(std::integral_constant<int, 12>{});
+            else if (a.q == 8) run(std::integral_constant<int, 8>{});
+            else run(std::integral_constant<int, 16>{});
+            if (slice >= a.P) mx = 0.0f;
 #pragma unroll
-                for (int k = 0; k < QP; ++k) out[k] = static_cast<double>(hi[k]) + static_cast<double>(lo[k]);
-            }
-        };
-        if (a.q == 10) run(std::integral_constant<int, 10>{});
-        else if (a.q == 12) run(std::integral_constant<int, 12>{});
-        else if (a.q == 8) run(std::integral_constant<int, 8>{});
-        else run(std::integral_constant<int, 16>{});
-        if (slice >= a.P) mx = 0.0f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0 && a.absmax) atomicMax(reinterpret_cast<unsigned int*>(a.absmax), __float_as_uint(mx));
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0 && a.absmax) atomicMax(reinterpret_cast<unsigned int*>(a.absmax), __float_as_uint(mx));
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
