@@ -56,16 +56,16 @@ __device__ __forceinline__ void cheb_chunk(const float (&v)[8], const float* __r
 
 
 // Target-side evaluation of one 32-column accumulator chunk (one row per thread, raw
-// TMEM words in r): 32 independent Horner (monomial coefficients) or Clenshaw (Chebyshev
-// coefficients) chains over the degrees, the coefficients of the chunk's 32 slices read as
-// eight broadcast LDS.128 per degree from the degree-major table bt0[k * ppad + p]; the
+// TMEM words in r): twice 16 independent Horner (monomial coefficients) or Clenshaw
+// (Chebyshev coefficients) chains over the degrees, the coefficients of 16 slices read as
+// four broadcast LDS.128 per degree from the degree-major table bt0[k * ppad + p]; the
 // values are added to (s, c) four at a time, each group sum with Kahan compensation.
 // Projections outside [-R, R] (or NaN) set bad.
 template <int QP, bool HORNER>
 __device__ __forceinline__ void cheb_chunk32(const uint32_t (&r)[32], const float* __restrict__ bt0, int ppad,
                                              float R, float inv_R, float& s, float& c, bool& bad) {
-    // Horner keeps one value per chain, Clenshaw two: the latter runs in two halves of 16
-    constexpr int W = HORNER ? 32 : 16;
+    // two halves of 16 independent chains (the register budget of 384 threads)
+    constexpr int W = 16;
 #pragma unroll
     for (int h = 0; h < 32; h += W) {
         float u[W], b1[W], b2[HORNER ? 1 : W];

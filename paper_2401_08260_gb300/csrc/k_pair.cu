@@ -50,7 +50,8 @@ constexpr int QM = 128;                      // rows per CTA (TMEM lanes); pair 
 constexpr int QN = 256;                      // MMA N (128 rows of B from each CTA)
 constexpr int QK = 64;                       // K elements per stage
 constexpr int QSTAGES = 3;
-constexpr int QTHREADS = 320;                // warp 0 TMA, 1 MMA, 2-9 workers (convert + epilogue)
+constexpr int QTHREADS = 384;                // warp 0 TMA, 1 MMA, 4-11 workers (convert + epilogue)
+constexpr int WORKER0 = 4;                   // first worker warp (TMEM lane quarter = warp % 4)
 constexpr int WORKER_WARPS = 8;              // each converts 16 of the 128 rows of a stage
 constexpr int CVT_BYTES = QM * QK * 4;       // 128 FP32 rows x 64 (two 32-column boxes)
 constexpr int DIR_BYTES = QM * QK * 2;       // 128 BF16 direction rows x 64, one sub-tile
@@ -125,7 +126,7 @@ __device__ __forceinline__ void convert_rows16(unsigned char* cv, int lane, int 
 }
 
 template <int SIDE>
-__global__ void __maxnreg__(200)
+__global__ void __launch_bounds__(QTHREADS, 1)
     k_pair_cheb(const __grid_constant__ CUtensorMap map_pts, const __grid_constant__ CUtensorMap map_dir, PairArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -243,11 +244,11 @@ __global__ void __maxnreg__(200)
             }
             drain_mma_pair(&sm->drain, a.err, 16u);
         }
-    } else {
-        // ---------------- workers (warps 2-9): for each tile, convert this warp's 16 rows of
+    } else if (warp >= WORKER0) {
+        // ---------------- workers (warps 4-11; warps 2-3 have no role): for each tile, convert this warp's 16 rows of
         // every stage as it lands, then read the finished accumulators back (TMEM lane
         // quarter warp % 4, column group (warp - 2) / 4)
-        const int wi = warp - 2, q4 = warp & 3, grp = wi >> 2;
+        const int wi = warp - WORKER0, q4 = warp & 3, grp = wi >> 2;
         const uint32_t lane_off = static_cast<uint32_t>(q4 * 32) << 16;
         const uint32_t full0 = cluster_addr(&sm->full[0], 0);
         const uint32_t acc_empty0 = cluster_addr(&sm->acc_empty, 0);
