@@ -163,7 +163,8 @@ def algorithmic(wl, info, precision, kernel_name, launches_per_step, kernels, P=
     hi/lo split) written per point, plus, with the gradient, the same for the M x P
     per-slice derivatives it casts.  Other kernels: the 4-byte projections they read.
     The fused Chebyshev kernels that read the FP32 rows themselves move 4 d bytes per point
-    (plus 16 bytes of FP64 partial sums per target, or the 4-byte weight per source) beside
+    (plus two FP64 partial sums per 256-slice half per target, or the 4-byte weight per
+    source) beside
     their 2 d P flop; at d = 784, P = 512 the two minimum times are within 5% of each other,
     and the bound reported is the one with the longer minimum time under `peaks` (HBM copy
     bandwidth, sustained BF16).
@@ -175,7 +176,7 @@ def algorithmic(wl, info, precision, kernel_name, launches_per_step, kernels, P=
             (kernel_name.startswith("umma_cheb_target") and f32_direct(wl, kernels)):
         flops = 2.0 * pts * wl.d * P
         if kernel_name.startswith("pair_cheb_target"):
-            nbytes = pts * (4.0 * wl.d + 16.0)  # FP32 rows in, two FP64 partial sums out
+            nbytes = pts * (4.0 * wl.d + 8.0 * (4 if P > 256 else 2))  # FP32 rows in, FP64 partial sums out
         elif kernel_name.startswith("pair_cheb_moments"):
             nbytes = pts * (4.0 * wl.d + 4.0)  # FP32 rows and weights in (moment partials: per CTA pair)
         else:

@@ -480,7 +480,7 @@ bool fused_cheb_source(slk_plan plan, const float* x, int64_t ldx, const float* 
     double tol = plan->desc.tol;
     if (tol <= 0.0) tol = default_tol(SLK_GAUSSIAN, plan->desc.precision);
     FourierHost fh = choose_gaussian(plan->desc.param, d, R, plan->desc.n_coeff, plan->desc.method, tol);
-    if (fh.method != SLK_FOURIER_CHEB || !umma_moments_fit(fh.cheb_qp) || (pair && !pair_cheb_fits(P, fh.cheb_qp)))
+    if (fh.method != SLK_FOURIER_CHEB || !umma_moments_fit(fh.cheb_qp) || (pair && !pair_cheb_fits(P, fh.cheb_qp, d)))
         return false;
     plan->fh = fh;
     plan->R = R;
@@ -612,8 +612,8 @@ bool sum_fused_cheb(slk_plan plan, const T* y, int64_t M, int64_t ldy, void* s_u
             return false;
         const void* coef = plan->fd.horner ? plan->fd.mono : plan->beta.get();
         // aligned FP32 rows and P <= 512: the CTA-pair kernel, all slices of a tile at once
-        const bool pair = umma_f32_operand_ok(y, ldy) && pair_cheb_fits(plan->P, plan->fh.cheb_qp);
-        const int parts = pair ? 2 : static_cast<int>(umma_cheb_parts(plan->P));
+        const bool pair = umma_f32_operand_ok(y, ldy) && pair_cheb_fits(plan->P, plan->fh.cheb_qp, plan->d);
+        const int parts = static_cast<int>(pair ? pair_cheb_parts(plan->P) : umma_cheb_parts(plan->P));
         DevBuf<double> part(static_cast<size_t>(parts) * M, st);
         if (pair)
             launch_pair_cheb_target(y, ldy, plan->mu32.get(), M, plan->xib.get(), plan->P, plan->d,

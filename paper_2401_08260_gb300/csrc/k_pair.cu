@@ -4,30 +4,29 @@
 // with the projection of Algorithm 1 fused in) read the caller's FP32 points directly:
 //   target side  t(y) = sum_p sum_l beta[p][l] T_l(<xi_p, y - mu> / R)   (row sums per point)
 //   source side  mom[p][j] = sum_n w_n T_j(<xi_p, x_n - mu> / R)          (moments per slice)
-// The pair of CTAs of a cluster of two forms one 256-point tile.  Each CTA brings in,
-// per 64-wide K stage, its own 128 FP32 point rows (two 32-column TMA boxes, converted
-// in place to centred BF16 in the tensor core's 128-byte-swizzled layout by its eight
-// worker warps) and its own 128 rows of each 256-direction sub-tile; while it works on a
-// tile its producer streams the rows of its next tile into L2, one contiguous chunk per
-// stage.  The even CTA
-// issues M = 256, N = 256 MMAs (kind::f16, FP32 accumulate) for up to two sub-tiles,
-// i.e. all P <= 512 slices of the tile at once, into two 256-column accumulators of each
-// CTA's tensor memory:
+//
+// Work item: one 256-point tile against one 256-slice half of the P <= 512 directions,
+// computed by the two CTAs of a cluster of two.  Each CTA brings in, per 64-wide K stage,
+// its own 128 FP32 point rows (two 32-column TMA boxes, converted in place to centred BF16
+// in the tensor core's 128-byte-swizzled layout by three converter warps) and its own 128
+// rows of the half's directions; the even CTA issues M = 256, N = 256 MMAs (kind::f16,
+// FP32 accumulate) into one of two 256-column accumulators of each CTA's tensor memory,
+// so that the epilogue of one item overlaps the MMAs of the next:
 //   target side: A = points (rows = TMEM lanes), B = directions, D[point][slice];
 //   source side: A = directions (rows = slices), B = points, D[slice][point].
-// Every point is therefore read once, and each direction once per 256 points (the CTA
-// pair shares the tile through the pair MMA, not through any shared load).
+// Items go round the pairs in order, so with an even number of pairs the two pairs that
+// take the two halves of a tile work on it at the same time and the second read of its
+// points is served by L2; while a CTA works on an item, its poller streams the rows of
+// its next item's tile into L2, one contiguous chunk per stage.
 //
-// Signals between the two CTAs are remote mbarrier arrivals at cluster scope:
-//   workers of both CTAs     -> full[s] of the even CTA  (stage converted, 16 arrivals)
-//   even CTA's MMA commit    -> its own empty[s]; its producer forwards the release to the
-//                               odd CTA's empty[s] when it refills that stage
-//   even CTA's MMA commit    -> its own acc_full; one worker thread forwards it
-//   workers of both CTAs     -> acc_empty of the even CTA (16 arrivals)
-// The worker warps alternate between converting the stages of a tile and reading its
-// accumulators back once the MMAs are done (the 512 TMEM columns hold one tile's two
-// accumulators); each reads 32 columns at a time, the next load in flight while it
-// evaluates the current one.
+// One thread of each CTA (warp 0) polls its barriers without blocking and issues
+// whatever is ready: TMA loads of free stages and, on the even CTA, the MMAs of converted
+// stages.  Signals between the CTAs are remote mbarrier arrivals at cluster scope:
+//   odd CTA's converter warps    -> full[s] of the even CTA (release: their writes)
+//   even CTA's poller            -> empty[s] of the odd CTA when the pair's MMAs released it
+//                                   (relaxed: a pure signal)
+//   one even-CTA epilogue thread -> acc_full[b] of the odd CTA
+//   epilogue warps of both       -> acc_empty[b] of the even CTA (16 arrivals)
 // Every wait is bounded; on a timeout the CTA records an error bit and skips the rest.
 // Before exit each CTA waits for its own TMA fills, the even CTA for its last MMAs, and
 // both meet at a cluster barrier before tensor memory is freed.
@@ -49,24 +48,25 @@ using namespace umma;
 constexpr int QM = 128;                      // rows per CTA (TMEM lanes); pair MMA M = 256
 constexpr int QN = 256;                      // MMA N (128 rows of B from each CTA)
 constexpr int QK = 64;                       // K elements per stage
-constexpr int QSTAGES = 3;
-constexpr int QTHREADS = 384;                // warp 0 TMA, 1 MMA, 4-11 workers (convert + epilogue)
-constexpr int WORKER0 = 4;                   // first worker warp (TMEM lane quarter = warp % 4)
-constexpr int WORKER_WARPS = 8;              // each converts 16 of the 128 rows of a stage
+constexpr int QSTAGES = 4;
+constexpr int QTHREADS = 384;                // warp 0 poller, 1-3 converters, 4-11 epilogue
+constexpr int CVT_WARPS = 3;
+constexpr int EPI0 = 4;                      // first epilogue warp (TMEM lane quarter = warp % 4)
 constexpr int CVT_BYTES = QM * QK * 4;       // 128 FP32 rows x 64 (two 32-column boxes)
-constexpr int DIR_BYTES = QM * QK * 2;       // 128 BF16 direction rows x 64, one sub-tile
-constexpr int QSTAGE_BYTES = CVT_BYTES + 2 * DIR_BYTES;
-constexpr int QMAX_P = 2 * QN;               // slices per pass (two accumulators)
-constexpr uint32_t QTMEM_COLS = 512;
+constexpr int DIR_BYTES = QM * QK * 2;       // 128 BF16 direction rows x 64
+constexpr int QSTAGE_BYTES = CVT_BYTES + DIR_BYTES;
+constexpr int QMAX_P = 2 * QN;               // two halves of 256 slices
+constexpr uint32_t QTMEM_COLS = 512;         // two 256-column accumulators
 
 enum { SIDE_TARGET = 0, SIDE_SOURCE = 1 };
 
 struct PairSmem {
     uint64_t raw[QSTAGES];    // this CTA's TMA bytes of a stage have landed
-    uint64_t full[QSTAGES];   // even CTA: both CTAs' converters finished a stage
+    uint64_t cvt[QSTAGES];    // even CTA: its converters finished a stage (3 arrivals)
+    uint64_t full[QSTAGES];   // even CTA: the odd CTA's converters finished a stage (3 arrivals)
     uint64_t empty[QSTAGES];  // the stage may be refilled
-    uint64_t acc_full;        // the tile's accumulators are complete
-    uint64_t acc_empty;       // even CTA: both CTAs' epilogues have read them
+    uint64_t acc_full[2];     // an accumulator holds a finished item
+    uint64_t acc_empty[2];    // even CTA: both CTAs' epilogues have read it
     uint64_t drain;           // even CTA: its last MMAs completed
     uint32_t tmem_base;
 };
@@ -76,40 +76,45 @@ struct PairArgs {
     int P;          // slices (<= 512)
     int d;
     int tiles;      // 256-point tiles
+    int halves;     // 256-slice halves (1 or 2)
     int q;          // Chebyshev terms
     int horner;     // target side: monomial coefficients
     float R, inv_R;
     const float* mu;    // centre (d values)
     const float* beta;  // target side: P x q coefficients
-    double* part;       // target side: 2 x ldp FP64 row sums
+    double* part;       // target side: 2 * halves rows of ldp FP64 row sums
     int64_t ldp;
     const float* pts;   // the FP32 points (for the L2 prefetch), row stride ldpts
     int64_t ldpts;
     const float* w;     // source side: weights of the n points
-    double* mom;        // source side: moment partials [(pair * halves + h) * P + p][q]
+    double* mom;        // source side: moment partials [chunk * P + p][q]
     float* absmax;      // source side: max |z| over the points
     unsigned* err;
 };
 
-// dynamic shared memory: the stage ring, the barriers and (target side) the q x 512
-// coefficients; at most 226 KB (q = 16)
-__host__ __device__ constexpr size_t pair_smem_bytes(int beta_terms) {
-    return 1024 + static_cast<size_t>(QSTAGES) * QSTAGE_BYTES + ((sizeof(PairSmem) + 15) & ~size_t(15)) +
-           static_cast<size_t>(QMAX_P) * beta_terms * sizeof(float);
+// dynamic shared memory: the stage ring, the barriers, (target side) the q x 512
+// coefficients and the d values of the centre (read by the converters from shared memory,
+// so that no global load is outstanding when they signal the other CTA)
+__host__ __device__ constexpr size_t pair_beta_offset() {
+    return static_cast<size_t>(QSTAGES) * QSTAGE_BYTES + ((sizeof(PairSmem) + 15) & ~size_t(15));
 }
-constexpr size_t kPairSmemMax = pair_smem_bytes(16);
+__host__ __device__ constexpr size_t pair_smem_bytes(int beta_terms, int d) {
+    return 1024 + pair_beta_offset() + static_cast<size_t>(QMAX_P) * beta_terms * sizeof(float) +
+           ((static_cast<size_t>(d) * sizeof(float) + 15) & ~size_t(15));
+}
+constexpr size_t kPairSmemMax = 227 * 1024;
 
-// Convert 16 of one stage's 128 FP32 rows (rows 16 wi .. 16 wi + 15; the stage holds two
+// Convert 16 of one stage's 128 FP32 rows (rows 16 bi .. 16 bi + 15; the stage holds two
 // unswizzled 32-column boxes of 128 bytes per row) to centred BF16 in place over the first
 // box, 128-byte swizzle (16-byte chunk c of row r at c ^ (r % 8)); rows at or beyond n are
 // written as zeros.  Lane l takes columns 4j..4j+3 (j = l % 16) of rows 2u + l / 16; m holds
 // the centre at those columns (the same arithmetic as the single-CTA converting kernel).
-__device__ __forceinline__ void convert_rows16(unsigned char* cv, int lane, int wi, const float (&m)[4], int row0,
+__device__ __forceinline__ void convert_rows16(unsigned char* cv, int lane, int bi, const float (&m)[4], int row0,
                                                int n) {
     constexpr int HALF = QM * 128;
     const int j = lane & 15, rr = lane >> 4;
     const unsigned char* src = cv + (j >> 3) * HALF + (j & 7) * 16;
-    const int r0 = wi * 16;
+    const int r0 = bi * 16;
     float4 v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) v[u] = *reinterpret_cast<const float4*>(src + (r0 + 2 * u + rr) * 128);
@@ -129,24 +134,29 @@ template <int SIDE>
 __global__ void __launch_bounds__(QTHREADS, 1)
     k_pair_cheb(const __grid_constant__ CUtensorMap map_pts, const __grid_constant__ CUtensorMap map_dir, PairArgs a) {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // 1024-byte aligned start, derived from the shared array itself so that every access
+    // through it compiles to a shared-memory instruction
+    unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     PairSmem* sm = reinterpret_cast<PairSmem*>(base + QSTAGES * QSTAGE_BYTES);
-    float* sbeta = reinterpret_cast<float*>(base + QSTAGES * QSTAGE_BYTES + ((sizeof(PairSmem) + 15) & ~size_t(15)));
+    float* sbeta = reinterpret_cast<float*>(base + pair_beta_offset());
+    float* smu = sbeta + (SIDE == SIDE_TARGET ? QMAX_P * a.q : 0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_rank();
     const int pair = static_cast<int>(blockIdx.x >> 1), npairs = static_cast<int>(gridDim.x >> 1);
     const int kblocks = (a.d + QK - 1) / QK;
-    const int nsub = a.P > QN ? 2 : 1;
-    const uint32_t stage_tx = CVT_BYTES + nsub * DIR_BYTES;
+    const int items = a.tiles * a.halves;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < QSTAGES; ++s) {
             mbar_init(&sm->raw[s], 1);
-            mbar_init(&sm->full[s], 2 * WORKER_WARPS);  // one arrival per worker warp of each CTA
+            mbar_init(&sm->cvt[s], CVT_WARPS);
+            mbar_init(&sm->full[s], CVT_WARPS);  // even CTA: one arrival per converter warp of the odd CTA
             mbar_init(&sm->empty[s], 1);
         }
-        mbar_init(&sm->acc_full, 1);
-        mbar_init(&sm->acc_empty, 2 * WORKER_WARPS);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sm->acc_full[b], 1);
+            mbar_init(&sm->acc_empty[b], 2 * 8);
+        }
         mbar_init(&sm->drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -155,6 +165,7 @@ __global__ void __launch_bounds__(QTHREADS, 1)
             const int l = e / QMAX_P, p = e - l * QMAX_P;
             sbeta[e] = p < a.P ? a.beta[static_cast<int64_t>(p) * a.q + l] : 0.0f;
         }
+    for (int k = threadIdx.x; k < a.d; k += blockDim.x) smu[k] = a.mu[k];
     if (warp == 2) tmem_alloc_pair(&sm->tmem_base, QTMEM_COLS);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -163,174 +174,176 @@ __global__ void __launch_bounds__(QTHREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = sm->tmem_base;
 
-    int ntile = 0;
-    for (int t = pair; t < a.tiles; t += npairs) ++ntile;
-    const int total = ntile * kblocks;
+    // this pair's items: pair, pair + npairs, ...; item -> (tile, half)
+    int nloc = 0;
+    for (int it = pair; it < items; it += npairs) ++nloc;
+    const int total = nloc * kblocks;
+    auto item_of = [&](int li) { return pair + li * npairs; };
+    auto prow_of = [&](int li) { return (item_of(li) / a.halves) * (2 * QM) + static_cast<int>(rank) * QM; };
 
     if (warp == 0) {
-        // ---------------- producer: TMA loads of this CTA's stages, L2 prefetch of its next tile
+        // ---------------- poller (one thread): TMA loads, the even CTA's MMAs, the odd CTA's forwards
         if (lane == 0) {
-            int issued = 0;
-            // rows of the next tile brought into L2 a chunk per stage (contiguous bytes of
-            // the row-major points), so that the TMA loads of a tile find it there
+            // rows of the next item's tile brought into L2 a chunk per stage (contiguous bytes
+            // of the row-major points), so that its TMA loads find them there
             const int chunk = (QM + kblocks - 1) / kblocks;
-            auto prefetch_rows = [&](int tile, int kb) {
-                const int rbase = tile * (2 * QM) + static_cast<int>(rank) * QM;
+            auto prefetch_rows = [&](int li, int kb) {
+                if (li >= nloc) return;
+                const int rbase = prow_of(li);
                 const int r0 = rbase + kb * chunk;
                 int r1 = r0 + chunk;
                 if (r1 > rbase + QM) r1 = rbase + QM;
                 if (r1 > a.n) r1 = a.n;
-                if (tile >= a.tiles || r0 >= r1) return;
+                if (r0 >= r1) return;
                 // from the first element of row r0 to the last element of row r1 - 1, rounded
                 // down to 16 bytes (never past the caller's rows)
                 const int64_t bytes = ((static_cast<int64_t>(r1 - r0 - 1) * a.ldpts + a.d) * 4) & ~int64_t(15);
                 if (bytes > 0)
                     bulk_prefetch_l2(a.pts + static_cast<int64_t>(r0) * a.ldpts, static_cast<uint32_t>(bytes));
             };
-            for (int gg = 0; gg < total; ++gg) {
-                const int tile = pair + (gg / kblocks) * npairs, kb = gg % kblocks, s = gg % QSTAGES;
-                if (gg >= QSTAGES) {
-                    // released by the pair's MMAs: on the even CTA by their commit, on the odd
-                    // CTA by the even CTA's producer forwarding that release
-                    const bool ok = rank == 0 ? mbar_wait(&sm->empty[s], ((gg / QSTAGES) - 1) & 1)
-                                              : mbar_wait_cluster(&sm->empty[s], ((gg / QSTAGES) - 1) & 1);
-                    if (!ok) {
-                        atomicOr(a.err, 8u);
-                        break;
-                    }
-                    if (rank == 0) mbar_arrive_cluster(cluster_addr(&sm->empty[s], 1));
-                }
-                const int prow = tile * (2 * QM) + static_cast<int>(rank) * QM;
+            auto issue = [&](int g) {
+                const int li = g / kblocks, kb = g % kblocks, s = g % QSTAGES;
+                const int half = item_of(li) % a.halves;
                 unsigned char* st = base + s * QSTAGE_BYTES;
-                mbar_expect_tx(&sm->raw[s], stage_tx);
-                tma_load_2d(st, &map_pts, &sm->raw[s], kb * QK, prow);
-                tma_load_2d(st + QM * 128, &map_pts, &sm->raw[s], kb * QK + 32, prow);
-                for (int j = 0; j < nsub; ++j)
-                    tma_load_2d(st + CVT_BYTES + j * DIR_BYTES, &map_dir, &sm->raw[s], kb * QK,
-                                j * QN + static_cast<int>(rank) * QM);
-                ++issued;
-                prefetch_rows(tile + npairs, kb);
-            }
-            drain_fills(sm->raw, QSTAGES, issued);
-        }
-    } else if (warp == 1) {
-        // ---------------- MMA issuer (even CTA): M = 256 over the pair, one or two sub-tiles
-        if (rank == 0 && lane == 0) {
+                mbar_expect_tx(&sm->raw[s], CVT_BYTES + DIR_BYTES);
+                tma_load_2d(st, &map_pts, &sm->raw[s], kb * QK, prow_of(li));
+                tma_load_2d(st + QM * 128, &map_pts, &sm->raw[s], kb * QK + 32, prow_of(li));
+                tma_load_2d(st + CVT_BYTES, &map_dir, &sm->raw[s], kb * QK, half * QN + static_cast<int>(rank) * QM);
+                prefetch_rows(li + 1, kb);
+            };
             const uint32_t idesc = instr_desc(1u, 2 * QM, QN);
-            for (int g = 0; g < total; ++g) {
-                const int kb = g % kblocks, t = g / kblocks, s = g % QSTAGES;
-                if (kb == 0 && t >= 1 && !mbar_wait_cluster(&sm->acc_empty, (t - 1) & 1)) {
-                    atomicOr(a.err, 16u);
-                    break;
-                }
-                if (!mbar_wait_cluster(&sm->full[s], (g / QSTAGES) & 1)) {
-                    atomicOr(a.err, 16u);
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                unsigned char* st = base + s * QSTAGE_BYTES;
-#pragma unroll
-                for (int k = 0; k < QK / 16; ++k)
-                    for (int j = 0; j < nsub; ++j) {
-                        const uint64_t dp = smem_desc(st + k * 32);
-                        const uint64_t dd = smem_desc(st + CVT_BYTES + j * DIR_BYTES + k * 32);
-                        if (SIDE == SIDE_TARGET)
-                            umma_f16_pair(tmem + j * QN, dp, dd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
-                        else
-                            umma_f16_pair(tmem + j * QN, dd, dp, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+            const uint32_t peer_empty0 = cluster_addr(&sm->empty[0], 1);
+            int gf = 0, gm = 0;  // next fill, next MMA stage (even CTA)
+            unsigned idle = 0;
+            while (gf < total || (rank == 0 && gm < total)) {
+                bool progress = false;
+                if (gf < total) {
+                    const int s = gf % QSTAGES;
+                    const uint32_t ph = ((gf / QSTAGES) - 1) & 1;
+                    if (gf < QSTAGES || mbar_test_cta(&sm->empty[s], ph)) {
+                        // the even CTA passes the release of the stage on to the odd CTA (a pure
+                        // signal: the MMAs that read the stage have completed)
+                        if (rank == 0 && gf >= QSTAGES)
+                            mbar_arrive_cluster_relaxed(peer_empty0 + static_cast<uint32_t>(s * sizeof(uint64_t)));
+                        issue(gf);
+                        ++gf;
+                        progress = true;
                     }
-                umma_commit_pair(&sm->empty[s]);
-                if (kb == kblocks - 1) umma_commit_pair(&sm->acc_full);
+                }
+                if (rank == 0 && gm < gf) {
+                    const int s = gm % QSTAGES, kb = gm % kblocks, li = gm / kblocks, b = li & 1;
+                    const uint32_t ph = (gm / QSTAGES) & 1;
+                    const bool acc_free = kb != 0 || li < 2 || mbar_test(&sm->acc_empty[b], ((li >> 1) - 1) & 1);
+                    if (acc_free && mbar_test_cta(&sm->cvt[s], ph) && mbar_test(&sm->full[s], ph)) {
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        unsigned char* st = base + s * QSTAGE_BYTES;
+#pragma unroll
+                        for (int k = 0; k < QK / 16; ++k) {
+                            const uint64_t dp = smem_desc(st + k * 32);
+                            const uint64_t dd = smem_desc(st + CVT_BYTES + k * 32);
+                            if (SIDE == SIDE_TARGET)
+                                umma_f16_pair(tmem + b * QN, dp, dd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                            else
+                                umma_f16_pair(tmem + b * QN, dd, dp, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                        }
+                        umma_commit_pair(&sm->empty[s]);
+                        if (kb == kblocks - 1) umma_commit_pair(&sm->acc_full[b]);
+                        ++gm;
+                        progress = true;
+                    }
+                }
+                if (progress) {
+                    idle = 0;
+                } else if (++idle > WAIT_LIMIT) {
+                    atomicOr(a.err, rank == 0 ? 16u : 8u);
+                    break;
+                }
             }
-            drain_mma_pair(&sm->drain, a.err, 16u);
+            drain_fills(sm->raw, QSTAGES, gf);
+            if (rank == 0) drain_mma_pair(&sm->drain, a.err, 16u);
         }
-    } else if (warp >= WORKER0) {
-        // ---------------- workers (warps 4-11; warps 2-3 have no role): for each tile, convert this warp's 16 rows of
-        // every stage as it lands, then read the finished accumulators back (TMEM lane
-        // quarter warp % 4, column group (warp - 2) / 4)
-        const int wi = warp - WORKER0, q4 = warp & 3, grp = wi >> 2;
-        const uint32_t lane_off = static_cast<uint32_t>(q4 * 32) << 16;
-        const uint32_t full0 = cluster_addr(&sm->full[0], 0);
-        const uint32_t acc_empty0 = cluster_addr(&sm->acc_empty, 0);
-        const uint32_t peer_full = cluster_addr(&sm->acc_full, 1);
-        const bool forwarder = rank == 0 && wi == 0 && lane == 0;
-        // the centre's four columns of this lane for the next stage, loaded a stage ahead
-        float mnext[4];
-        auto load_mu = [&](int kb) {
+    } else if (warp < EPI0) {
+        // ---------------- converters (warps 1-3) of this CTA's points: 16-row batches
+        // cw, cw + 3, ... of every stage
+        const int cw = warp - 1;
+        const uint32_t lead_full0 = cluster_addr(&sm->full[0], 0);
+        for (int g = 0; g < total; ++g) {
+            const int s = g % QSTAGES, kb = g % kblocks;
+            float m[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int k = kb * QK + 4 * (lane & 15) + e;
-                mnext[e] = k < a.d ? __ldg(a.mu + k) : 0.0f;
+                m[e] = k < a.d ? smu[k] : 0.0f;
             }
-        };
-        load_mu(0);
-        bool ok = true;
-        // convert the stages of local tile t; false on a timeout
-        auto convert_tile = [&](int t) {
-            const int tile = pair + t * npairs;
-            for (int kb = 0; kb < kblocks; ++kb) {
-                const int g = t * kblocks + kb, s = g % QSTAGES;
-                float m[4] = {mnext[0], mnext[1], mnext[2], mnext[3]};
-                load_mu(kb + 1 < kblocks ? kb + 1 : 0);
-                const bool got = mbar_wait(&sm->raw[s], (g / QSTAGES) & 1);
-                if (!__all_sync(0xffffffffu, got)) {
-                    if (lane == 0) atomicOr(a.err, 8u);
-                    return false;
-                }
-                convert_rows16(base + s * QSTAGE_BYTES, lane, wi, m, tile * (2 * QM) + static_cast<int>(rank) * QM,
-                               a.n);
-                // generic-proxy writes, read next by the tensor core (async proxy)
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive_cluster(full0 + static_cast<uint32_t>(s * sizeof(uint64_t)));
+            const bool got = mbar_wait(&sm->raw[s], (g / QSTAGES) & 1);
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0) atomicOr(a.err, 8u);
+                break;
             }
-            return true;
-        };
-        auto wait_acc = [&](int t) {
-            if (!mbar_wait_cluster(&sm->acc_full, t & 1)) {
+            const int row0 = prow_of(g / kblocks);
+            for (int bi = cw; bi < QM / 16; bi += CVT_WARPS)
+                convert_rows16(base + s * QSTAGE_BYTES, lane, bi, m, row0, a.n);
+            // generic-proxy writes, read next by the tensor core (async proxy)
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            // even CTA: its own converters' barrier; odd CTA: straight to the even CTA's full[s]
+            if (lane == 0) {
+                if (rank == 0) mbar_arrive(&sm->cvt[s]);
+                else mbar_arrive_cluster(lead_full0 + static_cast<uint32_t>(s * sizeof(uint64_t)));
+            }
+        }
+    } else {
+        // ---------------- epilogue (warps 4-11): TMEM lane quarter warp % 4, column half
+        // grp = (warp - 4) / 4 of the item's accumulator
+        const int q4 = warp & 3, grp = (warp - EPI0) >> 2;
+        const uint32_t lane_off = static_cast<uint32_t>(q4 * 32) << 16;
+        const uint32_t acc_empty0 = cluster_addr(&sm->acc_empty[0], 0);
+        const uint32_t peer_full0 = cluster_addr(&sm->acc_full[0], 1);
+        const bool forwarder = rank == 0 && warp == EPI0 && lane == 0;
+        auto wait_acc = [&](int li) {
+            const int b = li & 1;
+            if (!mbar_wait_cluster(&sm->acc_full[b], (li >> 1) & 1)) {
                 atomicOr(a.err, 32u);
                 return false;
             }
-            if (forwarder) mbar_arrive_cluster(peer_full);
+            if (forwarder) mbar_arrive_cluster(peer_full0 + static_cast<uint32_t>(b * sizeof(uint64_t)));
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             return true;
         };
-        auto release_acc = [&]() {
+        auto release_acc = [&](int li) {
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive_cluster(acc_empty0);
+            if (lane == 0) mbar_arrive_cluster(acc_empty0 + static_cast<uint32_t>((li & 1) * sizeof(uint64_t)));
         };
+        constexpr int NC = QN / 2;  // columns per thread
         if (SIDE == SIDE_TARGET) {
-            // row sums of t_p(z) over the slices of this warp's column group
-            const uint32_t col0 = nsub == 2 ? grp * QN : grp * (QN / 2);
-            const int ncols = nsub == 2 ? QN : QN / 2;
+            // row sums of t_p(z) over this warp's 128 slices of the item's half
             bool bad = false;
             auto run = [&](auto qp_tag, auto horner_tag) {
                 constexpr int QP = decltype(qp_tag)::value;
                 constexpr bool HORNER = decltype(horner_tag)::value;
-                for (int t = 0; t < ntile && ok; ++t) {
-                    if (!convert_tile(t) || !wait_acc(t)) {
-                        ok = false;
-                        break;
-                    }
-                    const int tile = pair + t * npairs;
-                    const int row = tile * (2 * QM) + static_cast<int>(rank) * QM + q4 * 32 + lane;
+                for (int li = 0; li < nloc; ++li) {
+                    if (!wait_acc(li)) break;
+                    const int item = item_of(li), half = item % a.halves;
+                    const int row = (item / a.halves) * (2 * QM) + static_cast<int>(rank) * QM + q4 * 32 + lane;
+                    const float* bt = sbeta + half * QN + grp * NC;
                     float sum = 0.0f, comp = 0.0f;  // Kahan
                     uint32_t ra[32], rb[32];
-                    const uint32_t tbase = tmem + lane_off + col0;
+                    const uint32_t tbase = tmem + lane_off + (li & 1) * QN + grp * NC;
                     tmem_ld32_issue(tbase, ra);
                     tmem_wait32(ra);
-                    for (int cc = 0; cc < ncols; cc += 64) {
+#pragma unroll 1
+                    for (int cc = 0; cc < NC; cc += 64) {
                         tmem_ld32_issue(tbase + cc + 32, rb);
-                        cheb_chunk32<QP, HORNER>(ra, sbeta + col0 + cc, QMAX_P, a.R, a.inv_R, sum, comp, bad);
+                        cheb_chunk32<QP, HORNER>(ra, bt + cc, QMAX_P, a.R, a.inv_R, sum, comp, bad);
                         tmem_wait32(rb);
-                        if (cc + 64 < ncols) tmem_ld32_issue(tbase + cc + 64, ra);
-                        cheb_chunk32<QP, HORNER>(rb, sbeta + col0 + cc + 32, QMAX_P, a.R, a.inv_R, sum, comp, bad);
-                        if (cc + 64 < ncols) tmem_wait32(ra);
+                        if (cc + 64 < NC) tmem_ld32_issue(tbase + cc + 64, ra);
+                        cheb_chunk32<QP, HORNER>(rb, bt + cc + 32, QMAX_P, a.R, a.inv_R, sum, comp, bad);
+                        if (cc + 64 < NC) tmem_wait32(ra);
                     }
-                    release_acc();
+                    release_acc(li);
                     if (row < a.n)
-                        a.part[static_cast<int64_t>(grp) * a.ldp + row] =
+                        a.part[static_cast<int64_t>(half * 2 + grp) * a.ldp + row] =
                             static_cast<double>(sum) - static_cast<double>(comp);
                 }
             };
@@ -342,58 +355,54 @@ __global__ void __launch_bounds__(QTHREADS, 1)
             else a.horner ? run(std::integral_constant<int, 16>{}, T_{}) : run(std::integral_constant<int, 16>{}, F_{});
             if (bad) atomicOr(a.err, 4u);
         } else {
-            // one slice's moments per thread over all tiles: two sub-tiles, group j owns the
-            // slices of accumulator j (all 256 points); one sub-tile, both groups own the same
-            // slices, each over half of the points
-            const uint32_t col0 = nsub == 2 ? grp * QN : 0;
-            const int pt_off = nsub == 2 ? 0 : grp * (QN / 2);
-            const int ncols = nsub == 2 ? QN : QN / 2;
-            const int slice = (nsub == 2 ? grp * QN : 0) + static_cast<int>(rank) * QM + q4 * 32 + lane;
+            // one slice's moments per thread over this warp's 128 points of every item; a pair
+            // keeps one half of the slices throughout (the host launches an even number of
+            // pairs when there are two halves)
+            const int half = pair % a.halves;
+            const int slice = half * QN + static_cast<int>(rank) * QM + q4 * 32 + lane;
             float mx = 0.0f;
             auto run = [&](auto qp_tag) {
                 constexpr int QP = decltype(qp_tag)::value;
                 float hi[QP], lo[QP];
 #pragma unroll
                 for (int k = 0; k < QP; ++k) hi[k] = lo[k] = 0.0f;
-                auto chunk = [&](const uint32_t (&r)[32], int tile, int cc, float (&tt)[QP]) {
-                    // accumulator column c holds point tile * 256 + c (columns 0-127 from the
-                    // even CTA's rows of B, 128-255 from the odd CTA's)
-                    const int pt0 = tile * (2 * QM) + pt_off + cc;
-                    const float wl = pt0 + lane < a.n ? __ldg(a.w + pt0 + lane) : 0.0f;
-                    float v[32];
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-                    mom_chunk<QP>(v, wl, a.inv_R, a.n - pt0, tt, mx);
-                };
-                for (int t = 0; t < ntile && ok; ++t) {
-                    if (!convert_tile(t) || !wait_acc(t)) {
-                        ok = false;
-                        break;
-                    }
-                    const int tile = pair + t * npairs;
+                for (int li = 0; li < nloc; ++li) {
+                    if (!wait_acc(li)) break;
+                    const int tile = item_of(li) / a.halves;
                     float tt[QP];
 #pragma unroll
                     for (int k = 0; k < QP; ++k) tt[k] = 0.0f;
+                    auto chunk = [&](const uint32_t (&r)[32], int cc) {
+                        // accumulator column c holds point tile * 256 + c (columns 0-127 from the
+                        // even CTA's rows of B, 128-255 from the odd CTA's)
+                        const int pt0 = tile * (2 * QM) + grp * NC + cc;
+                        const float wl = pt0 + lane < a.n ? __ldg(a.w + pt0 + lane) : 0.0f;
+                        float v[32];
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+                        mom_chunk<QP>(v, wl, a.inv_R, a.n - pt0, tt, mx);
+                    };
                     uint32_t ra[32], rb[32];
-                    const uint32_t tbase = tmem + lane_off + col0 + pt_off;
+                    const uint32_t tbase = tmem + lane_off + (li & 1) * QN + grp * NC;
                     tmem_ld32_issue(tbase, ra);
                     tmem_wait32(ra);
-                    for (int cc = 0; cc < ncols; cc += 64) {
+#pragma unroll 1
+                    for (int cc = 0; cc < NC; cc += 64) {
                         tmem_ld32_issue(tbase + cc + 32, rb);
-                        chunk(ra, tile, cc, tt);
+                        chunk(ra, cc);
                         tmem_wait32(rb);
-                        if (cc + 64 < ncols) tmem_ld32_issue(tbase + cc + 64, ra);
-                        chunk(rb, tile, cc + 32, tt);
-                        if (cc + 64 < ncols) tmem_wait32(ra);
+                        if (cc + 64 < NC) tmem_ld32_issue(tbase + cc + 64, ra);
+                        chunk(rb, cc + 32);
+                        if (cc + 64 < NC) tmem_wait32(ra);
                     }
-                    release_acc();
+                    release_acc(li);
 #pragma unroll
                     for (int k = 0; k < QP; ++k) two_sum_into(hi[k], lo[k], tt[k]);
                 }
                 if (slice < a.P) {
-                    const int halves = nsub == 2 ? 1 : 2;
-                    const int h = nsub == 2 ? 0 : grp;
-                    double* out = a.mom + (static_cast<int64_t>(pair * halves + h) * a.P + slice) * QP;
+                    // chunk: the pair (of a pair of pairs with two halves) and the column half
+                    const int c = (a.halves == 2 ? pair >> 1 : pair) * 2 + grp;
+                    double* out = a.mom + (static_cast<int64_t>(c) * a.P + slice) * QP;
 #pragma unroll
                     for (int k = 0; k < QP; ++k) out[k] = static_cast<double>(hi[k]) + static_cast<double>(lo[k]);
                 }
@@ -420,8 +429,10 @@ __global__ void __launch_bounds__(QTHREADS, 1)
 }
 
 }  // namespace
-
-bool pair_cheb_fits(int P, int q) { return P >= 1 && P <= QMAX_P && (q == 8 || q == 10 || q == 12 || q == 16); }
+bool pair_cheb_fits(int P, int q, int d) {
+    return P >= 1 && P <= QMAX_P && (q == 8 || q == 10 || q == 12 || q == 16) && d >= 1 &&
+           pair_smem_bytes(q, d) <= kPairSmemMax;
+}
 
 namespace {
 
@@ -467,7 +478,7 @@ void launch_pairs(const CUtensorMap& mp, const CUtensorMap& md, const PairArgs& 
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(static_cast<unsigned>(2 * npairs));
     cfg.blockDim = dim3(QTHREADS);
-    cfg.dynamicSmemBytes = pair_smem_bytes(SIDE == SIDE_TARGET ? a.q : 0);
+    cfg.dynamicSmemBytes = pair_smem_bytes(SIDE == SIDE_TARGET ? a.q : 0, a.d);
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
@@ -480,6 +491,7 @@ PairArgs pair_args(int64_t n, int P, int d, int q, double R, const float* mu, un
     a.P = P;
     a.d = d;
     a.tiles = static_cast<int>(ceil_div(n, 2 * QM));
+    a.halves = P > QN ? 2 : 1;
     a.q = q;
     a.R = static_cast<float>(R);
     a.inv_R = static_cast<float>(1.0 / R);
@@ -494,7 +506,7 @@ void launch_pair_cheb_target(const float* y, int64_t ldy, const float* mu, int64
                              const float* coef, int q, int horner, double R, double* part, int64_t ldp, unsigned* err,
                              cudaStream_t st) {
     if (n <= 0) return;
-    SLK_REQUIRE(pair_cheb_fits(P, q), "slice or term count unsupported by the CTA-pair Chebyshev kernel");
+    SLK_REQUIRE(pair_cheb_fits(P, q, d), "slice count, term count or dimension unsupported by the CTA-pair Chebyshev kernel");
     SLK_REQUIRE(umma_f32_operand_ok(y, ldy), "FP32 targets need 16-byte aligned rows");
     SLK_REQUIRE(n < (int64_t(1) << 31) - 2 * QM, "too many targets for one launch");
     const CUtensorMap mp = tmap_f32_rows(y, n, d, ldy, QM);
@@ -507,19 +519,29 @@ void launch_pair_cheb_target(const float* y, int64_t ldy, const float* mu, int64
     a.part = part;
     a.ldp = ldp;
     const int units = pair_units<SIDE_TARGET>();
-    const int npairs = a.tiles < units ? a.tiles : units;
+    const int items = a.tiles * a.halves;
+    // an even number of pairs (when there are more items) keeps the two halves of a tile together
+    const int npairs = items < units ? items : (units & ~1);
     SLK_TIMED("pair_cheb_target", st);
     launch_pairs<SIDE_TARGET>(mp, md, a, npairs, st);
 }
 
-int64_t pair_moments_chunks(int P) {
-    const int halves = P > QN ? 1 : 2;
-    return static_cast<int64_t>(pair_units<SIDE_SOURCE>()) * halves;
+int64_t pair_cheb_parts(int P) { return P > QN ? 4 : 2; }
+
+// Source-side launches use every co-resident pair (an even number of them with two halves,
+// each pair keeping one half of the slices in its registers).
+static int source_pairs(int P) {
+    const int units = pair_units<SIDE_SOURCE>();
+    const int pairs = P > QN ? (units & ~1) : units;
+    SLK_REQUIRE(pairs >= 1, "too few co-resident CTA pairs for the fused moments kernel");
+    return pairs;
 }
+
+int64_t pair_moments_chunks(int P) { return 2 * static_cast<int64_t>(P > QN ? source_pairs(P) / 2 : source_pairs(P)); }
 
 void launch_pair_moments(const float* x, int64_t ldx, const float* mu, int64_t n, const void* xib, int P, int d,
                          const float* w, int q, double R, double* mom, float* absmax, unsigned* err, cudaStream_t st) {
-    SLK_REQUIRE(pair_cheb_fits(P, q), "slice or term count unsupported by the CTA-pair Chebyshev kernel");
+    SLK_REQUIRE(pair_cheb_fits(P, q, d), "slice count, term count or dimension unsupported by the CTA-pair Chebyshev kernel");
     SLK_REQUIRE(umma_f32_operand_ok(x, ldx), "FP32 sources need 16-byte aligned rows");
     SLK_REQUIRE(n >= 1 && n < (int64_t(1) << 31) - 2 * QM, "source count out of range for one launch");
     const CUtensorMap mp = tmap_f32_rows(x, n, d, ldx, QM);
@@ -532,7 +554,7 @@ void launch_pair_moments(const float* x, int64_t ldx, const float* mu, int64_t n
     a.absmax = absmax;
     SLK_TIMED("pair_cheb_moments", st);
     // every pair writes its partial moments (zeros when it has no tile)
-    launch_pairs<SIDE_SOURCE>(mp, md, a, pair_units<SIDE_SOURCE>(), st);
+    launch_pairs<SIDE_SOURCE>(mp, md, a, source_pairs(P), st);
 }
 
 }  // namespace slk

@@ -141,7 +141,9 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256,
     constexpr int EPI_WARPS = EPI == EPI_CHEB || EPI == EPI_MOM ? 8 : 4;
     constexpr int STAGES = G::STAGES;
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // 1024-byte aligned start, derived from the shared array itself so that every access
+    // through it compiles to a shared-memory instruction
+    unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     constexpr int A_BYTES = G::A_BYTES, B_BYTES = G::B_BYTES;
     constexpr int STAGE_BYTES = G::STAGE_BYTES;
     Smem* sm = reinterpret_cast<Smem*>(base + STAGES * STAGE_BYTES);
@@ -553,7 +555,9 @@ __global__ void __launch_bounds__(X3_THREADS, 1)
                       int P, int d, int col_tiles, float* __restrict__ Z, int64_t ldz, float* __restrict__ absmax,
                       unsigned* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // 1024-byte aligned start, derived from the shared array itself so that every access
+    // through it compiles to a shared-memory instruction
+    unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     constexpr int A_BYTES = BM * BK * 2, B_BYTES = X3_BN * BK * 2;
     constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);
     SmemX3* sm = reinterpret_cast<SmemX3*>(base + X3_STAGES * STAGE_BYTES);

@@ -84,12 +84,14 @@ void launch_umma_moments(const void* xa, int64_t n, const void* xib, int P, int 
 // ------------------------------------------------------------ k_pair.cu
 // The two fused Chebyshev sides on CTA pairs (tcgen05 cta_group::2, M = 256) reading the
 // FP32 points directly (centred and rounded to BF16 in shared memory, the same operand as
-// the single-CTA kernels), all P <= 512 slices of a 256-point tile in one pass.
-//   target side: part receives 2 rows of n FP64 partial row sums (row stride ldp);
+// the single-CTA kernels); work items of 256 points x 256 slices, P <= 512.
+//   target side: part receives pair_cheb_parts(P) rows of n FP64 partial row sums (row
+//                stride ldp);
 //   source side: mom receives pair_moments_chunks(P) x P x q FP64 partials, *absmax the
 //                largest |z| over the points.
 // Both need umma_f32_operand_ok on the points; q is 8, 10, 12 or 16.
-bool pair_cheb_fits(int P, int q);
+bool pair_cheb_fits(int P, int q, int d);
+int64_t pair_cheb_parts(int P);
 void launch_pair_cheb_target(const float* y, int64_t ldy, const float* mu, int64_t n, const void* xib, int P, int d,
                              const float* coef, int q, int horner, double R, double* part, int64_t ldp, unsigned* err,
                              cudaStream_t st);

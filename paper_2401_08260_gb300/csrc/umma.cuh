@@ -173,18 +173,40 @@ __device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
     return r;
 }
 
-// release-arrive on an mbarrier of any CTA of the cluster (shared::cluster address)
+// arrive (default release semantics) on an mbarrier of any CTA of the cluster
+// (shared::cluster address).  The cluster-scope form (.release.cluster) was measured to
+// hold the issuing thread for about a microsecond per arrival; the default form is the
+// one used for remote arrivals in the common CUDA cluster pipelines.
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cl_addr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cl_addr) : "memory");
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cl_addr) : "memory");
 }
 
-// bounded wait with cluster-scope acquire (the arrivals may come from the other CTA)
+// arrival on an mbarrier of any CTA of the cluster that orders no data (a pure signal,
+// e.g. that a stage's consumers are done with it)
+__device__ __forceinline__ void mbar_arrive_cluster_relaxed(uint32_t cl_addr) {
+    asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cl_addr) : "memory");
+}
+
+// non-blocking test of a barrier that only this CTA's threads (or its own MMA commits)
+// arrive on (CTA-scope acquire)
+__device__ __forceinline__ bool mbar_test_cta(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// bounded wait on a barrier that the other CTA of the cluster may also arrive on
 __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity) {
     const uint32_t addr = smem_u32(bar);
     for (unsigned it = 0; it < WAIT_LIMIT; ++it) {
         uint32_t done;
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
             " selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
             : "r"(addr), "r"(parity)
@@ -192,6 +214,18 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity
         if (done) return true;
     }
     return false;
+}
+
+// non-blocking: has the phase with the given parity completed?
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
 }
 
 // all threads of both CTAs of the cluster
