@@ -19,6 +19,8 @@ The oracle computes what the paper defines, plainly and slowly:
   Lemma 2.6 (an independent second evaluator).
 * ``negdist_alg2`` -- Algorithm 2 plus the permutation step of Section 3.2,
   used to check that the sorting route is exact.
+* ``rff_features``, ``rff_sum`` -- the random Fourier feature estimators RFF-1 and
+  RFF-2 of Section 4.3 (the paper's comparison system), on given features.
 
 Projections <xi_p, x_n> are a matrix product (numpy FP64); everything else is
 in ``slk_oracle.c`` (FP64, OpenMP over independent outputs).
@@ -226,6 +228,47 @@ def negdist_alg2(zx, w, zy, cdv: float) -> np.ndarray:
     t = np.empty(L)
     t[order] = t_sorted
     return t[:M]
+
+
+def rff_features(kernel, param: float, d: int, D: int, rng: np.random.Generator):
+    """Random Fourier features of Section 4.3: D samples v_p of the spectral measure mu of
+    the kernel (K(x, y) = E_{v ~ mu} cos<x - y, v>, Bochner's theorem) and D phases
+    b_p ~ U[0, 2 pi).  Gaussian F(r) = exp(-r^2 / (2 sigma^2)): mu = N(0, sigma^-2 I);
+    Laplacian F(r) = exp(-alpha r): mu = the multivariate Cauchy law with scale alpha,
+    sampled as alpha g / |h| with g ~ N(0, I_d), h ~ N(0, 1).  Returns (V (D x d), b (D,))."""
+    k = _kid(kernel)
+    g = rng.standard_normal((D, d))
+    if k == GAUSSIAN:
+        V = g / float(param)
+    elif k == LAPLACIAN:
+        h = rng.standard_normal(D)
+        V = float(param) * g / np.abs(h)[:, None]
+    else:
+        raise ValueError("random Fourier features need a positive definite kernel (Gaussian or Laplacian)")
+    b = 2.0 * math.pi * rng.random(D)
+    return V, b
+
+
+def rff_sum(X, Y, w, V, b, variant: int) -> np.ndarray:
+    """Random Fourier feature estimate of s_m = sum_n w_n K(x_n, y_m) (Section 4.3), in FP64.
+
+    variant 1 (RFF-1):  s_m = (2 / D) sum_p cos(<y_m, v_p> + b_p) sum_n w_n cos(<x_n, v_p> + b_p)
+    variant 2 (RFF-2):  s_m = (1 / D) sum_p [cos<y_m, v_p> C_p + sin<y_m, v_p> S_p],
+                        C_p = sum_n w_n cos<x_n, v_p>,  S_p = sum_n w_n sin<x_n, v_p>.
+    The printed equations omit the 1 / D of the sample average of the expectations they
+    subsample; it is restored here."""
+    X, Y, w, V, b = _c64(X), _c64(Y), _c64(w), _c64(V), _c64(b)
+    D = V.shape[0]
+    Zx = X @ V.T  # N x D
+    Zy = Y @ V.T  # M x D
+    if variant == 1:
+        C = np.cos(Zx + b[None, :]).T @ w
+        return (2.0 / D) * (np.cos(Zy + b[None, :]) @ C)
+    if variant == 2:
+        C = np.cos(Zx).T @ w
+        S = np.sin(Zx).T @ w
+        return (np.cos(Zy) @ C + np.sin(Zy) @ S) / D
+    raise ValueError("variant is 1 or 2")
 
 
 def sampled_targets(M: int, count: int, seed: int = 5) -> np.ndarray:
