@@ -638,6 +638,64 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- slicing vs random Fourier features
+
+def run_rff(args):
+    """Section 4.3's comparison on this GPU: the setup of the paper's Table 2 (d = 1000,
+    N = M = 1e5, x, y ~ N(0, 0.1^2 I), w ~ U[0,1]; Gaussian sigma^2 = 5 with D = P,
+    Laplacian alpha = 0.25 with D = 2P) for slicing and RFF-1 / RFF-2, all FP32: device time of
+    one estimate (features / directions drawn by the library) and the per-summand l1 error
+    against the direct sum at a seeded sample of targets (FP64 oracle on the host)."""
+    import torch
+    import oracle
+    from paper_2401_08260_gb300 import slk
+    dev = torch.device("cuda", 0)
+    d, N, M = 1000, args.rff_n, args.rff_n
+    rng = np.random.Generator(np.random.PCG64(1))
+    X = (0.1 * rng.standard_normal((N, d))).astype(np.float32)
+    Y = (0.1 * rng.standard_normal((M, d))).astype(np.float32)
+    w = rng.random(N).astype(np.float32)
+    idx = oracle.sampled_targets(M, args.rff_targets)
+    xs, ws, ys = (torch.from_numpy(a).to(dev) for a in (X, w, Y))
+    rows = []
+
+    def timed(fn):
+        fn()  # warm-up (and the value)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        out = fn()
+        t1.record()
+        torch.cuda.synchronize()
+        return out, t0.elapsed_time(t1)
+
+    for kernel, param, dfac in (("gaussian", math.sqrt(5.0), 1), ("laplacian", 0.25, 2)):
+        ref = oracle.direct_sum(kernel, param, X, Y[idx], w)
+        wsum = float(np.abs(w.astype(np.float64)).sum())
+
+        def l1(s):
+            got = s.double().cpu().numpy()[idx]
+            return float(np.sum(np.abs(got - ref)) / (len(idx) * wsum))
+
+        for P in args.rff_p:
+            s, ms = timed(lambda: slk.kernel_sum(xs, ws, ys, kernel, param, P=P, precision="f32", seed=2))
+            row = {"kernel": kernel, "P": P, "slicing_ms": ms, "slicing_l1": l1(s)}
+            for v in (1, 2):
+                D = dfac * P
+                s, ms = timed(lambda: slk.rff_sum(xs, ws, ys, kernel, param, D, variant=v, precision="f32", seed=3))
+                row[f"rff{v}_D"] = D
+                row[f"rff{v}_ms"] = ms
+                row[f"rff{v}_l1"] = l1(s)
+            rows.append(row)
+    line = {"metric": "slicing vs random Fourier features (per-summand l1 error, device ms)", "unit": "ms",
+            "n_gpus": 1, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "Table 2 setup", "d": d, "N": N, "M": M, "x, y": "N(0, 0.1^2 I)", "w": "U[0,1]",
+                       "targets_checked": int(len(idx))},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -661,6 +719,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
+    ap.add_argument("--rff", action="store_true", help="run the slicing vs random Fourier features comparison")
+    ap.add_argument("--rff-n", type=int, default=100_000)
+    ap.add_argument("--rff-p", type=int, nargs="+", default=[200, 1000, 5000])
+    ap.add_argument("--rff-targets", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-load", type=float, default=0.8, help="arrival rate / plain capacity")
     ap.add_argument("--serve-workers", type=int, default=4)
@@ -671,7 +733,9 @@ def main():
         ap.error("at least 3 warm-up steps")
     if args.steps is None:
         args.steps = 10 if args.impl == "reference" else 200
-    if args.serve:
+    if args.rff:
+        run_rff(args)
+    elif args.serve:
         run_serve(args)
     elif args.impl == "reference":
         run_reference(args)

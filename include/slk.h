@@ -277,6 +277,45 @@ slk_status slk_kernel_sum(const slk_plan_desc* desc, const void* x, int64_t N, i
 slk_status slk_sum_noalloc(slk_plan plan, const void* y, int64_t M, int64_t ldy, void* s, void* stream);
 
 /*
+ * Random Fourier features (Section 4.3): the comparison system of the paper's Table 2,
+ * for shift-invariant positive definite kernels with K(x, y) = E_{v ~ mu} cos<x - y, v>
+ * (Bochner's theorem).  D samples v_p of the spectral measure mu -- Gaussian
+ * F = exp(-r^2 / (2 sigma^2)): mu = N(0, sigma^-2 I); Laplacian F = exp(-alpha r): the
+ * multivariate Cauchy law of scale alpha, sampled as alpha g / |h| with g ~ N(0, I_d),
+ * h ~ N(0, 1) -- and phases b_p ~ U[0, 2 pi) give
+ *   variant 1 (RFF-1): s_m = (2 / D) sum_p cos(<y_m, v_p> + b_p) sum_n w_n cos(<x_n, v_p> + b_p)
+ *   variant 2 (RFF-2): s_m = (1 / D) sum_p [cos<y_m, v_p> C_p + sin<y_m, v_p> S_p],
+ *                      C_p = sum_n w_n cos<x_n, v_p>,  S_p = sum_n w_n sin<x_n, v_p>
+ * (the paper prints the sums over p without the 1 / D of the sample average).
+ */
+typedef struct {
+    int32_t kernel;           /* SLK_GAUSSIAN (param = sigma) or SLK_LAPLACIAN (param = alpha) */
+    int32_t precision;        /* SLK_PREC_F64 or SLK_PREC_F32 (storage and arithmetic) */
+    double param;
+    int32_t d;                /* dimension >= 1 */
+    int32_t D;                /* number of features, 1 .. 65535 */
+    int32_t variant;          /* 1 (RFF-1) or 2 (RFF-2) */
+    int32_t reserved0;
+    uint64_t seed;            /* seed of the library's feature draw (when features == NULL) */
+    const double* features;   /* optional D x (d + 1) row-major FP64 rows (v_p, b_p), host or
+                                 device; NULL = draw them (Philox4x32-10 keyed by seed) */
+    int32_t reserved[4];
+} slk_rff_desc;
+
+/*
+ * s[m] (M values, host or device, the precision's type) = the RFF estimate of the kernel
+ * sums of the N sources x (row stride ldx, weights w) at the M targets y (row stride ldy);
+ * inputs host or device.  Synchronous on stream when any pointer is on the host.
+ * Errors: SLK_ERR_INVALID (kernel not Gaussian or Laplacian, precision not F64/F32,
+ * D or d out of range, NULL pointers, N < 1, strides below d), SLK_ERR_OOM, SLK_ERR_CUDA.
+ */
+slk_status slk_rff_sum(const slk_rff_desc* desc, const void* x, int64_t N, int64_t ldx, const void* w,
+                       const void* y, int64_t M, int64_t ldy, void* s, void* stream);
+/* The features the library draws for desc (seed, kernel, param, d, D) into the host array
+ * features (D x (d + 1) doubles: v_p then b_p per row). */
+slk_status slk_rff_features(const slk_rff_desc* desc, double* features);
+
+/*
  * Profiling support (not part of the paper's method).  Every kernel launch of
  * the library is counted; while timing is enabled, each launch is also
  * bracketed by CUDA events recorded on the stream it is launched on.

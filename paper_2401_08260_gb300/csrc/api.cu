@@ -1031,6 +1031,94 @@ slk_status slk_kernel_sum(const slk_plan_desc* desc, const void* x, int64_t N, i
 
 }  // extern "C"
 
+// ------------------------------------------------------------ random Fourier features
+
+namespace {
+
+void validate_rff(const slk_rff_desc* desc) {
+    SLK_REQUIRE(desc, "desc is NULL");
+    SLK_REQUIRE(desc->kernel == SLK_GAUSSIAN || desc->kernel == SLK_LAPLACIAN,
+                "random Fourier features need a positive definite kernel (Gaussian or Laplacian)");
+    SLK_REQUIRE(desc->precision == SLK_PREC_F64 || desc->precision == SLK_PREC_F32, "precision must be F64 or F32");
+    SLK_REQUIRE(desc->param > 0.0 && std::isfinite(desc->param), "param must be > 0");
+    SLK_REQUIRE(desc->d >= 1, "d must be >= 1");
+    SLK_REQUIRE(desc->D >= 1 && desc->D <= 65535, "D must be in 1 .. 65535");
+    SLK_REQUIRE(desc->variant == 1 || desc->variant == 2, "variant must be 1 or 2");
+}
+
+// The features on the device (D x (d + 1) FP64): the caller's, or the library's draw.
+DevBuf<double> rff_features_dev(const slk_rff_desc* desc, cudaStream_t st) {
+    const size_t n = static_cast<size_t>(desc->D) * (desc->d + 1);
+    DevBuf<double> feat(n, st);
+    if (desc->features) {
+        SLK_CHECK_CUDA(cudaMemcpyAsync(feat.get(), desc->features, sizeof(double) * n, cudaMemcpyDefault, st));
+        if (!is_device_pointer(desc->features)) SLK_CHECK_CUDA(cudaStreamSynchronize(st));
+    } else {
+        launch_rff_draw(feat.get(), desc->D, desc->d, desc->kernel == SLK_LAPLACIAN, desc->param, desc->seed, st);
+    }
+    return feat;
+}
+
+template <class T>
+void rff_impl(const slk_rff_desc* desc, const void* x, int64_t N, int64_t ldx, const void* w, const void* y, int64_t M,
+              int64_t ldy, void* s_user, cudaStream_t st) {
+    const int D = desc->D, d = desc->d;
+    InView<T> xv(x, N, d, ldx, st), yv(y, M, d, ldy, st), wv(w, N, 1, 1, st);
+    DevBuf<double> feat = rff_features_dev(desc, st);
+    DevBuf<T> V(static_cast<size_t>(D) * d, st), b(D, st);
+    launch_rff_split<T>(feat.get(), D, d, V.get(), b.get(), st);
+    DevBuf<double2> cs(D, st);
+    {
+        DevBuf<T> Zx(static_cast<size_t>(D) * N, st);
+        launch_project_simt<T>(V.get(), D, xv.ptr, N, d, xv.ld, nullptr, Zx.get(), N, st);
+        launch_rff_source<T>(Zx.get(), D, N, wv.ptr, b.get(), desc->variant, cs.get(), st);
+    }
+    DevBuf<T> Zy(static_cast<size_t>(D) * M, st);
+    launch_project_simt<T>(V.get(), D, yv.ptr, M, d, yv.ld, nullptr, Zy.get(), M, st);
+    if (is_device_pointer(s_user)) {
+        launch_rff_target<T>(Zy.get(), D, M, b.get(), cs.get(), desc->variant, static_cast<T*>(s_user), st);
+    } else {
+        DevBuf<T> s(M, st);
+        launch_rff_target<T>(Zy.get(), D, M, b.get(), cs.get(), desc->variant, s.get(), st);
+        SLK_CHECK_CUDA(cudaMemcpyAsync(s_user, s.get(), sizeof(T) * M, cudaMemcpyDeviceToHost, st));
+        SLK_CHECK_CUDA(cudaStreamSynchronize(st));
+    }
+}
+
+}  // namespace
+
+extern "C" slk_status slk_rff_sum(const slk_rff_desc* desc, const void* x, int64_t N, int64_t ldx, const void* w,
+                                  const void* y, int64_t M, int64_t ldy, void* s, void* stream) {
+    set_last_error("");
+    return guarded([&] {
+        validate_rff(desc);
+        SLK_REQUIRE(x && w, "x and w must not be NULL");
+        SLK_REQUIRE(N >= 1 && M >= 0, "N must be >= 1 and M >= 0");
+        SLK_REQUIRE(ldx >= desc->d && (M == 0 || ldy >= desc->d), "row strides must be >= d");
+        if (M == 0) return;
+        SLK_REQUIRE(y && s, "y and s must not be NULL");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        if (desc->precision == SLK_PREC_F64) rff_impl<double>(desc, x, N, ldx, w, y, M, ldy, s, st);
+        else rff_impl<float>(desc, x, N, ldx, w, y, M, ldy, s, st);
+        SLK_CHECK_CUDA(cudaGetLastError());
+    });
+}
+
+extern "C" slk_status slk_rff_features(const slk_rff_desc* desc, double* features) {
+    set_last_error("");
+    return guarded([&] {
+        validate_rff(desc);
+        SLK_REQUIRE(features, "features must not be NULL");
+        cudaStream_t st = nullptr;
+        slk_rff_desc own = *desc;
+        own.features = nullptr;
+        DevBuf<double> feat = rff_features_dev(&own, st);
+        SLK_CHECK_CUDA(cudaMemcpyAsync(features, feat.get(), sizeof(double) * own.D * (own.d + 1),
+                                       cudaMemcpyDeviceToHost, st));
+        SLK_CHECK_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
 namespace {
 
 template <class T>

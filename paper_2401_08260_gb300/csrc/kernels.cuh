@@ -99,6 +99,21 @@ int64_t pair_moments_chunks(int P);
 void launch_pair_moments(const float* x, int64_t ldx, const float* mu, int64_t n, const void* xib, int P, int d,
                          const float* w, int q, double R, double* mom, float* absmax, unsigned* err, cudaStream_t st);
 
+// ------------------------------------------------------------ k_rff.cu
+// Random Fourier features (Section 4.3, comparison system).  feat: D x (d + 1) FP64 rows
+// (v_p, b_p) drawn from the kernel's spectral measure (Gaussian: N(0, param^-2 I); Laplacian:
+// multivariate Cauchy of scale param) and U[0, 2 pi) phases, Philox4x32-10 keyed by seed.
+void launch_rff_draw(double* feat, int D, int d, int laplacian, double param, uint64_t seed, cudaStream_t st);
+// V (D x d) and b (D) in the working precision from feat.
+template <class T>
+void launch_rff_split(const double* feat, int D, int d, T* V, T* b, cudaStream_t st);
+// cs[p] = (C_p, S_p) from the projections Z (D x n, row stride n) of the sources.
+template <class T>
+void launch_rff_source(const T* Z, int D, int64_t n, const T* w, const T* b, int variant, double2* cs, cudaStream_t st);
+// s (m targets) from their projections Z (D x m) and cs.
+template <class T>
+void launch_rff_target(const T* Z, int D, int64_t m, const T* b, const double2* cs, int variant, T* s, cudaStream_t st);
+
 // s[i] = scale * sum_{r < parts} part[r * n + i] (fixed order).
 template <class T>
 void launch_sum_parts(const double* part, int parts, int64_t n, double scale, T* s, cudaStream_t st);

@@ -53,6 +53,13 @@ class PlanInfo(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64)]
 
 
+class RffDesc(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("precision", ctypes.c_int32), ("param", ctypes.c_double),
+                ("d", ctypes.c_int32), ("D", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("seed", ctypes.c_uint64), ("features", ctypes.c_void_p),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
 class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -80,6 +87,10 @@ _SIGNATURES = {
     "slk_fourier_params": (ctypes.c_int, [ctypes.POINTER(PlanDesc), ctypes.c_double, ctypes.POINTER(PlanInfo)]),
     "slk_sum_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "slk_rff_sum": (ctypes.c_int, [ctypes.POINTER(RffDesc), ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                   ctypes.c_void_p, ctypes.c_void_p]),
+    "slk_rff_features": (ctypes.c_int, [ctypes.POINTER(RffDesc), ctypes.c_void_p]),
     "slk_launch_count": (ctypes.c_int64, []),
     "slk_device_alloc_count": (ctypes.c_int64, []),
     "slk_timing_enable": (ctypes.c_int, [ctypes.c_int32]),
@@ -342,6 +353,55 @@ def kernel_sum(x, w, y, kernel: str, param: float = 0.0, P: int = 256, precision
     _check(lib.slk_kernel_sum(ctypes.byref(desc), xa.ptr, xa.rows, xa.ld, wa.ptr, ya.ptr, ya.rows, ya.ld, oa.ptr,
                               _stream_of(x)))
     del dirs
+    return out
+
+
+def _rff_desc(kernel: str, param: float, d: int, D: int, variant: int, precision: str, seed: int, features):
+    if kernel not in ("gaussian", "laplacian"):
+        raise ValueError("random Fourier features need the Gaussian or the Laplacian kernel")
+    desc = RffDesc()
+    desc.kernel = KERNELS[kernel]
+    desc.precision = PRECISIONS[precision]
+    desc.param = float(param)
+    desc.d = int(d)
+    desc.D = int(D)
+    desc.variant = int(variant)
+    desc.seed = int(seed)
+    keep = None
+    if features is not None:
+        keep = np.ascontiguousarray(np.asarray(features, dtype=np.float64))
+        if keep.shape != (D, d + 1):
+            raise ValueError(f"features must be D x (d + 1) = {D} x {d + 1}")
+        desc.features = keep.ctypes.data
+    return desc, keep
+
+
+def rff_sum(x, w, y, kernel: str, param: float, D: int, variant: int = 2, precision: str = "f32", seed: int = 0,
+            features=None, out=None):
+    """Random Fourier feature estimate of s_m = sum_n w_n K(x_n, y_m) (Section 4.3; RFF-1 for
+    variant 1, RFF-2 for variant 2) on the library's kernels (slk_rff_sum).  features: an
+    optional D x (d + 1) array of rows (v_p, b_p); None = the library's draw from seed."""
+    lib = load()
+    dtype = _dtype_for(precision)
+    xa, wa, ya = _Arr(x, dtype, 2), _Arr(w, dtype, 1), _Arr(y, dtype, 2)
+    desc, keep = _rff_desc(kernel, param, int(x.shape[1]), D, variant, precision, seed, features)
+    if out is None:
+        if torch is not None and isinstance(y, torch.Tensor):
+            out = torch.empty(ya.rows, dtype=ya.keep.dtype, device=ya.keep.device)
+        else:
+            out = np.empty(ya.rows, dtype=dtype)
+    oa = _Arr(out, dtype, 1)
+    _check(lib.slk_rff_sum(ctypes.byref(desc), xa.ptr, xa.rows, xa.ld, wa.ptr, ya.ptr, ya.rows, ya.ld, oa.ptr,
+                           _stream_of(x)))
+    del keep
+    return out
+
+
+def rff_features(kernel: str, param: float, d: int, D: int, seed: int = 0) -> np.ndarray:
+    """The D x (d + 1) features (v_p, b_p) the library draws for these arguments."""
+    desc, _ = _rff_desc(kernel, param, d, D, 2, "f64", seed, None)
+    out = np.empty((D, d + 1), dtype=np.float64)
+    _check(load().slk_rff_features(ctypes.byref(desc), out.ctypes.data))
     return out
 
 

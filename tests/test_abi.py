@@ -46,7 +46,8 @@ def test_struct_layout_matches_header(tmp_path):
     from paper_2401_08260_gb300 import slk
     src = tmp_path / "probe.c"
     structs = [("slk_plan_desc", slk.PlanDesc), ("slk_plan_info", slk.PlanInfo), ("slk_kernel_time", slk.KernelTime),
-               ("slk_serve_desc", slk.ServeDesc), ("slk_request", slk.RequestDesc), ("slk_result", slk.RequestResult)]
+               ("slk_serve_desc", slk.ServeDesc), ("slk_request", slk.RequestDesc), ("slk_result", slk.RequestResult),
+               ("slk_rff_desc", slk.RffDesc)]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "slk_serve.h"', "int main(void){"]
     expect = []
     for cname, py in structs:

@@ -92,8 +92,17 @@ def test_roofline_amount_covers_every_launch_of_a_step():
     assert amount * 3 == pytest.approx((2 * 10 ** 6 + 4096) * (4 * 786 + 2 * ld16))
     amount, unit, bound = bench.algorithmic(wl3, {}, "bf16", "umma_cheb_target", 1, kernels3, peaks=peaks)
     assert (unit, bound) == ("flop", "tensor") and amount == pytest.approx(2.0 * 10 ** 6 * 786 * 512)
-    traffic = bench.measured_traffic(wl, "center_cast", 2, kernels)
-    assert traffic * 2 == pytest.approx(bench.NCU_TRAFFIC_PER_POINT[("gauss_d784", "center_cast")] * (10 ** 6 + 4096))
+    # the CTA-pair kernels: 4 d bytes per point, plus two FP64 partial sums per 256-slice half
+    # per target or the 4-byte weight per source
+    pair_kernels = {"gather_rows": (1, 0.01), "pair_cheb_moments": (1, 1.0), "pair_cheb_target": (1, 1.0)}
+    amount, unit, bound = bench.algorithmic(wl, {}, "bf16", "pair_cheb_target", 1, pair_kernels, peaks=peaks)
+    assert (unit, bound) == ("byte", "hbm") and amount == pytest.approx(10 ** 6 * (4 * 784 + 32))
+    amount, unit, bound = bench.algorithmic(wl, {}, "bf16", "pair_cheb_moments", 1, pair_kernels, peaks=peaks)
+    assert (unit, bound) == ("byte", "hbm") and amount == pytest.approx(10 ** 6 * (4 * 784 + 4))
+    # traffic is reported only from a capture of the kernel as it is
+    for name in ("center_cast", "pair_cheb_target"):
+        if (wl.name, name) not in bench.NCU_TRAFFIC_PER_POINT:
+            assert bench.measured_traffic(wl, name, 1, pair_kernels) is None
 
 
 def test_default_steps_per_arm(monkeypatch):
