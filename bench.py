@@ -557,10 +557,55 @@ def serve_desc(spec, xi):
     return desc
 
 
+def _serve_stream(srv, specs, arrivals, dev, keyed: bool, max_outstanding: int):
+    """Submit the requests at their arrival times (at most max_outstanding in flight), poll
+    them as they finish; returns (latencies in ms, plan-cache hits, batched requests, wall s,
+    slice-points)."""
+    import torch
+    from paper_2401_08260_gb300 import slk  # noqa: F401
+    cache = {}
+    pending, lat, cached, batched = {}, [], 0, 0
+    slice_points = 0
+
+    def collect(rid, timeout_us):
+        nonlocal cached, batched
+        res = srv.poll(rid, timeout_us=timeout_us)
+        if res is None:
+            return False
+        assert res["status"] == 0, res
+        lat.append(res["total_ms"])
+        cached += res["plan_cached"]
+        batched += res["batch_requests"] > 1
+        pending.pop(rid)
+        return True
+
+    t_start = time.perf_counter()
+    for i, spec in enumerate(specs):
+        while True:
+            now = time.perf_counter() - t_start
+            if now >= arrivals[i] and len(pending) < max_outstanding:
+                break
+            for rid in list(pending):
+                collect(rid, 0)
+            time.sleep(0.0002)
+        x, w, y, xi = serve_inputs(spec, dev, cache)
+        out = torch.empty(spec["M"], device=dev)
+        torch.cuda.synchronize()
+        rid = srv.submit(x, w, y, out, serve_desc(spec, xi), source_key=spec["key"] if keyed else 0)
+        pending[rid] = (out, y)
+        slice_points += (spec["N"] + spec["M"]) * spec["P"]
+    for rid in list(pending):
+        collect(rid, -1)
+    return lat, cached, batched, time.perf_counter() - t_start, slice_points
+
+
 def run_serve(args):
-    """Serving benchmark: a Poisson stream of requests served concurrently (memory-budgeted
-    admission, worker streams, plan cache), beside the plain one-request-at-a-time method
-    (plan + sum per request, in arrival order) on the same GPU, same requests, same accuracy."""
+    """Serving benchmark: one Poisson stream of requests served twice on the same GPU, same
+    requests and arrival times, same accuracy: by the plain method (one request at a time,
+    plan + sum each, no plan cache: a server with one worker and no source keys) and by the
+    concurrent server (memory-budgeted admission, worker streams, plan cache, repeats queued
+    behind their plan's build and batched).  The arrival rate is `--serve-load` x the plain
+    method's capacity, measured first by running every request alone."""
     import torch
     from paper_2401_08260_gb300 import build, slk
     build.build()
@@ -568,9 +613,8 @@ def run_serve(args):
     torch.cuda.set_device(dev)
     specs = serve_requests(args.serve_requests, max_nm=args.serve_max_nm)
     cache = {}
-    # ---- plain method: one request at a time, no plan cache (this also measures capacity)
+    # ---- capacity of the plain method: every request alone, in order
     service = []
-    outs = {}
     for spec in specs:
         x, w, y, xi = serve_inputs(spec, dev, cache)
         torch.cuda.synchronize()
@@ -584,55 +628,27 @@ def run_serve(args):
     rate = args.serve_load / mean_service
     rng = np.random.Generator(np.random.PCG64(12))
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(specs)))
-    # simulated FIFO single server with the measured plain service times
-    finish, lat_plain = 0.0, []
-    for a, s in zip(arrivals, service):
-        start = max(a, finish)
-        finish = start + s
-        lat_plain.append((finish - a) * 1e3)
-    # ---- served: submit at the arrival times, poll as requests finish
-    srv = slk.Server(workers=args.serve_workers)
-    cache.clear()
-    pending, lat, cached, outstanding = {}, [], 0, []
-    t_start = time.perf_counter()
-    slice_points = 0
-    for i, spec in enumerate(specs):
-        while True:
-            now = time.perf_counter() - t_start
-            if now >= arrivals[i] and len(pending) < args.serve_max_outstanding:
-                break
-            # collect finished requests while waiting
-            for rid in list(pending):
-                res = srv.poll(rid, timeout_us=0)
-                if res is not None:
-                    assert res["status"] == 0, res
-                    lat.append(res["total_ms"])
-                    cached += res["plan_cached"]
-                    pending.pop(rid)
-            time.sleep(0.0002)
-        x, w, y, xi = serve_inputs(spec, dev, cache)
-        out = torch.empty(spec["M"], device=dev)
-        torch.cuda.synchronize()
-        rid = srv.submit(x, w, y, out, serve_desc(spec, xi), source_key=spec["key"])
-        pending[rid] = (out, y)
-        slice_points += (spec["N"] + spec["M"]) * spec["P"]
-    for rid in list(pending):
-        res = srv.poll(rid, timeout_us=-1)
-        assert res["status"] == 0, res
-        lat.append(res["total_ms"])
-        cached += res["plan_cached"]
-    wall = time.perf_counter() - t_start
+    # ---- plain method served at the arrival times: one worker, no cache
+    srv = slk.Server(workers=1)
+    lat_p, _, _, wall_p, _ = _serve_stream(srv, specs, arrivals, dev, False, args.serve_max_outstanding)
     srv.close()
+    # ---- the concurrent server
+    srv = slk.Server(workers=args.serve_workers)
+    lat, cached, batched, wall, slice_points = _serve_stream(srv, specs, arrivals, dev, True,
+                                                             args.serve_max_outstanding)
+    srv.close()
+    repeats = sum(1 for s_ in specs if s_["repeat"])
     line = {"metric": "serving p50/p99 latency", "unit": "ms", "higher_is_better": False,
             "value": float(np.percentile(lat, 50)), "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "throughput_req_s": len(specs) / wall,
             "slice_points_per_s": slice_points / wall, "n_gpus": 1, "requests": len(specs),
             "load": args.serve_load, "arrival_rate_req_s": rate, "workers": args.serve_workers,
-            "plan_cache_hits": cached, "data": "synthetic",
-            "plain_one_at_a_time": {"p50_ms": float(np.percentile(lat_plain, 50)),
-                                    "p99_ms": float(np.percentile(lat_plain, 99)),
+            "repeats": repeats, "plan_cache_hits": cached, "batched_requests": batched, "data": "synthetic",
+            "plain_one_at_a_time": {"p50_ms": float(np.percentile(lat_p, 50)),
+                                    "p99_ms": float(np.percentile(lat_p, 99)),
+                                    "throughput_req_s": len(specs) / wall_p,
                                     "mean_service_ms": mean_service * 1e3,
-                                    "throughput_req_s": 1.0 / mean_service},
+                                    "capacity_req_s": 1.0 / mean_service},
             "config": {"workload": "serving mix", "N_M": f"log-uniform [1e3, {args.serve_max_nm:g}]",
                        "d": list(SERVE_D), "P": list(SERVE_P), "kernels": list(SERVE_KERNELS), "repeats": 0.3}}
     print(json.dumps(line), flush=True)

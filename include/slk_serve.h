@@ -11,7 +11,10 @@
  * others run starts as soon as a worker and memory are free.  Requests that
  * name the same nonzero source_key reuse one cached plan (the source side of
  * every slice is computed once), so repeated queries against the same x cost
- * only their target side.
+ * only their target side; queued requests on the same cached plan are served
+ * together by one sum over their concatenated targets (a request waiting for a
+ * plan that another request is building stays queued without holding up the
+ * requests behind it).
  *
  * Ownership: the caller owns x, w, y and s and keeps them valid and unchanged
  * until the request has been polled as finished.  Pointers may be host or
@@ -49,6 +52,9 @@ typedef struct {
 typedef struct {
     slk_status status;        /* status of the request (SLK_OK, or the failing call's status) */
     int32_t plan_cached;      /* 1 if a cached plan served the request */
+    int32_t batch_requests;   /* requests served by the same sum (the queued requests on one
+                                 cached plan are batched: their targets are concatenated into
+                                 one sum); 1 = alone */
     double queue_ms;          /* submission -> admission */
     double run_ms;            /* admission -> finished (plan, sum and synchronisation) */
     double total_ms;          /* submission -> finished */

@@ -1,7 +1,8 @@
 // Request serving: admission by a device-memory budget, concurrent worker
-// streams, and a cache of source-side plans (include/slk_serve.h).
+// streams, a cache of source-side plans, and batches of the queued requests that
+// query one cached plan (include/slk_serve.h).
 //
-// The server only uses the library's public calls (slk_plan_create, slk_sum,
+// The server uses the library's public calls (slk_plan_create, slk_sum,
 // slk_plan_sync, slk_plan_destroy), one CUDA stream per worker thread.
 #include <algorithm>
 #include <atomic>
@@ -46,6 +47,7 @@ struct Request {
     slk_request req{};
     int64_t need = 0;  // reserved bytes while running
     bool cached = false;
+    int batch = 1;  // requests served by the same launches (the cached plan's sum)
     bool done = false;
     slk_status status = SLK_OK;
     std::string message;
@@ -69,7 +71,10 @@ struct slk_server_s {
     std::vector<cudaStream_t> streams;  // one per worker; destroyed after the cached plans
 
     void worker_loop(int index);
+    bool waits_for_build(const Request* r) const;
     bool try_admit(Request* r);
+    std::vector<Request*> take_batch(Request* first);
+    void run_batch(const std::vector<Request*>& batch, CacheEntry* entry, cudaStream_t st);
     void evict_for(int64_t need);
     void finish(Request* r, CacheEntry* entry, slk_plan plan, bool keep_plan, int64_t plan_bytes);
 };
@@ -101,6 +106,14 @@ extern "C" int64_t slk_request_bytes(const slk_plan_desc* desc, int64_t N, int64
     return base + std::max(create, persist + sum);
 }
 
+// A request whose sources' plan another request is building stays queued behind that build
+// (so that it runs on the cached plan) without holding up the requests queued after it.
+bool slk_server_s::waits_for_build(const Request* r) const {
+    if (!r->req.source_key) return false;
+    auto it = cache.find(r->req.source_key);
+    return it != cache.end() && !it->second->ready && !it->second->failed;
+}
+
 bool slk_server_s::try_admit(Request* r) {
     const slk_request& q = r->req;
     CacheEntry* entry = nullptr;
@@ -129,6 +142,91 @@ bool slk_server_s::try_admit(Request* r) {
         cache[q.source_key] = std::move(e);
     }
     return true;
+}
+
+// Requests that query the same cached plan share its sum: after `first` (admitted on a ready
+// cached plan) the queued requests with the same source key are admitted too, in order, as
+// long as memory allows, up to kMaxBatch requests and kMaxBatchRows targets in all.
+constexpr size_t kMaxBatch = 32;
+constexpr int64_t kMaxBatchRows = int64_t(1) << 22;
+
+std::vector<Request*> slk_server_s::take_batch(Request* first) {
+    std::vector<Request*> batch{first};
+    if (!first->cached) return batch;
+    int64_t rows = first->req.M;
+    for (auto it = pending.begin(); it != pending.end() && batch.size() < kMaxBatch;) {
+        Request* q = *it;
+        if (q->req.source_key != first->req.source_key || rows + q->req.M > kMaxBatchRows) {
+            ++it;
+            continue;
+        }
+        if (!try_admit(q)) break;
+        q->t_start = first->t_start;
+        rows += q->req.M;
+        batch.push_back(q);
+        it = pending.erase(it);
+    }
+    for (Request* q : batch) q->batch = static_cast<int>(batch.size());
+    return batch;
+}
+
+// One sum over the concatenated targets of a batch on the cached plan: the targets are
+// gathered into one array, summed, and each request's outputs copied back.
+void slk_server_s::run_batch(const std::vector<Request*>& batch, CacheEntry* entry, cudaStream_t st) {
+    const slk_plan_desc& desc = batch[0]->req.desc;
+    const int64_t e = desc.precision == SLK_PREC_F64 ? 8 : 4, d = desc.d;
+    int64_t rows = 0;
+    for (Request* q : batch) rows += q->req.M;
+    slk_status s = SLK_OK;
+    std::string msg;
+    void* ycat = nullptr;
+    void* scat = nullptr;
+    if (cudaMallocAsync(&ycat, static_cast<size_t>(rows * d * e), st) != cudaSuccess ||
+        cudaMallocAsync(&scat, static_cast<size_t>(rows * e), st) != cudaSuccess) {
+        cudaGetLastError();
+        s = SLK_ERR_OOM;
+        msg = "device allocation for a batch of requests failed";
+    }
+    int64_t off = 0;
+    for (Request* q : batch) {
+        if (s != SLK_OK) break;
+        if (cudaMemcpy2DAsync(static_cast<char*>(ycat) + off * d * e, d * e, q->req.y, q->req.ldy * e, d * e,
+                              q->req.M, cudaMemcpyDefault, st) != cudaSuccess) {
+            cudaGetLastError();
+            s = SLK_ERR_CUDA;
+            msg = "gathering the targets of a batch failed";
+        }
+        off += q->req.M;
+    }
+    if (s == SLK_OK) {
+        std::lock_guard<std::mutex> use(entry->use);
+        s = slk_sum(entry->plan, ycat, rows, d, scat, st);
+        if (s == SLK_OK) s = slk_plan_sync(entry->plan);
+        if (s != SLK_OK) msg = slk_last_error();
+    }
+    off = 0;
+    for (Request* q : batch) {
+        if (s != SLK_OK) break;
+        if (cudaMemcpyAsync(q->req.s, static_cast<char*>(scat) + off * e, static_cast<size_t>(q->req.M * e),
+                            cudaMemcpyDefault, st) != cudaSuccess) {
+            cudaGetLastError();
+            s = SLK_ERR_CUDA;
+            msg = "returning the outputs of a batch failed";
+        }
+        off += q->req.M;
+    }
+    if (ycat) cudaFreeAsync(ycat, st);
+    if (scat) cudaFreeAsync(scat, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && s == SLK_OK) {
+        cudaGetLastError();
+        s = SLK_ERR_CUDA;
+        msg = "a batch of requests failed on the device";
+    }
+    for (Request* q : batch) {
+        q->status = s;
+        q->message = msg;
+        finish(q, entry, nullptr, false, 0);
+    }
 }
 
 void slk_server_s::evict_for(int64_t need) {
@@ -173,22 +271,39 @@ void slk_server_s::worker_loop(int index) {
     cudaStream_t st = streams[index];
     for (;;) {
         Request* r = nullptr;
+        std::vector<Request*> batch;
         {
-            // admit the oldest queued request as soon as memory allows (FIFO)
+            // admit the oldest admissible queued request as soon as memory allows: requests
+            // waiting for a plan under construction are passed over (they stay queued), the
+            // first one that does not fit the budget ends the scan (nothing overtakes it)
             std::unique_lock<std::mutex> lk(mu);
             for (;;) {
-                if (!pending.empty() && try_admit(pending.front())) {
-                    r = pending.front();
-                    pending.pop_front();
+                for (auto it = pending.begin(); it != pending.end(); ++it) {
+                    if (waits_for_build(*it)) continue;
+                    if (try_admit(*it)) {
+                        r = *it;
+                        pending.erase(it);
+                    }
                     break;
                 }
+                if (r) break;
                 if (stop && pending.empty()) break;
                 cv.wait(lk);  // woken by a submission, a finished request or shutdown
             }
             if (!r) break;
             r->t_start = Clock::now();
+            batch = take_batch(r);
         }
         cv.notify_all();
+        if (batch.size() > 1) {
+            CacheEntry* entry = nullptr;
+            {
+                std::lock_guard<std::mutex> g(mu);
+                entry = cache.find(r->req.source_key)->second.get();
+            }
+            run_batch(batch, entry, st);
+            continue;
+        }
         const slk_request& q = r->req;
         CacheEntry* entry = nullptr;
         if (q.source_key) {
@@ -321,6 +436,7 @@ slk_status slk_serve_poll(slk_server srv, uint64_t id, int64_t timeout_us, slk_r
     std::memset(res, 0, sizeof(*res));
     res->status = r->status;
     res->plan_cached = r->cached ? 1 : 0;
+    res->batch_requests = r->batch;
     res->queue_ms = ms_between(r->t_submit, r->t_start);
     res->run_ms = ms_between(r->t_start, r->t_done);
     res->total_ms = ms_between(r->t_submit, r->t_done);

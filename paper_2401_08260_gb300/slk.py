@@ -442,8 +442,9 @@ class RequestDesc(ctypes.Structure):
 
 
 class RequestResult(ctypes.Structure):
-    _fields_ = [("status", ctypes.c_int), ("plan_cached", ctypes.c_int32), ("queue_ms", ctypes.c_double),
-                ("run_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("message", ctypes.c_char * 128)]
+    _fields_ = [("status", ctypes.c_int), ("plan_cached", ctypes.c_int32), ("batch_requests", ctypes.c_int32),
+                ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("message", ctypes.c_char * 128)]
 
 
 _SERVE_SIGNATURES = {
@@ -481,7 +482,8 @@ def request_bytes(desc: PlanDesc, N: int, M: int) -> int:
 
 class Server:
     """Concurrent request server on the current device (admission by a memory budget,
-    worker streams, a cache of source-side plans keyed by `source_key`)."""
+    worker streams, a cache of source-side plans keyed by `source_key`, and batches of the
+    queued requests that query one cached plan)."""
 
     def __init__(self, workers: int = 0, memory_budget: int = 0, plan_cache_bytes: int = 0):
         lib = _serve_lib()
@@ -515,7 +517,8 @@ class Server:
             return None
         _check(st)
         self._keep.pop(rid, None)
-        return {"status": int(res.status), "plan_cached": bool(res.plan_cached), "queue_ms": res.queue_ms,
+        return {"status": int(res.status), "plan_cached": bool(res.plan_cached),
+                "batch_requests": int(res.batch_requests), "queue_ms": res.queue_ms,
                 "run_ms": res.run_ms, "total_ms": res.total_ms, "message": res.message.decode(errors="replace")}
 
     def close(self):

@@ -1,5 +1,6 @@
 """Serving: concurrent requests of uneven sizes and kernels give the same
-results as each request alone; repeated sources reuse one cached plan;
+results as each request alone; repeated sources reuse one cached plan and the
+queued repeats of one source are served together by one batched sum;
 admission respects the memory budget."""
 import math
 
@@ -43,11 +44,12 @@ def test_alone_and_in_the_mix_agree():
     reqs = []
     for i, (kernel, d, precision, N, M, P) in enumerate(_specs()):
         x, y, w, xi, param = _inputs(dev, kernel, d, N, M, P, 1000 + i)
-        # the same sources queried twice with different targets (a plan-cache hit)
-        y2 = y.flip(0).contiguous() * 0.9
+        # the same sources queried three times with different targets: the repeats wait for
+        # the first request's plan and are then served together from the cache
+        ys = [y, y.flip(0).contiguous() * 0.9, (y[: max(1, M // 3)] - 0.1).contiguous()]
         alone = Plan(x, w, kernel, param, P=P, precision=precision, directions=xi, radius=8.0)
-        reqs.append(dict(x=x, w=w, y=y, y2=y2, kernel=kernel, param=param, P=P, precision=precision, xi=xi,
-                         ref=alone.sum(y).cpu().numpy(), ref2=alone.sum(y2).cpu().numpy(), wsum=float(w.sum())))
+        reqs.append(dict(x=x, w=w, ys=ys, kernel=kernel, param=param, P=P, precision=precision, xi=xi,
+                         refs=[alone.sum(t).cpu().numpy() for t in ys], wsum=float(w.sum())))
         alone.close()
     torch.cuda.synchronize()
     srv = Server(workers=4)
@@ -58,20 +60,21 @@ def test_alone_and_in_the_mix_agree():
         xis.append(xi)
         desc = slk.make_desc(r["kernel"], r["param"], r["x"].shape[1], r["P"], r["precision"], radius=8.0)
         desc.directions = xi.ctypes.data
-        r["out"] = torch.empty(r["y"].shape[0], device=dev)
-        r["out2"] = torch.empty(r["y2"].shape[0], device=dev)
-        ids.append((k, 1, srv.submit(r["x"], r["w"], r["y"], r["out"], desc, source_key=k + 1)))
-        ids.append((k, 2, srv.submit(r["x"], r["w"], r["y2"], r["out2"], desc, source_key=k + 1)))
-    cached = 0
-    for k, which, rid in ids:
+        r["outs"] = [torch.empty(t.shape[0], device=dev) for t in r["ys"]]
+        for j, (t, o) in enumerate(zip(r["ys"], r["outs"])):
+            ids.append((k, j, srv.submit(r["x"], r["w"], t, o, desc, source_key=k + 1)))
+    cached, batched = 0, 0
+    for k, j, rid in ids:
         res = srv.poll(rid, timeout_us=120_000_000)
         assert res is not None and res["status"] == 0, res
         cached += res["plan_cached"]
+        batched += res["batch_requests"] > 1
         r = reqs[k]
-        got = r["out"] if which == 1 else r["out2"]
-        ref = r["ref"] if which == 1 else r["ref2"]
-        assert rel_inf(got, ref, r["wsum"]) <= 1e-5, (k, which, r["kernel"], r["precision"])
-    assert cached >= len(reqs) // 2  # most repeats hit the cache (a repeat may start before its plan is built)
+        assert rel_inf(r["outs"][j], r["refs"][j], r["wsum"]) <= 1e-5, (k, j, r["kernel"], r["precision"])
+    # every repeat waited for its plan and used it; the two repeats of a source queued behind
+    # its build were served by one sum over their concatenated targets
+    assert cached == 2 * len(reqs), cached
+    assert batched >= len(reqs), batched
     srv.close()
 
 
