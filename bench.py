@@ -591,8 +591,10 @@ def _serve_stream(srv, specs, arrivals, dev, keyed: bool, max_outstanding: int):
         x, w, y, xi = serve_inputs(spec, dev, cache)
         out = torch.empty(spec["M"], device=dev)
         torch.cuda.synchronize()
-        rid = srv.submit(x, w, y, out, serve_desc(spec, xi), source_key=spec["key"] if keyed else 0)
-        pending[rid] = (out, y)
+        desc = serve_desc(spec, xi)
+        rid = srv.submit(x, w, y, out, desc, source_key=spec["key"] if keyed else 0)
+        # the request reads the directions through desc when it starts: keep them until polled
+        pending[rid] = (out, y, xi, desc)
         slice_points += (spec["N"] + spec["M"]) * spec["P"]
     for rid in list(pending):
         collect(rid, -1)

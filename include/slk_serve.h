@@ -16,8 +16,9 @@
  * plan that another request is building stays queued without holding up the
  * requests behind it).
  *
- * Ownership: the caller owns x, w, y and s and keeps them valid and unchanged
- * until the request has been polled as finished.  Pointers may be host or
+ * Ownership: the caller owns x, w, y, s and the descriptor's directions array
+ * and keeps them valid and unchanged until the request has been polled as
+ * finished (a queued request reads them only when it starts).  Pointers may be host or
  * device pointers (as in slk.h).  A cached plan keeps no pointer to x or w.
  */
 #ifndef SLK_SERVE_H

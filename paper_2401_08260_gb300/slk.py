@@ -496,7 +496,8 @@ class Server:
 
     def submit(self, x, w, y, out, desc: PlanDesc, source_key: int = 0) -> int:
         """Queue s = kernel sums of (x, w) at y into `out`; returns the request id.
-        x, w, y and out stay referenced until the request is polled."""
+        x, w, y and out stay referenced until the request is polled; an array that
+        desc.directions points to must be kept alive by the caller until then too."""
         dtype = np.float64 if desc.precision == PRECISIONS["f64"] else np.float32
         xa, wa, ya, oa = _Arr(x, dtype, 2), _Arr(w, dtype, 1), _Arr(y, dtype, 2), _Arr(out, dtype, 1)
         r = RequestDesc()
