@@ -332,6 +332,19 @@ void slk_server_s::worker_loop(int index) {
             if (entry && s == SLK_OK && slk_plan_get_info(plan, &info) == SLK_OK) {
                 std::lock_guard<std::mutex> g(mu);
                 plan_bytes = info.device_bytes;
+                // room for the new plan: the least recently used cached plans no request holds go
+                while (cache_bytes + plan_bytes > cache_cap && plan_bytes <= cache_cap) {
+                    CacheEntry* victim = nullptr;
+                    for (auto& kv : cache) {
+                        CacheEntry* c = kv.second.get();
+                        if (c->ready && c->refs == 0 && (!victim || c->last_use < victim->last_use)) victim = c;
+                    }
+                    if (!victim) break;
+                    slk_plan_destroy(victim->plan);
+                    in_use -= victim->bytes;
+                    cache_bytes -= victim->bytes;
+                    cache.erase(victim->key);
+                }
                 keep = cache_bytes + plan_bytes <= cache_cap;
             }
             if (!keep) slk_plan_destroy(plan);
