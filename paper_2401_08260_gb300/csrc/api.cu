@@ -525,15 +525,19 @@ void plan_sort_source(slk_plan plan, const T* Zx, const T* w, cudaStream_t st) {
     while (static_cast<int64_t>(nb) * 8 < N && nb < (1 << 22)) nb <<= 1;
     plan->NB = nb;
     plan->kw.alloc(sorted_pairs_bytes<T>(P, N), st);
+    plan->kmin.alloc(P, st);
+    plan->kscale.alloc(P, st);
+    // the sources grouped by equal-width bucket (Section 3.2 needs only the prefix sums at
+    // bucket starts plus the sources of a target's own bucket, in any order)
+    launch_slice_minmax<T>(Zx, P, N, N, nb, plan->kmin.get(), plan->kscale.get(), st);
     {
         const size_t sb = sort_pairs_scratch<T>(P, N);
         DevBuf<unsigned char> scratch(sb, st);
-        launch_sort_pairs<T>(Zx, P, N, N, w, plan->kw.get(), scratch.get(), sb, st);
+        launch_sort_pairs<T>(Zx, P, N, N, w, plan->kw.get(), scratch.get(), sb, plan->kmin.get(), plan->kscale.get(),
+                             nb, st);
     }
     plan->rec.alloc(static_cast<size_t>(P) * (nb + 1) * kBucketRecordBytes, st);
-    plan->kmin.alloc(P, st);
-    plan->kscale.alloc(P, st);
-    launch_bucket_tables<T>(P, N, plan->kw.get(), nb, plan->kmin.get(), plan->kscale.get(), plan->rec.get(), st);
+    launch_bucket_tables<T>(P, N, plan->kw.get(), nb, plan->kmin.get(), plan->kscale.get(), plan->rec.get(), true, st);
 }
 
 template <class T>

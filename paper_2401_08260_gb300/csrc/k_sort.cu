@@ -1,15 +1,15 @@
 // Sorting route of Section 3.2 (negative distance kernel; the non-smooth part
 // of the Laplacian in Section 3.3).
 //
-// Per slice the sources are sorted by their projection (segmented LSD radix
-// sort on order-preserving key bits, 8-bit digits, stable, with the source
-// index as payload) and stored as (key, w) pairs in sorted order.  The sorted
-// range of each slice is cut into NB buckets of equal key width; FP64
-// exclusive prefix sums of w and w z are kept only at bucket starts:
+// Per slice the key range [min z, max z] of the sources is cut into NB buckets of equal
+// width, and the sources are grouped by bucket (a segmented stable LSD radix sort on the
+// digits of the bucket index, one 8-bit pass per byte of NB - 1, carrying the weight) into
+// (key, w) pairs, ascending by bucket and in source order within a bucket.  Exclusive
+// prefix sums of w and w z are kept only at bucket starts:
 //     A_b = sum over sources in buckets < b of w,   B_b = same of w z.
 // A target z in bucket b then has
 //     A_< = A_b + sum_{sources of bucket b with key < z} w,   B_< likewise,
-// (a short scan of the sorted bucket, stopped at the insertion point) and
+// (a scan of bucket b's few sources, in any order) and
 //     t(z) = -c_d sum_n w_n |z - x_n| = -c_d [ z (2 A_< - W) - (2 B_< - S) ],
 // W, S the totals.  This is Algorithm 2 regrouped: splitting the sum at z gives
 //     sum_{x<z} w (z - x) + sum_{x>=z} w (x - z) = z (2 A_< - W) - (2 B_< - S),
@@ -38,12 +38,34 @@ struct KW {
     T key, w;
 };
 
+// Equal-width key buckets of a slice: b = floor((z - kmin) * kscale) clamped to [0, NB).
+__device__ inline int bucket_of(float z, float kmin, float kscale, int NB) {
+    float f = (z - kmin) * kscale;
+    int b = f < 0.0f ? 0 : (f >= static_cast<float>(NB) ? NB - 1 : static_cast<int>(f));
+    return b;
+}
+
+// Radix digit of a key: its own bits (a full sort), or the bits of its slice's bucket index
+// (BUCKETED: the keys end up grouped by bucket, in source order within a bucket).
+struct Buckets {
+    const float* kmin;
+    const float* kscale;
+    int NB;
+};
+template <bool BUCKETED, class U>
+__device__ __forceinline__ int radix_digit(U k, int shift, const Buckets& bk, int p) {
+    if constexpr (BUCKETED)
+        return (bucket_of(static_cast<float>(key_from_bits(k)), bk.kmin[p], bk.kscale[p], bk.NB) >> shift) & 0xff;
+    else
+        return static_cast<int>((k >> shift) & 0xffu);
+}
+
 // Digit histogram of one tile: hist[(p * 256 + digit) * tiles + tile].  FIRST: the keys are
 // the order-preserving bits of the projections z (row stride ldz), otherwise the bits array.
-template <class T, class U, bool FIRST>
+template <class T, class U, bool FIRST, bool BUCKETED>
 __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const T* __restrict__ z, int64_t ldz,
                                                           const U* __restrict__ keys, int64_t n, int shift, int tiles,
-                                                          int32_t* __restrict__ hist) {
+                                                          int32_t* __restrict__ hist, Buckets bk) {
     __shared__ int32_t h[RS_BINS];
     const int p = blockIdx.y, tile = blockIdx.x;
     h[threadIdx.x] = 0;
@@ -59,7 +81,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const T* __restrict__
 #pragma unroll
     for (int r = 0; r < RS_ITEMS; ++r) {
         const int64_t i = base + r * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[static_cast<int>((k[r] >> shift) & 0xffu)], 1);
+        if (i < n) atomicAdd(&h[radix_digit<BUCKETED>(k[r], shift, bk, p)], 1);
     }
     __syncthreads();
     hist[(static_cast<int64_t>(p) * RS_BINS + threadIdx.x) * tiles + tile] = h[threadIdx.x];
@@ -132,13 +154,13 @@ constexpr size_t radix_pass_smem() {
 // memory, and each digit's run is written to its global offset (from the scanned histogram)
 // in contiguous stores.  FIRST reads the projections and the weights (source index order);
 // LAST writes (key, w) pairs instead of bits and payload.
-template <class T, class U, bool FIRST, bool LAST>
+template <class T, class U, bool FIRST, bool LAST, bool BUCKETED>
 __global__ void __launch_bounds__(RS_THREADS, 5) k_radix_pass(const T* __restrict__ z, int64_t ldz, const T* __restrict__ w,
                                                           const U* __restrict__ kin, const T* __restrict__ vin,
                                                           int64_t n, int shift, int tiles,
                                                           const int32_t* __restrict__ hist,
                                                           const int32_t* __restrict__ dbase, U* __restrict__ kout,
-                                                          T* __restrict__ vout, KW<T>* __restrict__ pout) {
+                                                          T* __restrict__ vout, KW<T>* __restrict__ pout, Buckets bk) {
     extern __shared__ __align__(16) unsigned char rs_smem[];
     U* sk = reinterpret_cast<U*>(rs_smem);
     T* sv = reinterpret_cast<T*>(sk + RS_TILE);
@@ -176,7 +198,7 @@ __global__ void __launch_bounds__(RS_THREADS, 5) k_radix_pass(const T* __restric
     for (int r = 0; r < RS_ITEMS; ++r) {
         const int64_t e = base + warp * RUN + r * 32 + lane;
         const bool valid = e < n;
-        const int digit = valid ? static_cast<int>((key[r] >> shift) & 0xffu) : RS_BINS + lane;
+        const int digit = valid ? radix_digit<BUCKETED>(key[r], shift, bk, p) : RS_BINS + lane;
         const unsigned peers = __match_any_sync(0xffffffffu, digit);
         const int before = valid ? mycnt[digit] : 0;
         rank[r] = before + __popc(peers & lt_mask);
@@ -214,7 +236,7 @@ __global__ void __launch_bounds__(RS_THREADS, 5) k_radix_pass(const T* __restric
     for (int r = 0; r < RS_ITEMS; ++r) {
         const int64_t e = base + warp * RUN + r * 32 + lane;
         if (e < n) {
-            const int digit = static_cast<int>((key[r] >> shift) & 0xffu);
+            const int digit = radix_digit<BUCKETED>(key[r], shift, bk, p);
             const int pos = loc[digit] + wcnt[warp * RS_BINS + digit] + rank[r];
             sk[pos] = key[r];
             sv[pos] = val[r];
@@ -224,7 +246,7 @@ __global__ void __launch_bounds__(RS_THREADS, 5) k_radix_pass(const T* __restric
     const int cnt = static_cast<int>(n - base < RS_TILE ? n - base : RS_TILE);
     for (int j = threadIdx.x; j < cnt; j += RS_THREADS) {
         const U k = sk[j];
-        const int digit = static_cast<int>((k >> shift) & 0xffu);
+        const int digit = radix_digit<BUCKETED>(k, shift, bk, p);
         const int64_t g = seg + glob[digit] + (j - loc[digit]);
         if (LAST) {
             pout[g] = KW<T>{key_from_bits(k), sv[j]};
@@ -237,10 +259,41 @@ __global__ void __launch_bounds__(RS_THREADS, 5) k_radix_pass(const T* __restric
 
 // ------------------------------------------------------------ sorted pairs and bucket sums
 
-__device__ inline int bucket_of(float z, float kmin, float kscale, int NB) {
-    float f = (z - kmin) * kscale;
-    int b = f < 0.0f ? 0 : (f >= static_cast<float>(NB) ? NB - 1 : static_cast<int>(f));
-    return b;
+
+// Bucket geometry of every slice from its projections (one block per slice): kmin = the
+// smallest key, kscale = NB / (largest - smallest) (0 when all keys are equal), in the same
+// float arithmetic as bucket_of.
+template <class T>
+__global__ void __launch_bounds__(256) k_slice_minmax(const T* __restrict__ Z, int64_t n, int64_t ldz, int NB,
+                                                     float* __restrict__ kmin, float* __restrict__ kscale) {
+    const int p = blockIdx.x;
+    const T* row = Z + static_cast<int64_t>(p) * ldz;
+    float lo = INFINITY, hi = -INFINITY;
+    for (int64_t i = threadIdx.x; i < n; i += 256) {
+        const float v = static_cast<float>(row[i]);
+        lo = fminf(lo, v);
+        hi = fmaxf(hi, v);
+    }
+    __shared__ float slo[8], shi[8];
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        slo[threadIdx.x >> 5] = lo;
+        shi[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < 8; ++k) {
+            lo = fminf(lo, slo[k]);
+            hi = fmaxf(hi, shi[k]);
+        }
+        lo = fminf(lo, slo[0]);
+        hi = fmaxf(hi, shi[0]);
+        kmin[p] = lo;
+        kscale[p] = hi > lo ? static_cast<float>(NB) / (hi - lo) : 0.0f;
+    }
 }
 
 template <class T>
@@ -637,23 +690,19 @@ __global__ void __launch_bounds__(256) k_negdist_target(const T* __restrict__ Z,
         const BucketRec<T>* rb = rec + static_cast<int64_t>(p) * (NB + 1);
         const int b = bucket_of(static_cast<float>(z), kmin[p], kscale[p], NB);
         const BucketRec<T> r = rb[b];  // one sector: prefix entry and the bucket's pair range
-        const int32_t hi = r.end;
-        int32_t i = r.start;
-        T a = T(0), bz = T(0);
-        for (; i < hi; ++i) {
+        // the bucket's sources in any order: those below z, and (gradient) those equal to z
+        T a = T(0), bz = T(0), aeq = T(0);
+        for (int32_t i = r.start; i < r.end; ++i) {
             const KW<T> e = ks[i];
-            if (!(e.key < z)) break;
-            a += e.w;
-            bz = fma(e.w, e.key, bz);
+            if (e.key < z) {
+                a += e.w;
+                bz = fma(e.w, e.key, bz);
+            } else if (G && e.key == z) {
+                aeq += e.w;
+            }
         }
         const Pre<T> eb = r.e, tot = rb[NB].e;
         if (G) {
-            T aeq = T(0);
-            for (; i < hi; ++i) {
-                const KW<T> e = ks[i];
-                if (e.key != z) break;
-                aeq += e.w;
-            }
             const T g = scale * negdist_slope(eb, tot, a, aeq, cd);
             T* gp = G + m * P + p;
             *gp = accumulate_G ? *gp + g : g;
@@ -681,39 +730,32 @@ size_t sort_pairs_scratch(int P, int64_t n) {
            1024;
 }
 
-template <class T, class U, bool FIRST, bool LAST>
+template <class T, class U, bool FIRST, bool LAST, bool BUCKETED>
 void radix_pass(dim3 grid, const T* z, int64_t ldz, const T* w, const U* kin, const T* vin, int64_t n, int shift,
-                int tiles, const int32_t* hist, const int32_t* dbase, U* kout, T* vout, KW<T>* pout, cudaStream_t st) {
+                int tiles, const int32_t* hist, const int32_t* dbase, U* kout, T* vout, KW<T>* pout, const Buckets& bk,
+                cudaStream_t st) {
     constexpr size_t smem = radix_pass_smem<T, U>();
     static bool attr = false;
     if (!attr) {
-        SLK_CHECK_CUDA(cudaFuncSetAttribute(k_radix_pass<T, U, FIRST, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            static_cast<int>(smem)));
+        SLK_CHECK_CUDA(cudaFuncSetAttribute(k_radix_pass<T, U, FIRST, LAST, BUCKETED>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
         attr = true;
     }
-    k_radix_pass<T, U, FIRST, LAST><<<grid, RS_THREADS, smem, st>>>(z, ldz, w, kin, vin, n, shift, tiles, hist, dbase,
-                                                                    kout, vout, pout);
+    k_radix_pass<T, U, FIRST, LAST, BUCKETED><<<grid, RS_THREADS, smem, st>>>(z, ldz, w, kin, vin, n, shift, tiles,
+                                                                              hist, dbase, kout, vout, pout, bk);
 }
 
-template <class T>
-void launch_sort_pairs(const T* z, int P, int64_t n, int64_t ldz, const T* w, void* kw, void* scratch,
-                       size_t scratch_bytes, cudaStream_t st) {
-    using U = typename KeyOf<T>::U;
-    SLK_REQUIRE(n < (int64_t(1) << 31), "segments longer than 2^31 are not supported");
-    SLK_REQUIRE(scratch_bytes >= sort_pairs_scratch<T>(P, n), "sort scratch too small");
-    SLK_REQUIRE(P <= 65535, "too many segments for one sort launch");
-    if (n <= 0) return;
+template <class T, class U, bool BUCKETED>
+void sort_passes(const T* z, int P, int64_t n, int64_t ldz, const T* w, KW<T>* pairs, unsigned char* s, int passes,
+                 const Buckets& bk, cudaStream_t st) {
     const int tiles = static_cast<int>(ceil_div(n, RS_TILE));
     const size_t total = static_cast<size_t>(P) * n;
-    unsigned char* s = static_cast<unsigned char*>(scratch);
     U* k0 = reinterpret_cast<U*>(s);
     U* k1 = k0 + total;
     T* v0 = reinterpret_cast<T*>(k1 + total);
     T* v1 = v0 + total;
     int32_t* hist = reinterpret_cast<int32_t*>(v1 + total);
     int32_t* dbase = hist + static_cast<size_t>(P) * RS_BINS * tiles;  // P x 256 digit bases
-    KW<T>* pairs = static_cast<KW<T>*>(kw);
-    constexpr int passes = KeyOf<T>::passes;
     dim3 gt(tiles, P);
     const U* kin = nullptr;
     const T* vin = nullptr;
@@ -721,10 +763,13 @@ void launch_sort_pairs(const T* z, int P, int64_t n, int64_t ldz, const T* w, vo
         const int shift = 8 * pass;
         U* kout = (pass & 1) ? k1 : k0;
         T* vout = (pass & 1) ? v1 : v0;
+        const bool first = pass == 0, last = pass == passes - 1;
         {
             SLK_TIMED("radix_hist", st);
-            if (pass == 0) k_radix_hist<T, U, true><<<gt, RS_THREADS, 0, st>>>(z, ldz, nullptr, n, shift, tiles, hist);
-            else k_radix_hist<T, U, false><<<gt, RS_THREADS, 0, st>>>(nullptr, 0, kin, n, shift, tiles, hist);
+            if (first)
+                k_radix_hist<T, U, true, BUCKETED><<<gt, RS_THREADS, 0, st>>>(z, ldz, nullptr, n, shift, tiles, hist, bk);
+            else
+                k_radix_hist<T, U, false, BUCKETED><<<gt, RS_THREADS, 0, st>>>(nullptr, 0, kin, n, shift, tiles, hist, bk);
         }
         SLK_CHECK_LAUNCH();
         {
@@ -736,20 +781,54 @@ void launch_sort_pairs(const T* z, int P, int64_t n, int64_t ldz, const T* w, vo
         SLK_CHECK_LAUNCH();
         {
             SLK_TIMED("radix_scatter", st);
-            if (pass == 0)
-                radix_pass<T, U, true, false>(gt, z, ldz, w, nullptr, nullptr, n, shift, tiles, hist, dbase, kout, vout,
-                                              nullptr, st);
-            else if (pass == passes - 1)
-                radix_pass<T, U, false, true>(gt, nullptr, 0, nullptr, kin, vin, n, shift, tiles, hist, dbase, nullptr,
-                                              nullptr, pairs, st);
+            if (first && last)
+                radix_pass<T, U, true, true, BUCKETED>(gt, z, ldz, w, nullptr, nullptr, n, shift, tiles, hist, dbase,
+                                                       nullptr, nullptr, pairs, bk, st);
+            else if (first)
+                radix_pass<T, U, true, false, BUCKETED>(gt, z, ldz, w, nullptr, nullptr, n, shift, tiles, hist, dbase,
+                                                        kout, vout, nullptr, bk, st);
+            else if (last)
+                radix_pass<T, U, false, true, BUCKETED>(gt, nullptr, 0, nullptr, kin, vin, n, shift, tiles, hist, dbase,
+                                                        nullptr, nullptr, pairs, bk, st);
             else
-                radix_pass<T, U, false, false>(gt, nullptr, 0, nullptr, kin, vin, n, shift, tiles, hist, dbase, kout,
-                                               vout, nullptr, st);
+                radix_pass<T, U, false, false, BUCKETED>(gt, nullptr, 0, nullptr, kin, vin, n, shift, tiles, hist,
+                                                         dbase, kout, vout, nullptr, bk, st);
         }
         SLK_CHECK_LAUNCH();
         kin = kout;
         vin = vout;
     }
+}
+
+template <class T>
+void launch_sort_pairs(const T* z, int P, int64_t n, int64_t ldz, const T* w, void* kw, void* scratch,
+                       size_t scratch_bytes, const float* kmin, const float* kscale, int NB, cudaStream_t st) {
+    using U = typename KeyOf<T>::U;
+    SLK_REQUIRE(n < (int64_t(1) << 31), "segments longer than 2^31 are not supported");
+    SLK_REQUIRE(scratch_bytes >= sort_pairs_scratch<T>(P, n), "sort scratch too small");
+    SLK_REQUIRE(P <= 65535, "too many segments for one sort launch");
+    if (n <= 0) return;
+    unsigned char* s = static_cast<unsigned char*>(scratch);
+    KW<T>* pairs = static_cast<KW<T>*>(kw);
+    if (NB > 0) {
+        // group by bucket only: one 8-bit digit pass per byte of the bucket index
+        int bits = 0;
+        while ((1 << bits) < NB) ++bits;
+        const int passes = bits > 8 ? (bits + 7) / 8 : 1;
+        sort_passes<T, U, true>(z, P, n, ldz, w, pairs, s, passes, Buckets{kmin, kscale, NB}, st);
+    } else {
+        sort_passes<T, U, false>(z, P, n, ldz, w, pairs, s, KeyOf<T>::passes, Buckets{nullptr, nullptr, 0}, st);
+    }
+}
+
+template <class T>
+void launch_slice_minmax(const T* Z, int P, int64_t n, int64_t ldz, int NB, float* kmin, float* kscale,
+                         cudaStream_t st) {
+    {
+        SLK_TIMED("slice_minmax", st);
+        k_slice_minmax<T><<<P, 256, 0, st>>>(Z, n, ldz, NB, kmin, kscale);
+    }
+    SLK_CHECK_LAUNCH();
 }
 
 template <class T>
@@ -759,13 +838,16 @@ int64_t sorted_pairs_bytes(int P, int64_t n) {
 
 template <class T>
 void launch_bucket_tables(int P, int64_t n, const void* kw, int NB, float* kmin, float* kscale, void* rec,
-                          cudaStream_t st) {
+                          bool have_geometry, cudaStream_t st) {
     const KW<T>* pairs = static_cast<const KW<T>*>(kw);
-    {
-        SLK_TIMED("bucket_minmax", st);
-        k_bucket_minmax<T><<<static_cast<unsigned>(ceil_div(P, 128)), 128, 0, st>>>(pairs, P, n, NB, kmin, kscale);
+    if (!have_geometry) {
+        // fully sorted pairs: the bucket geometry from the first and last key of each slice
+        {
+            SLK_TIMED("bucket_minmax", st);
+            k_bucket_minmax<T><<<static_cast<unsigned>(ceil_div(P, 128)), 128, 0, st>>>(pairs, P, n, NB, kmin, kscale);
+        }
+        SLK_CHECK_LAUNCH();
     }
-    SLK_CHECK_LAUNCH();
     const int nchunk = static_cast<int>(ceil_div(n, PS_CHUNK));
     DevBuf<double2> cs(static_cast<size_t>(P) * (nchunk + 1), st);
     dim3 g(static_cast<unsigned>(nchunk), P);
@@ -809,9 +891,11 @@ void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const void
 
 #define SLK_INST(T)                                                                                                   \
     template size_t sort_pairs_scratch<T>(int, int64_t);                                                              \
-    template void launch_sort_pairs<T>(const T*, int, int64_t, int64_t, const T*, void*, void*, size_t, cudaStream_t); \
+    template void launch_sort_pairs<T>(const T*, int, int64_t, int64_t, const T*, void*, void*, size_t, const float*, \
+                                       const float*, int, cudaStream_t);                                               \
+    template void launch_slice_minmax<T>(const T*, int, int64_t, int64_t, int, float*, float*, cudaStream_t);         \
     template int64_t sorted_pairs_bytes<T>(int, int64_t);                                                             \
-    template void launch_bucket_tables<T>(int, int64_t, const void*, int, float*, float*, void*, cudaStream_t);       \
+    template void launch_bucket_tables<T>(int, int64_t, const void*, int, float*, float*, void*, bool, cudaStream_t); \
     template void launch_negdist_target<T>(const T*, int, int64_t, int64_t, const void*, int64_t, const void*, int,   \
                                            const float*, const float*, double, double, double*, T*, int,             \
                                            cudaStream_t);

@@ -197,26 +197,35 @@ void launch_nfft_target(const T* Z, int P, int64_t n, int64_t ldz, const Fourier
                         T* G, unsigned* err, cudaStream_t st);
 
 // ------------------------------------------------------------ k_sort.cu
-// Per slice p < P, the n sources sorted by their projection z[p * ldz + i] into (key, w)
-// pairs (kw, P x n, sorted order), w the source weights: a segmented LSD radix sort on
-// order-preserving key bits (8-bit digits, stable) carrying the weight as payload.
+// Per slice p < P, the n sources ordered by their projection z[p * ldz + i] into (key, w)
+// pairs (kw, P x n), w the source weights, by a segmented stable LSD radix sort with 8-bit
+// digits carrying the weight as payload.  NB > 0: the digits are those of the equal-width
+// bucket index bucket_of(z; kmin[p], kscale[p], NB) (one pass per byte of NB - 1), so the
+// pairs come out grouped by bucket in ascending bucket order, in source order within a
+// bucket; NB = 0: the digits are the order-preserving bits of z (a full sort).
 template <class T>
 void launch_sort_pairs(const T* z, int P, int64_t n, int64_t ldz, const T* w, void* kw, void* scratch,
-                       size_t scratch_bytes, cudaStream_t st);
+                       size_t scratch_bytes, const float* kmin, const float* kscale, int NB, cudaStream_t st);
+// kmin[p] = the smallest of the n projections of slice p, kscale[p] = NB / (largest - smallest)
+// (0 if they are all equal): the bucket geometry of the grouping above.
+template <class T>
+void launch_slice_minmax(const T* Z, int P, int64_t n, int64_t ldz, int NB, float* kmin, float* kscale,
+                         cudaStream_t st);
 template <class T>
 size_t sort_pairs_scratch(int P, int64_t n);
 // Bytes of the sorted (key, w) pairs of P segments of n sources.
 template <class T>
 int64_t sorted_pairs_bytes(int P, int64_t n);
-// From the sorted pairs: NB equal-width buckets per slice over [key_min, key_max] (kmin,
-// kscale) and one 32-byte record per bucket b <= NB, rec[p][b]: the exclusive prefix sums
-// of w and w*key at the bucket's first sorted index (16 bytes: two doubles for FP64 data,
-// double-float pairs (hi, lo) for FP32 data), that index and the first index of the next
-// bucket (a target's lookup reads one record); rec[p][NB] holds the totals.
+// From pairs grouped by bucket: one 32-byte record per bucket b <= NB, rec[p][b]: the
+// exclusive prefix sums of w and w*key at the bucket's first index (16 bytes: two doubles for
+// FP64 data, double-float pairs (hi, lo) for FP32 data), that index and the first index of
+// the next bucket (a target's lookup reads one record); rec[p][NB] holds the totals.
+// have_geometry: kmin / kscale already hold the buckets the pairs were grouped by;
+// otherwise the pairs are fully sorted and the geometry is set from their first and last keys.
 constexpr int64_t kBucketRecordBytes = 32;
 template <class T>
 void launch_bucket_tables(int P, int64_t n, const void* kw, int NB, float* kmin, float* kscale, void* rec,
-                          cudaStream_t st);
+                          bool have_geometry, cudaStream_t st);
 // Negative-distance 1-D sums at the targets (Section 3.2 in the range-free
 // form t = -c_d [z (2 A_< - W) - (2 B_< - S)]) summed over slices into acc[m],
 // times `scale`; with G != NULL writes g = scale c_d (W - A_< - A_<=) into
