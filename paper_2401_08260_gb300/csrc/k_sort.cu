@@ -684,40 +684,24 @@ __global__ void __launch_bounds__(256) k_negdist_target(const T* __restrict__ Z,
     const int64_t m = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (m >= n) return;
     T sum = T(0), comp = T(0);  // Kahan
-    // software pipeline over the slices: the projection two slices ahead and the bucket record
-    // one slice ahead are requested before the current bucket is scanned
-    auto load_z = [&](int p) { return p < p1 ? Z[static_cast<int64_t>(p) * ldz + m] : T(0); };
-    auto load_rec = [&](int p, T z) {
-        const int b = bucket_of(static_cast<float>(z), kmin[p], kscale[p], NB);
-        return rec[static_cast<int64_t>(p) * (NB + 1) + b];  // one sector: prefix entry and pair range
-    };
-    T z_cur = load_z(p0), z_next = load_z(p0 + 1);
-    BucketRec<T> r_cur = load_rec(p0, z_cur);
     for (int p = p0; p < p1; ++p) {
-        const T z_after = load_z(p + 2);
-        BucketRec<T> r_next{};
-        if (p + 1 < p1) r_next = load_rec(p + 1, z_next);
-        const T z = z_cur;
-        const BucketRec<T> r = r_cur;
+        const T z = Z[static_cast<int64_t>(p) * ldz + m];
         const KW<T>* ks = kw + static_cast<int64_t>(p) * nx;
-        // the bucket's sources in any order, four loads in flight at a time: those below z, and
-        // (gradient) those equal to z; NaN keys pad the last group (neither below nor equal)
+        const BucketRec<T>* rb = rec + static_cast<int64_t>(p) * (NB + 1);
+        const int b = bucket_of(static_cast<float>(z), kmin[p], kscale[p], NB);
+        const BucketRec<T> r = rb[b];  // one sector: prefix entry and the bucket's pair range
+        // the bucket's sources in any order: those below z, and (gradient) those equal to z
         T a = T(0), bz = T(0), aeq = T(0);
-        for (int32_t i0 = r.start; i0 < r.end; i0 += 4) {
-            KW<T> e[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) e[u] = i0 + u < r.end ? ks[i0 + u] : KW<T>{T(NAN), T(0)};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (e[u].key < z) {
-                    a += e[u].w;
-                    bz = fma(e[u].w, e[u].key, bz);
-                } else if (G && e[u].key == z) {
-                    aeq += e[u].w;
-                }
+        for (int32_t i = r.start; i < r.end; ++i) {
+            const KW<T> e = ks[i];
+            if (e.key < z) {
+                a += e.w;
+                bz = fma(e.w, e.key, bz);
+            } else if (G && e.key == z) {
+                aeq += e.w;
             }
         }
-        const Pre<T> eb = r.e, tot = rec[static_cast<int64_t>(p) * (NB + 1) + NB].e;
+        const Pre<T> eb = r.e, tot = rb[NB].e;
         if (G) {
             const T g = scale * negdist_slope(eb, tot, a, aeq, cd);
             T* gp = G + m * P + p;
@@ -729,9 +713,6 @@ __global__ void __launch_bounds__(256) k_negdist_target(const T* __restrict__ Z,
             comp = (tt - sum) - y;
             sum = tt;
         }
-        z_cur = z_next;
-        z_next = z_after;
-        r_cur = r_next;
     }
     if (!G) acc[m] += static_cast<double>(scale) * (static_cast<double>(sum) - static_cast<double>(comp));
 }
