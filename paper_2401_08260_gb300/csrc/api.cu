@@ -520,9 +520,11 @@ template <class T>
 void plan_sort_source(slk_plan plan, const T* Zx, const T* w, cudaStream_t st) {
     const int P = plan->P;
     const int64_t N = plan->N;
-    // about 8 sources per bucket
+    // buckets of about 4 sources (a target scans its bucket's sources in any order), or of
+    // about 8 when the records of all slices would exceed 4 GB
     int nb = 1;
-    while (static_cast<int64_t>(nb) * 8 < N && nb < (1 << 22)) nb <<= 1;
+    while (static_cast<int64_t>(nb) * 4 < N && nb < (1 << 22)) nb <<= 1;
+    if (nb > 1 && static_cast<int64_t>(P) * (nb + 1) * kBucketRecordBytes > (int64_t(4) << 30)) nb >>= 1;
     plan->NB = nb;
     plan->kw.alloc(sorted_pairs_bytes<T>(P, N), st);
     plan->kmin.alloc(P, st);
