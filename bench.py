@@ -161,7 +161,11 @@ def algorithmic(wl, info, precision, kernel_name, launches_per_step, kernels, P=
     slice-point (FP32 ALU).  Chebyshev moments / Clenshaw: two FMAs per term, 4 q flop
     per slice-point (FP32 ALU).  Centring cast: 4 d bytes read + 2 ld16 (x2 for the
     hi/lo split) written per point, plus, with the gradient, the same for the M x P
-    per-slice derivatives it casts.  Other kernels: the 4-byte projections they read.
+    per-slice derivatives it casts.  Sorting route: per source key and pass 4 B read
+    (histogram) or a (key, w) pair read and written (scatter); the bucket tables read the
+    pairs and write one 32-byte record per bucket; the target lookups read the 4-byte target
+    projections and, once per slice, the sorted pairs and records they search (gradient:
+    plus the derivatives written).  Other kernels: the 4-byte projections they read.
     The fused Chebyshev kernels that read the FP32 rows themselves move 4 d bytes per point
     (plus two FP64 partial sums per 256-slice half per target, or the 4-byte weight per
     source) beside
@@ -185,9 +189,46 @@ def algorithmic(wl, info, precision, kernel_name, launches_per_step, kernels, P=
         t_hbm = nbytes / (pk.get("hbm_gbs", 6689.8) * 1e9)
         t_tc = flops / (pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1772.1)) * 1e12)
         return (nbytes, "byte", "hbm") if t_hbm >= t_tc else (flops, "flop", "tensor")
+    if kernel_name.startswith("umma_project"):
+        # 16-bit rows in (hi and lo parts for the FP16x3 split), FP32 projections out; the
+        # bound with the longer minimum time (d = 50 is HBM-bound, d >= 784 tensor-bound)
+        flops = 2.0 * pts * wl.d * P
+        ld16 = (wl.d + 7) // 8 * 8
+        nbytes = pts * (2.0 * ld16 * (2 if kernel_name.startswith("umma_project_x3") else 1) + 4.0 * P)
+        pk = peaks or {}
+        t_hbm = nbytes / (pk.get("hbm_gbs", 6689.8) * 1e9)
+        t_tc = flops / (pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1772.1)) * 1e12)
+        return (nbytes, "byte", "hbm") if t_hbm >= t_tc else (flops, "flop", "tensor")
     if kernel_name.startswith(("gemm", "umma")):
         bound = "tensor" if kernel_name.startswith("umma") else "alu"
         return 2.0 * pts * wl.d * P, "flop", bound
+    nb = int(info.get("sort_buckets", 0) or 0)
+    if nb > 0 and kernel_name.startswith(("radix_", "slice_minmax", "pair_chunk_sums", "pair_prefix_tab",
+                                          "negdist_target")):
+        # sorting route (sources of every slice grouped by key bucket): per source key of a
+        # pass, 4 B read (histogram) or 8 B read + 8 B written (scatter of the (key, w) pair);
+        # the per-slice state the targets look up (sorted pairs and 32-byte bucket records) is
+        # counted once per slice, the 4-byte target projection once per slice-point
+        kb = 8.0 if precision == "f64" else 4.0
+        pairs = 2.0 * kb * wl.N
+        records = 32.0 * (nb + 1)
+        if kernel_name.startswith("radix_hist"):
+            return kb * wl.N * P, "byte", "hbm"
+        if kernel_name.startswith("radix_scatter"):
+            return 2.0 * pairs * P, "byte", "hbm"
+        if kernel_name.startswith("radix_scan"):
+            tiles = -(-wl.N // 2048)
+            return 2.0 * 4.0 * 256 * tiles * P, "byte", "hbm"
+        if kernel_name.startswith("slice_minmax"):
+            return per * kb * wl.N * P, "byte", "hbm"
+        if kernel_name.startswith("pair_chunk_sums"):
+            return per * pairs * P, "byte", "hbm"
+        if kernel_name.startswith("pair_prefix_tab"):
+            return per * (pairs + records) * P, "byte", "hbm"
+        amount = per * (kb * wl.M + pairs + records) * P
+        if kernel_name.startswith("negdist_target_grad"):
+            amount += per * kb * wl.M * P  # the per-slice derivatives written
+        return amount, "byte", "hbm"
     if kernel_name.startswith("ndft_source") or kernel_name.startswith("ndft_target"):
         K = info["k_hi"] - info["k_lo"] + 1
         return 8.0 * K * pts * P, "flop", "alu"

@@ -140,7 +140,7 @@ typedef struct {
     int32_t cheb_horner;      /* 1: targets evaluate the Chebyshev sum by Horner's rule on its
                                  monomial coefficients (chosen only where that rounding bound is
                                  within twice Clenshaw's), 0: Clenshaw's recurrence */
-    int32_t reserved0;
+    int32_t sort_buckets;     /* sorting route: equal-width key buckets per slice (NB; 0 if none) */
     double period;            /* L: period of the Fourier summation in projected units */
     double radius;            /* certified window half-width R */
     double model_error;       /* certified bound: truncation + periodisation + window (per unit sum|w|) */

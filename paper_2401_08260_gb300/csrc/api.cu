@@ -951,6 +951,7 @@ slk_status slk_plan_get_info(slk_plan plan, slk_plan_info* info) {
         info->N = plan->N;
         info->c_d = plan->cd;
         info->device_bytes = plan->device_bytes();
+        info->sort_buckets = plan->NB;
         if (plan->fourier) {
             info->method = plan->fh.method;
             info->n_coeff = plan->fh.n_coeff;

@@ -21,8 +21,8 @@
 // The FP16 "x3" variant (k_umma_project_x3) splits both operands into a high
 // and a scaled low FP16 part (a = a_hi + 2^-11 a_lo') and forms
 // a_hi b_hi + 2^-11 (a_hi b_lo' + a_lo' b_hi) (error ~ 2^-22 relative per
-// product, about FP32), promoting the dominant product to FP32 registers
-// after every 16-wide K step (see the kernel's comment).
+// product, about FP32), promoting each 16-wide K step's three products, folded
+// into one accumulator, to FP32 registers (see the kernel's comment).
 //
 // Every mbarrier wait is bounded: on timeout the kernel records an error bit,
 // skips the remaining work, still frees its tensor memory and returns.
@@ -525,18 +525,19 @@ __global__ void __launch_bounds__(EPI == EPI_CHEB || EPI == EPI_MOM ? 384 : 256,
 // rounds toward zero inside each MMA, so every partial sum it forms is biased
 // towards zero by about 2^-24 of itself; summed over K these biases add up to
 // a systematic relative error (about the number of chained MMA steps x 2^-24)
-// that slicing does not average out.  Here the dominant product a_hi b_hi of
-// every 16-wide K step goes to a fresh accumulator (three TMEM buffers in
-// rotation) and the epilogue warps add it into FP32 registers with
-// round-to-nearest, so the tensor core only ever rounds one 16-term group;
-// the small correction a_hi b_lo + a_lo b_hi (scaled by 2^-11, so its drift
-// is negligible) stays in one accumulator.
-// Tile: 128 points x 128 slices; TMEM columns: D1[0..2] at 0, 128, 256, D2 at 384.
+// that slicing does not average out.  Here every 16-wide K step goes to a fresh
+// accumulator (four TMEM buffers in rotation): the two correction products
+// a_hi b_lo' + a_lo' b_hi first (2^11-scaled low parts), then the dominant
+// product a_hi b_hi with the accumulator scaled by 2^-11 on input (the MMA's
+// input-D scale), so the buffer holds the whole step's contribution after one
+// rounding of a 16-term group.  The epilogue warps add each buffer into FP32
+// registers with round-to-nearest.
+// Tile: 128 points x 128 slices; TMEM columns: D[0..3] at 0, 128, 256, 384.
 // Warps: 0 TMA, 1 MMA, 2 TMEM allocation, 4-11 epilogue (warp 4 + q + 4 h owns
 // TMEM lanes 32q..32q+31 and columns 64h..64h+63).
 constexpr int X3_BN = 128;
 constexpr int X3_STAGES = 3;
-constexpr int X3_BUF = 3;
+constexpr int X3_BUF = 4;
 constexpr int X3_THREADS = 384;
 
 struct SmemX3 {
@@ -544,7 +545,6 @@ struct SmemX3 {
     uint64_t empty[X3_STAGES];
     uint64_t d1_full[X3_BUF];
     uint64_t d1_empty[X3_BUF];
-    uint64_t accum;
     uint64_t drain;
     uint32_t tmem_base;
 };
@@ -567,6 +567,7 @@ __global__ void __launch_bounds__(X3_THREADS, 1)
     const int kblocks = (d + BK - 1) / BK;
     const int ksteps = kblocks * (BK / 16);
     constexpr uint32_t TMEM_COLS = 512;
+    static_assert(X3_BUF * X3_BN <= static_cast<int>(TMEM_COLS), "accumulators exceed tensor memory");
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < X3_STAGES; ++s) {
@@ -577,7 +578,6 @@ __global__ void __launch_bounds__(X3_THREADS, 1)
             mbar_init(&sm->d1_full[b], 1);
             mbar_init(&sm->d1_empty[b], 8);  // one arrival per epilogue warp
         }
-        mbar_init(&sm->accum, 1);
         mbar_init(&sm->drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -610,7 +610,6 @@ __global__ void __launch_bounds__(X3_THREADS, 1)
         drain_fills(sm->full, X3_STAGES, fills);
     } else if (warp == 1 && lane == 0) {
         const uint32_t idesc = instr_desc(0u, BM, X3_BN);
-        const uint32_t d2 = tmem + X3_BUF * X3_BN;
         bool ok = true;
         for (int kb = 0; kb < kblocks && ok; ++kb) {
             const int s = kb % X3_STAGES;
@@ -632,14 +631,14 @@ __global__ void __launch_bounds__(X3_THREADS, 1)
                 const uint64_t ah = smem_desc(st + k * 32), bh = smem_desc(st + A_BYTES + k * 32);
                 const uint64_t al = smem_desc(st + A_BYTES + B_BYTES + k * 32);
                 const uint64_t bl = smem_desc(st + 2 * A_BYTES + B_BYTES + k * 32);
-                umma_f16(tmem + b * X3_BN, ah, bh, idesc, 0u);
+                const uint32_t dt = tmem + b * X3_BN;
+                umma_f16(dt, ah, bl, idesc, 0u);
+                umma_f16(dt, al, bh, idesc, 1u);
+                umma_f16_scale_d<11>(dt, ah, bh, idesc);
                 umma_commit(&sm->d1_full[b]);
-                umma_f16(d2, ah, bl, idesc, t > 0 ? 1u : 0u);
-                umma_f16(d2, al, bh, idesc, 1u);
             }
             umma_commit(&sm->empty[s]);
         }
-        umma_commit(&sm->accum);
         drain_mma(&sm->drain, err);
     } else if (warp >= 4) {
         const int q = warp & 3, h = (warp - 4) >> 2;
@@ -658,39 +657,30 @@ __global__ void __launch_bounds__(X3_THREADS, 1)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-            for (int c = 0; c < 64; c += 32) {
-                float v[32];
-                tmem_ld32(tmem + lane_off + b * X3_BN + cbase + c, v);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) acc[c + j] = __fadd_rn(acc[c + j], v[j]);
-            }
+            uint32_t v0[32], v1[32];
+            tmem_ld32_issue(tmem + lane_off + b * X3_BN + cbase, v0);
+            tmem_ld32_issue(tmem + lane_off + b * X3_BN + cbase + 32, v1);
+            tmem_wait32(v0);
+            tmem_wait32(v1);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm->d1_empty[b]);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                acc[j] = __fadd_rn(acc[j], __uint_as_float(v0[j]));
+                acc[32 + j] = __fadd_rn(acc[32 + j], __uint_as_float(v1[j]));
+            }
         }
         float mx = 0.0f;
-        if (ok && mbar_wait(&sm->accum, 0)) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok && row < n) {
 #pragma unroll
-            for (int c = 0; c < 64; c += 32) {
-                float v[32];
-                tmem_ld32(tmem + lane_off + X3_BUF * X3_BN + cbase + c, v);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) acc[c + j] = fmaf(v[j], 0x1.0p-11f, acc[c + j]);
-            }
-            if (row < n) {
-#pragma unroll
-                for (int j = 0; j < 64; ++j) {
-                    const int p = col0 + cbase + j;
-                    if (p < P) {
-                        Z[static_cast<int64_t>(p) * ldz + row] = acc[j];
-                        mx = fmaxf(mx, fabsf(acc[j]));
-                    }
+            for (int j = 0; j < 64; ++j) {
+                const int p = col0 + cbase + j;
+                if (p < P) {
+                    Z[static_cast<int64_t>(p) * ldz + row] = acc[j];
+                    mx = fmaxf(mx, fabsf(acc[j]));
                 }
             }
-        } else if (ok) {
-            atomicOr(err, 32u);
         }
         if (absmax) {
 #pragma unroll

@@ -101,6 +101,18 @@ __device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64
         : "memory");
 }
 
+// D = A B + 2^-S D (the accumulator scaled by a power of two before the product is added;
+// S in [0, 15]): folds an earlier, 2^S-scaled partial product into the same accumulator
+template <int S>
+__device__ __forceinline__ void umma_f16_scale_d(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc) {
+    static_assert(S >= 0 && S <= 15, "input scale of the accumulator is 0..15");
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, 1, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p, %4;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "n"(S)
+        : "memory");
+}
+
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");

@@ -48,7 +48,7 @@ class PlanInfo(ctypes.Structure):
                 ("P", ctypes.c_int32), ("N", ctypes.c_int64), ("method", ctypes.c_int32),
                 ("n_coeff", ctypes.c_int32), ("n_grid", ctypes.c_int32), ("window", ctypes.c_int32),
                 ("k_lo", ctypes.c_int32), ("k_hi", ctypes.c_int32), ("cheb_terms", ctypes.c_int32),
-                ("cheb_horner", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("period", ctypes.c_double),
+                ("cheb_horner", ctypes.c_int32), ("sort_buckets", ctypes.c_int32), ("period", ctypes.c_double),
                 ("radius", ctypes.c_double), ("model_error", ctypes.c_double), ("c_d", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64)]
 
