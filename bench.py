@@ -160,8 +160,8 @@ def algorithmic(wl, info, precision, kernel_name, launches_per_step, kernels, P=
     NDFT source / target: one complex multiply-add per band coefficient, 8 K flop per
     slice-point (FP32 ALU).  Chebyshev moments / Clenshaw: two FMAs per term, 4 q flop
     per slice-point (FP32 ALU).  Centring cast: 4 d bytes read + 2 ld16 (x2 for the
-    hi/lo split) written per point, plus, with the gradient, the same for the M x P
-    per-slice derivatives it casts.  Sorting route: per source key and pass 4 B read
+    hi/lo split) written per point; the gradient's derivative cast: 4 B read and 2 B
+    written per target slice-point.  Sorting route: per source key and pass 4 B read
     (histogram) or a (key, w) pair read and written (scatter); the bucket tables read the
     pairs and write one 32-byte record per bucket; the target lookups read the 4-byte target
     projections and, once per slice, the sorted pairs and records they search (gradient:
@@ -226,7 +226,7 @@ def algorithmic(wl, info, precision, kernel_name, launches_per_step, kernels, P=
         if kernel_name.startswith("pair_prefix_tab"):
             return per * (pairs + records) * P, "byte", "hbm"
         amount = per * (kb * wl.M + pairs + records) * P
-        if kernel_name.startswith("negdist_target_grad"):
+        if kernel_name.startswith(("negdist_target_grad", "negdist_target_both")):
             amount += per * kb * wl.M * P  # the per-slice derivatives written
         return amount, "byte", "hbm"
     if kernel_name.startswith("ndft_source") or kernel_name.startswith("ndft_target"):
@@ -237,10 +237,10 @@ def algorithmic(wl, info, precision, kernel_name, launches_per_step, kernels, P=
     if kernel_name.startswith("center_cast"):
         k = 2 if precision == "f16x3" else 1
         ld16 = (wl.d + 7) // 8 * 8
-        amount = pts * (4.0 * wl.d + 2.0 * ld16 * k)
-        if grad:
-            amount += per * wl.M * (4.0 * P + 2.0 * ((P + 7) // 8 * 8))
-        return amount, "byte", "hbm"
+        return pts * (4.0 * wl.d + 2.0 * ld16 * k), "byte", "hbm"
+    if kernel_name.startswith("derivs_bf16"):
+        # the M x P derivatives of the gradient: FP32 in, BF16 out (row pitch ld16(P))
+        return per * wl.M * (4.0 * P + 2.0 * ((P + 7) // 8 * 8)), "byte", "hbm"
     return 4.0 * pts * P, "byte", "hbm"
 
 
@@ -360,6 +360,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     gy = torch.empty_like(y) if args.grad else None
+    g_saved = torch.empty(wl.P, wl.M, dtype=y.dtype, device=dev) if args.grad else None
     sharded = args.parallel == "slices"
     if sharded:
         from paper_2401_08260_gb300.shard import ShardedPlan, SliceShard
@@ -379,9 +380,12 @@ def run_ours(args):
             sp.close()
             return
         plan = slk.Plan(x, w, **kw)
-        plan.sum(y, out=s, sync=False)
         if args.grad:
-            plan.grad(y, out=gy, sync=False)
+            # forward with the per-slice derivatives kept, backward product from them
+            plan.sum_derivs(y, out=s, g=g_saved, sync=False)
+            plan.grad_derivs(g_saved, out=gy, sync=False)
+        else:
+            plan.sum(y, out=s, sync=False)
         plan.close()
 
     for _ in range(args.warmup):
@@ -477,9 +481,12 @@ def run_ours(args):
                 sp.close()
                 return
             plan = slk.Plan(xh, wh, **kw_host)
-            plan.sum(yh, out=sh, sync=True)
             if args.grad:
-                plan.grad(yh, out=gh, sync=True)
+                # the derivatives stay on the device between the two calls
+                plan.sum_derivs(yh, out=sh, g=g_saved, sync=True)
+                plan.grad_derivs(g_saved, out=gh, sync=True)
+            else:
+                plan.sum(yh, out=sh, sync=True)
             plan.close()
 
         host_step()

@@ -188,6 +188,32 @@ slk_status slk_grad(slk_plan plan, const void* y, int64_t M, int64_t ldy, const 
                     void* stream);
 
 /*
+ * Sums and per-slice derivatives in one pass: s as slk_sum, and, from the same
+ * projection of the targets and the same evaluation of every slice's 1-D sum,
+ *     g[p * ldd + m] = t_p'(z),  z = <xi_p, y_m - mu>,
+ * the derivative of slice p's 1-D sum at target m (Section 3.2's sorting sums:
+ * c_d (W - A_<(z) - A_<=(z)) with sign(0) = 0; Sections 3.1 and 3.3: the derivative
+ * of the evaluated Fourier or Chebyshev sum; the Laplacian adds both), in the units
+ * of s, so that the gradient of sum_m gs_m s_m is gs_m (1/P) sum_p g[p][m] xi_p
+ * (slk_grad_derivs).  This is the forward pass of a training step: the backward pass
+ * then needs neither the targets nor a second evaluation.
+ * g: P rows of M values, row stride ldd >= M (slice-major), float for F32 / BF16 /
+ * F16X3 plans and double for F64, caller-owned device or host memory; M < 2^31.
+ * Errors as slk_sum.
+ */
+slk_status slk_sum_derivs(slk_plan plan, const void* y, int64_t M, int64_t ldy, void* s, void* g, int64_t ldd,
+                          void* stream);
+
+/*
+ * Gradient from saved derivatives: gy_m = gs_m (1/P) sum_p g[p * ldd + m] xi_p for the
+ * g that slk_sum_derivs wrote (the backward product of slk_grad without projecting or
+ * evaluating the targets again).  gs may be NULL (all ones); gy is M x d with row stride
+ * ldgy.  Errors: SLK_ERR_INVALID, SLK_ERR_OOM, SLK_ERR_CUDA.
+ */
+slk_status slk_grad_derivs(slk_plan plan, const void* g, int64_t M, int64_t ldd, const void* gs, void* gy,
+                           int64_t ldgy, void* stream);
+
+/*
  * Projections of n points onto the plan's directions (Algorithm 1, the inner
  * products <xi_p, x_i>), centred by the plan's centre mu:
  *     Z[p * ldz + i] = <xi_p, x_i - mu>,   p < P, i < n,

@@ -333,6 +333,19 @@ void fourier_setup(slk_plan plan, cudaStream_t st) {
     fd.W = fh.W;
     fd.win_base = fh.win_base;
     fd.beta = fh.beta;
+    std::memset(&fd.wp, 0, sizeof(fd.wp));
+    static_assert(kWinPolyDeg == 8, "the even/odd tap polynomials have degree 8");
+    if (fh.m > 0 && fh.m <= kWinPolyMaxM && fh.wpoly.size() == static_cast<size_t>(fh.m) * (kWinPolyDeg + 1)) {
+        for (int t = 0; t < (fh.m + 1) / 2; ++t) {
+            const double* a = fh.wpoly.data() + static_cast<size_t>(t) * (kWinPolyDeg + 1);
+            for (int j = 0; j <= 4; ++j) fd.wp.ev[t][j] = static_cast<float>(a[2 * j]);
+            for (int j = 0; j <= 3; ++j) {
+                fd.wp.od[t][j] = static_cast<float>(a[2 * j + 1]);
+                fd.wp.de[t][j] = static_cast<float>((2 * j + 1) * a[2 * j + 1]);
+                fd.wp.dq[t][j] = static_cast<float>((2 * j + 2) * a[2 * j + 2]);
+            }
+        }
+    }
     fd.R = plan->R;
     fd.q = fh.cheb_qp;
     fd.horner = 0;
@@ -396,8 +409,10 @@ void plan_fourier_source(slk_plan plan, const T* Zx, const T* w, cudaStream_t st
     } else {
         int64_t ne = nfft_source_scratch(P, N, fd);
         DevBuf<T> scratch(ne, st);
-        launch_nfft_source<T>(Zx, P, N, N, w, fd, fh.n_coeff, plan->mult.get(), reinterpret_cast<T*>(plan->hgrid.get()),
-                              scratch.get(), ne, plan->err_dev.get(), st);
+        // the sorting route's pairs (Laplacian), when built, feed a spreading in key order
+        const T* pairs = plan->sorting ? reinterpret_cast<const T*>(plan->kw.get()) : nullptr;
+        launch_nfft_source<T>(Zx, P, N, N, w, pairs, fd, fh.n_coeff, plan->mult.get(),
+                              reinterpret_cast<T*>(plan->hgrid.get()), scratch.get(), ne, plan->err_dev.get(), st);
     }
     // the host copies of the coefficient tables must outlive the async copies
     SLK_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -598,13 +613,17 @@ void create_impl(slk_plan plan, const void* x_user, int64_t ldx, const void* w_u
         if (tol <= 0.0) tol = default_tol(kernel, plan->desc.precision);
         if (kernel == SLK_GAUSSIAN) plan->fh = choose_gaussian(plan->desc.param, d, R, plan->desc.n_coeff, plan->desc.method, tol);
         else plan->fh = fourier_smooth(plan->desc, d, R, tol);
-        plan->fourier = true;
-        plan_fourier_source<T>(plan, Zx.get(), wv.ptr, st);
+        if (!plan->f64) add_window_poly_error(&plan->fh);
     }
+    // the sorting route first: its pairs, grouped by key, also feed the Laplacian's spreading
     if (kernel == SLK_NEGDIST || kernel == SLK_LAPLACIAN) {
         plan->sorting = true;
         plan->sort_scale = kernel == SLK_LAPLACIAN ? plan->desc.param : 1.0;
         plan_sort_source<T>(plan, Zx.get(), wv.ptr, st);
+    }
+    if (need_fourier) {
+        plan->fourier = true;
+        plan_fourier_source<T>(plan, Zx.get(), wv.ptr, st);
     }
 }
 
@@ -650,6 +669,42 @@ bool sum_fused_cheb(slk_plan plan, const T* y, int64_t M, int64_t ldy, void* s_u
     return false;
 }
 
+// The target side of every slice at the projected targets Zy (P x M, row stride M): with
+// acc, the 1-D sums summed over slices into acc[m]; with G, their derivatives dt_p/dz into
+// G[p * ldg + m] (slice-major); either or both (Algorithm 1; Sections 3.1-3.3 and their
+// derivatives).  For the Laplacian the sorting part adds its derivative to the Fourier part's.
+template <class T>
+void target_side(slk_plan plan, const T* Zy, int64_t M, double* acc, T* G, int64_t ldg, cudaStream_t st) {
+    const int P = plan->P;
+    if (plan->fourier) {
+        if (plan->fh.method == SLK_FOURIER_CHEB)
+            launch_cheb_target<T>(Zy, P, M, M, plan->fd, reinterpret_cast<const T*>(plan->beta.get()), acc, G, ldg,
+                                  plan->err_dev.get(), st);
+        else if (plan->fh.method == SLK_FOURIER_NDFT)
+            launch_ndft_target<T>(Zy, P, M, M, plan->fd, reinterpret_cast<const Cplx<T>*>(plan->cw.get()),
+                                  reinterpret_cast<const T*>(plan->cw0.get()), acc, G, ldg, plan->err_dev.get(), st);
+        else
+            launch_nfft_target<T>(Zy, P, M, M, plan->fd, reinterpret_cast<const T*>(plan->hgrid.get()), acc, G, ldg,
+                                  plan->err_dev.get(), st);
+    }
+    if (plan->sorting)
+        launch_negdist_target<T>(Zy, P, M, M, plan->kw.get(), plan->N, plan->rec.get(), plan->NB, plan->kmin.get(),
+                                 plan->kscale.get(), plan->cd, plan->sort_scale, acc, G, ldg, plan->fourier ? 1 : 0, st);
+}
+
+// s = acc / P into the caller's s (device or host)
+template <class T>
+void finish_sum(const double* acc, int64_t M, int P, void* s_user, cudaStream_t st) {
+    if (is_device_pointer(s_user)) {
+        launch_finalize<T>(acc, static_cast<T*>(s_user), M, 1.0 / P, st);
+    } else {
+        DevBuf<T> s(M, st);
+        launch_finalize<T>(acc, s.get(), M, 1.0 / P, st);
+        SLK_CHECK_CUDA(cudaMemcpyAsync(s_user, s.get(), sizeof(T) * M, cudaMemcpyDeviceToHost, st));
+        SLK_CHECK_CUDA(cudaStreamSynchronize(st));
+    }
+}
+
 template <class T>
 void sum_impl(slk_plan plan, const void* y_user, int64_t M, int64_t ldy, void* s_user, cudaStream_t st) {
     const int P = plan->P, d = plan->d;
@@ -659,31 +714,8 @@ void sum_impl(slk_plan plan, const void* y_user, int64_t M, int64_t ldy, void* s
     project<T>(plan, yv.ptr, M, yv.ld, Zy.get(), nullptr, st);
     DevBuf<double> acc(M, st);
     SLK_CHECK_CUDA(cudaMemsetAsync(acc.get(), 0, sizeof(double) * M, st));
-    if (plan->fourier) {
-        if (plan->fh.method == SLK_FOURIER_CHEB)
-            launch_cheb_target<T>(Zy.get(), P, M, M, plan->fd, reinterpret_cast<const T*>(plan->beta.get()), acc.get(),
-                                  nullptr, plan->err_dev.get(), st);
-        else if (plan->fh.method == SLK_FOURIER_NDFT)
-            launch_ndft_target<T>(Zy.get(), P, M, M, plan->fd, reinterpret_cast<const Cplx<T>*>(plan->cw.get()),
-                                  reinterpret_cast<const T*>(plan->cw0.get()), acc.get(), nullptr, plan->err_dev.get(),
-                                  st);
-        else
-            launch_nfft_target<T>(Zy.get(), P, M, M, plan->fd, reinterpret_cast<const T*>(plan->hgrid.get()), acc.get(),
-                                  nullptr, plan->err_dev.get(), st);
-    }
-    if (plan->sorting)
-        launch_negdist_target<T>(Zy.get(), P, M, M, plan->kw.get(), plan->N, plan->rec.get(), plan->NB,
-                                 plan->kmin.get(), plan->kscale.get(), plan->cd,
-                                 plan->sort_scale, acc.get(), nullptr, 0, st);
-    const bool s_dev = is_device_pointer(s_user);
-    if (s_dev) {
-        launch_finalize<T>(acc.get(), static_cast<T*>(s_user), M, 1.0 / P, st);
-    } else {
-        DevBuf<T> s(M, st);
-        launch_finalize<T>(acc.get(), s.get(), M, 1.0 / P, st);
-        SLK_CHECK_CUDA(cudaMemcpyAsync(s_user, s.get(), sizeof(T) * M, cudaMemcpyDeviceToHost, st));
-        SLK_CHECK_CUDA(cudaStreamSynchronize(st));
-    }
+    target_side<T>(plan, Zy.get(), M, acc.get(), static_cast<T*>(nullptr), 0, st);
+    finish_sum<T>(acc.get(), M, P, s_user, st);
 }
 
 template <class T>
@@ -697,6 +729,34 @@ void project_impl(slk_plan plan, const void* x_user, int64_t n, int64_t ldx, voi
     if (!is_device_pointer(Z_user)) SLK_CHECK_CUDA(cudaStreamSynchronize(st));
 }
 
+// Backward product (Algorithm 1 differentiated): gy_m = gs_m (1/P) sum_p G[p * ldG + m] xi_p
+// into the caller's gy (M x d, row stride ldgy, device or host); gs device memory or NULL.
+template <class T>
+void backward_product(slk_plan plan, const T* G, int64_t ldG, int64_t M, const T* gs, void* gy_user, int64_t ldgy,
+                      cudaStream_t st) {
+    const int P = plan->P, d = plan->d;
+    const bool g_dev = is_device_pointer(gy_user);
+    DevBuf<T> gy_tmp(g_dev ? 0 : static_cast<size_t>(M) * d, st);
+    T* out = g_dev ? static_cast<T*>(gy_user) : gy_tmp.get();
+    const int64_t ldo = g_dev ? ldgy : d;
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+        if (plan->tc) {
+            // on tensor cores: BF16 operands (the derivatives transposed to M x P), FP32 accumulate
+            DevBuf<unsigned char> g16(static_cast<size_t>(M) * umma_operand_ld(P) * 2, st);
+            launch_derivs_bf16(G, P, M, ldG, g16.get(), st);
+            launch_grad_umma(g16.get(), M, P, plan->xit16.get(), d, gs, 1.0 / P, out, ldo, plan->err_dev.get(), st);
+            done = true;
+        }
+    }
+    if (!done) launch_grad_gemm<T>(G, ldG, M, P, xi_of<T>(plan), d, gs, 1.0 / P, out, ldo, st);
+    if (!g_dev) {
+        SLK_CHECK_CUDA(cudaMemcpy2DAsync(gy_user, sizeof(T) * ldgy, out, sizeof(T) * d, sizeof(T) * d, M,
+                                         cudaMemcpyDeviceToHost, st));
+        SLK_CHECK_CUDA(cudaStreamSynchronize(st));
+    }
+}
+
 template <class T>
 void grad_impl(slk_plan plan, const void* y_user, int64_t M, int64_t ldy, const void* gs_user, void* gy_user,
                int64_t ldg, cudaStream_t st) {
@@ -704,53 +764,42 @@ void grad_impl(slk_plan plan, const void* y_user, int64_t M, int64_t ldy, const 
     InView<T> yv(y_user, M, d, ldy, st);
     DevBuf<T> Zy(static_cast<size_t>(P) * M, st);
     project<T>(plan, yv.ptr, M, yv.ld, Zy.get(), nullptr, st);
-    DevBuf<T> G(static_cast<size_t>(M) * P, st);
-    if (plan->fourier) {
-        if (plan->fh.method == SLK_FOURIER_CHEB)
-            launch_cheb_target<T>(Zy.get(), P, M, M, plan->fd, reinterpret_cast<const T*>(plan->beta.get()), nullptr,
-                                  G.get(), plan->err_dev.get(), st);
-        else if (plan->fh.method == SLK_FOURIER_NDFT)
-            launch_ndft_target<T>(Zy.get(), P, M, M, plan->fd, reinterpret_cast<const Cplx<T>*>(plan->cw.get()),
-                                  reinterpret_cast<const T*>(plan->cw0.get()), nullptr, G.get(), plan->err_dev.get(),
-                                  st);
-        else
-            launch_nfft_target<T>(Zy.get(), P, M, M, plan->fd, reinterpret_cast<const T*>(plan->hgrid.get()), nullptr,
-                                  G.get(), plan->err_dev.get(), st);
-    }
-    if (plan->sorting)
-        launch_negdist_target<T>(Zy.get(), P, M, M, plan->kw.get(), plan->N, plan->rec.get(), plan->NB,
-                                 plan->kmin.get(), plan->kscale.get(), plan->cd,
-                                 plan->sort_scale, nullptr, G.get(), plan->fourier ? 1 : 0, st);
+    DevBuf<T> G(static_cast<size_t>(P) * M, st);
+    target_side<T>(plan, Zy.get(), M, nullptr, G.get(), M, st);
     InView<T> gsv(gs_user, gs_user ? M : 0, 1, 1, st);
-    const bool g_dev = is_device_pointer(gy_user);
-    if constexpr (sizeof(T) == 4) {
-        if (plan->tc) {
-            // backward product on tensor cores (BF16 operands, FP32 accumulate)
-            DevBuf<unsigned char> g16(static_cast<size_t>(M) * umma_operand_ld(P) * 2, st);
-            launch_center_cast(G.get(), M, P, P, nullptr, g16.get(), nullptr, 0, st);
-            DevBuf<T> gy_tmp(g_dev ? 0 : static_cast<size_t>(M) * d, st);
-            T* out = g_dev ? static_cast<T*>(gy_user) : gy_tmp.get();
-            const int64_t ldo = g_dev ? ldg : d;
-            launch_grad_umma(g16.get(), M, P, plan->xit16.get(), d, gs_user ? gsv.ptr : nullptr, 1.0 / P, out, ldo,
-                             plan->err_dev.get(), st);
-            if (!g_dev) {
-                SLK_CHECK_CUDA(cudaMemcpy2DAsync(gy_user, sizeof(T) * ldg, out, sizeof(T) * d, sizeof(T) * d, M,
-                                                 cudaMemcpyDeviceToHost, st));
-                SLK_CHECK_CUDA(cudaStreamSynchronize(st));
-            }
-            return;
-        }
-    }
-    if (g_dev) {
-        launch_grad_gemm<T>(G.get(), M, P, xi_of<T>(plan), d, gs_user ? gsv.ptr : nullptr, 1.0 / P,
-                            static_cast<T*>(gy_user), ldg, st);
-    } else {
-        DevBuf<T> gy(static_cast<size_t>(M) * d, st);
-        launch_grad_gemm<T>(G.get(), M, P, xi_of<T>(plan), d, gs_user ? gsv.ptr : nullptr, 1.0 / P, gy.get(), d, st);
-        SLK_CHECK_CUDA(cudaMemcpy2DAsync(gy_user, sizeof(T) * ldg, gy.get(), sizeof(T) * d, sizeof(T) * d, M,
+    backward_product<T>(plan, G.get(), M, M, gs_user ? gsv.ptr : nullptr, gy_user, ldg, st);
+}
+
+// Sums and the per-slice derivatives from one projection of the targets and one evaluation
+// of the target side (the sorting route's lookup serves both).
+template <class T>
+void sum_derivs_impl(slk_plan plan, const void* y_user, int64_t M, int64_t ldy, void* s_user, void* g_user,
+                     int64_t ldd, cudaStream_t st) {
+    const int P = plan->P, d = plan->d;
+    InView<T> yv(y_user, M, d, ldy, st);
+    DevBuf<T> Zy(static_cast<size_t>(P) * M, st);
+    project<T>(plan, yv.ptr, M, yv.ld, Zy.get(), nullptr, st);
+    DevBuf<double> acc(M, st);
+    SLK_CHECK_CUDA(cudaMemsetAsync(acc.get(), 0, sizeof(double) * M, st));
+    const bool g_dev = is_device_pointer(g_user);
+    DevBuf<T> gtmp(g_dev ? 0 : static_cast<size_t>(P) * M, st);
+    T* G = g_dev ? static_cast<T*>(g_user) : gtmp.get();
+    const int64_t ldG = g_dev ? ldd : M;
+    target_side<T>(plan, Zy.get(), M, acc.get(), G, ldG, st);
+    finish_sum<T>(acc.get(), M, P, s_user, st);
+    if (!g_dev) {
+        SLK_CHECK_CUDA(cudaMemcpy2DAsync(g_user, sizeof(T) * ldd, G, sizeof(T) * M, sizeof(T) * M, P,
                                          cudaMemcpyDeviceToHost, st));
         SLK_CHECK_CUDA(cudaStreamSynchronize(st));
     }
+}
+
+template <class T>
+void grad_derivs_impl(slk_plan plan, const void* g_user, int64_t M, int64_t ldd, const void* gs_user, void* gy_user,
+                      int64_t ldgy, cudaStream_t st) {
+    InView<T> gv(g_user, plan->P, static_cast<int>(M), ldd, st);
+    InView<T> gsv(gs_user, gs_user ? M : 0, 1, 1, st);
+    backward_product<T>(plan, gv.ptr, gv.ld, M, gs_user ? gsv.ptr : nullptr, gy_user, ldgy, st);
 }
 
 void validate_desc(const slk_plan_desc* desc) {
@@ -887,6 +936,55 @@ slk_status slk_grad(slk_plan plan, const void* y, int64_t M, int64_t ldy, const 
     });
 }
 
+slk_status slk_sum_derivs(slk_plan plan, const void* y, int64_t M, int64_t ldy, void* s, void* g, int64_t ldd,
+                          void* stream) {
+    set_last_error("");
+    return guarded([&] {
+        SLK_REQUIRE(plan, "plan is NULL");
+        slk_status prev = collect(plan, false);
+        if (prev != SLK_OK) throw Error{prev, slk_last_error()};
+        SLK_REQUIRE(M >= 0, "M must be >= 0");
+        if (M == 0) return;
+        SLK_REQUIRE(y && s && g, "y, s and g must not be NULL");
+        SLK_REQUIRE(ldy >= plan->d, "ldy must be >= d");
+        SLK_REQUIRE(ldd >= M, "ldd must be >= M");
+        SLK_REQUIRE(M <= INT32_MAX, "M must be < 2^31");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        if (plan->f64) sum_derivs_impl<double>(plan, y, M, ldy, s, g, ldd, st);
+        else sum_derivs_impl<float>(plan, y, M, ldy, s, g, ldd, st);
+        finish_call(plan, st);
+        plan->stream = st;
+        if (!is_device_pointer(s) || !is_device_pointer(g)) {
+            slk_status e = collect(plan, true);
+            if (e != SLK_OK) throw Error{e, slk_last_error()};
+        }
+    });
+}
+
+slk_status slk_grad_derivs(slk_plan plan, const void* g, int64_t M, int64_t ldd, const void* gs, void* gy,
+                           int64_t ldgy, void* stream) {
+    set_last_error("");
+    return guarded([&] {
+        SLK_REQUIRE(plan, "plan is NULL");
+        slk_status prev = collect(plan, false);
+        if (prev != SLK_OK) throw Error{prev, slk_last_error()};
+        SLK_REQUIRE(M >= 0, "M must be >= 0");
+        if (M == 0) return;
+        SLK_REQUIRE(g && gy, "g and gy must not be NULL");
+        SLK_REQUIRE(ldd >= M && ldgy >= plan->d, "ldd must be >= M and ldgy >= d");
+        SLK_REQUIRE(M <= INT32_MAX, "M must be < 2^31");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        if (plan->f64) grad_derivs_impl<double>(plan, g, M, ldd, gs, gy, ldgy, st);
+        else grad_derivs_impl<float>(plan, g, M, ldd, gs, gy, ldgy, st);
+        finish_call(plan, st);
+        plan->stream = st;
+        if (!is_device_pointer(gy)) {
+            slk_status e = collect(plan, true);
+            if (e != SLK_OK) throw Error{e, slk_last_error()};
+        }
+    });
+}
+
 slk_status slk_plan_project(slk_plan plan, const void* x, int64_t n, int64_t ldx, void* Z, int64_t ldz, void* stream) {
     set_last_error("");
     return guarded([&] {
@@ -985,10 +1083,10 @@ slk_status slk_fourier_params(const slk_plan_desc* desc, double radius, slk_plan
         const bool f64 = desc->precision == SLK_PREC_F64;
         double tol = desc->tol;
         if (tol <= 0.0) tol = default_tol(desc->kernel, desc->precision);
-        (void)f64;
         FourierHost fh = desc->kernel == SLK_GAUSSIAN
                              ? choose_gaussian(desc->param, desc->d, radius, desc->n_coeff, desc->method, tol)
                              : fourier_smooth(*desc, desc->d, radius, tol);
+        if (!f64) add_window_poly_error(&fh);
         std::memset(info, 0, sizeof(*info));
         info->kernel = desc->kernel;
         info->precision = desc->precision;
@@ -1226,21 +1324,7 @@ void sum_noalloc_impl(slk_plan plan, const T* y, int64_t M, int64_t ldy, T* s, u
     if (!projected) launch_project_simt<T>(xi_of<T>(plan), P, y, M, d, ldy, mu_of<T>(plan), Zy, M, st);
     // the array keeps the previous call's contents: the accumulator must start at zero
     SLK_CHECK_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * M, st));
-    if (plan->fourier) {
-        if (plan->fh.method == SLK_FOURIER_CHEB)
-            launch_cheb_target<T>(Zy, P, M, M, plan->fd, reinterpret_cast<const T*>(plan->beta.get()), acc, nullptr,
-                                  plan->err_dev.get(), st);
-        else if (plan->fh.method == SLK_FOURIER_NDFT)
-            launch_ndft_target<T>(Zy, P, M, M, plan->fd, reinterpret_cast<const Cplx<T>*>(plan->cw.get()),
-                                  reinterpret_cast<const T*>(plan->cw0.get()), acc, nullptr, plan->err_dev.get(), st);
-        else
-            launch_nfft_target<T>(Zy, P, M, M, plan->fd, reinterpret_cast<const T*>(plan->hgrid.get()), acc, nullptr,
-                                  plan->err_dev.get(), st);
-    }
-    if (plan->sorting)
-        launch_negdist_target<T>(Zy, P, M, M, plan->kw.get(), plan->N, plan->rec.get(), plan->NB,
-                                 plan->kmin.get(), plan->kscale.get(), plan->cd,
-                                 plan->sort_scale, acc, nullptr, 0, st);
+    target_side<T>(plan, Zy, M, acc, static_cast<T*>(nullptr), 0, st);
     launch_finalize<T>(acc, s, M, 1.0 / P, st);
 }
 

@@ -13,6 +13,11 @@
 
 namespace slk {
 
+// NFFT window taps of FP32 plans as polynomials: degree (the even/odd split of the kernels
+// assumes 8), and the widest window (cells)
+constexpr int kWinPolyDeg = 8;
+constexpr int kWinPolyMaxM = 16;
+
 // ---------------------------------------------------------------- errors
 
 struct Error {

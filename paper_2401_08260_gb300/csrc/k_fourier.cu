@@ -15,6 +15,8 @@
 //
 // Because the projected data occupy only |z| <= R << L/2, only the grid cells
 // [win_base, win_base + W) that a window can touch are stored.
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace slk {
@@ -28,11 +30,24 @@ constexpr int SPREAD_NARROW_W = 64;
 constexpr int SPREAD_WARPS = 8;
 constexpr int SPREAD_CHUNK = 4096;  // sources per warp in the narrow spread
 
-template <class T>
-__device__ inline T es_window(T s, T two_over_m, T beta) {
-    T x = s * two_over_m;
-    T q = T(1) - x * x;
-    return q > T(0) ? exp(beta * (sqrt(q) - T(1))) : (q == T(0) ? exp(-beta) : T(0));
+// psi(s) = exp(beta (sqrt(1 - x^2) - 1)) = exp(-beta x^2 / (1 + sqrt(1 - x^2))), x = 2 s / m,
+// and 0 for |x| > 1.  The second form has no cancellation near x = 0 (where the first loses
+// beta times the rounding of the square root); FP32 takes the square root as q rsqrt(q) and
+// the exponential as exp2 of the exponent times log2(e).
+__device__ inline float es_window(float s, float two_over_m, float beta) {
+    const float x = s * two_over_m;
+    const float x2 = x * x;
+    const float q = 1.0f - x2;
+    if (!(q >= 0.0f)) return 0.0f;
+    const float r = q > 0.0f ? q * rsqrtf(q) : 0.0f;
+    return exp2f((-beta * 1.44269504088896341f) * __fdividef(x2, 1.0f + r));
+}
+__device__ inline double es_window(double s, double two_over_m, double beta) {
+    const double x = s * two_over_m;
+    const double x2 = x * x;
+    const double q = 1.0 - x2;
+    if (!(q >= 0.0)) return 0.0;
+    return exp(-beta * x2 / (1.0 + sqrt(q)));
 }
 
 // derivative of psi with respect to s
@@ -43,6 +58,35 @@ __device__ inline T es_window_deriv(T s, T two_over_m, T beta) {
     if (q <= T(1e-6)) return T(0);
     T r = sqrt(q);
     return exp(beta * (r - T(1))) * beta * (-x * two_over_m) / r;
+}
+
+// The weights of all MM taps of a point whose first window cell lies at s0 (FP32: g =
+// s0 + (MM - 1) / 2 in [-1/2, 1/2), the plan's even/odd tap polynomials, two taps from one
+// evaluation of E_t and O_t; FP64: psi itself).  DERIV: the derivatives d psi / ds instead.
+template <int MM, bool DERIV>
+__device__ __forceinline__ void window_taps(const WinPoly& wp, float s0, float, float, float (&wt)[MM]) {
+    const float g = s0 + 0.5f * static_cast<float>(MM - 1), h = g * g;
+#pragma unroll
+    for (int t = 0; t < (MM + 1) / 2; ++t) {
+        float e, o;
+        if (DERIV) {
+            e = fmaf(fmaf(fmaf(wp.de[t][3], h, wp.de[t][2]), h, wp.de[t][1]), h, wp.de[t][0]);
+            o = fmaf(fmaf(fmaf(wp.dq[t][3], h, wp.dq[t][2]), h, wp.dq[t][1]), h, wp.dq[t][0]);
+        } else {
+            e = fmaf(fmaf(fmaf(fmaf(wp.ev[t][4], h, wp.ev[t][3]), h, wp.ev[t][2]), h, wp.ev[t][1]), h, wp.ev[t][0]);
+            o = fmaf(fmaf(fmaf(wp.od[t][3], h, wp.od[t][2]), h, wp.od[t][1]), h, wp.od[t][0]);
+        }
+        const float go = g * o;
+        wt[t] = e + go;
+        if (MM - 1 - t != t) wt[MM - 1 - t] = DERIV ? go - e : e - go;
+    }
+}
+template <int MM, bool DERIV>
+__device__ __forceinline__ void window_taps(const WinPoly&, double s0, double two_over_m, double beta,
+                                            double (&wt)[MM]) {
+#pragma unroll
+    for (int t = 0; t < MM; ++t)
+        wt[t] = DERIV ? es_window_deriv(s0 + double(t), two_over_m, beta) : es_window(s0 + double(t), two_over_m, beta);
 }
 
 template <class T>
@@ -178,12 +222,12 @@ __global__ void k_ndft_reduce(const T* __restrict__ partial, int nchunk, int P, 
 // ------------------------------------------------------------ NDFT target
 
 // One thread per target: t_p(z) = 2 Re sum_j cw[p][j] e^{+i (k_lo + j) th} + cw0[p] for every
-// slice, averaged into acc[m]; GRAD writes dt_p/dz into G[m][p] instead.
+// slice, averaged into acc[m]; GRAD writes dt_p/dz into G[p * ldg + m] instead.
 template <class T, int KMAX, bool GRAD>
 __global__ void __launch_bounds__(256) k_ndft_target(const T* __restrict__ Z, int P, int64_t n, int64_t ldz,
                                                      T two_over_L, int k_lo, int K, const Cplx<T>* __restrict__ cw,
                                                      const T* __restrict__ cw0, int slice_chunk, T R,
-                                                     double* __restrict__ acc, T* __restrict__ G,
+                                                     double* __restrict__ acc, T* __restrict__ G, int64_t ldg,
                                                      unsigned* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     Cplx<T>* scw = reinterpret_cast<Cplx<T>*>(smem_raw);
@@ -223,7 +267,7 @@ __global__ void __launch_bounds__(256) k_ndft_target(const T* __restrict__ Z, in
                 }
             }
             // th = 2 pi z / L: dt_p/dz = 2 * dt * 2 pi / L
-            if (GRAD) G[m * P + p] = T(2) * dt * two_pi_over_L;
+            if (GRAD) G[p * ldg + m] = T(2) * dt * two_pi_over_L;
             else sum.add(T(2) * t + scw0[q]);
         }
     }
@@ -239,7 +283,7 @@ template <class T, int KMAX, bool GRAD>
 __global__ void __launch_bounds__(256) k_ndft_target_warp(const T* __restrict__ Z, int P, int64_t n, int64_t ldz,
                                                           T two_over_L, int k_lo, int K,
                                                           const Cplx<T>* __restrict__ cw, const T* __restrict__ cw0,
-                                                          T R, double* __restrict__ acc, T* __restrict__ G,
+                                                          T R, double* __restrict__ acc, T* __restrict__ G, int64_t ldg,
                                                           unsigned* __restrict__ err) {
     const int lane = threadIdx.x & 31;
     const int64_t m = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -269,7 +313,7 @@ __global__ void __launch_bounds__(256) k_ndft_target_warp(const T* __restrict__ 
                 ci = ni;
             }
         }
-        if (GRAD) G[m * P + p] = T(2) * dt * two_pi_over_L;
+        if (GRAD) G[p * ldg + m] = T(2) * dt * two_pi_over_L;
         else sum.add(T(2) * t + cw0[p]);
     }
     if (bad) atomicOr(err, 4u);
@@ -417,11 +461,11 @@ __global__ void k_cheb_reduce(const TP* __restrict__ partial, int nchunk, int P,
 }
 
 // Target side: t_p(z) = sum_l beta[p][l] T_l(z / R) by Clenshaw's recurrence, summed over
-// slices into acc[m]; GRAD writes dt_p/dz = (1/R) sum_l l beta_l U_{l-1}(v) into G[m][p].
+// slices into acc[m]; GRAD writes dt_p/dz = (1/R) sum_l l beta_l U_{l-1}(v) into G[p * ldg + m].
 template <class T, int QMAX, bool GRAD, bool HORNER>
 __global__ void __launch_bounds__(256) k_cheb_target(const T* __restrict__ Z, int P, int64_t n, int64_t ldz, T inv_R,
                                                      int q, const T* __restrict__ beta, int slice_chunk, T R,
-                                                     double* __restrict__ acc, T* __restrict__ G,
+                                                     double* __restrict__ acc, T* __restrict__ G, int64_t ldg,
                                                      unsigned* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     T* sb = reinterpret_cast<T*>(smem_raw);
@@ -458,7 +502,7 @@ __global__ void __launch_bounds__(256) k_cheb_target(const T* __restrict__ Z, in
                     b2 = b1;
                     b1 = bk;
                 }
-                G[m * P + p] = b1 * inv_R;
+                G[p * ldg + m] = b1 * inv_R;
             } else if (HORNER) {
                 // b holds the monomial coefficients
                 T r = b[QMAX - 1];
@@ -529,9 +573,9 @@ __global__ void __launch_bounds__(256) k_spread_narrow(const T* __restrict__ Z, 
 
 // Wide window: one slice per block row, a block-shared window with shared
 // atomics (sources spread over many cells, little contention).
-template <class T>
+template <class T, int MMAX>
 __global__ void __launch_bounds__(256) k_spread_wide(const T* __restrict__ Z, int P, int64_t n, int64_t ldz,
-                                                     const T* __restrict__ w, T scale_u, int m, T two_over_m, T beta,
+                                                     const T* __restrict__ w, T scale_u, int m, T two_over_m, T beta, const WinPoly wp,
                                                      int W, int win_base, int64_t chunk, T* __restrict__ partial,
                                                      unsigned* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
@@ -553,8 +597,79 @@ __global__ void __launch_bounds__(256) k_spread_wide(const T* __restrict__ Z, in
             bad = true;
             continue;
         }
-        T s = c0 - u;
-        for (int t = 0; t < m; ++t, s += T(1)) atomicAdd(&win[r0 + t], wv * es_window(s, two_over_m, beta));
+        T wt[MMAX];
+        window_taps<MMAX, false>(wp, c0 - u, two_over_m, beta, wt);
+#pragma unroll
+        for (int t = 0; t < MMAX; ++t)
+            if (t < m) atomicAdd(&win[r0 + t], wv * wt[t]);
+    }
+    if (bad) atomicOr(err, 1u);
+    __syncthreads();
+    for (int r = threadIdx.x; r < W; r += blockDim.x)
+        partial[(static_cast<int64_t>(blockIdx.x) * P + p) * W + r] = win[r];
+}
+
+// Spreading from sources grouped by key bucket (the sorting route's pairs: (key, w)
+// interleaved, slice p's n pairs at pairs + 2 p n, buckets much narrower than a grid cell,
+// so the pairs ascend in grid cell).  Each lane walks its warp's share of the block's chunk
+// with stride 32 (coalesced loads); its points then stay in one window position for long
+// runs, so it accumulates the m taps in registers and adds them to the block's shared window
+// only when the position changes (and at the end).  Any order is correct; the grouping only
+// makes the shared-memory additions rare.
+template <class T, int MMAX>
+__global__ void __launch_bounds__(256) k_spread_sorted(const T* __restrict__ pairs, int64_t n, T scale_u, int m,
+                                                       T two_over_m, T beta, const WinPoly wp, int W, int win_base,
+                                                       int64_t chunk, T* __restrict__ partial,
+                                                       unsigned* __restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    T* win = reinterpret_cast<T*>(smem_raw);
+    const int p = blockIdx.y, P = gridDim.y;
+    for (int r = threadIdx.x; r < W; r += blockDim.x) win[r] = T(0);
+    __syncthreads();
+    const int64_t i0 = static_cast<int64_t>(blockIdx.x) * chunk;
+    const int64_t i1 = (i0 + chunk < n) ? i0 + chunk : n;
+    const T* kw = pairs + 2 * static_cast<int64_t>(p) * n;
+    const T half_m = T(0.5) * T(m);
+    T acc[MMAX];
+#pragma unroll
+    for (int t = 0; t < MMAX; ++t) acc[t] = T(0);
+    int cur = -1;
+    bool bad = false;
+    // warp w takes the w-th eighth of the chunk, its lanes every 32nd pair of it: loads stay
+    // coalesced and a lane's successive points are only 32 apart in key order
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t per_warp = chunk / (blockDim.x >> 5);
+    const int64_t w0 = i0 + warp * per_warp;
+    const int64_t w1 = (w0 + per_warp < i1) ? w0 + per_warp : i1;
+    for (int64_t i = w0 + lane; i < w1; i += 32) {
+        const T key = kw[2 * i], wv = kw[2 * i + 1];
+        const T u = key * scale_u;
+        const T c0 = ceil(u - half_m);
+        const int r0 = static_cast<int>(c0) - win_base;
+        if (r0 < 0 || r0 + m > W) {
+            bad = true;
+            continue;
+        }
+        if (r0 != cur) {
+            if (cur >= 0) {
+#pragma unroll
+                for (int t = 0; t < MMAX; ++t)
+                    if (t < m) atomicAdd(&win[cur + t], acc[t]);
+            }
+#pragma unroll
+            for (int t = 0; t < MMAX; ++t) acc[t] = T(0);
+            cur = r0;
+        }
+        T wt[MMAX];
+        window_taps<MMAX, false>(wp, c0 - u, two_over_m, beta, wt);
+#pragma unroll
+        for (int t = 0; t < MMAX; ++t)
+            if (t < m) acc[t] = fma(wv, wt[t], acc[t]);
+    }
+    if (cur >= 0) {
+#pragma unroll
+        for (int t = 0; t < MMAX; ++t)
+            if (t < m) atomicAdd(&win[cur + t], acc[t]);
     }
     if (bad) atomicOr(err, 1u);
     __syncthreads();
@@ -641,11 +756,11 @@ __global__ void __launch_bounds__(512) k_fft_multiply(const T* __restrict__ g, i
 
 // ------------------------------------------------------------ NFFT interpolation
 
-template <class T>
+template <class T, int MMAX>
 __global__ void __launch_bounds__(256) k_nfft_target(const T* __restrict__ Z, int P, int64_t n, int64_t ldz, T scale_u,
-                                                     int m, T two_over_m, T beta, int W, int win_base,
+                                                     int m, T two_over_m, T beta, const WinPoly wp, int W, int win_base,
                                                      const T* __restrict__ h, int slice_chunk, T R,
-                                                     double* __restrict__ acc, T* __restrict__ G,
+                                                     double* __restrict__ acc, T* __restrict__ G, int64_t ldg,
                                                      unsigned* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     T* sh = reinterpret_cast<T*>(smem_raw);
@@ -680,13 +795,19 @@ __global__ void __launch_bounds__(256) k_nfft_target(const T* __restrict__ Z, in
                 continue;
             }
             const T* row = sh + static_cast<size_t>(q) * W + r0;
-            T s = c0 - u, t = T(0);
+            T t = T(0), wt[MMAX];
             if (G) {
                 // d/du sum_j h_j psi(u - j) = -sum_j h_j psi'(j - u)
-                for (int k = 0; k < m; ++k, s += T(1)) t -= row[k] * es_window_deriv(s, two_over_m, beta);
-                G[mi * P + p] = t * scale_u;
+                window_taps<MMAX, true>(wp, c0 - u, two_over_m, beta, wt);
+#pragma unroll
+                for (int k = 0; k < MMAX; ++k)
+                    if (k < m) t -= row[k] * wt[k];
+                G[p * ldg + mi] = t * scale_u;
             } else {
-                for (int k = 0; k < m; ++k, s += T(1)) t += row[k] * es_window(s, two_over_m, beta);
+                window_taps<MMAX, false>(wp, c0 - u, two_over_m, beta, wt);
+#pragma unroll
+                for (int k = 0; k < MMAX; ++k)
+                    if (k < m) t = fma(row[k], wt[k], t);
                 sum.add(t);
             }
         }
@@ -698,6 +819,35 @@ __global__ void __launch_bounds__(256) k_nfft_target(const T* __restrict__ Z, in
 }  // namespace
 
 // ------------------------------------------------------------ launchers
+
+// Calls f(std::integral_constant<int, MM>{}) with MM >= m taps: the window's exact width for
+// the FP32 kernels (their taps unrolled with no idle ones), 8, 12 or 16 for FP64.
+template <class T, class F>
+void tap_dispatch(int m, F&& f) {
+    SLK_REQUIRE(m >= 4 && m <= kWinPolyMaxM, "NFFT window of %d cells", m);
+    if constexpr (sizeof(T) == 4) {
+        switch (m) {
+            case 4: f(std::integral_constant<int, 4>{}); break;
+            case 5: f(std::integral_constant<int, 5>{}); break;
+            case 6: f(std::integral_constant<int, 6>{}); break;
+            case 7: f(std::integral_constant<int, 7>{}); break;
+            case 8: f(std::integral_constant<int, 8>{}); break;
+            case 9: f(std::integral_constant<int, 9>{}); break;
+            case 10: f(std::integral_constant<int, 10>{}); break;
+            case 11: f(std::integral_constant<int, 11>{}); break;
+            case 12: f(std::integral_constant<int, 12>{}); break;
+            case 13: f(std::integral_constant<int, 13>{}); break;
+            case 14: f(std::integral_constant<int, 14>{}); break;
+            case 15: f(std::integral_constant<int, 15>{}); break;
+            default: f(std::integral_constant<int, 16>{}); break;
+        }
+    } else {
+        if (m <= 8) f(std::integral_constant<int, 8>{});
+        else if (m <= 12) f(std::integral_constant<int, 12>{});
+        else f(std::integral_constant<int, 16>{});
+    }
+}
+
 
 int64_t ndft_source_scratch(int P, int64_t n, const FourierDev& fd) {
     int K = fd.k_hi - fd.k_lo + 1;
@@ -746,7 +896,12 @@ constexpr int64_t kNdftWarpTargets = 32768;
 
 template <class T>
 void launch_ndft_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const Cplx<T>* cw,
-                        const T* cw0, double* acc, T* G, unsigned* err, cudaStream_t st) {
+                        const T* cw0, double* acc, T* G, int64_t ldg, unsigned* err, cudaStream_t st) {
+    if (acc && G) {
+        launch_ndft_target<T>(Z, P, n, ldz, fd, cw, cw0, acc, nullptr, 0, err, st);
+        launch_ndft_target<T>(Z, P, n, ldz, fd, cw, cw0, nullptr, G, ldg, err, st);
+        return;
+    }
     if (n <= 0) return;
     const int K = fd.k_hi - fd.k_lo + 1;
     SLK_REQUIRE(K >= 1 && K <= NDFT_KMAX, "NDFT band of %d coefficients exceeds %d", K, NDFT_KMAX);
@@ -763,10 +918,10 @@ void launch_ndft_target(const T* Z, int P, int64_t n, int64_t ldz, const Fourier
         const unsigned wblocks = static_cast<unsigned>(ceil_div(n, 8));
         if (G)
             SLK_NDFT_DISPATCH(K, (k_ndft_target_warp<T, KM, true><<<wblocks, 256, 0, st>>>(
-                                     Z, P, n, ldz, two_over_L, fd.k_lo, K, cw, cw0, static_cast<T>(fd.R), acc, G, err)));
+                                     Z, P, n, ldz, two_over_L, fd.k_lo, K, cw, cw0, static_cast<T>(fd.R), acc, G, ldg, err)));
         else
             SLK_NDFT_DISPATCH(K, (k_ndft_target_warp<T, KM, false><<<wblocks, 256, 0, st>>>(
-                                     Z, P, n, ldz, two_over_L, fd.k_lo, K, cw, cw0, static_cast<T>(fd.R), acc, G, err)));
+                                     Z, P, n, ldz, two_over_L, fd.k_lo, K, cw, cw0, static_cast<T>(fd.R), acc, G, ldg, err)));
         SLK_CHECK_LAUNCH();
         return;
     }
@@ -774,13 +929,13 @@ void launch_ndft_target(const T* Z, int P, int64_t n, int64_t ldz, const Fourier
         SLK_NDFT_DISPATCH(K, {
             cudaFuncSetAttribute(k_ndft_target<T, KM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
             k_ndft_target<T, KM, true><<<blocks, 256, smem, st>>>(Z, P, n, ldz, two_over_L, fd.k_lo, K, cw, cw0, chunk,
-                                                                 static_cast<T>(fd.R), acc, G, err);
+                                                                 static_cast<T>(fd.R), acc, G, ldg, err);
         });
     } else {
         SLK_NDFT_DISPATCH(K, {
             cudaFuncSetAttribute(k_ndft_target<T, KM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
             k_ndft_target<T, KM, false><<<blocks, 256, smem, st>>>(Z, P, n, ldz, two_over_L, fd.k_lo, K, cw, cw0,
-                                                                  chunk, static_cast<T>(fd.R), acc, G, err);
+                                                                  chunk, static_cast<T>(fd.R), acc, G, ldg, err);
         });
     }
     SLK_CHECK_LAUNCH();
@@ -848,7 +1003,12 @@ void launch_cheb_reduce_f64(const double* partial, int nchunk, int P, const Four
 
 template <class T>
 void launch_cheb_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const T* beta, double* acc,
-                        T* G, unsigned* err, cudaStream_t st) {
+                        T* G, int64_t ldg, unsigned* err, cudaStream_t st) {
+    if (acc && G) {
+        launch_cheb_target<T>(Z, P, n, ldz, fd, beta, acc, nullptr, 0, err, st);
+        launch_cheb_target<T>(Z, P, n, ldz, fd, beta, nullptr, G, ldg, err, st);
+        return;
+    }
     if (n <= 0) return;
     const int q = fd.q;
     int chunk = static_cast<int>((48 * 1024) / (sizeof(T) * q));
@@ -860,14 +1020,14 @@ void launch_cheb_target(const T* Z, int P, int64_t n, int64_t ldz, const Fourier
     SLK_TIMED(G ? "cheb_target_grad" : "cheb_target", st);
     if (G) {
         SLK_CHEB_DISPATCH(q, (k_cheb_target<T, QM, true, false><<<blocks, 256, smem, st>>>(
-                                 Z, P, n, ldz, inv_R, q, beta, chunk, static_cast<T>(fd.R), acc, G, err)));
+                                 Z, P, n, ldz, inv_R, q, beta, chunk, static_cast<T>(fd.R), acc, G, ldg, err)));
     } else if (fd.horner && fd.mono) {
         const T* mono = static_cast<const T*>(fd.mono);
         SLK_CHEB_DISPATCH(q, (k_cheb_target<T, QM, false, true><<<blocks, 256, smem, st>>>(
-                                 Z, P, n, ldz, inv_R, q, mono, chunk, static_cast<T>(fd.R), acc, G, err)));
+                                 Z, P, n, ldz, inv_R, q, mono, chunk, static_cast<T>(fd.R), acc, G, ldg, err)));
     } else {
         SLK_CHEB_DISPATCH(q, (k_cheb_target<T, QM, false, false><<<blocks, 256, smem, st>>>(
-                                 Z, P, n, ldz, inv_R, q, beta, chunk, static_cast<T>(fd.R), acc, G, err)));
+                                 Z, P, n, ldz, inv_R, q, beta, chunk, static_cast<T>(fd.R), acc, G, ldg, err)));
     }
     SLK_CHECK_LAUNCH();
 }
@@ -877,9 +1037,9 @@ template void launch_cheb_source<float>(const float*, int, int64_t, int64_t, con
 template void launch_cheb_source<double>(const double*, int, int64_t, int64_t, const double*, const FourierDev&,
                                          const double*, double*, double*, unsigned*, double, double*, int64_t, cudaStream_t);
 template void launch_cheb_target<float>(const float*, int, int64_t, int64_t, const FourierDev&, const float*, double*,
-                                        float*, unsigned*, cudaStream_t);
+                                        float*, int64_t, unsigned*, cudaStream_t);
 template void launch_cheb_target<double>(const double*, int, int64_t, int64_t, const FourierDev&, const double*,
-                                         double*, double*, unsigned*, cudaStream_t);
+                                         double*, double*, int64_t, unsigned*, cudaStream_t);
 
 int64_t nfft_source_scratch(int P, int64_t n, const FourierDev& fd) {
     int64_t nchunk;
@@ -889,17 +1049,34 @@ int64_t nfft_source_scratch(int P, int64_t n, const FourierDev& fd) {
 }
 
 template <class T>
-void launch_nfft_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, const FourierDev& fd, int n_coeff,
-                        const double* mult, T* h, T* scratch, int64_t scratch_elems, unsigned* err, cudaStream_t st) {
+void launch_nfft_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, const T* pairs, const FourierDev& fd,
+                        int n_coeff, const double* mult, T* h, T* scratch, int64_t scratch_elems, unsigned* err,
+                        cudaStream_t st) {
     SLK_REQUIRE(scratch_elems >= nfft_source_scratch(P, n, fd), "NFFT scratch too small");
     SLK_REQUIRE(fd.W <= fd.n_g, "NFFT window wider than the grid");
+    SLK_REQUIRE(fd.m >= 1 && fd.m <= 16, "NFFT window of %d cells", fd.m);
     const T scale_u = static_cast<T>(fd.n_g / fd.L);
     const T two_over_m = static_cast<T>(2.0 / fd.m);
     const T beta = static_cast<T>(fd.beta);
     // scratch layout: [partials nchunk x P x W] [reduced grid P x W]
     T* partial = scratch;
     int64_t nchunk;
-    if (fd.W <= SPREAD_NARROW_W) {
+    if (pairs) {
+        // sources grouped by key: taps accumulated in registers along each thread's run
+        const int64_t chunk = 65536;
+        nchunk = ceil_div(n, chunk);
+        const size_t smem = sizeof(T) * fd.W;
+        SLK_REQUIRE(smem <= 200 * 1024, "NFFT window too wide");
+        dim3 grid(static_cast<unsigned>(nchunk), P);
+        SLK_TIMED("spread_sorted", st);
+        tap_dispatch<T>(fd.m, [&](auto mm) {
+            constexpr int MM = decltype(mm)::value;
+            SLK_CHECK_CUDA(cudaFuncSetAttribute(k_spread_sorted<T, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                200 * 1024));
+            k_spread_sorted<T, MM><<<grid, 256, smem, st>>>(pairs, n, scale_u, fd.m, two_over_m, beta, fd.wp, fd.W,
+                                                           fd.win_base, chunk, partial, err);
+        });
+    } else if (fd.W <= SPREAD_NARROW_W) {
         nchunk = ceil_div(n, static_cast<int64_t>(SPREAD_WARPS) * SPREAD_CHUNK);
         size_t smem = sizeof(T) * SPREAD_WARPS * fd.W * 32;
         static bool attr_set[2] = {false, false};
@@ -921,15 +1098,18 @@ void launch_nfft_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, c
         SLK_REQUIRE(smem <= 200 * 1024, "NFFT window too wide");
         static bool attr_set[2] = {false, false};
         if (!attr_set[sizeof(T) == 8]) {
-            SLK_CHECK_CUDA(
-                cudaFuncSetAttribute(k_spread_wide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
             attr_set[sizeof(T) == 8] = true;
         }
         dim3 grid(static_cast<unsigned>(nchunk), P);
         {
             SLK_TIMED("spread_wide", st);
-            k_spread_wide<T><<<grid, 256, smem, st>>>(Z, P, n, ldz, w, scale_u, fd.m, two_over_m, beta, fd.W, fd.win_base,
-                                                       chunk, partial, err);
+            tap_dispatch<T>(fd.m, [&](auto mm) {
+                constexpr int MM = decltype(mm)::value;
+                SLK_CHECK_CUDA(
+                    cudaFuncSetAttribute(k_spread_wide<T, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+                k_spread_wide<T, MM><<<grid, 256, smem, st>>>(Z, P, n, ldz, w, scale_u, fd.m, two_over_m, beta, fd.wp,
+                                                              fd.W, fd.win_base, chunk, partial, err);
+            });
         }
     }
     SLK_CHECK_LAUNCH();
@@ -960,7 +1140,12 @@ void launch_nfft_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, c
 
 template <class T>
 void launch_nfft_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const T* h, double* acc,
-                        T* G, unsigned* err, cudaStream_t st) {
+                        T* G, int64_t ldg, unsigned* err, cudaStream_t st) {
+    if (acc && G) {
+        launch_nfft_target<T>(Z, P, n, ldz, fd, h, acc, nullptr, 0, err, st);
+        launch_nfft_target<T>(Z, P, n, ldz, fd, h, nullptr, G, ldg, err, st);
+        return;
+    }
     if (n <= 0) return;
     // slices whose grid windows a block holds at once: about 24 KB, so that several blocks share
     // an SM (the loop over slices is latency-bound; occupancy hides it)
@@ -969,16 +1154,17 @@ void launch_nfft_target(const T* Z, int P, int64_t n, int64_t ldz, const Fourier
     if (chunk < 1) chunk = 1;
     size_t smem = sizeof(T) * fd.W * chunk;
     SLK_REQUIRE(smem <= 100 * 1024, "NFFT window too wide for the interpolation");
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[sizeof(T) == 8]) {
-        SLK_CHECK_CUDA(cudaFuncSetAttribute(k_nfft_target<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-        attr_set[sizeof(T) == 8] = true;
-    }
     {
         SLK_TIMED("nfft_target", st);
-        k_nfft_target<T><<<static_cast<unsigned>(ceil_div(n, 256)), 256, smem, st>>>(
-            Z, P, n, ldz, static_cast<T>(fd.n_g / fd.L), fd.m, static_cast<T>(2.0 / fd.m), static_cast<T>(fd.beta), fd.W,
-            fd.win_base, h, chunk, static_cast<T>(fd.R), acc, G, err);
+        const unsigned blocks = static_cast<unsigned>(ceil_div(n, 256));
+        tap_dispatch<T>(fd.m, [&](auto mm) {
+            constexpr int MM = decltype(mm)::value;
+            SLK_CHECK_CUDA(
+                cudaFuncSetAttribute(k_nfft_target<T, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+            k_nfft_target<T, MM><<<blocks, 256, smem, st>>>(
+                Z, P, n, ldz, static_cast<T>(fd.n_g / fd.L), fd.m, static_cast<T>(2.0 / fd.m), static_cast<T>(fd.beta),
+                fd.wp, fd.W, fd.win_base, h, chunk, static_cast<T>(fd.R), acc, G, ldg, err);
+        });
     }
     SLK_CHECK_LAUNCH();
 }
@@ -988,17 +1174,19 @@ template void launch_ndft_source<float>(const float*, int, int64_t, int64_t, con
 template void launch_ndft_source<double>(const double*, int, int64_t, int64_t, const double*, const FourierDev&,
                                          const double*, Cplx<double>*, double*, double*, int64_t, cudaStream_t);
 template void launch_ndft_target<float>(const float*, int, int64_t, int64_t, const FourierDev&, const Cplx<float>*,
-                                        const float*, double*, float*, unsigned*, cudaStream_t);
+                                        const float*, double*, float*, int64_t, unsigned*, cudaStream_t);
 template void launch_ndft_target<double>(const double*, int, int64_t, int64_t, const FourierDev&,
-                                         const Cplx<double>*, const double*, double*, double*, unsigned*,
+                                         const Cplx<double>*, const double*, double*, double*, int64_t, unsigned*,
                                          cudaStream_t);
-template void launch_nfft_source<float>(const float*, int, int64_t, int64_t, const float*, const FourierDev&, int,
-                                        const double*, float*, float*, int64_t, unsigned*, cudaStream_t);
-template void launch_nfft_source<double>(const double*, int, int64_t, int64_t, const double*, const FourierDev&, int,
-                                         const double*, double*, double*, int64_t, unsigned*, cudaStream_t);
+template void launch_nfft_source<float>(const float*, int, int64_t, int64_t, const float*, const float*,
+                                        const FourierDev&, int, const double*, float*, float*, int64_t, unsigned*,
+                                        cudaStream_t);
+template void launch_nfft_source<double>(const double*, int, int64_t, int64_t, const double*, const double*,
+                                         const FourierDev&, int, const double*, double*, double*, int64_t, unsigned*,
+                                         cudaStream_t);
 template void launch_nfft_target<float>(const float*, int, int64_t, int64_t, const FourierDev&, const float*, double*,
-                                        float*, unsigned*, cudaStream_t);
+                                        float*, int64_t, unsigned*, cudaStream_t);
 template void launch_nfft_target<double>(const double*, int, int64_t, int64_t, const FourierDev&, const double*,
-                                         double*, double*, unsigned*, cudaStream_t);
+                                         double*, double*, int64_t, unsigned*, cudaStream_t);
 
 }  // namespace slk

@@ -99,15 +99,16 @@ void launch_project_simt(const T* xi, int P, const T* x, int64_t n, int d, int64
 }
 
 template <class T>
-void launch_grad_gemm(const T* G, int64_t M, int P, const T* xi, int d, const T* gs, double scale, T* gy,
+void launch_grad_gemm(const T* G, int64_t ldG, int64_t M, int P, const T* xi, int d, const T* gs, double scale, T* gy,
                       int64_t ldg, cudaStream_t st) {
     if (M <= 0) return;
-    // rows r = targets (A = G, row-major M x P), columns c = coordinates (B(c, p) = xi[p][c])
+    // rows r = targets (A(m, p) = G[p * ldG + m], slice-major), columns c = coordinates
+    // (B(c, p) = xi[p][c])
     dim3 grid(static_cast<unsigned>(ceil_div(M, BM)), static_cast<unsigned>(ceil_div(d, BN)));
     SLK_REQUIRE(grid.y <= 65535, "dimension too large for one backward launch");
     {
         SLK_TIMED("gemm_tile", st);
-        k_gemm_tile<T, T, T, T><<<grid, 256, 0, st>>>(M, d, P, G, P, 1, xi, 1, d, nullptr, gy, ldg, scale, gs, 1);
+        k_gemm_tile<T, T, T, T><<<grid, 256, 0, st>>>(M, d, P, G, 1, ldG, xi, 1, d, nullptr, gy, ldg, scale, gs, 1);
     }
     SLK_CHECK_LAUNCH();
 }
@@ -116,9 +117,9 @@ template void launch_project_simt<float>(const float*, int, const float*, int64_
                                          int64_t, cudaStream_t);
 template void launch_project_simt<double>(const double*, int, const double*, int64_t, int, int64_t, const double*,
                                           double*, int64_t, cudaStream_t);
-template void launch_grad_gemm<float>(const float*, int64_t, int, const float*, int, const float*, double, float*,
-                                      int64_t, cudaStream_t);
-template void launch_grad_gemm<double>(const double*, int64_t, int, const double*, int, const double*, double, double*,
-                                       int64_t, cudaStream_t);
+template void launch_grad_gemm<float>(const float*, int64_t, int64_t, int, const float*, int, const float*, double,
+                                      float*, int64_t, cudaStream_t);
+template void launch_grad_gemm<double>(const double*, int64_t, int64_t, int, const double*, int, const double*, double,
+                                       double*, int64_t, cudaStream_t);
 
 }  // namespace slk

@@ -51,11 +51,12 @@ struct Buckets {
     const float* kmin;
     const float* kscale;
     int NB;
+    int mask;  // digit mask of a pass (digits of dbits <= 8 bits)
 };
 template <bool BUCKETED, class U>
 __device__ __forceinline__ int radix_digit(U k, int shift, const Buckets& bk, int p) {
     if constexpr (BUCKETED)
-        return (bucket_of(static_cast<float>(key_from_bits(k)), bk.kmin[p], bk.kscale[p], bk.NB) >> shift) & 0xff;
+        return (bucket_of(static_cast<float>(key_from_bits(k)), bk.kmin[p], bk.kscale[p], bk.NB) >> shift) & bk.mask;
     else
         return static_cast<int>((k >> shift) & 0xffu);
 }
@@ -485,12 +486,39 @@ __global__ void __launch_bounds__(PS_THREADS) k_pair_chunk_sums(const KW<T>* __r
     }
 }
 
+// A prefix entry from lane src of the warp
+__device__ __forceinline__ Pre<float> shfl_pre(const Pre<float>& e, int src) {
+    return Pre<float>{__shfl_sync(0xffffffffu, e.ahi, src), __shfl_sync(0xffffffffu, e.alo, src),
+                      __shfl_sync(0xffffffffu, e.bhi, src), __shfl_sync(0xffffffffu, e.blo, src)};
+}
+__device__ __forceinline__ Pre<double> shfl_pre(const Pre<double>& e, int src) {
+    return Pre<double>{__shfl_sync(0xffffffffu, e.a, src), __shfl_sync(0xffffffffu, e.b, src)};
+}
+
+// One whole 32-byte record in one store (a record written in pieces leaves partial sectors,
+// which the memory system completes with a read of the sector from DRAM)
+template <class T>
+__device__ __forceinline__ void store_record(BucketRec<T>* dst, const Pre<T>& e, int32_t start, int32_t end) {
+    static_assert(sizeof(Pre<T>) == 16, "prefix entries are 16 bytes");
+    uint32_t v[8];
+    memcpy(v, &e, sizeof(e));
+    v[4] = static_cast<uint32_t>(start);
+    v[5] = static_cast<uint32_t>(end);
+    v[6] = 0u;
+    v[7] = 0u;
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst), "r"(v[0]), "r"(v[1]),
+                 "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
 // Bucket records from the sorted pairs and the scanned chunk sums (cs[p][c] = exclusive
-// prefix before chunk c): every sorted index i that starts buckets (b(i-1), b(i)] writes
-// their start i and prefix entry (the prefix of (w, w key) before i), and i as the end of
-// bucket b(i-1) and of the empty buckets between; the last index ends its bucket and fills
-// the buckets above it (record NB holds the totals).  Each thread takes PS_ITEMS
-// consecutive pairs.
+// prefix before chunk c): the thread holding the first pair i of bucket b writes record b
+// whole (prefix entry before i, start i, end = the first pair of a higher bucket), together
+// with the records of the empty buckets just below b (start = end = i); the thread of the
+// last pair also writes the records above its bucket (record NB holds the totals).  Each
+// thread takes PS_ITEMS consecutive pairs; a bucket's end, when it lies beyond the thread's
+// pairs, comes from a block-wide scan of the threads' first bucket starts (and, past the
+// block's chunk, from one look-ahead per block).
 template <class T>
 __global__ void __launch_bounds__(PS_THREADS) k_pair_prefix_tab(const KW<T>* __restrict__ kw, int64_t n, int nchunk,
                                                                const double2* __restrict__ cs, int NB,
@@ -499,6 +527,8 @@ __global__ void __launch_bounds__(PS_THREADS) k_pair_prefix_tab(const KW<T>* __r
                                                                BucketRec<T>* __restrict__ rec) {
     __shared__ PairSum<T> wsum[PS_THREADS / 32];
     __shared__ PairSum<T> chunk_start;
+    __shared__ int64_t warp_next[PS_THREADS / 32];
+    __shared__ int64_t block_next;
     const int p = blockIdx.y, c = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const KW<T>* ks = kw + static_cast<int64_t>(p) * n;
@@ -537,37 +567,85 @@ __global__ void __launch_bounds__(PS_THREADS) k_pair_prefix_tab(const KW<T>* __r
     start.norm();
     T la = T(0), lb = T(0);  // the run within this thread's pairs, plain arithmetic
     int bprev = i0 == 0 ? -1 : (i0 < n ? bucket_of(static_cast<float>(ks[i0 - 1].key), lo, sc, NB) : NB);
+    // bucket of every pair (NB past the end, so that index n starts the sentinel "bucket")
+    int bk[PS_ITEMS];
+#pragma unroll
+    for (int r = 0; r < PS_ITEMS; ++r) bk[r] = i0 + r < n ? bucket_of(static_cast<float>(el[r].key), lo, sc, NB) : NB;
+    // first bucket start among this thread's positions (n counts as one), then the first one
+    // after this thread: a suffix minimum over the block's threads
+    constexpr int64_t kNone = INT64_MAX;
+    int64_t first = kNone;
+#pragma unroll
+    for (int r = PS_ITEMS - 1; r >= 0; --r)
+        if (i0 + r <= n && bk[r] > (r ? bk[r - 1] : bprev)) first = i0 + r;
+    int64_t after = kNone;  // min of `first` over the later lanes of this warp
+    {
+        int64_t v = first;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t u = __shfl_down_sync(0xffffffffu, v, o);
+            if (lane + o < 32) v = u < v ? u : v;
+        }
+        // v: min over lanes >= lane; the later lanes' minimum is the next lane's v
+        const int64_t nxt = __shfl_down_sync(0xffffffffu, v, 1);
+        after = lane < 31 ? nxt : kNone;
+        if (lane == 0) warp_next[warp] = v;
+    }
+    if (threadIdx.x == PS_THREADS - 1) {
+        // the first start past the block's chunk: one look-ahead over the last bucket's pairs
+        const int64_t e = static_cast<int64_t>(c + 1) * PS_CHUNK;
+        if (e >= n) {
+            block_next = n;
+        } else {
+            const int blast = bucket_of(static_cast<float>(ks[e - 1].key), lo, sc, NB);
+            int64_t j = e;
+            while (j < n && bucket_of(static_cast<float>(ks[j].key), lo, sc, NB) == blast) ++j;
+            block_next = j;
+        }
+    }
+    __syncthreads();
+    for (int q = warp + 1; q < PS_THREADS / 32; ++q) after = warp_next[q] < after ? warp_next[q] : after;
+    if (after == kNone) after = block_next;
 #pragma unroll
     for (int r = 0; r < PS_ITEMS; ++r) {
         const int64_t i = i0 + r;
-        if (i >= n) break;
-        const int bi = bucket_of(static_cast<float>(el[r].key), lo, sc, NB);
-        if (bi > bprev) {
-            // bucket bprev ends here, the empty buckets between start and end here, bucket bi
-            // starts here (each field is written by exactly one thread)
+        const int bi = bk[r];
+        const bool starts = i < n && bi > bprev;
+        Pre<T> e{};
+        if (starts) {
+            // bucket bi starts here: its whole record
             PairSum<T> pre = start;
             pre.plus(PairSum<T>::from_pair(la, lb));
-            const Pre<T> e = pre.entry();
-            if (bprev >= 0) rb[bprev].end = static_cast<int32_t>(i);
-            for (int q = bprev + 1; q <= bi; ++q) {
-                rb[q].e = e;
-                rb[q].start = static_cast<int32_t>(i);
-                if (q < bi) rb[q].end = static_cast<int32_t>(i);
-            }
-            bprev = bi;
+            e = pre.entry();
+            int64_t end = after;
+#pragma unroll
+            for (int j = PS_ITEMS - 1; j > r; --j)
+                if (i0 + j <= n && bk[j] > bk[j - 1]) end = i0 + j;
+            store_record(rb + bi, e, static_cast<int32_t>(i), static_cast<int32_t>(end));
         }
-        la += el[r].w;
-        lb = fma(el[r].w, el[r].key, lb);
+        // the empty buckets above bprev start and end here: filled by the whole warp, one
+        // lane's run after another (long runs occur in the sparse tails of a slice)
+        const int q0 = starts ? bprev + 1 : 0, q1 = starts ? bi : 0;
+        unsigned todo = __ballot_sync(0xffffffffu, q1 > q0);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int a0 = __shfl_sync(0xffffffffu, q0, src), a1 = __shfl_sync(0xffffffffu, q1, src);
+            const int32_t at = __shfl_sync(0xffffffffu, static_cast<int32_t>(i), src);
+            const Pre<T> es = shfl_pre(e, src);
+            for (int q = a0 + lane; q < a1; q += 32) store_record(rb + q, es, at, at);
+        }
+        if (starts) bprev = bi;
+        if (i < n) {
+            la += el[r].w;
+            lb = fma(el[r].w, el[r].key, lb);
+        }
         if (i == n - 1) {
             PairSum<T> tot = start;
             tot.plus(PairSum<T>::from_pair(la, lb));
-            const Pre<T> e = tot.entry();
-            rb[bi].end = static_cast<int32_t>(n);
-            for (int q = bi + 1; q <= NB; ++q) {
-                rb[q].e = e;
-                rb[q].start = static_cast<int32_t>(n);
-                rb[q].end = static_cast<int32_t>(n);
-            }
+            const Pre<T> et = tot.entry();
+            for (int q = bi + 1; q <= NB; ++q)
+                store_record(rb + q, et, static_cast<int32_t>(n), static_cast<int32_t>(n));
         }
     }
 }
@@ -628,6 +706,13 @@ __global__ void __launch_bounds__(1024) k_row_exclusive_scan(double2* __restrict
     if (threadIdx.x == 0) row[NB] = make_double2(ca_s, cb_s);
 }
 
+// 32 bytes (one sector, 32-byte aligned) of read-only data in one load
+__device__ __forceinline__ void ld_sector(const void* ptr, float (&r)[8]) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7])
+        : "l"(ptr));
+}
+
 // ------------------------------------------------------------ targets
 
 // Per-slice value and derivative at z from the prefix entry of z's bucket (e), the totals
@@ -671,42 +756,73 @@ __device__ __forceinline__ double negdist_slope(const Pre<double>& e, const Pre<
 }
 
 // Slices [p0, p1): for target m, bucket b of z; A_< and B_< from the bucket's prefix entry
-// plus the sorted pairs of bucket b below z (and A_<= for the gradient), the value or
-// derivative by negdist_value / negdist_slope; per-slice values summed with Kahan
-// compensation, then added to the FP64 accumulator once per launch.
-template <class T>
+// plus the pairs of bucket b below z (and A_<= for the gradient); VAL: the values by
+// negdist_value, summed over the slices with Kahan compensation and added to the FP64
+// accumulator once per launch; DER: the derivatives by negdist_slope into G[p * ldg + m]
+// (coalesced across the warp).  One lookup serves both.
+template <class T, bool VAL, bool DER>
 __global__ void __launch_bounds__(256) k_negdist_target(const T* __restrict__ Z, int P, int p0, int p1, int64_t n,
                                                        int64_t ldz, const KW<T>* __restrict__ kw, int64_t nx,
                                                        const BucketRec<T>* __restrict__ rec, int NB,
                                                        const float* __restrict__ kmin, const float* __restrict__ kscale,
-                                                       T cd, T scale,
-                                                       double* __restrict__ acc, T* __restrict__ G, int accumulate_G) {
+                                                       T cd, T scale, double* __restrict__ acc, T* __restrict__ G,
+                                                       int64_t ldg, int accumulate_G) {
     const int64_t m = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (m >= n) return;
     T sum = T(0), comp = T(0);  // Kahan
     for (int p = p0; p < p1; ++p) {
         const T z = Z[static_cast<int64_t>(p) * ldz + m];
-        const KW<T>* ks = kw + static_cast<int64_t>(p) * nx;
         const BucketRec<T>* rb = rec + static_cast<int64_t>(p) * (NB + 1);
         const int b = bucket_of(static_cast<float>(z), kmin[p], kscale[p], NB);
-        const BucketRec<T> r = rb[b];  // one sector: prefix entry and the bucket's pair range
         // the bucket's sources in any order: those below z, and (gradient) those equal to z
         T a = T(0), bz = T(0), aeq = T(0);
-        for (int32_t i = r.start; i < r.end; ++i) {
-            const KW<T> e = ks[i];
-            if (e.key < z) {
-                a += e.w;
-                bz = fma(e.w, e.key, bz);
-            } else if (G && e.key == z) {
-                aeq += e.w;
+        Pre<T> eb;
+        if constexpr (sizeof(T) == 4) {
+            // the record in one 32-byte load, the pairs in aligned 32-byte chunks of four: one
+            // sector per load instead of one load per pair (the lanes of a warp read unrelated
+            // buckets, so every load is a separate sector access)
+            float rr[8];
+            ld_sector(rb + b, rr);
+            eb = Pre<T>{rr[0], rr[1], rr[2], rr[3]};
+            const int64_t base = static_cast<int64_t>(p) * nx;
+            const int64_t g0 = base + __float_as_int(rr[4]), g1 = base + __float_as_int(rr[5]);
+            for (int64_t g = g0 & ~int64_t(3); g < g1; g += 4) {
+                float v[8];
+                ld_sector(kw + g, v);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (g + j >= g0 && g + j < g1) {
+                        const float key = v[2 * j], wv = v[2 * j + 1];
+                        if (key < z) {
+                            a += wv;
+                            if (VAL) bz = fmaf(wv, key, bz);
+                        } else if (DER && key == z) {
+                            aeq += wv;
+                        }
+                    }
+                }
+            }
+        } else {
+            const KW<T>* ks = kw + static_cast<int64_t>(p) * nx;
+            const BucketRec<T> r = rb[b];  // one sector: prefix entry and the bucket's pair range
+            eb = r.e;
+            for (int32_t i = r.start; i < r.end; ++i) {
+                const KW<T> e = ks[i];
+                if (e.key < z) {
+                    a += e.w;
+                    if (VAL) bz = fma(e.w, e.key, bz);
+                } else if (DER && e.key == z) {
+                    aeq += e.w;
+                }
             }
         }
-        const Pre<T> eb = r.e, tot = rb[NB].e;
-        if (G) {
+        const Pre<T> tot = rb[NB].e;
+        if (DER) {
             const T g = scale * negdist_slope(eb, tot, a, aeq, cd);
-            T* gp = G + m * P + p;
+            T* gp = G + static_cast<int64_t>(p) * ldg + m;
             *gp = accumulate_G ? *gp + g : g;
-        } else {
+        }
+        if (VAL) {
             const T t = negdist_value(eb, tot, a, bz, z, cd);
             const T y = t - comp;
             const T tt = sum + y;
@@ -714,7 +830,7 @@ __global__ void __launch_bounds__(256) k_negdist_target(const T* __restrict__ Z,
             sum = tt;
         }
     }
-    if (!G) acc[m] += static_cast<double>(scale) * (static_cast<double>(sum) - static_cast<double>(comp));
+    if (VAL) acc[m] += static_cast<double>(scale) * (static_cast<double>(sum) - static_cast<double>(comp));
 }
 
 }  // namespace
@@ -747,7 +863,7 @@ void radix_pass(dim3 grid, const T* z, int64_t ldz, const T* w, const U* kin, co
 
 template <class T, class U, bool BUCKETED>
 void sort_passes(const T* z, int P, int64_t n, int64_t ldz, const T* w, KW<T>* pairs, unsigned char* s, int passes,
-                 const Buckets& bk, cudaStream_t st) {
+                 int dbits, const Buckets& bk, cudaStream_t st) {
     const int tiles = static_cast<int>(ceil_div(n, RS_TILE));
     const size_t total = static_cast<size_t>(P) * n;
     U* k0 = reinterpret_cast<U*>(s);
@@ -760,7 +876,7 @@ void sort_passes(const T* z, int P, int64_t n, int64_t ldz, const T* w, KW<T>* p
     const U* kin = nullptr;
     const T* vin = nullptr;
     for (int pass = 0; pass < passes; ++pass) {
-        const int shift = 8 * pass;
+        const int shift = dbits * pass;
         U* kout = (pass & 1) ? k1 : k0;
         T* vout = (pass & 1) ? v1 : v0;
         const bool first = pass == 0, last = pass == passes - 1;
@@ -815,9 +931,12 @@ void launch_sort_pairs(const T* z, int P, int64_t n, int64_t ldz, const T* w, vo
         int bits = 0;
         while ((1 << bits) < NB) ++bits;
         const int passes = bits > 8 ? (bits + 7) / 8 : 1;
-        sort_passes<T, U, true>(z, P, n, ldz, w, pairs, s, passes, Buckets{kmin, kscale, NB}, st);
+        const int dbits = 8;
+        sort_passes<T, U, true>(z, P, n, ldz, w, pairs, s, passes, dbits, Buckets{kmin, kscale, NB, (1 << dbits) - 1},
+                                st);
     } else {
-        sort_passes<T, U, false>(z, P, n, ldz, w, pairs, s, KeyOf<T>::passes, Buckets{nullptr, nullptr, 0}, st);
+        sort_passes<T, U, false>(z, P, n, ldz, w, pairs, s, KeyOf<T>::passes, 8, Buckets{nullptr, nullptr, 0, 0xff},
+                                 st);
     }
 }
 
@@ -833,13 +952,14 @@ void launch_slice_minmax(const T* Z, int P, int64_t n, int64_t ldz, int NB, floa
 
 template <class T>
 int64_t sorted_pairs_bytes(int P, int64_t n) {
-    return static_cast<int64_t>(sizeof(KW<T>)) * P * n;
+    return static_cast<int64_t>(sizeof(KW<T>)) * P * n + kPairPadBytes;
 }
 
 template <class T>
 void launch_bucket_tables(int P, int64_t n, const void* kw, int NB, float* kmin, float* kscale, void* rec,
                           bool have_geometry, cudaStream_t st) {
     const KW<T>* pairs = static_cast<const KW<T>*>(kw);
+    SLK_REQUIRE(reinterpret_cast<uintptr_t>(rec) % 32 == 0, "bucket records must be 32-byte aligned");
     if (!have_geometry) {
         // fully sorted pairs: the bucket geometry from the first and last key of each slice
         {
@@ -872,19 +992,34 @@ void launch_bucket_tables(int P, int64_t n, const void* kw, int NB, float* kmin,
 template <class T>
 void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const void* kw, int64_t nx, const void* rec,
                            int NB, const float* kmin, const float* kscale, double cd, double scale, double* acc, T* G,
-                           int accumulate_G, cudaStream_t st) {
-    if (n <= 0) return;
+                           int64_t ldg, int accumulate_G, cudaStream_t st) {
+    if (n <= 0 || (!acc && !G)) return;
+    SLK_REQUIRE(!G || ldg >= n, "derivative rows shorter than the targets");
     // slices per launch: keep one batch's pairs (the randomly accessed state) within ~64 MB of L2
     const int64_t per_slice = static_cast<int64_t>(sizeof(KW<T>)) * nx + static_cast<int64_t>(NB + 1) * kBucketRecordBytes;
     int batch = static_cast<int>((int64_t(64) << 20) / (per_slice > 0 ? per_slice : 1));
     if (batch < 1) batch = 1;
     if (batch > P) batch = P;
+    const unsigned blocks = static_cast<unsigned>(ceil_div(n, 256));
+    const KW<T>* pairs = static_cast<const KW<T>*>(kw);
+    const BucketRec<T>* recs = static_cast<const BucketRec<T>*>(rec);
+    // FP32: records and four-pair chunks are read as aligned 32-byte sectors (the pair array
+    // carries kPairPadBytes of padding for the last chunk)
+    SLK_REQUIRE(reinterpret_cast<uintptr_t>(kw) % 32 == 0 && reinterpret_cast<uintptr_t>(rec) % 32 == 0,
+                "sorted pairs and bucket records must be 32-byte aligned");
+    const T c = static_cast<T>(cd), sc = static_cast<T>(scale);
     for (int p0 = 0; p0 < P; p0 += batch) {
         const int p1 = p0 + batch < P ? p0 + batch : P;
-        SLK_TIMED(G ? "negdist_target_grad" : "negdist_target", st);
-        k_negdist_target<T><<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, st>>>(
-            Z, P, p0, p1, n, ldz, static_cast<const KW<T>*>(kw), nx, static_cast<const BucketRec<T>*>(rec), NB, kmin,
-            kscale, static_cast<T>(cd), static_cast<T>(scale), acc, G, accumulate_G);
+        SLK_TIMED(acc && G ? "negdist_target_both" : (G ? "negdist_target_grad" : "negdist_target"), st);
+        if (acc && G)
+            k_negdist_target<T, true, true><<<blocks, 256, 0, st>>>(Z, P, p0, p1, n, ldz, pairs, nx, recs, NB, kmin,
+                                                                    kscale, c, sc, acc, G, ldg, accumulate_G);
+        else if (G)
+            k_negdist_target<T, false, true><<<blocks, 256, 0, st>>>(Z, P, p0, p1, n, ldz, pairs, nx, recs, NB, kmin,
+                                                                     kscale, c, sc, acc, G, ldg, accumulate_G);
+        else
+            k_negdist_target<T, true, false><<<blocks, 256, 0, st>>>(Z, P, p0, p1, n, ldz, pairs, nx, recs, NB, kmin,
+                                                                     kscale, c, sc, acc, G, ldg, accumulate_G);
         SLK_CHECK_LAUNCH();
     }
 }
@@ -897,7 +1032,7 @@ void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const void
     template int64_t sorted_pairs_bytes<T>(int, int64_t);                                                             \
     template void launch_bucket_tables<T>(int, int64_t, const void*, int, float*, float*, void*, bool, cudaStream_t); \
     template void launch_negdist_target<T>(const T*, int, int64_t, int64_t, const void*, int64_t, const void*, int,   \
-                                           const float*, const float*, double, double, double*, T*, int,             \
+                                           const float*, const float*, double, double, double*, T*, int64_t, int,    \
                                            cudaStream_t);
 SLK_INST(float)
 SLK_INST(double)

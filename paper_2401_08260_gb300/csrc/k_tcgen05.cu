@@ -863,6 +863,29 @@ __global__ void k_transpose_cast(const float* __restrict__ src, int rows, int co
     }
 }
 
+// g16[m][p] = BF16(G[p * ldG + m]) through a 32 x 32 shared tile (reads coalesced along m,
+// writes along p), zero for P <= p < ldo
+__global__ void __launch_bounds__(256) k_derivs_bf16(const float* __restrict__ G, int P, int64_t M, int64_t ldG,
+                                                     __nv_bfloat16* __restrict__ g16, int ldo) {
+    __shared__ float tile[32][33];
+    const int64_t m0 = static_cast<int64_t>(blockIdx.x) * 32;
+    const int p0 = static_cast<int>(blockIdx.y) * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < 32; j += 8) {
+        const int p = p0 + ty + j;
+        const int64_t m = m0 + tx;
+        tile[ty + j][tx] = (p < P && m < M) ? G[static_cast<int64_t>(p) * ldG + m] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 32; j += 8) {
+        const int64_t m = m0 + ty + j;
+        const int p = p0 + tx;
+        if (m < M && p < ldo) g16[m * ldo + p] = __float2bfloat16_rn(tile[tx][ty + j]);
+    }
+}
+
 }  // namespace
 
 int64_t umma_operand_ld(int d) { return (d + 7) / 8 * 8; }
@@ -881,6 +904,18 @@ void launch_transpose_bf16(const float* src, int rows, int cols, void* dst, cuda
     SLK_TIMED("transpose_cast", st);
     k_transpose_cast<__nv_bfloat16><<<static_cast<unsigned>(ceil_div(total, 256) < 4096 ? ceil_div(total, 256) : 4096),
                                       256, 0, st>>>(src, rows, cols, static_cast<__nv_bfloat16*>(dst), ldd);
+    SLK_CHECK_LAUNCH();
+}
+
+void launch_derivs_bf16(const float* G, int P, int64_t M, int64_t ldG, void* g16, cudaStream_t st) {
+    if (M <= 0) return;
+    const int ldo = static_cast<int>(umma_operand_ld(P));
+    dim3 grid(static_cast<unsigned>(ceil_div(M, 32)), static_cast<unsigned>(ceil_div(ldo, 32)));
+    SLK_REQUIRE(grid.y <= 65535 && ceil_div(M, 32) <= 2147483647, "derivative matrix too large for one cast");
+    {
+        SLK_TIMED("derivs_bf16", st);
+        k_derivs_bf16<<<grid, 256, 0, st>>>(G, P, M, ldG, static_cast<__nv_bfloat16*>(g16), ldo);
+    }
     SLK_CHECK_LAUNCH();
 }
 

@@ -32,9 +32,10 @@ void launch_finalize(const double* acc, T* s, int64_t n, double scale, cudaStrea
 template <class T>
 void launch_project_simt(const T* xi, int P, const T* x, int64_t n, int d, int64_t ldx, const T* mu, T* Z,
                          int64_t ldz, cudaStream_t st);
-// gy[i][k] = scale * gs[i] * sum_p G[i][p] xi[p][k]   (gs may be NULL = ones).
+// gy[i][k] = scale * gs[i] * sum_p G[p * ldG + i] xi[p][k]   (gs may be NULL = ones;
+// G slice-major, P rows of M derivatives).
 template <class T>
-void launch_grad_gemm(const T* G, int64_t M, int P, const T* xi, int d, const T* gs, double scale, T* gy,
+void launch_grad_gemm(const T* G, int64_t ldG, int64_t M, int P, const T* xi, int d, const T* gs, double scale, T* gy,
                       int64_t ldg, cudaStream_t st);
 
 // ------------------------------------------------------------ k_tcgen05.cu
@@ -122,12 +123,30 @@ template <class T>
 void launch_accumulate_scaled(double* acc, const T* t, double a, int64_t n, bool first, cudaStream_t st);
 // dst[c][r] = BF16(src[r][c]) (rows x cols FP32 in; cols x ld16(rows) out, zero padded).
 void launch_transpose_bf16(const float* src, int rows, int cols, void* dst, cudaStream_t st);
+// The backward product's A operand: g16[m][p] = BF16(G[p * ldG + m]) for the slice-major
+// derivatives G (P rows of M), M rows of pitch ld16(P) out, zero padded; tiled through
+// shared memory so that both sides are coalesced.
+void launch_derivs_bf16(const float* G, int P, int64_t M, int64_t ldG, void* g16, cudaStream_t st);
 // Backward product on tensor cores: gy[m][k] = scale * gs[m] * sum_p G[m][p] xi[p][k] with G (M x P)
 // and xi^T (d x P) in BF16 (row pitch ld16(P)); gs may be NULL (ones).
 void launch_grad_umma(const void* g16, int64_t M, int P, const void* xit16, int d, const float* gs, double scale,
                       float* gy, int64_t ldg, unsigned* err, cudaStream_t st);
 
 // ------------------------------------------------------------ k_fourier.cu
+// The NFFT window's taps as polynomials (FP32 plans): a point whose first window cell lies at
+// offset s0 = g + 1/2 - m/2 cells (g in [-1/2, 1/2)) gives tap t < m the weight psi(s0 + t),
+// a degree-8 polynomial P_t(g).  psi is even, so P_{m-1-t}(g) = P_t(-g): with h = g^2,
+// P_t = E_t(h) + g O_t(h) and P_{m-1-t} = E_t(h) - g O_t(h), and likewise for the derivatives
+// P_t' = D_t(h) + g Q_t(h), P_{m-1-t}' = g Q_t(h) - D_t(h); stored for t < ceil(m / 2).
+// Passed to the kernels by value (uniform operands of their multiply-adds).
+constexpr int kWinPolyHalf = (kWinPolyMaxM + 1) / 2;
+struct WinPoly {
+    float ev[kWinPolyHalf][5];  // E_t: coefficients of h^0 .. h^4
+    float od[kWinPolyHalf][4];  // O_t: h^0 .. h^3
+    float de[kWinPolyHalf][4];  // D_t: h^0 .. h^3
+    float dq[kWinPolyHalf][4];  // Q_t: h^0 .. h^3
+};
+
 struct FourierDev {
     // geometry of the periodic 1-D problem (Section 3.1 with the rescaling of
     // the paragraph "Rescaling"): x~ = z / L, period 1 in x~
@@ -145,6 +164,8 @@ struct FourierDev {
     int q;
     int horner;
     const void* mono;
+    // NFFT window taps as polynomials (used by the FP32 kernels)
+    WinPoly wp;
 };
 
 // Chebyshev evaluation of the truncated Fourier sum (Jacobi-Anger expansion on [-R, R]):
@@ -167,34 +188,38 @@ void launch_cheb_reduce_f64(const double* partial, int nchunk, int P, const Four
                             float* beta, float* mono, unsigned* mono_bad, double mono_ratio, cudaStream_t st);
 template <class T>
 void launch_cheb_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const T* beta, double* acc,
-                        T* G, unsigned* err, cudaStream_t st);
+                        T* G, int64_t ldg, unsigned* err, cudaStream_t st);
 
 // NDFT, source side: cw[p][j] = c_{k_lo+j} * sum_n w_n exp(-2 pi i k z_{p,n} / L),
 // j = 0..K-1 (and cw0[p] = c_0 sum_n w_n if has_k0).  coef holds c_k (FP64).
 template <class T>
 void launch_ndft_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, const FourierDev& fd,
                         const double* coef, Cplx<T>* cw, T* cw0, T* scratch, int64_t scratch_elems, cudaStream_t st);
-// NDFT, target side: acc[m] += sum_p t_p(z_{p,m});  with G != NULL writes
-// G[m][p] = dt_p/dz instead (for the gradient).  Targets outside [-R, R] set
-// bit 4 of *err.
+// NDFT, target side: with acc != NULL, acc[m] += sum_p t_p(z_{p,m}); with G != NULL,
+// G[p * ldg + m] = dt_p/dz (the per-slice derivatives of the gradient, slice-major); either
+// or both.  Targets outside [-R, R] set bit 4 of *err.  The other target launchers
+// (Chebyshev, NFFT) take acc and G the same way.
 template <class T>
 void launch_ndft_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const Cplx<T>* cw,
-                        const T* cw0, double* acc, T* G, unsigned* err, cudaStream_t st);
+                        const T* cw0, double* acc, T* G, int64_t ldg, unsigned* err, cudaStream_t st);
 // NFFT, source side: spread w onto the grid window of every slice (partial
 // sums per point chunk, then a fixed-order reduction), FFT, multiply by
-// mult[k] = c_k / Psi(k/n_g)^2 for |k| < n_coeff/2, inverse FFT; h is P x W.
+// mult[k] = c_k / Psi(k/n_g)^2 for |k| < n_coeff/2, inverse FFT; h is P x W.  With
+// pairs != NULL the sources are read from the sorting route's (key, w) pairs instead of
+// (Z, w): P x n pairs grouped by key bucket (launch_sort_pairs), which the spreading
+// exploits to add most window taps in registers.
 template <class T>
-void launch_nfft_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, const FourierDev& fd, int n_coeff,
-                        const double* mult, T* h, T* scratch, int64_t scratch_elems, unsigned* err, cudaStream_t st);
+void launch_nfft_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, const T* pairs, const FourierDev& fd,
+                        int n_coeff, const double* mult, T* h, T* scratch, int64_t scratch_elems, unsigned* err,
+                        cudaStream_t st);
 // Scratch elements launch_nfft_source needs.
 int64_t nfft_source_scratch(int P, int64_t n, const FourierDev& fd);
 int64_t ndft_source_scratch(int P, int64_t n, const FourierDev& fd);
-// NFFT, target side: acc[m] += sum_p sum_j h[p][j] psi(n_g z/L - j); with
-// G != NULL writes the derivative dt_p/dz into G[m][p] instead.  Targets
-// outside [-R, R] set bit 4 of *err.
+// NFFT, target side: acc[m] += sum_p sum_j h[p][j] psi(n_g z/L - j) and / or the
+// derivative dt_p/dz into G[p * ldg + m].  Targets outside [-R, R] set bit 4 of *err.
 template <class T>
 void launch_nfft_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const T* h, double* acc,
-                        T* G, unsigned* err, cudaStream_t st);
+                        T* G, int64_t ldg, unsigned* err, cudaStream_t st);
 
 // ------------------------------------------------------------ k_sort.cu
 // Per slice p < P, the n sources ordered by their projection z[p * ldz + i] into (key, w)
@@ -213,7 +238,9 @@ void launch_slice_minmax(const T* Z, int P, int64_t n, int64_t ldz, int NB, floa
                          cudaStream_t st);
 template <class T>
 size_t sort_pairs_scratch(int P, int64_t n);
-// Bytes of the sorted (key, w) pairs of P segments of n sources.
+// Bytes of the sorted (key, w) pairs of P segments of n sources, plus kPairPadBytes after
+// them (the target lookups read FP32 pairs in aligned 32-byte chunks of four).
+constexpr int64_t kPairPadBytes = 32;
 template <class T>
 int64_t sorted_pairs_bytes(int P, int64_t n);
 // From pairs grouped by bucket: one 32-byte record per bucket b <= NB, rec[p][b]: the
@@ -227,13 +254,14 @@ template <class T>
 void launch_bucket_tables(int P, int64_t n, const void* kw, int NB, float* kmin, float* kscale, void* rec,
                           bool have_geometry, cudaStream_t st);
 // Negative-distance 1-D sums at the targets (Section 3.2 in the range-free
-// form t = -c_d [z (2 A_< - W) - (2 B_< - S)]) summed over slices into acc[m],
-// times `scale`; with G != NULL writes g = scale c_d (W - A_< - A_<=) into
-// G[m][p] instead (the derivative, sign(0) = 0).  Slices are processed in
-// batches whose sorted pairs fit in L2.
+// form t = -c_d [z (2 A_< - W) - (2 B_< - S)]): with acc != NULL summed over slices into
+// acc[m], times `scale`; with G != NULL the derivative g = scale c_d (W - A_< - A_<=)
+// (sign(0) = 0) written to G[p * ldg + m] (added to it if accumulate_G); both from one
+// lookup per slice-point when both are given.  Slices are processed in batches whose
+// pairs and bucket records fit in L2.
 template <class T>
 void launch_negdist_target(const T* Z, int P, int64_t n, int64_t ldz, const void* kw, int64_t nx, const void* rec,
                            int NB, const float* kmin, const float* kscale, double cd, double scale, double* acc, T* G,
-                           int accumulate_G, cudaStream_t st);
+                           int64_t ldg, int accumulate_G, cudaStream_t st);
 
 }  // namespace slk

@@ -154,6 +154,60 @@ double window_error(int m, double beta, int n_g, int kmax) {
     return 2.0 * worst + 2.0 * m * std::exp(-beta);
 }
 
+// psi(s) in FP64, in the cancellation-free form exp(-beta x^2 / (1 + sqrt(1 - x^2)))
+double es_psi_host(double s, int m, double beta) {
+    const double x = 2.0 * s / m, q = 1.0 - x * x;
+    return q >= 0.0 ? std::exp(-beta * x * x / (1.0 + std::sqrt(q))) : 0.0;
+}
+
+// The window's taps as polynomials for the FP32 kernels: a point whose first cell lies at
+// s0 = g + 1/2 - m/2 (g in [-1/2, 1/2)) weights cell t < m by psi(s0 + t); per tap, the
+// degree-kWinPolyDeg interpolant at the (symmetric) Chebyshev points of g, written in powers of g
+// (a Vandermonde solve in FP64 by Gaussian elimination with partial pivoting; on this
+// interval the coefficients stay below about one).  Its largest error on a 2001-point grid
+// goes to wpoly_err: about 2e-9 for m >= 9 and below exp(-beta) otherwise (the square-root
+// branch point of psi at the window's edge, where psi = exp(-beta), limits it).
+void fit_window_poly(FourierHost* fp) {
+    constexpr int D = kWinPolyDeg, n = kWinPolyDeg + 1;
+    const int m = fp->m;
+    fp->wpoly.assign(static_cast<size_t>(m) * n, 0.0);
+    double worst = 0.0;
+    for (int t = 0; t < m; ++t) {
+        double A[n][n + 1];
+        for (int j = 0; j < n; ++j) {
+            const double g = 0.5 * std::cos(PI * (j + 0.5) / n);
+            double pw = 1.0;
+            for (int k = 0; k < n; ++k, pw *= g) A[j][k] = pw;
+            A[j][n] = es_psi_host(g + 0.5 + t - 0.5 * m, m, fp->beta);
+        }
+        for (int c = 0; c < n; ++c) {
+            int piv = c;
+            for (int r = c + 1; r < n; ++r)
+                if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+            for (int k = 0; k <= n; ++k) std::swap(A[c][k], A[piv][k]);
+            for (int r = 0; r < n; ++r) {
+                if (r == c) continue;
+                const double f = A[r][c] / A[c][c];
+                for (int k = c; k <= n; ++k) A[r][k] -= f * A[c][k];
+            }
+        }
+        double* a = fp->wpoly.data() + static_cast<size_t>(t) * n;
+        for (int k = 0; k < n; ++k) a[k] = A[k][n] / A[k][k];
+    }
+    // the kernels evaluate tap t >= ceil(m / 2) as P_{m-1-t}(-g) (psi is even): measure that
+    for (int t = 0; t < m; ++t) {
+        const bool mirror = t >= (m + 1) / 2;
+        const double* a = fp->wpoly.data() + static_cast<size_t>(mirror ? m - 1 - t : t) * n;
+        for (int i = 0; i <= 2000; ++i) {
+            const double g = -0.5 + i / 2000.0, x = mirror ? -g : g;
+            double v = a[D];
+            for (int k = D - 1; k >= 0; --k) v = v * x + a[k];
+            worst = std::max(worst, std::fabs(v - es_psi_host(g + 0.5 + t - 0.5 * m, m, fp->beta)));
+        }
+    }
+    fp->wpoly_err = worst;
+}
+
 void choose_window(FourierHost* fp, double tol_w) {
     const int kmax = fp->n_coeff / 2;
     for (int m = 4; m <= 16; ++m) {
@@ -168,7 +222,9 @@ void choose_window(FourierHost* fp, double tol_w) {
     }
     fp->psi.resize(kmax);
     for (int k = 0; k < kmax; ++k) fp->psi[k] = es_Psi(static_cast<double>(k) / fp->n_g, fp->m, fp->beta);
+    fit_window_poly(fp);
 }
+
 
 void set_active_window(FourierHost* fp) {
     double umax = fp->R * fp->n_g / fp->L;
@@ -390,6 +446,15 @@ std::mutex cache_mu;
 std::map<std::tuple<int, double, int, double, double, int, int>, FourierHost> cache;
 
 }  // namespace
+
+void add_window_poly_error(FourierHost* fp) {
+    if (fp->method != SLK_FOURIER_NFFT) return;
+    // the polynomial taps' error enters spreading and interpolation once each, over the m
+    // cells of a window
+    const double e = 2.0 * fp->m * fp->wpoly_err;
+    fp->window_err += e;
+    fp->model_err += e;
+}
 
 double cd_host(int d) { return std::sqrt(PI) * std::exp(std::lgamma(0.5 * (d + 1)) - std::lgamma(0.5 * d)); }
 

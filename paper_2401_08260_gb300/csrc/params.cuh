@@ -17,6 +17,10 @@ struct FourierHost {
     std::vector<double> coef;  // NDFT: c_{k_lo..k_hi}, then c_0; Laplacian: c_0..c_{N_c/2-1}
     int n_g = 0, m = 0, W = 0, win_base = 0;
     double beta = 0.0;
+    // the window's m taps as degree-kWinPolyDeg polynomials in g in [-1/2, 1/2) (see
+    // fit_window_poly): wpoly[t * (kWinPolyDeg + 1) + k], and their largest error
+    std::vector<double> wpoly;
+    double wpoly_err = 0.0;
     std::vector<double> psi;   // Psi(k / n_g), k < N_c / 2
     std::vector<double> mult;  // c_k / Psi(k / n_g)^2, k < N_c / 2
     // Chebyshev evaluation (Jacobi-Anger): q terms, certified error; the device works with
@@ -29,6 +33,10 @@ struct FourierHost {
 };
 
 double cd_host(int d);
+// The FP32 kernels evaluate the NFFT window's taps as polynomials: add their fitted error
+// (wpoly_err, over spreading and interpolation) to the certified window and model errors of
+// an NFFT choice.  FP64 plans evaluate the window itself and skip this.
+void add_window_poly_error(FourierHost* fp);
 FourierHost choose_gaussian(double sigma, int d, double R, int n_coeff_req, int method, double tol);
 // max_nc: largest N_c whose grid (2 N_c complex values) fits one block's shared memory
 // Fourier coefficients of a Laplacian-type counterpart on the window: the Laplacian's

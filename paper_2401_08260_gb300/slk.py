@@ -77,6 +77,10 @@ _SIGNATURES = {
                                ctypes.c_void_p]),
     "slk_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
                                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "slk_sum_derivs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "slk_grad_derivs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "slk_plan_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "slk_plan_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
@@ -151,6 +155,7 @@ class _Arr:
             self.keep = a
             self.ptr = a.data_ptr()
             self.rows = a.shape[0]
+            self.cols = a.shape[1] if ndim == 2 else 1
         else:
             a = np.asarray(a)
             if a.dtype != dtype:
@@ -160,6 +165,7 @@ class _Arr:
             self.ptr = a.ctypes.data
             self.ld = a.shape[1] if ndim == 2 else 1
             self.rows = a.shape[0]
+            self.cols = a.shape[1] if ndim == 2 else 1
 
 
 def _plan_desc(kernel: str, param: float, d: int, P: int, precision: str, n_coeff: int = 0, method: str = "auto",
@@ -251,6 +257,44 @@ class Plan:
                 out = np.empty((ya.rows, self.d), dtype=self.dtype)
         oa = _Arr(out, self.dtype, 2)
         _check(lib.slk_grad(self._h, ya.ptr, ya.rows, ya.ld, ga.ptr if ga else None, oa.ptr, oa.ld, _stream_of(y)))
+        if sync:
+            _check(lib.slk_plan_sync(self._h))
+        return out
+
+    def sum_derivs(self, y, out=None, g=None, sync: bool = True):
+        """(s, g): the sums at the rows of y and the per-slice derivatives g (P x M,
+        g[p, m] = t_p'(<xi_p, y_m - mu>)) from one projection and one evaluation.  out and g
+        may be given (device or host, independently of y)."""
+        lib = load()
+        ya = _Arr(y, self.dtype, 2)
+        on_dev = torch is not None and isinstance(y, torch.Tensor)
+        if out is None:
+            out = torch.empty(ya.rows, dtype=ya.keep.dtype, device=ya.keep.device) if on_dev else \
+                np.empty(ya.rows, dtype=self.dtype)
+        if g is None:
+            g = torch.empty(self.P, ya.rows, dtype=ya.keep.dtype, device=ya.keep.device) if on_dev else \
+                np.empty((self.P, ya.rows), dtype=self.dtype)
+        s = out
+        sa, gd = _Arr(s, self.dtype, 1), _Arr(g, self.dtype, 2)
+        _check(lib.slk_sum_derivs(self._h, ya.ptr, ya.rows, ya.ld, sa.ptr, gd.ptr, gd.ld, _stream_of(y)))
+        if sync:
+            _check(lib.slk_plan_sync(self._h))
+        return s, g
+
+    def grad_derivs(self, g, gs=None, out=None, sync: bool = True):
+        """Gradient of sum_m gs_m s_m with respect to y from the derivatives g (P x M) that
+        sum_derivs returned: gy_m = gs_m (1/P) sum_p g[p, m] xi_p."""
+        lib = load()
+        gd = _Arr(g, self.dtype, 2)
+        M = gd.cols
+        ga = _Arr(gs, self.dtype, 1) if gs is not None else None
+        if out is None:
+            if torch is not None and isinstance(g, torch.Tensor):
+                out = torch.empty(M, self.d, dtype=gd.keep.dtype, device=gd.keep.device)
+            else:
+                out = np.empty((M, self.d), dtype=self.dtype)
+        oa = _Arr(out, self.dtype, 2)
+        _check(lib.slk_grad_derivs(self._h, gd.ptr, M, gd.ld, ga.ptr if ga else None, oa.ptr, oa.ld, _stream_of(g)))
         if sync:
             _check(lib.slk_plan_sync(self._h))
         return out
@@ -408,19 +452,24 @@ def rff_features(kernel: str, param: float, d: int, D: int, seed: int = 0) -> np
 if torch is not None:
 
     class SlicedKernelSum(torch.autograd.Function):
-        """s = sliced kernel sum at targets y; backward gives the y-gradient from the
-        library's derivative sums (sign(0) = 0) and the backward product."""
+        """s = sliced kernel sum at targets y; the forward pass also keeps the per-slice
+        derivatives (sign(0) = 0), from which backward forms the y-gradient by the backward
+        product alone."""
 
         @staticmethod
         def forward(ctx, y, plan: Plan):
             ctx.plan = plan
-            ctx.save_for_backward(y)
-            return plan.sum(y.detach())
+            if not y.requires_grad:
+                return plan.sum(y.detach())
+            # the per-slice derivatives come from the same pass and are kept for backward
+            s, g = plan.sum_derivs(y.detach())
+            ctx.save_for_backward(g)
+            return s
 
         @staticmethod
         def backward(ctx, grad_s):
-            (y,) = ctx.saved_tensors
-            gy = ctx.plan.grad(y.detach(), gs=grad_s.contiguous().to(y.dtype))
+            (g,) = ctx.saved_tensors
+            gy = ctx.plan.grad_derivs(g, gs=grad_s.contiguous().to(g.dtype))
             return gy, None
 
     def sliced_kernel_sum(y, plan: Plan):

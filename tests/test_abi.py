@@ -90,6 +90,8 @@ def test_invalid_descriptors_are_rejected_without_a_device(lib):
     # NULL plan handles
     assert lib.slk_sum(None, buf, 1, 4, buf, None) == 1
     assert lib.slk_grad(None, buf, 1, 4, None, buf, 4, None) == 1
+    assert lib.slk_sum_derivs(None, buf, 1, 4, buf, buf, 1, None) == 1
+    assert lib.slk_grad_derivs(None, buf, 1, 1, None, buf, 4, None) == 1
     assert lib.slk_plan_sync(None) == 1
     assert lib.slk_plan_destroy(None) == 0
 
