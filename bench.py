@@ -189,12 +189,12 @@ def algorithmic(wl, info, precision, kernel_name, launches_per_step, kernels, P=
         t_hbm = nbytes / (pk.get("hbm_gbs", 6689.8) * 1e9)
         t_tc = flops / (pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1772.1)) * 1e12)
         return (nbytes, "byte", "hbm") if t_hbm >= t_tc else (flops, "flop", "tensor")
-    if kernel_name.startswith("umma_project"):
+    if kernel_name.startswith(("umma_project", "pair_project")):
         # 16-bit rows in (hi and lo parts for the FP16x3 split), FP32 projections out; the
         # bound with the longer minimum time (d = 50 is HBM-bound, d >= 784 tensor-bound)
         flops = 2.0 * pts * wl.d * P
         ld16 = (wl.d + 7) // 8 * 8
-        nbytes = pts * (2.0 * ld16 * (2 if kernel_name.startswith("umma_project_x3") else 1) + 4.0 * P)
+        nbytes = pts * (2.0 * ld16 * (2 if kernel_name.endswith("project_x3") else 1) + 4.0 * P)
         pk = peaks or {}
         t_hbm = nbytes / (pk.get("hbm_gbs", 6689.8) * 1e9)
         t_tc = flops / (pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1772.1)) * 1e12)
@@ -431,12 +431,10 @@ def run_ours(args):
     job_world = 1 if sharded else world
     value = job_rate((wl.N + wl.M) * wl.P, job_world, ms)
 
-    # ---------------- dominant kernel roofline
+    # ---------------- roofline of every timed kernel, the dominant one on the line itself
     peaks, peak_kind = _peaks()
-    top = max(kernels.items(), key=lambda kv: kv[1][1]) if kernels else None
-    roofline = None
-    if top:
-        name, (n_launch, tot_ms) = top
+
+    def kernel_roofline(name, n_launch, tot_ms):
         per_step = n_launch / args.steps
         amount, unit, bound = algorithmic(wl, info, precision, name, per_step, kernels, P=P_local, grad=args.grad,
                                           peaks=peaks)
@@ -455,11 +453,20 @@ def run_ours(args):
             peak = peaks["hbm_gbs"]
             achieved = amount / avg_s / 1e9
             runit = "GB/s"
-        roofline = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": runit,
-                    "frac": achieved / peak, "traffic": measured_traffic(wl, name, per_step, kernels),
-                    "peak_source": peak_kind,
-                    "launch_ms": tot_ms / n_launch,
-                    "share": tot_ms / sum(v[1] for v in kernels.values())}
+        return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": runit,
+                "frac": achieved / peak, "traffic": measured_traffic(wl, name, per_step, kernels),
+                "peak_source": peak_kind, "launch_ms": tot_ms / n_launch,
+                "share": tot_ms / sum(v[1] for v in kernels.values())}
+
+    top = max(kernels.items(), key=lambda kv: kv[1][1]) if kernels else None
+    roofline = kernel_roofline(top[0], *top[1]) if top else None
+    # per kernel: ms per step, the fraction of its bound's peak, and that bound
+    kernel_fracs = {}
+    for kname, (n_launch, tot_ms) in sorted(kernels.items(), key=lambda kv: -kv[1][1]):
+        if n_launch <= 0 or tot_ms <= 0.0:
+            continue
+        r = kernel_roofline(kname, n_launch, tot_ms)
+        kernel_fracs[kname] = {"ms_per_step": tot_ms / args.steps, "bound": r["bound"], "frac": r["frac"]}
 
     # ---------------- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -524,11 +531,14 @@ def run_ours(args):
                            "P": wl.P, "n_coeff": info["n_coeff"], "method": {1: "nfft", 2: "ndft", 3: "cheb"}.get(info["method"]),
                            "parallelism": (f"slices{world}" if sharded else f"replicas{world}") if world > 1
                            else "single",
-                           "l2": "inputs larger than L2 (no flush needed)",
+                           "l2": ("inputs larger than L2 (no flush needed)"
+                                  if (wl.x.nbytes + wl.y.nbytes + wl.w.nbytes) > 2 * 129e6
+                                  else "inputs smaller than L2, not flushed between steps (warm cache)"),
                            "model_error": info["model_error"], "backward": bool(args.grad)},
                 "roofline": roofline, "cpu_baseline": cpu, "errors": errors, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches,
-                "kernels_ms_per_step": {k: v[1] / args.steps for k, v in kernels.items()}}
+                "kernels_ms_per_step": {k: v[1] / args.steps for k, v in kernels.items()},
+                "kernel_rooflines": kernel_fracs}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

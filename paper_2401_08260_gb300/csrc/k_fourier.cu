@@ -81,6 +81,51 @@ __device__ __forceinline__ void window_taps(const WinPoly& wp, float s0, float, 
         if (MM - 1 - t != t) wt[MM - 1 - t] = DERIV ? go - e : e - go;
     }
 }
+// One tap at a time by Horner's rule on the same polynomials (tap t >= ceil(MM / 2) as the
+// mirrored tap at -g): more multiply-adds than window_taps, but each tap's chain interleaves
+// with the use of its weight (the interpolation reads a grid value per tap).
+template <int MM, bool DERIV>
+__device__ __forceinline__ float window_tap(const WinPoly& wp, int t, float g) {
+    const bool mirror = t >= (MM + 1) / 2;
+    const int u = mirror ? MM - 1 - t : t;
+    const float x = mirror ? -g : g;
+    float v;
+    if (DERIV) {
+        v = wp.dq[u][3];
+        v = fmaf(v, x, wp.de[u][3]);
+        v = fmaf(v, x, wp.dq[u][2]);
+        v = fmaf(v, x, wp.de[u][2]);
+        v = fmaf(v, x, wp.dq[u][1]);
+        v = fmaf(v, x, wp.de[u][1]);
+        v = fmaf(v, x, wp.dq[u][0]);
+        v = fmaf(v, x, wp.de[u][0]);
+        return mirror ? -v : v;
+    }
+    v = wp.ev[u][4];
+    v = fmaf(v, x, wp.od[u][3]);
+    v = fmaf(v, x, wp.ev[u][3]);
+    v = fmaf(v, x, wp.od[u][2]);
+    v = fmaf(v, x, wp.ev[u][2]);
+    v = fmaf(v, x, wp.od[u][1]);
+    v = fmaf(v, x, wp.ev[u][1]);
+    v = fmaf(v, x, wp.od[u][0]);
+    return fmaf(v, x, wp.ev[u][0]);
+}
+template <int MM, bool DERIV>
+__device__ __forceinline__ double window_tap(const WinPoly&, int t, double s0, double two_over_m, double beta) {
+    return DERIV ? es_window_deriv(s0 + double(t), two_over_m, beta) : es_window(s0 + double(t), two_over_m, beta);
+}
+
+// tap t's weight (or derivative) for a point whose first window cell lies at s0
+template <int MM, bool DERIV>
+__device__ __forceinline__ float tap_value(const WinPoly& wp, int t, float s0, float, float) {
+    return window_tap<MM, DERIV>(wp, t, s0 + 0.5f * static_cast<float>(MM - 1));
+}
+template <int MM, bool DERIV>
+__device__ __forceinline__ double tap_value(const WinPoly& wp, int t, double s0, double two_over_m, double beta) {
+    return window_tap<MM, DERIV>(wp, t, s0, two_over_m, beta);
+}
+
 template <int MM, bool DERIV>
 __device__ __forceinline__ void window_taps(const WinPoly&, double s0, double two_over_m, double beta,
                                             double (&wt)[MM]) {
@@ -757,7 +802,7 @@ __global__ void __launch_bounds__(512) k_fft_multiply(const T* __restrict__ g, i
 // ------------------------------------------------------------ NFFT interpolation
 
 template <class T, int MMAX>
-__global__ void __launch_bounds__(256) k_nfft_target(const T* __restrict__ Z, int P, int64_t n, int64_t ldz, T scale_u,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_nfft_target(const T* __restrict__ Z, int P, int64_t n, int64_t ldz, T scale_u,
                                                      int m, T two_over_m, T beta, const WinPoly wp, int W, int win_base,
                                                      const T* __restrict__ h, int slice_chunk, T R,
                                                      double* __restrict__ acc, T* __restrict__ G, int64_t ldg,
@@ -795,19 +840,18 @@ __global__ void __launch_bounds__(256) k_nfft_target(const T* __restrict__ Z, in
                 continue;
             }
             const T* row = sh + static_cast<size_t>(q) * W + r0;
-            T t = T(0), wt[MMAX];
+            const T s0 = c0 - u;
+            T t = T(0);
             if (G) {
                 // d/du sum_j h_j psi(u - j) = -sum_j h_j psi'(j - u)
-                window_taps<MMAX, true>(wp, c0 - u, two_over_m, beta, wt);
 #pragma unroll
                 for (int k = 0; k < MMAX; ++k)
-                    if (k < m) t -= row[k] * wt[k];
+                    if (k < m) t -= row[k] * tap_value<MMAX, true>(wp, k, s0, two_over_m, beta);
                 G[p * ldg + mi] = t * scale_u;
             } else {
-                window_taps<MMAX, false>(wp, c0 - u, two_over_m, beta, wt);
 #pragma unroll
                 for (int k = 0; k < MMAX; ++k)
-                    if (k < m) t = fma(row[k], wt[k], t);
+                    if (k < m) t = fma(row[k], tap_value<MMAX, false>(wp, k, s0, two_over_m, beta), t);
                 sum.add(t);
             }
         }

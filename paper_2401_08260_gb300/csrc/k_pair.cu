@@ -428,6 +428,220 @@ __global__ void __launch_bounds__(QTHREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------- FP16 hi/lo projection
+// Z = Xi (X - mu)^T to FP32 accuracy on CTA pairs: the split of the single-CTA kernel
+// k_umma_project_x3 (a = a_hi + 2^-11 a_lo' for both operands; per 16-wide K step the
+// correction products a_hi b_lo' + a_lo' b_hi, then a_hi b_hi with the accumulator scaled by
+// 2^-11 on input, into a fresh accumulator that the epilogue adds into FP32 registers with
+// round-to-nearest), with a pair computing a 256-point x 256-slice tile by M = 256, N = 256
+// MMAs: each CTA loads its own 128 point rows and its own 128 direction rows (hi and lo) per
+// 64-wide K stage, so every byte brought into shared memory feeds twice the MMA work of the
+// single CTA's 128 x 128 tile.
+//   warp 0:     poller: TMA loads; even CTA: the MMAs and the release of a stage to the odd
+//               CTA; odd CTA: a remote arrival on the even CTA's peer_full when its bytes landed
+//   warp 1:     tensor memory (two 256-column accumulators per CTA)
+//   warps 2-17: epilogue, TMEM lane quarter warp % 4 and 64 columns (warp - 2) / 4 each
+constexpr int X3P_STAGES = 3;
+constexpr int X3P_THREADS = 576;
+constexpr int X3P_EPI0 = 2;
+constexpr int X3P_EPI_WARPS = 16;
+constexpr int X3P_TILE_BYTES = QM * QK * 2;  // 128 rows x 64 16-bit values
+constexpr int X3P_STAGE_BYTES = 4 * X3P_TILE_BYTES;
+constexpr uint32_t X3P_TMEM_COLS = 512;
+
+struct X3PairSmem {
+    uint64_t full[X3P_STAGES];       // this CTA's TMA bytes of a stage have landed
+    uint64_t peer_full[X3P_STAGES];  // even CTA: the odd CTA's bytes of a stage have landed
+    uint64_t empty[X3P_STAGES];      // the stage may be refilled
+    uint64_t d_full[2];              // an accumulator holds a finished K step
+    uint64_t d_empty[2];             // even CTA: both CTAs' epilogue warps have read it
+    uint64_t drain;                  // even CTA: its last MMAs completed
+    uint32_t tmem_base;
+};
+
+struct X3PairArgs {
+    int n, P, d, col_tiles;
+    float* Z;
+    int64_t ldz;
+    float* absmax;
+    unsigned* err;
+};
+
+__host__ __device__ constexpr size_t x3_pair_smem_bytes() {
+    return 1024 + static_cast<size_t>(X3P_STAGES) * X3P_STAGE_BYTES + sizeof(X3PairSmem);
+}
+
+__global__ void __launch_bounds__(X3P_THREADS, 1)
+    k_pair_project_x3(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                      const __grid_constant__ CUtensorMap map_a2, const __grid_constant__ CUtensorMap map_b2,
+                      X3PairArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    X3PairSmem* sm = reinterpret_cast<X3PairSmem*>(base + X3P_STAGES * X3P_STAGE_BYTES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const int pair = static_cast<int>(blockIdx.x >> 1);
+    const int row0 = (pair / a.col_tiles) * (2 * QM) + static_cast<int>(rank) * QM;  // this CTA's points
+    const int col0 = (pair % a.col_tiles) * QN;                                     // the pair's slices
+    const int brow0 = col0 + static_cast<int>(rank) * QM;                           // this CTA's directions
+    const int kblocks = (a.d + QK - 1) / QK;
+    const int ksteps = kblocks * (QK / 16);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < X3P_STAGES; ++s) {
+            mbar_init(&sm->full[s], 1);
+            mbar_init(&sm->peer_full[s], 1);
+            mbar_init(&sm->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sm->d_full[b], 1);
+            mbar_init(&sm->d_empty[b], 2 * X3P_EPI_WARPS);
+        }
+        mbar_init(&sm->drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc_pair(&sm->tmem_base, X3P_TMEM_COLS);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    // both CTAs' barriers initialised and tensor memory allocated before any remote arrival
+    cluster_barrier();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = sm->tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc(0u, 2 * QM, QN);
+            const uint32_t peer_empty0 = cluster_addr(&sm->empty[0], 1);
+            const uint32_t lead_pfull0 = cluster_addr(&sm->peer_full[0], 0);
+            int gf = 0, gp = 0, gk = 0;  // next fill, next forward (odd), next K step (even)
+            unsigned idle = 0;
+            while (gf < kblocks || (rank == 1 && gp < kblocks) || (rank == 0 && gk < ksteps)) {
+                bool progress = false;
+                if (gf < kblocks) {
+                    const int s = gf % X3P_STAGES;
+                    if (gf < X3P_STAGES || mbar_test_cta(&sm->empty[s], ((gf / X3P_STAGES) - 1) & 1)) {
+                        // the even CTA passes the release of the stage on to the odd CTA
+                        if (rank == 0 && gf >= X3P_STAGES)
+                            mbar_arrive_cluster_relaxed(peer_empty0 + static_cast<uint32_t>(s * sizeof(uint64_t)));
+                        unsigned char* st = base + s * X3P_STAGE_BYTES;
+                        mbar_expect_tx(&sm->full[s], X3P_STAGE_BYTES);
+                        tma_load_2d(st, &map_a, &sm->full[s], gf * QK, row0);
+                        tma_load_2d(st + X3P_TILE_BYTES, &map_b, &sm->full[s], gf * QK, brow0);
+                        tma_load_2d(st + 2 * X3P_TILE_BYTES, &map_a2, &sm->full[s], gf * QK, row0);
+                        tma_load_2d(st + 3 * X3P_TILE_BYTES, &map_b2, &sm->full[s], gf * QK, brow0);
+                        ++gf;
+                        progress = true;
+                    }
+                }
+                if (rank == 1 && gp < gf) {
+                    const int s = gp % X3P_STAGES;
+                    if (mbar_test_cta(&sm->full[s], (gp / X3P_STAGES) & 1)) {
+                        mbar_arrive_cluster(lead_pfull0 + static_cast<uint32_t>(s * sizeof(uint64_t)));
+                        ++gp;
+                        progress = true;
+                    }
+                }
+                if (rank == 0 && gk < ksteps) {
+                    const int g = gk >> 2, k = gk & 3, s = g % X3P_STAGES, b = gk & 1;
+                    bool ready = g < gf;
+                    if (ready && k == 0)
+                        ready = mbar_test_cta(&sm->full[s], (g / X3P_STAGES) & 1) &&
+                                mbar_test(&sm->peer_full[s], (g / X3P_STAGES) & 1);
+                    if (ready && gk >= 2) ready = mbar_test(&sm->d_empty[b], ((gk >> 1) - 1) & 1);
+                    if (ready) {
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        unsigned char* st = base + s * X3P_STAGE_BYTES;
+                        const uint64_t ah = smem_desc(st + k * 32);
+                        const uint64_t bh = smem_desc(st + X3P_TILE_BYTES + k * 32);
+                        const uint64_t al = smem_desc(st + 2 * X3P_TILE_BYTES + k * 32);
+                        const uint64_t bl = smem_desc(st + 3 * X3P_TILE_BYTES + k * 32);
+                        const uint32_t dt = tmem + static_cast<uint32_t>(b * QN);
+                        umma_f16_pair(dt, ah, bl, idesc, 0u);
+                        umma_f16_pair(dt, al, bh, idesc, 1u);
+                        umma_f16_pair_scale_d<11>(dt, ah, bh, idesc);
+                        umma_commit_pair(&sm->d_full[b]);
+                        if (k == QK / 16 - 1) umma_commit_pair(&sm->empty[s]);
+                        ++gk;
+                        progress = true;
+                    }
+                }
+                if (progress) {
+                    idle = 0;
+                } else if (++idle > WAIT_LIMIT) {
+                    atomicOr(a.err, rank == 0 ? 16u : 8u);
+                    break;
+                }
+            }
+            drain_fills(sm->full, X3P_STAGES, gf);
+            if (rank == 0) drain_mma_pair(&sm->drain, a.err, 16u);
+        }
+    } else if (warp >= X3P_EPI0) {
+        const int q4 = warp & 3, cg = (warp - X3P_EPI0) >> 2;
+        const uint32_t lane_off = static_cast<uint32_t>(q4 * 32) << 16;
+        const uint32_t d_empty0 = cluster_addr(&sm->d_empty[0], 0);
+        const uint32_t peer_dfull0 = cluster_addr(&sm->d_full[0], 1);
+        const bool forwarder = rank == 0 && warp == X3P_EPI0 && lane == 0;
+        float acc[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) acc[j] = 0.0f;
+        bool ok = true;
+        for (int t = 0; t < ksteps; ++t) {
+            const int b = t & 1;
+            if (!mbar_wait_cluster(&sm->d_full[b], (t >> 1) & 1)) {
+                atomicOr(a.err, 32u);
+                ok = false;
+                break;
+            }
+            // the odd CTA's epilogue learns of the finished step from the even CTA
+            if (forwarder) mbar_arrive_cluster(peer_dfull0 + static_cast<uint32_t>(b * sizeof(uint64_t)));
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // 16 columns at a time (the 64 running sums leave room for one load in flight)
+            const uint32_t ta = tmem + lane_off + static_cast<uint32_t>(b * QN + cg * 64);
+            uint32_t v[16];
+#pragma unroll
+            for (int c = 0; c < 48; c += 16) {
+                tmem_ld16_issue(ta + c, v);
+                tmem_wait16(v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[c + j] = __fadd_rn(acc[c + j], __uint_as_float(v[j]));
+            }
+            tmem_ld16_issue(ta + 48, v);
+            tmem_wait16(v);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(d_empty0 + static_cast<uint32_t>(b * sizeof(uint64_t)));
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[48 + j] = __fadd_rn(acc[48 + j], __uint_as_float(v[j]));
+        }
+        float mx = 0.0f;
+        const int row = row0 + q4 * 32 + lane;
+        if (ok && row < a.n) {
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                const int p = col0 + cg * 64 + j;
+                if (p < a.P) {
+                    a.Z[static_cast<int64_t>(p) * a.ldz + row] = acc[j];
+                    mx = fmaxf(mx, fabsf(acc[j]));
+                }
+            }
+        }
+        if (a.absmax) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) atomicMax(reinterpret_cast<unsigned int*>(a.absmax), __float_as_uint(mx));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    // neither CTA frees its tensor memory or leaves while the pair's MMAs or arrivals may
+    // still reach it
+    cluster_barrier();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tmem_dealloc_pair(tmem, X3P_TMEM_COLS);
+    }
+}
+
 }  // namespace
 bool pair_cheb_fits(int P, int q, int d) {
     return P >= 1 && P <= QMAX_P && (q == 8 || q == 10 || q == 12 || q == 16) && d >= 1 &&
@@ -555,6 +769,49 @@ void launch_pair_moments(const float* x, int64_t ldx, const float* mu, int64_t n
     SLK_TIMED("pair_cheb_moments", st);
     // every pair writes its partial moments (zeros when it has no tile)
     launch_pairs<SIDE_SOURCE>(mp, md, a, source_pairs(P), st);
+}
+
+void launch_pair_project_x3(const void* xa, const void* xa_lo, int64_t n, const void* xib, const void* xib_lo, int P,
+                            int d, float* Z, int64_t ldz, float* absmax, unsigned* err, cudaStream_t st) {
+    if (n <= 0) return;
+    SLK_REQUIRE(n < (int64_t(1) << 31) - 2 * QM, "too many points for one projection");
+    const int64_t ld = umma_operand_ld(d);
+    // the FP16 operands move through the 16-bit, 128-byte-swizzled maps of the BF16 path
+    const CUtensorMap ma = tmap_bf16_sw128(xa, n, d, ld, QM);
+    const CUtensorMap mb = tmap_bf16_sw128(xib, P, d, ld, QM);
+    const CUtensorMap ma2 = tmap_bf16_sw128(xa_lo, n, d, ld, QM);
+    const CUtensorMap mb2 = tmap_bf16_sw128(xib_lo, P, d, ld, QM);
+    X3PairArgs a{};
+    a.n = static_cast<int>(n);
+    a.P = P;
+    a.d = d;
+    a.col_tiles = static_cast<int>(ceil_div(P, QN));
+    a.Z = Z;
+    a.ldz = ldz;
+    a.absmax = absmax;
+    a.err = err;
+    const int64_t pairs = ceil_div(n, 2 * QM) * a.col_tiles;
+    SLK_REQUIRE(2 * pairs < (int64_t(1) << 31), "too many points for one projection");
+    static bool attr = false;
+    if (!attr) {
+        SLK_CHECK_CUDA(cudaFuncSetAttribute(k_pair_project_x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            static_cast<int>(x3_pair_smem_bytes())));
+        attr = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attrs[1];
+    attrs[0].id = cudaLaunchAttributeClusterDimension;
+    attrs[0].val.clusterDim.x = 2;
+    attrs[0].val.clusterDim.y = 1;
+    attrs[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(static_cast<unsigned>(2 * pairs));
+    cfg.blockDim = dim3(X3P_THREADS);
+    cfg.dynamicSmemBytes = x3_pair_smem_bytes();
+    cfg.stream = st;
+    cfg.attrs = attrs;
+    cfg.numAttrs = 1;
+    SLK_TIMED("pair_project_x3", st);
+    SLK_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_pair_project_x3, ma, mb, ma2, mb2, a));
 }
 
 }  // namespace slk

@@ -1046,6 +1046,12 @@ void launch_project_umma(const void* xa, const void* xa_lo, int64_t n, const voi
     const int64_t blocks = ceil_div(n, BM) * col_tiles;
     SLK_REQUIRE(blocks < (int64_t(1) << 31), "too many points");
     dim3 grid(static_cast<unsigned>(blocks));
+    if (split && P > X3_BN) {
+        // more slices than one 128-column tile: CTA pairs with 256 x 256 tiles (twice the MMA
+        // work per byte of operands brought into shared memory)
+        launch_pair_project_x3(xa, xa_lo, n, xib, xib_lo, P, d, Z, ldz, absmax, err, st);
+        return;
+    }
     if (split) {
         static bool attr = false;
         if (!attr) {

@@ -99,6 +99,12 @@ void launch_pair_cheb_target(const float* y, int64_t ldy, const float* mu, int64
 int64_t pair_moments_chunks(int P);
 void launch_pair_moments(const float* x, int64_t ldx, const float* mu, int64_t n, const void* xib, int P, int d,
                          const float* w, int q, double R, double* mom, float* absmax, unsigned* err, cudaStream_t st);
+// The FP16 hi/lo (FP32-accurate) projection of launch_project_umma(split = 1) on CTA pairs:
+// 256-point x 256-slice tiles, M = 256 and N = 256 pair MMAs, each CTA loading its own 128
+// point rows and 128 direction rows (hi and lo) per K stage; same operands, same promotion of
+// every 16-wide K step, same output (Z slice-major with row stride ldz, absmax if not NULL).
+void launch_pair_project_x3(const void* xa, const void* xa_lo, int64_t n, const void* xib, const void* xib_lo, int P,
+                            int d, float* Z, int64_t ldz, float* absmax, unsigned* err, cudaStream_t st);
 
 // ------------------------------------------------------------ k_rff.cu
 // Random Fourier features (Section 4.3, comparison system).  feat: D x (d + 1) FP64 rows
