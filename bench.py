@@ -238,10 +238,16 @@ def algorithmic(wl, info, precision, kernel_name, launches_per_step, kernels, P=
         k = 2 if precision == "f16x3" else 1
         ld16 = (wl.d + 7) // 8 * 8
         return pts * (4.0 * wl.d + 2.0 * ld16 * k), "byte", "hbm"
+    if kernel_name.startswith("spread_sorted"):
+        return 8.0 * pts * P, "byte", "hbm"  # the (key, w) pair of every source slice-point
     if kernel_name.startswith("derivs_bf16"):
         # the M x P derivatives of the gradient: FP32 in, BF16 out (row pitch ld16(P))
         return per * wl.M * (4.0 * P + 2.0 * ((P + 7) // 8 * 8)), "byte", "hbm"
-    return 4.0 * pts * P, "byte", "hbm"
+    if kernel_name.startswith(("nfft_target", "ndft_reduce", "spread_")):
+        return 4.0 * pts * P, "byte", "hbm"
+    # bookkeeping kernels (reductions of partial sums, the sample mean, casts of the
+    # directions, the FFT of a few thousand grid cells): no roofline model
+    return None, None, None
 
 
 def cpu_sample(wl, budget_s: float):
@@ -438,6 +444,8 @@ def run_ours(args):
         per_step = n_launch / args.steps
         amount, unit, bound = algorithmic(wl, info, precision, name, per_step, kernels, P=P_local, grad=args.grad,
                                           peaks=peaks)
+        if amount is None:
+            return None
         avg_s = tot_ms / n_launch * 1e-3
         if bound == "tensor":
             # a kernel timed inside a long step: the sustained dense BF16 figure (FP16 runs at the same rate)
@@ -466,7 +474,8 @@ def run_ours(args):
         if n_launch <= 0 or tot_ms <= 0.0:
             continue
         r = kernel_roofline(kname, n_launch, tot_ms)
-        kernel_fracs[kname] = {"ms_per_step": tot_ms / args.steps, "bound": r["bound"], "frac": r["frac"]}
+        kernel_fracs[kname] = {"ms_per_step": tot_ms / args.steps, "bound": r["bound"] if r else None,
+                               "frac": r["frac"] if r else None}
 
     # ---------------- end to end through the C ABI with pinned host buffers
     e2e = None

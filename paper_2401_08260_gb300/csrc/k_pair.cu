@@ -439,7 +439,8 @@ __global__ void __launch_bounds__(QTHREADS, 1)
 // single CTA's 128 x 128 tile.
 //   warp 0:     poller: TMA loads; even CTA: the MMAs and the release of a stage to the odd
 //               CTA; odd CTA: a remote arrival on the even CTA's peer_full when its bytes landed
-//   warp 1:     tensor memory (two 256-column accumulators per CTA)
+//   warp 1:     tensor memory (two 256-column accumulators per CTA); even CTA: passes each
+//               finished K step on to the odd CTA's epilogue
 //   warps 2-17: epilogue, TMEM lane quarter warp % 4 and 64 columns (warp - 2) / 4 each
 constexpr int X3P_STAGES = 3;
 constexpr int X3P_THREADS = 576;
@@ -575,12 +576,23 @@ __global__ void __launch_bounds__(X3P_THREADS, 1)
             drain_fills(sm->full, X3P_STAGES, gf);
             if (rank == 0) drain_mma_pair(&sm->drain, a.err, 16u);
         }
+    } else if (warp == 1) {
+        // even CTA: pass every finished K step on to the odd CTA's epilogue as soon as it lands
+        if (rank == 0 && lane == 0) {
+            const uint32_t peer_dfull0 = cluster_addr(&sm->d_full[0], 1);
+            for (int t = 0; t < ksteps; ++t) {
+                const int b = t & 1;
+                if (!mbar_wait_cluster(&sm->d_full[b], (t >> 1) & 1)) {
+                    atomicOr(a.err, 32u);
+                    break;
+                }
+                mbar_arrive_cluster(peer_dfull0 + static_cast<uint32_t>(b * sizeof(uint64_t)));
+            }
+        }
     } else if (warp >= X3P_EPI0) {
         const int q4 = warp & 3, cg = (warp - X3P_EPI0) >> 2;
         const uint32_t lane_off = static_cast<uint32_t>(q4 * 32) << 16;
         const uint32_t d_empty0 = cluster_addr(&sm->d_empty[0], 0);
-        const uint32_t peer_dfull0 = cluster_addr(&sm->d_full[0], 1);
-        const bool forwarder = rank == 0 && warp == X3P_EPI0 && lane == 0;
         float acc[64];
 #pragma unroll
         for (int j = 0; j < 64; ++j) acc[j] = 0.0f;
@@ -592,8 +604,6 @@ __global__ void __launch_bounds__(X3P_THREADS, 1)
                 ok = false;
                 break;
             }
-            // the odd CTA's epilogue learns of the finished step from the even CTA
-            if (forwarder) mbar_arrive_cluster(peer_dfull0 + static_cast<uint32_t>(b * sizeof(uint64_t)));
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             // 16 columns at a time (the 64 running sums leave room for one load in flight)
             const uint32_t ta = tmem + lane_off + static_cast<uint32_t>(b * QN + cg * 64);

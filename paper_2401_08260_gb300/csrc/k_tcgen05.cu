@@ -552,8 +552,8 @@ struct SmemX3 {
 __global__ void __launch_bounds__(X3_THREADS, 1)
     k_umma_project_x3(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                       const __grid_constant__ CUtensorMap map_a2, const __grid_constant__ CUtensorMap map_b2, int n,
-                      int P, int d, int col_tiles, float* __restrict__ Z, int64_t ldz, float* __restrict__ absmax,
-                      unsigned* __restrict__ err) {
+                      int P, int d, int col_tiles, int tiles, float* __restrict__ Z, int64_t ldz,
+                      float* __restrict__ absmax, unsigned* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     // 1024-byte aligned start, derived from the shared array itself so that every access
     // through it compiles to a shared-memory instruction
@@ -562,10 +562,14 @@ __global__ void __launch_bounds__(X3_THREADS, 1)
     constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);
     SmemX3* sm = reinterpret_cast<SmemX3*>(base + X3_STAGES * STAGE_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row0 = static_cast<int>(blockIdx.x / col_tiles) * BM;
-    const int col0 = static_cast<int>(blockIdx.x % col_tiles) * X3_BN;
     const int kblocks = (d + BK - 1) / BK;
     const int ksteps = kblocks * (BK / 16);
+    // persistent: this CTA's tiles are blockIdx.x, blockIdx.x + gridDim.x, ...; tile ->
+    // (row tile, column tile) with the column tiles of a row tile adjacent
+    int ntile = 0;
+    for (int tl = static_cast<int>(blockIdx.x); tl < tiles; tl += static_cast<int>(gridDim.x)) ++ntile;
+    const int total = ntile * kblocks;
+    auto tile_of = [&](int li) { return static_cast<int>(blockIdx.x) + li * static_cast<int>(gridDim.x); };
     constexpr uint32_t TMEM_COLS = 512;
     static_assert(X3_BUF * X3_BN <= static_cast<int>(TMEM_COLS), "accumulators exceed tensor memory");
 
@@ -594,9 +598,10 @@ __global__ void __launch_bounds__(X3_THREADS, 1)
 
     if (warp == 0 && lane == 0) {
         int fills = 0;
-        for (int kb = 0; kb < kblocks; ++kb, ++fills) {
-            const int s = kb % X3_STAGES;
-            if (kb >= X3_STAGES && !mbar_wait(&sm->empty[s], ((kb / X3_STAGES) - 1) & 1)) {
+        for (int g = 0; g < total; ++g, ++fills) {
+            const int s = g % X3_STAGES, kb = g % kblocks, tile = tile_of(g / kblocks);
+            const int row0 = (tile / col_tiles) * BM, col0 = (tile % col_tiles) * X3_BN;
+            if (g >= X3_STAGES && !mbar_wait(&sm->empty[s], ((g / X3_STAGES) - 1) & 1)) {
                 atomicOr(err, 8u);
                 break;
             }
@@ -611,16 +616,16 @@ __global__ void __launch_bounds__(X3_THREADS, 1)
     } else if (warp == 1 && lane == 0) {
         const uint32_t idesc = instr_desc(0u, BM, X3_BN);
         bool ok = true;
-        for (int kb = 0; kb < kblocks && ok; ++kb) {
-            const int s = kb % X3_STAGES;
-            if (!mbar_wait(&sm->full[s], (kb / X3_STAGES) & 1)) {
+        for (int g = 0; g < total && ok; ++g) {
+            const int s = g % X3_STAGES;
+            if (!mbar_wait(&sm->full[s], (g / X3_STAGES) & 1)) {
                 atomicOr(err, 16u);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             unsigned char* st = base + s * STAGE_BYTES;
             for (int k = 0; k < BK / 16; ++k) {
-                const int t = kb * (BK / 16) + k;  // global K step
+                const int t = g * (BK / 16) + k;  // K step, counted over this CTA's tiles
                 const int b = t % X3_BUF;
                 if (t >= X3_BUF && !mbar_wait(&sm->d1_empty[b], ((t / X3_BUF) - 1) & 1)) {
                     atomicOr(err, 16u);
@@ -642,43 +647,47 @@ __global__ void __launch_bounds__(X3_THREADS, 1)
         drain_mma(&sm->drain, err);
     } else if (warp >= 4) {
         const int q = warp & 3, h = (warp - 4) >> 2;
-        const int row = row0 + q * 32 + lane;
         const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
         const int cbase = h * 64;
-        float acc[64];
-#pragma unroll
-        for (int j = 0; j < 64; ++j) acc[j] = 0.0f;
-        bool ok = true;
-        for (int t = 0; t < ksteps; ++t) {
-            const int b = t % X3_BUF;
-            if (!mbar_wait(&sm->d1_full[b], (t / X3_BUF) & 1)) {
-                atomicOr(err, 32u);
-                ok = false;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            uint32_t v0[32], v1[32];
-            tmem_ld32_issue(tmem + lane_off + b * X3_BN + cbase, v0);
-            tmem_ld32_issue(tmem + lane_off + b * X3_BN + cbase + 32, v1);
-            tmem_wait32(v0);
-            tmem_wait32(v1);
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sm->d1_empty[b]);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                acc[j] = __fadd_rn(acc[j], __uint_as_float(v0[j]));
-                acc[32 + j] = __fadd_rn(acc[32 + j], __uint_as_float(v1[j]));
-            }
-        }
         float mx = 0.0f;
-        if (ok && row < n) {
+        bool ok = true;
+        int t = 0;  // K step, counted over this CTA's tiles
+        for (int li = 0; li < ntile && ok; ++li) {
+            const int tile = tile_of(li);
+            const int row = (tile / col_tiles) * BM + q * 32 + lane, col0 = (tile % col_tiles) * X3_BN;
+            float acc[64];
 #pragma unroll
-            for (int j = 0; j < 64; ++j) {
-                const int p = col0 + cbase + j;
-                if (p < P) {
-                    Z[static_cast<int64_t>(p) * ldz + row] = acc[j];
-                    mx = fmaxf(mx, fabsf(acc[j]));
+            for (int j = 0; j < 64; ++j) acc[j] = 0.0f;
+            for (int k = 0; k < ksteps; ++k, ++t) {
+                const int b = t % X3_BUF;
+                if (!mbar_wait(&sm->d1_full[b], (t / X3_BUF) & 1)) {
+                    atomicOr(err, 32u);
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                uint32_t v0[32], v1[32];
+                tmem_ld32_issue(tmem + lane_off + b * X3_BN + cbase, v0);
+                tmem_ld32_issue(tmem + lane_off + b * X3_BN + cbase + 32, v1);
+                tmem_wait32(v0);
+                tmem_wait32(v1);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm->d1_empty[b]);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    acc[j] = __fadd_rn(acc[j], __uint_as_float(v0[j]));
+                    acc[32 + j] = __fadd_rn(acc[32 + j], __uint_as_float(v1[j]));
+                }
+            }
+            if (ok && row < n) {
+#pragma unroll
+                for (int j = 0; j < 64; ++j) {
+                    const int p = col0 + cbase + j;
+                    if (p < P) {
+                        Z[static_cast<int64_t>(p) * ldz + row] = acc[j];
+                        mx = fmaxf(mx, fabsf(acc[j]));
+                    }
                 }
             }
         }
@@ -1059,9 +1068,13 @@ void launch_project_umma(const void* xa, const void* xa_lo, int64_t n, const voi
                                                 static_cast<int>(x3_smem_bytes())));
             attr = true;
         }
+        // persistent: one CTA per SM (shared memory and tensor memory admit one), tiles in turn
+        const int sms = sm_count_dev();
+        const unsigned cta = static_cast<unsigned>(blocks < sms ? blocks : sms);
         SLK_TIMED("umma_project_x3", st);
-        k_umma_project_x3<<<grid, X3_THREADS, x3_smem_bytes(), st>>>(ma, mb, ma2, mb2, static_cast<int>(n), P, d,
-                                                                     col_tiles, Z, ldz, absmax, err);
+        k_umma_project_x3<<<cta, X3_THREADS, x3_smem_bytes(), st>>>(ma, mb, ma2, mb2, static_cast<int>(n), P, d,
+                                                                    col_tiles, static_cast<int>(blocks), Z, ldz,
+                                                                    absmax, err);
     } else {
         SLK_TIMED("umma_project_bf16", st);
         launch_persistent<EPI_Z>(ma, mb, n, P, d, col_tiles, Z, ldz, absmax, err, nullptr, 1.0f,
