@@ -533,7 +533,9 @@ def run_ours(args):
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "slice-points/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "warmup": args.warmup, "ms_per_step": ms,
+                "device_ms_per_step": dev_ms / args.steps, "wall_ms_per_step": t_wall * 1e3 / args.steps,
+                "higher_is_better": True,
                 "scaling": "strong" if sharded else "weak",
                 "vs_baseline": None, "dtype": precision, "data": "synthetic",
                 "config": {"workload": args.workload, "kernel": wl.kernel, "N": wl.N, "M": wl.M, "d": wl.d,

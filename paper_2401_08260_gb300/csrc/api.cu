@@ -136,6 +136,7 @@ struct slk_plan_s {
     DevBuf<unsigned char> cw;   // Cplx<T> P x K
     DevBuf<unsigned char> cw0;  // T P
     DevBuf<unsigned char> hgrid;  // T P x W
+    DevBuf<unsigned char> itab;   // FP32 NFFT plans: the interpolant per grid cell (launch_interp_table)
 
     // sorting side (negative distance, Laplacian non-smooth part)
     bool sorting = false;
@@ -157,7 +158,7 @@ struct slk_plan_s {
     ~slk_plan_s() {
         for (DevBuf<double>* b : {&xi64, &mu64, &coef, &mult, &chebM}) b->stream = stream;
         for (DevBuf<float>* b : {&xi32, &mu32, &kmin, &kscale}) b->stream = stream;
-        for (DevBuf<unsigned char>* b : {&xib, &xib_lo, &xit16, &beta, &mono, &cw, &cw0, &hgrid, &kw, &rec})
+        for (DevBuf<unsigned char>* b : {&xib, &xib_lo, &xit16, &beta, &mono, &cw, &cw0, &hgrid, &itab, &kw, &rec})
             b->stream = stream;
         err_dev.stream = stream;
         if (done) cudaEventDestroy(done);
@@ -167,7 +168,7 @@ struct slk_plan_s {
     int64_t device_bytes() const {
         return static_cast<int64_t>(xi64.bytes() + xi32.bytes() + mu64.bytes() + mu32.bytes() + xib.bytes() +
                                     xib_lo.bytes() + xit16.bytes() + coef.bytes() +
-                                    mult.bytes() + chebM.bytes() + beta.bytes() + mono.bytes() + cw.bytes() + cw0.bytes() + hgrid.bytes() + kw.bytes() +
+                                    mult.bytes() + chebM.bytes() + beta.bytes() + mono.bytes() + cw.bytes() + cw0.bytes() + hgrid.bytes() + itab.bytes() + kw.bytes() +
                                     rec.bytes() + kmin.bytes() + kscale.bytes());
     }
 };
@@ -350,6 +351,7 @@ void fourier_setup(slk_plan plan, cudaStream_t st) {
     fd.q = fh.cheb_qp;
     fd.horner = 0;
     fd.mono = nullptr;
+    fd.itab = nullptr;
     if (fh.method == SLK_FOURIER_CHEB) {
         plan->chebM.alloc(fh.cheb_M.size(), st);
         SLK_CHECK_CUDA(cudaMemcpyAsync(plan->chebM.get(), fh.cheb_M.data(), sizeof(double) * fh.cheb_M.size(),
@@ -413,6 +415,13 @@ void plan_fourier_source(slk_plan plan, const T* Zx, const T* w, cudaStream_t st
         const T* pairs = plan->sorting ? reinterpret_cast<const T*>(plan->kw.get()) : nullptr;
         launch_nfft_source<T>(Zx, P, N, N, w, pairs, fd, fh.n_coeff, plan->mult.get(),
                               reinterpret_cast<T*>(plan->hgrid.get()), scratch.get(), ne, plan->err_dev.get(), st);
+        if constexpr (sizeof(T) == 4) {
+            // FP32: the target side reads the interpolant tabulated per grid cell
+            plan->itab.alloc(sizeof(float) * interp_table_floats(P, fd), st);
+            launch_interp_table(reinterpret_cast<const float*>(plan->hgrid.get()), P, fd,
+                                reinterpret_cast<float*>(plan->itab.get()), st);
+            fd.itab = plan->itab.get();
+        }
     }
     // the host copies of the coefficient tables must outlive the async copies
     SLK_CHECK_CUDA(cudaStreamSynchronize(st));

@@ -860,6 +860,103 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_nfft_target(con
     if (!G && mi < n) acc[mi] += sum.value();
 }
 
+// ------------------------------------------------------------ NFFT interpolation from a table
+
+// FP32 plans: the interpolant sum_t h[r + t] P_t(g) on grid cell r (the window's first cell
+// r + win_base) is itself a polynomial of degree kWinPolyDeg in g, with coefficients
+// C[r][k] = sum_t h[r + t] a_t[k] (a_t the tap polynomials of WinPoly, the mirrored taps as
+// a_{m-1-t}[k] = (-1)^k a_t[k]); one block per slice writes its ncell = W - m + 1 cells, 16
+// floats per cell (9 used, 64-byte rows for aligned vector loads), summed in FP64.
+constexpr int TAB_STRIDE = 16;
+
+__global__ void __launch_bounds__(256) k_interp_table(const float* __restrict__ h, int W, int m, const WinPoly wp,
+                                                      int ncell, float* __restrict__ tab) {
+    const int p = blockIdx.x;
+    const float* hp = h + static_cast<int64_t>(p) * W;
+    float* tp = tab + static_cast<int64_t>(p) * ncell * TAB_STRIDE;
+    for (int r = threadIdx.x; r < ncell; r += blockDim.x) {
+        double c[kWinPolyDeg + 1];
+#pragma unroll
+        for (int k = 0; k <= kWinPolyDeg; ++k) c[k] = 0.0;
+        for (int t = 0; t < m; ++t) {
+            const bool mirror = t >= (m + 1) / 2;
+            const int u = mirror ? m - 1 - t : t;
+            const double hv = static_cast<double>(hp[r + t]);
+#pragma unroll
+            for (int j = 0; j <= 4; ++j) c[2 * j] += hv * static_cast<double>(wp.ev[u][j]);
+#pragma unroll
+            for (int j = 0; j <= 3; ++j) c[2 * j + 1] += (mirror ? -hv : hv) * static_cast<double>(wp.od[u][j]);
+        }
+#pragma unroll
+        for (int k = 0; k < TAB_STRIDE; ++k) tp[static_cast<int64_t>(r) * TAB_STRIDE + k] = k <= kWinPolyDeg ? static_cast<float>(c[k]) : 0.0f;
+    }
+}
+
+// Target side from the table: one thread per target walks every slice (the slices in the same
+// order everywhere, so that the threads of an SM read one slice's 64-byte cells at a time from
+// L1); per slice one 48-byte read of the cell's coefficients and Horner's rule (and its
+// derivative for the gradient).  Same window check and Kahan slice sum as k_nfft_target.
+template <bool GRAD>
+__global__ void __launch_bounds__(256) k_nfft_target_tab(const float* __restrict__ Z, int P, int64_t n, int64_t ldz,
+                                                         float scale_u, int m, int win_base, int ncell,
+                                                         const float* __restrict__ tab, float R,
+                                                         double* __restrict__ acc, float* __restrict__ G, int64_t ldg,
+                                                         unsigned* __restrict__ err) {
+    const int64_t mi = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (mi >= n) return;
+    const float half_m = 0.5f * static_cast<float>(m), gofs = 0.5f * static_cast<float>(m - 1);
+    KahanF sum;
+    bool bad = false;
+    constexpr int U = 4;  // projections of four slices loaded together
+    for (int p0 = 0; p0 < P; p0 += U) {
+        float zq[U];
+#pragma unroll
+        for (int r = 0; r < U; ++r) zq[r] = p0 + r < P ? Z[static_cast<int64_t>(p0 + r) * ldz + mi] : 0.0f;
+#pragma unroll
+        for (int r = 0; r < U; ++r) {
+            const int p = p0 + r;
+            if (p >= P) break;
+            const float z = zq[r];
+            if (!(z <= R && z >= -R)) bad = true;  // outside the certified window (or NaN)
+            const float u = z * scale_u;
+            const float c0 = ceilf(u - half_m);
+            const int r0 = static_cast<int>(c0) - win_base;
+            if (r0 < 0 || r0 >= ncell) {
+                bad = true;
+                continue;
+            }
+            const float g = c0 - u + gofs;
+            const float4* cp = reinterpret_cast<const float4*>(tab + (static_cast<int64_t>(p) * ncell + r0) * TAB_STRIDE);
+            const float4 a = __ldg(cp), b = __ldg(cp + 1), c = __ldg(cp + 2);
+            if (GRAD) {
+                // d/du sum_j h_j psi(u - j) = -d/dg of the cell polynomial (g = c0 - u + const)
+                float dv = 8.0f * c.x;
+                dv = fmaf(dv, g, 7.0f * b.w);
+                dv = fmaf(dv, g, 6.0f * b.z);
+                dv = fmaf(dv, g, 5.0f * b.y);
+                dv = fmaf(dv, g, 4.0f * b.x);
+                dv = fmaf(dv, g, 3.0f * a.w);
+                dv = fmaf(dv, g, 2.0f * a.z);
+                dv = fmaf(dv, g, a.y);
+                G[static_cast<int64_t>(p) * ldg + mi] = -dv * scale_u;
+            } else {
+                float v = c.x;
+                v = fmaf(v, g, b.w);
+                v = fmaf(v, g, b.z);
+                v = fmaf(v, g, b.y);
+                v = fmaf(v, g, b.x);
+                v = fmaf(v, g, a.w);
+                v = fmaf(v, g, a.z);
+                v = fmaf(v, g, a.y);
+                v = fmaf(v, g, a.x);
+                sum.add(v);
+            }
+        }
+    }
+    if (bad) atomicOr(err, 4u);
+    if (!GRAD) acc[mi] += sum.value();
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ launchers
@@ -1182,6 +1279,19 @@ void launch_nfft_source(const T* Z, int P, int64_t n, int64_t ldz, const T* w, c
     SLK_CHECK_LAUNCH();
 }
 
+int64_t interp_table_floats(int P, const FourierDev& fd) {
+    return static_cast<int64_t>(P) * (fd.W - fd.m + 1) * TAB_STRIDE;
+}
+
+void launch_interp_table(const float* h, int P, const FourierDev& fd, float* tab, cudaStream_t st) {
+    SLK_REQUIRE(fd.W >= fd.m && fd.m >= 1 && fd.m <= kWinPolyMaxM, "NFFT window of %d cells over %d", fd.m, fd.W);
+    {
+        SLK_TIMED("interp_table", st);
+        k_interp_table<<<P, 256, 0, st>>>(h, fd.W, fd.m, fd.wp, fd.W - fd.m + 1, tab);
+    }
+    SLK_CHECK_LAUNCH();
+}
+
 template <class T>
 void launch_nfft_target(const T* Z, int P, int64_t n, int64_t ldz, const FourierDev& fd, const T* h, double* acc,
                         T* G, int64_t ldg, unsigned* err, cudaStream_t st) {
@@ -1191,6 +1301,24 @@ void launch_nfft_target(const T* Z, int P, int64_t n, int64_t ldz, const Fourier
         return;
     }
     if (n <= 0) return;
+    if constexpr (sizeof(T) == 4) {
+        if (fd.itab) {
+            const unsigned blocks = static_cast<unsigned>(ceil_div(n, 256));
+            const int ncell = fd.W - fd.m + 1;
+            const float* tab = static_cast<const float*>(fd.itab);
+            SLK_TIMED(G ? "nfft_target_grad" : "nfft_target", st);
+            if (G)
+                k_nfft_target_tab<true><<<blocks, 256, 0, st>>>(Z, P, n, ldz, static_cast<float>(fd.n_g / fd.L), fd.m,
+                                                               fd.win_base, ncell, tab, static_cast<float>(fd.R), acc, G,
+                                                               ldg, err);
+            else
+                k_nfft_target_tab<false><<<blocks, 256, 0, st>>>(Z, P, n, ldz, static_cast<float>(fd.n_g / fd.L), fd.m,
+                                                                fd.win_base, ncell, tab, static_cast<float>(fd.R), acc,
+                                                                G, ldg, err);
+            SLK_CHECK_LAUNCH();
+            return;
+        }
+    }
     // slices whose grid windows a block holds at once: about 24 KB, so that several blocks share
     // an SM (the loop over slices is latency-bound; occupancy hides it)
     int chunk = static_cast<int>((24 * 1024) / (sizeof(T) * fd.W));

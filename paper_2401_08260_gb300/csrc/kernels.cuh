@@ -172,7 +172,15 @@ struct FourierDev {
     const void* mono;
     // NFFT window taps as polynomials (used by the FP32 kernels)
     WinPoly wp;
+    // FP32 NFFT plans: the interpolant tabulated per grid cell (launch_interp_table), or NULL
+    const void* itab;
 };
+
+// FP32 NFFT plans: per slice and grid cell r < W - m + 1, the coefficients of the interpolant
+// sum_t h[p][r + t] psi(s0 + t) as a polynomial in g (s0 = g + 1/2 - m/2), 16 floats per cell
+// (9 used); launch_nfft_target<float> reads it when fd.itab is set.
+int64_t interp_table_floats(int P, const FourierDev& fd);
+void launch_interp_table(const float* h, int P, const FourierDev& fd, float* tab, cudaStream_t st);
 
 // Chebyshev evaluation of the truncated Fourier sum (Jacobi-Anger expansion on [-R, R]):
 // source side beta[p][l] = sum_j M[l][j] sum_n w_n T_j(z_{p,n}/R) (M is q x q, FP64);
