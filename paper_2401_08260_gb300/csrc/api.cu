@@ -135,8 +135,7 @@ struct slk_plan_s {
     DevBuf<unsigned char> mono;  // T P x q (the same polynomials in powers of z / R)
     DevBuf<unsigned char> cw;   // Cplx<T> P x K
     DevBuf<unsigned char> cw0;  // T P
-    DevBuf<unsigned char> hgrid;  // T P x W
-    DevBuf<unsigned char> itab;   // FP32 NFFT plans: the interpolant per grid cell (launch_interp_table)
+    DevBuf<unsigned char> hgrid;  // T P x W (FP32: then the interpolant per grid cell, launch_interp_table)
 
     // sorting side (negative distance, Laplacian non-smooth part)
     bool sorting = false;
@@ -158,7 +157,7 @@ struct slk_plan_s {
     ~slk_plan_s() {
         for (DevBuf<double>* b : {&xi64, &mu64, &coef, &mult, &chebM}) b->stream = stream;
         for (DevBuf<float>* b : {&xi32, &mu32, &kmin, &kscale}) b->stream = stream;
-        for (DevBuf<unsigned char>* b : {&xib, &xib_lo, &xit16, &beta, &mono, &cw, &cw0, &hgrid, &itab, &kw, &rec})
+        for (DevBuf<unsigned char>* b : {&xib, &xib_lo, &xit16, &beta, &mono, &cw, &cw0, &hgrid, &kw, &rec})
             b->stream = stream;
         err_dev.stream = stream;
         if (done) cudaEventDestroy(done);
@@ -168,7 +167,7 @@ struct slk_plan_s {
     int64_t device_bytes() const {
         return static_cast<int64_t>(xi64.bytes() + xi32.bytes() + mu64.bytes() + mu32.bytes() + xib.bytes() +
                                     xib_lo.bytes() + xit16.bytes() + coef.bytes() +
-                                    mult.bytes() + chebM.bytes() + beta.bytes() + mono.bytes() + cw.bytes() + cw0.bytes() + hgrid.bytes() + itab.bytes() + kw.bytes() +
+                                    mult.bytes() + chebM.bytes() + beta.bytes() + mono.bytes() + cw.bytes() + cw0.bytes() + hgrid.bytes() + kw.bytes() +
                                     rec.bytes() + kmin.bytes() + kscale.bytes());
     }
 };
@@ -369,7 +368,9 @@ void fourier_setup(slk_plan plan, cudaStream_t st) {
         plan->mult.alloc(fh.mult.size(), st);
         SLK_CHECK_CUDA(cudaMemcpyAsync(plan->mult.get(), fh.mult.data(), sizeof(double) * fh.mult.size(),
                                        cudaMemcpyHostToDevice, st));
-        plan->hgrid.alloc(sizeof(T) * P * fh.W, st);
+        // FP32: the interpolant table follows the grid window in the same buffer (64-byte aligned)
+        const size_t grid_bytes = (sizeof(T) * P * fh.W + 63) & ~size_t(63);
+        plan->hgrid.alloc(grid_bytes + (sizeof(T) == 4 ? sizeof(float) * interp_table_floats(P, fd) : 0), st);
     }
 }
 
@@ -417,10 +418,9 @@ void plan_fourier_source(slk_plan plan, const T* Zx, const T* w, cudaStream_t st
                               reinterpret_cast<T*>(plan->hgrid.get()), scratch.get(), ne, plan->err_dev.get(), st);
         if constexpr (sizeof(T) == 4) {
             // FP32: the target side reads the interpolant tabulated per grid cell
-            plan->itab.alloc(sizeof(float) * interp_table_floats(P, fd), st);
-            launch_interp_table(reinterpret_cast<const float*>(plan->hgrid.get()), P, fd,
-                                reinterpret_cast<float*>(plan->itab.get()), st);
-            fd.itab = plan->itab.get();
+            float* tab = reinterpret_cast<float*>(plan->hgrid.get() + ((sizeof(T) * P * fh.W + 63) & ~size_t(63)));
+            launch_interp_table(reinterpret_cast<const float*>(plan->hgrid.get()), P, fd, tab, st);
+            fd.itab = tab;
         }
     }
     // the host copies of the coefficient tables must outlive the async copies

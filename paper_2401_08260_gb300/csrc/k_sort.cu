@@ -53,20 +53,42 @@ struct Buckets {
     int NB;
     int mask;  // digit mask of a pass (digits of dbits <= 8 bits)
 };
-template <bool BUCKETED, class U>
-__device__ __forceinline__ int radix_digit(U k, int shift, const Buckets& bk, int p) {
-    if constexpr (BUCKETED)
-        return (bucket_of(static_cast<float>(key_from_bits(k)), bk.kmin[p], bk.kscale[p], bk.NB) >> shift) & bk.mask;
-    else
-        return static_cast<int>((k >> shift) & 0xffu);
-}
+// The digit function of a slice, its bucket geometry read once per thread (read through the
+// Buckets pointers at every use it would be reloaded after each global store)
+template <bool BUCKETED>
+struct DigitOf {
+    float lo = 0.0f, sc = 0.0f;
+    int NB = 0, mask = 0xff;
+    __device__ __forceinline__ DigitOf(const Buckets& bk, int p) {
+        if (BUCKETED) {
+            lo = bk.kmin[p];
+            sc = bk.kscale[p];
+            NB = bk.NB;
+            mask = bk.mask;
+        }
+    }
+    template <class U>
+    __device__ __forceinline__ int operator()(U k, int shift) const {
+        if constexpr (BUCKETED)
+            return (bucket_of(static_cast<float>(key_from_bits(k)), lo, sc, NB) >> shift) & mask;
+        else
+            return static_cast<int>((k >> shift) & 0xffu);
+    }
+};
+
+// Key bits and payload of the intermediate passes, interleaved (one store per key)
+template <class U, class T>
+struct alignas(sizeof(U) + sizeof(T)) KV {
+    U k;
+    T v;
+};
 
 // Digit histogram of one tile: hist[(p * 256 + digit) * tiles + tile].  FIRST: the keys are
 // the order-preserving bits of the projections z (row stride ldz), otherwise the bits array.
 template <class T, class U, bool FIRST, bool BUCKETED>
 __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const T* __restrict__ z, int64_t ldz,
-                                                          const U* __restrict__ keys, int64_t n, int shift, int tiles,
-                                                          int32_t* __restrict__ hist, Buckets bk) {
+                                                          const KV<U, T>* __restrict__ keys, int64_t n, int shift,
+                                                          int tiles, int32_t* __restrict__ hist, Buckets bk) {
     __shared__ int32_t h[RS_BINS];
     const int p = blockIdx.y, tile = blockIdx.x;
     h[threadIdx.x] = 0;
@@ -77,12 +99,13 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const T* __restrict__
 #pragma unroll
     for (int r = 0; r < RS_ITEMS; ++r) {
         const int64_t i = base + r * RS_THREADS + threadIdx.x;
-        if (i < n) k[r] = FIRST ? key_bits(z[static_cast<int64_t>(p) * ldz + i]) : keys[static_cast<int64_t>(p) * n + i];
+        if (i < n) k[r] = FIRST ? key_bits(z[static_cast<int64_t>(p) * ldz + i]) : keys[static_cast<int64_t>(p) * n + i].k;
     }
+    const DigitOf<BUCKETED> digit_of(bk, p);
 #pragma unroll
     for (int r = 0; r < RS_ITEMS; ++r) {
         const int64_t i = base + r * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[radix_digit<BUCKETED>(k[r], shift, bk, p)], 1);
+        if (i < n) atomicAdd(&h[digit_of(k[r], shift)], 1);
     }
     __syncthreads();
     hist[(static_cast<int64_t>(p) * RS_BINS + threadIdx.x) * tiles + tile] = h[threadIdx.x];
@@ -154,14 +177,14 @@ constexpr size_t radix_pass_smem() {
 // give every key its place in the tile's digit-sorted order, the tile is reordered in shared
 // memory, and each digit's run is written to its global offset (from the scanned histogram)
 // in contiguous stores.  FIRST reads the projections and the weights (source index order);
-// LAST writes (key, w) pairs instead of bits and payload.
+// LAST writes (key, w) pairs instead of the interleaved bits and payload.
 template <class T, class U, bool FIRST, bool LAST, bool BUCKETED>
 __global__ void __launch_bounds__(RS_THREADS, 5) k_radix_pass(const T* __restrict__ z, int64_t ldz, const T* __restrict__ w,
-                                                          const U* __restrict__ kin, const T* __restrict__ vin,
-                                                          int64_t n, int shift, int tiles,
-                                                          const int32_t* __restrict__ hist,
-                                                          const int32_t* __restrict__ dbase, U* __restrict__ kout,
-                                                          T* __restrict__ vout, KW<T>* __restrict__ pout, Buckets bk) {
+                                                          const KV<U, T>* __restrict__ kvin, int64_t n, int shift,
+                                                          int tiles, const int32_t* __restrict__ hist,
+                                                          const int32_t* __restrict__ dbase,
+                                                          KV<U, T>* __restrict__ kvout, KW<T>* __restrict__ pout,
+                                                          Buckets bk) {
     extern __shared__ __align__(16) unsigned char rs_smem[];
     U* sk = reinterpret_cast<U*>(rs_smem);
     T* sv = reinterpret_cast<T*>(sk + RS_TILE);
@@ -191,15 +214,17 @@ __global__ void __launch_bounds__(RS_THREADS, 5) k_radix_pass(const T* __restric
             key[r] = valid ? key_bits(z[static_cast<int64_t>(p) * ldz + e]) : U(0);
             val[r] = valid ? w[e] : T(0);
         } else {
-            key[r] = valid ? kin[seg + e] : U(0);
-            val[r] = valid ? vin[seg + e] : T(0);
+            const KV<U, T> kv = valid ? kvin[seg + e] : KV<U, T>{U(0), T(0)};
+            key[r] = kv.k;
+            val[r] = kv.v;
         }
     }
+    const DigitOf<BUCKETED> digit_of(bk, p);
 #pragma unroll
     for (int r = 0; r < RS_ITEMS; ++r) {
         const int64_t e = base + warp * RUN + r * 32 + lane;
         const bool valid = e < n;
-        const int digit = valid ? radix_digit<BUCKETED>(key[r], shift, bk, p) : RS_BINS + lane;
+        const int digit = valid ? digit_of(key[r], shift) : RS_BINS + lane;
         const unsigned peers = __match_any_sync(0xffffffffu, digit);
         const int before = valid ? mycnt[digit] : 0;
         rank[r] = before + __popc(peers & lt_mask);
@@ -237,7 +262,7 @@ __global__ void __launch_bounds__(RS_THREADS, 5) k_radix_pass(const T* __restric
     for (int r = 0; r < RS_ITEMS; ++r) {
         const int64_t e = base + warp * RUN + r * 32 + lane;
         if (e < n) {
-            const int digit = radix_digit<BUCKETED>(key[r], shift, bk, p);
+            const int digit = digit_of(key[r], shift);
             const int pos = loc[digit] + wcnt[warp * RS_BINS + digit] + rank[r];
             sk[pos] = key[r];
             sv[pos] = val[r];
@@ -247,14 +272,10 @@ __global__ void __launch_bounds__(RS_THREADS, 5) k_radix_pass(const T* __restric
     const int cnt = static_cast<int>(n - base < RS_TILE ? n - base : RS_TILE);
     for (int j = threadIdx.x; j < cnt; j += RS_THREADS) {
         const U k = sk[j];
-        const int digit = radix_digit<BUCKETED>(k, shift, bk, p);
+        const int digit = digit_of(k, shift);
         const int64_t g = seg + glob[digit] + (j - loc[digit]);
-        if (LAST) {
-            pout[g] = KW<T>{key_from_bits(k), sv[j]};
-        } else {
-            kout[g] = k;
-            vout[g] = sv[j];
-        }
+        if (LAST) pout[g] = KW<T>{key_from_bits(k), sv[j]};
+        else kvout[g] = KV<U, T>{k, sv[j]};
     }
 }
 
@@ -847,8 +868,8 @@ size_t sort_pairs_scratch(int P, int64_t n) {
 }
 
 template <class T, class U, bool FIRST, bool LAST, bool BUCKETED>
-void radix_pass(dim3 grid, const T* z, int64_t ldz, const T* w, const U* kin, const T* vin, int64_t n, int shift,
-                int tiles, const int32_t* hist, const int32_t* dbase, U* kout, T* vout, KW<T>* pout, const Buckets& bk,
+void radix_pass(dim3 grid, const T* z, int64_t ldz, const T* w, const KV<U, T>* kvin, int64_t n, int shift, int tiles,
+                const int32_t* hist, const int32_t* dbase, KV<U, T>* kvout, KW<T>* pout, const Buckets& bk,
                 cudaStream_t st) {
     constexpr size_t smem = radix_pass_smem<T, U>();
     static bool attr = false;
@@ -857,35 +878,33 @@ void radix_pass(dim3 grid, const T* z, int64_t ldz, const T* w, const U* kin, co
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
         attr = true;
     }
-    k_radix_pass<T, U, FIRST, LAST, BUCKETED><<<grid, RS_THREADS, smem, st>>>(z, ldz, w, kin, vin, n, shift, tiles,
-                                                                              hist, dbase, kout, vout, pout, bk);
+    k_radix_pass<T, U, FIRST, LAST, BUCKETED><<<grid, RS_THREADS, smem, st>>>(z, ldz, w, kvin, n, shift, tiles, hist,
+                                                                              dbase, kvout, pout, bk);
 }
 
 template <class T, class U, bool BUCKETED>
 void sort_passes(const T* z, int P, int64_t n, int64_t ldz, const T* w, KW<T>* pairs, unsigned char* s, int passes,
                  int dbits, const Buckets& bk, cudaStream_t st) {
+    static_assert(sizeof(KV<U, T>) == sizeof(U) + sizeof(T), "interleaved key and payload");
     const int tiles = static_cast<int>(ceil_div(n, RS_TILE));
     const size_t total = static_cast<size_t>(P) * n;
-    U* k0 = reinterpret_cast<U*>(s);
-    U* k1 = k0 + total;
-    T* v0 = reinterpret_cast<T*>(k1 + total);
-    T* v1 = v0 + total;
-    int32_t* hist = reinterpret_cast<int32_t*>(v1 + total);
+    KV<U, T>* kv0 = reinterpret_cast<KV<U, T>*>(s);
+    KV<U, T>* kv1 = kv0 + total;
+    int32_t* hist = reinterpret_cast<int32_t*>(kv1 + total);
     int32_t* dbase = hist + static_cast<size_t>(P) * RS_BINS * tiles;  // P x 256 digit bases
     dim3 gt(tiles, P);
-    const U* kin = nullptr;
-    const T* vin = nullptr;
+    const KV<U, T>* kvin = nullptr;
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = dbits * pass;
-        U* kout = (pass & 1) ? k1 : k0;
-        T* vout = (pass & 1) ? v1 : v0;
+        KV<U, T>* kvout = (pass & 1) ? kv1 : kv0;
         const bool first = pass == 0, last = pass == passes - 1;
         {
             SLK_TIMED("radix_hist", st);
             if (first)
                 k_radix_hist<T, U, true, BUCKETED><<<gt, RS_THREADS, 0, st>>>(z, ldz, nullptr, n, shift, tiles, hist, bk);
             else
-                k_radix_hist<T, U, false, BUCKETED><<<gt, RS_THREADS, 0, st>>>(nullptr, 0, kin, n, shift, tiles, hist, bk);
+                k_radix_hist<T, U, false, BUCKETED><<<gt, RS_THREADS, 0, st>>>(nullptr, 0, kvin, n, shift, tiles, hist,
+                                                                              bk);
         }
         SLK_CHECK_LAUNCH();
         {
@@ -898,21 +917,20 @@ void sort_passes(const T* z, int P, int64_t n, int64_t ldz, const T* w, KW<T>* p
         {
             SLK_TIMED("radix_scatter", st);
             if (first && last)
-                radix_pass<T, U, true, true, BUCKETED>(gt, z, ldz, w, nullptr, nullptr, n, shift, tiles, hist, dbase,
-                                                       nullptr, nullptr, pairs, bk, st);
+                radix_pass<T, U, true, true, BUCKETED>(gt, z, ldz, w, nullptr, n, shift, tiles, hist, dbase, nullptr,
+                                                       pairs, bk, st);
             else if (first)
-                radix_pass<T, U, true, false, BUCKETED>(gt, z, ldz, w, nullptr, nullptr, n, shift, tiles, hist, dbase,
-                                                        kout, vout, nullptr, bk, st);
+                radix_pass<T, U, true, false, BUCKETED>(gt, z, ldz, w, nullptr, n, shift, tiles, hist, dbase, kvout,
+                                                        nullptr, bk, st);
             else if (last)
-                radix_pass<T, U, false, true, BUCKETED>(gt, nullptr, 0, nullptr, kin, vin, n, shift, tiles, hist, dbase,
-                                                        nullptr, nullptr, pairs, bk, st);
+                radix_pass<T, U, false, true, BUCKETED>(gt, nullptr, 0, nullptr, kvin, n, shift, tiles, hist, dbase,
+                                                        nullptr, pairs, bk, st);
             else
-                radix_pass<T, U, false, false, BUCKETED>(gt, nullptr, 0, nullptr, kin, vin, n, shift, tiles, hist,
-                                                         dbase, kout, vout, nullptr, bk, st);
+                radix_pass<T, U, false, false, BUCKETED>(gt, nullptr, 0, nullptr, kvin, n, shift, tiles, hist, dbase,
+                                                         kvout, nullptr, bk, st);
         }
         SLK_CHECK_LAUNCH();
-        kin = kout;
-        vin = vout;
+        kvin = kvout;
     }
 }
 
