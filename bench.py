@@ -114,7 +114,11 @@ def plan_kwargs(wl, args):
 # profiles/) of the d = 784, P = 512 BF16 workload at n = 2e5 points; the traffic of these
 # kernels grows in proportion to the points.  An entry is valid only for the kernel as
 # captured and is removed when that kernel changes.
-NCU_TRAFFIC_PER_POINT = {}
+NCU_TRAFFIC_PER_POINT = {
+    # profiles/pair_cheb_d784_n200k.md: DRAM read + write of one launch over 2e5 points
+    ("gauss_d784", "pair_cheb_moments"): (631.9e6 + 3.2e6) / 2e5,
+    ("gauss_d784", "pair_cheb_target"): (631.6e6 + 8.5e6) / 2e5,
+}
 
 
 def f32_direct(wl, kernels):
