@@ -131,10 +131,13 @@ def f32_direct(wl, kernels):
 
 def step_points(wl, kernel_name, kernels):
     """Rows that one step's launches of a kernel process together.  The fused Chebyshev path
-    also centres, casts and projects a sample of min(4096, N) source rows; source-side
+    also centres, casts and projects a sample of min(4096, N) source rows (on the CTA-pair
+    route the only rows the centring cast sees); source-side
     kernels see the N sources, target-side kernels the M targets, the rest both."""
     S = min(4096, wl.N) if "gather_rows" in kernels else 0
     if kernel_name.startswith("center_cast"):
+        if "pair_cheb_moments" in kernels:
+            return S  # the CTA-pair moments kernel reads the FP32 sources itself
         return wl.N + S if f32_direct(wl, kernels) else wl.N + wl.M + S
     if kernel_name.startswith(("umma_cheb_moments", "pair_cheb_moments", "cheb_moments", "ndft_source", "spread")):
         return wl.N

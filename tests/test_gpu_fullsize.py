@@ -43,7 +43,7 @@ def _run(name, precision, n_sample, grad=False, method=None, n_tail=8):
 
 
 def test_gauss_d784_bf16_full():
-    wl, s, (ref, _), _, info = _run("gauss_d784", "bf16", 56)
+    wl, s, (ref, _), _, info = _run("gauss_d784", "bf16", 57)
     assert len(s) >= 64
     assert rel_inf(s, ref, np.abs(wl.w).sum()) <= 2e-3, info
 
