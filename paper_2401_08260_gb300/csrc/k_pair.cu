@@ -119,12 +119,16 @@ __device__ __forceinline__ void convert_rows16(unsigned char* cv, int lane, int 
 #pragma unroll
     for (int u = 0; u < 8; ++u) v[u] = *reinterpret_cast<const float4*>(src + (r0 + 2 * u + rr) * 128);
     __syncwarp();
+    // x - m as x + (-m), two columns per packed add (the same bits as the scalar subtraction)
+    const float2 nm01 = make_float2(-m[0], -m[1]), nm23 = make_float2(-m[2], -m[3]);
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         const int r = r0 + 2 * u + rr;
         union { __nv_bfloat162 h[2]; uint2 u2; } pk;
-        pk.h[0] = __floats2bfloat162_rn(v[u].x - m[0], v[u].y - m[1]);
-        pk.h[1] = __floats2bfloat162_rn(v[u].z - m[2], v[u].w - m[3]);
+        const float2 c01 = __fadd2_rn(make_float2(v[u].x, v[u].y), nm01);
+        const float2 c23 = __fadd2_rn(make_float2(v[u].z, v[u].w), nm23);
+        pk.h[0] = __floats2bfloat162_rn(c01.x, c01.y);
+        pk.h[1] = __floats2bfloat162_rn(c23.x, c23.y);
         if (row0 + r >= n) pk.u2 = make_uint2(0u, 0u);
         *reinterpret_cast<uint2*>(cv + r * 128 + (((j >> 1) ^ (r & 7)) << 4) + ((j & 1) << 3)) = pk.u2;
     }
@@ -319,9 +323,14 @@ __global__ void __launch_bounds__(QTHREADS, 1)
         if (SIDE == SIDE_TARGET) {
             // row sums of t_p(z) over this warp's 128 slices of the item's half
             bool bad = false;
+            float mabs = 0.0f;  // max |z| of the Horner chunks, checked against R at the end
             auto run = [&](auto qp_tag, auto horner_tag) {
                 constexpr int QP = decltype(qp_tag)::value;
                 constexpr bool HORNER = decltype(horner_tag)::value;
+                auto chunk = [&](const uint32_t (&r)[32], const float* bt0, float& s_, float& c_) {
+                    if constexpr (HORNER) horner_chunk32<QP>(r, bt0, QMAX_P, a.inv_R, s_, c_, mabs);
+                    else cheb_chunk32<QP, false>(r, bt0, QMAX_P, a.R, a.inv_R, s_, c_, bad);
+                };
                 for (int li = 0; li < nloc; ++li) {
                     if (!wait_acc(li)) break;
                     const int item = item_of(li), half = item % a.halves;
@@ -335,13 +344,14 @@ __global__ void __launch_bounds__(QTHREADS, 1)
 #pragma unroll 1
                     for (int cc = 0; cc < NC; cc += 64) {
                         tmem_ld32_issue(tbase + cc + 32, rb);
-                        cheb_chunk32<QP, HORNER>(ra, bt + cc, QMAX_P, a.R, a.inv_R, sum, comp, bad);
+                        chunk(ra, bt + cc, sum, comp);
                         tmem_wait32(rb);
                         if (cc + 64 < NC) tmem_ld32_issue(tbase + cc + 64, ra);
-                        cheb_chunk32<QP, HORNER>(rb, bt + cc + 32, QMAX_P, a.R, a.inv_R, sum, comp, bad);
+                        chunk(rb, bt + cc + 32, sum, comp);
                         if (cc + 64 < NC) tmem_wait32(ra);
                     }
                     release_acc(li);
+                    if (!(sum == sum)) bad = true;  // a NaN projection
                     if (row < a.n)
                         a.part[static_cast<int64_t>(half * 2 + grp) * a.ldp + row] =
                             static_cast<double>(sum) - static_cast<double>(comp);
@@ -353,6 +363,7 @@ __global__ void __launch_bounds__(QTHREADS, 1)
             else if (a.q == 12) a.horner ? run(std::integral_constant<int, 12>{}, T_{}) : run(std::integral_constant<int, 12>{}, F_{});
             else if (a.q == 8) a.horner ? run(std::integral_constant<int, 8>{}, T_{}) : run(std::integral_constant<int, 8>{}, F_{});
             else a.horner ? run(std::integral_constant<int, 16>{}, T_{}) : run(std::integral_constant<int, 16>{}, F_{});
+            if (!(mabs <= a.R)) bad = true;
             if (bad) atomicOr(a.err, 4u);
         } else {
             // one slice's moments per thread over this warp's 128 points of every item; a pair
@@ -369,9 +380,9 @@ __global__ void __launch_bounds__(QTHREADS, 1)
                 for (int li = 0; li < nloc; ++li) {
                     if (!wait_acc(li)) break;
                     const int tile = item_of(li) / a.halves;
-                    float tt[QP];
+                    float2 tt[QP];  // this item's sums over its even and odd points
 #pragma unroll
-                    for (int k = 0; k < QP; ++k) tt[k] = 0.0f;
+                    for (int k = 0; k < QP; ++k) tt[k] = make_float2(0.0f, 0.0f);
                     auto chunk = [&](const uint32_t (&r)[32], int cc) {
                         // accumulator column c holds point tile * 256 + c (columns 0-127 from the
                         // even CTA's rows of B, 128-255 from the odd CTA's)
@@ -380,7 +391,7 @@ __global__ void __launch_bounds__(QTHREADS, 1)
                         float v[32];
 #pragma unroll
                         for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-                        mom_chunk<QP>(v, wl, a.inv_R, a.n - pt0, tt, mx);
+                        mom_chunk2<QP>(v, wl, a.inv_R, a.n - pt0, tt, mx);
                     };
                     uint32_t ra[32], rb[32];
                     const uint32_t tbase = tmem + lane_off + (li & 1) * QN + grp * NC;
@@ -397,7 +408,7 @@ __global__ void __launch_bounds__(QTHREADS, 1)
                     }
                     release_acc(li);
 #pragma unroll
-                    for (int k = 0; k < QP; ++k) two_sum_into(hi[k], lo[k], tt[k]);
+                    for (int k = 0; k < QP; ++k) two_sum_into(hi[k], lo[k], tt[k].x + tt[k].y);
                 }
                 if (slice < a.P) {
                     // chunk: the pair (of a pair of pairs with two halves) and the column half
