@@ -117,7 +117,7 @@ def plan_kwargs(wl, args):
 NCU_TRAFFIC_PER_POINT = {
     # profiles/pair_cheb_d784_n200k.md: DRAM read + write of one launch over 2e5 points
     ("gauss_d784", "pair_cheb_moments"): (631.9e6 + 3.2e6) / 2e5,
-    ("gauss_d784", "pair_cheb_target"): (631.6e6 + 8.5e6) / 2e5,
+    ("gauss_d784", "pair_cheb_target"): (631.7e6 + 8.4e6) / 2e5,
 }
 
 
