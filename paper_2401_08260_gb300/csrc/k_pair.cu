@@ -104,33 +104,49 @@ __host__ __device__ constexpr size_t pair_smem_bytes(int beta_terms, int d) {
 }
 constexpr size_t kPairSmemMax = 227 * 1024;
 
-// Convert 16 of one stage's 128 FP32 rows (rows 16 bi .. 16 bi + 15; the stage holds two
+// Convert one converter warp's share of a stage's 128 FP32 rows (the stage holds two
 // unswizzled 32-column boxes of 128 bytes per row) to centred BF16 in place over the first
 // box, 128-byte swizzle (16-byte chunk c of row r at c ^ (r % 8)); rows at or beyond n are
-// written as zeros.  Lane l takes columns 4j..4j+3 (j = l % 16) of rows 2u + l / 16; m holds
-// the centre at those columns (the same arithmetic as the single-CTA converting kernel).
-__device__ __forceinline__ void convert_rows16(unsigned char* cv, int lane, int bi, const float (&m)[4], int row0,
-                                               int n) {
+// written as zeros.  The warp takes the 16-row batches cw, cw + CVT_WARPS, ... and reads all
+// of them before it writes any (one round trip to shared memory instead of one per batch; a
+// batch's rows are read and written only by its warp).  Lane l takes columns 4j..4j+3
+// (j = l % 16) of rows 2u + l / 16 of each batch; m holds the centre at those columns (the
+// same arithmetic as the single-CTA converting kernel).
+__device__ __forceinline__ void convert_share(unsigned char* cv, int lane, int cw, const float (&m)[4], int row0,
+                                              int n) {
     constexpr int HALF = QM * 128;
+    constexpr int NBATCH = QM / 16;
+    constexpr int PER_WARP = (NBATCH + CVT_WARPS - 1) / CVT_WARPS;
     const int j = lane & 15, rr = lane >> 4;
     const unsigned char* src = cv + (j >> 3) * HALF + (j & 7) * 16;
-    const int r0 = bi * 16;
-    float4 v[8];
+    float4 v[PER_WARP][8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = *reinterpret_cast<const float4*>(src + (r0 + 2 * u + rr) * 128);
+    for (int b = 0; b < PER_WARP; ++b) {
+        const int bi = cw + b * CVT_WARPS;
+        if (bi < NBATCH) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[b][u] = *reinterpret_cast<const float4*>(src + (bi * 16 + 2 * u + rr) * 128);
+        }
+    }
     __syncwarp();
     // x - m as x + (-m), two columns per packed add (the same bits as the scalar subtraction)
     const float2 nm01 = make_float2(-m[0], -m[1]), nm23 = make_float2(-m[2], -m[3]);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const int r = r0 + 2 * u + rr;
-        union { __nv_bfloat162 h[2]; uint2 u2; } pk;
-        const float2 c01 = __fadd2_rn(make_float2(v[u].x, v[u].y), nm01);
-        const float2 c23 = __fadd2_rn(make_float2(v[u].z, v[u].w), nm23);
-        pk.h[0] = __floats2bfloat162_rn(c01.x, c01.y);
-        pk.h[1] = __floats2bfloat162_rn(c23.x, c23.y);
-        if (row0 + r >= n) pk.u2 = make_uint2(0u, 0u);
-        *reinterpret_cast<uint2*>(cv + r * 128 + (((j >> 1) ^ (r & 7)) << 4) + ((j & 1) << 3)) = pk.u2;
+    for (int b = 0; b < PER_WARP; ++b) {
+        const int bi = cw + b * CVT_WARPS;
+        if (bi >= NBATCH) continue;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int r = bi * 16 + 2 * u + rr;
+            union { __nv_bfloat162 h[2]; uint2 u2; } pk;
+            const float2 c01 = __fadd2_rn(make_float2(v[b][u].x, v[b][u].y), nm01);
+            const float2 c23 = __fadd2_rn(make_float2(v[b][u].z, v[b][u].w), nm23);
+            pk.h[0] = __floats2bfloat162_rn(c01.x, c01.y);
+            pk.h[1] = __floats2bfloat162_rn(c23.x, c23.y);
+            if (row0 + r >= n) pk.u2 = make_uint2(0u, 0u);
+            *reinterpret_cast<uint2*>(cv + r * 128 + (((j >> 1) ^ (r & 7)) << 4) + ((j & 1) << 3)) = pk.u2;
+        }
     }
 }
 
@@ -285,8 +301,7 @@ __global__ void __launch_bounds__(QTHREADS, 1)
                 break;
             }
             const int row0 = prow_of(g / kblocks);
-            for (int bi = cw; bi < QM / 16; bi += CVT_WARPS)
-                convert_rows16(base + s * QSTAGE_BYTES, lane, bi, m, row0, a.n);
+            convert_share(base + s * QSTAGE_BYTES, lane, cw, m, row0, a.n);
             // generic-proxy writes, read next by the tensor core (async proxy)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
