@@ -115,9 +115,9 @@ def plan_kwargs(wl, args):
 # kernels grows in proportion to the points.  An entry is valid only for the kernel as
 # captured and is removed when that kernel changes.
 NCU_TRAFFIC_PER_POINT = {
-    # profiles/pair_cheb_d784_n200k.md: DRAM read + write of one launch over 2e5 points
-    ("gauss_d784", "pair_cheb_moments"): (631.9e6 + 3.2e6) / 2e5,
-    ("gauss_d784", "pair_cheb_target"): (631.7e6 + 8.4e6) / 2e5,
+    # none current: the Chebyshev pair kernels changed (converter loads batched per warp) after
+    # their last capture in profiles/pair_cheb_d784_n200k.md (631.9 + 3.2 MB and 631.7 + 8.4 MB
+    # of DRAM read + write per 2e5 points, equal to the algorithmic bytes)
 }
 
 
